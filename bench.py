@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the sliced tensor-network contraction path on GB300.
+
+Workload (default): the 30-qubit 5x6 grid random circuit, 14 cycles (seed 1); greedy plan
+(seed 3, 64 trials) sliced to 2^6 slices with every intermediate at most 2^26 entries;
+a sub-cube batch of 1024 amplitudes (10 open qubits, the other 20 bits seeded).  One
+step = all 64 slices of that batch, summed in FP64.  Metric: slices/s of the
+complex-half path (fp16 storage, FP32 arithmetic), with the complex64 path beside it,
+both with their amplitude error.
+
+Launch: `python bench.py [--steps K --warmup W]`; under torchrun each rank contracts its
+own sub-cube batch (independent problems, no collective on the data path: weak scaling).
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "s30": dict(rows=5, cols=6, cycles=14, seed=1, n_open=10, subcube_seed=2, plan_seed=3, trials=64, cap=26,
+                smin=6, smax=6),
+    "t12": dict(rows=3, cols=4, cycles=8, seed=1, n_open=4, subcube_seed=2, plan_seed=3, trials=8, cap=26,
+                smin=0, smax=64),
+}
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="s30", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="chalf", choices=["chalf", "cbf16", "c64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the complex64 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-cap", type=int, default=23, help="log2 size cap of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    from inputs import grid_circuit, subcube_spec
+
+    w = WORKLOADS[name]
+    circ = grid_circuit(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
+    fixed, open_q = subcube_spec(circ.n_qubits, w["n_open"], seed=w["subcube_seed"] + rank)
+    return w, circ, fixed, open_q
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------- oracle sample
+def oracle_sample(circ, fixed, open_q, cuts, cap_log2):
+    """Prepare a bounded oracle sample: slice 0 of the plan's slicing (cuts fixed to 0),
+    split further by the oracle's own sub-slicing at 2^cap_log2; returns (run, n_sub):
+    `run()` contracts one sub-slice, and a whole slice is n_sub such runs."""
+    from oracle import network as tn
+
+    tensors, open_labels = tn.circuit_tensors(circ, fixed, open_q)
+    tensors = tn.fix_labels(tensors, {("w", q, j): 0 for (q, j) in cuts})
+    order, extra = tn.search_order([t.labels for t in tensors], open_labels, cap_log2, trials=8)
+    sub = tn.fix_labels(tensors, {lab: 0 for lab in extra})
+
+    def run():
+        return tn.contract_network(sub, open_labels, order)
+
+    return run, 2 ** len(extra)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2504_09186_gb300 import tnc as T
+
+    w, circ, fixed, open_q = workload(args.workload, 0)
+    plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
+                         slices_min=w["smin"], slices_max=w["smax"])
+    cuts = plan.sliced_cuts()
+    run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 1.0 / (dt * n_sub)
+    cores = cpu_cores()
+    line = {
+        "impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: 5x6 grid RQC, 14 cycles, 2^6 slices, cap 2^26, 1024-amplitude sub-cube"},
+        "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step = 1 of {n_sub} oracle sub-contractions of slice 0 (cap 2^{args.cpu_sample_cap}); "
+                                   f"slices/s = 1 / (step time * {n_sub})"},
+        "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from oracle import metrics
+    from paper_2504_09186_gb300 import tnc as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w, circ, fixed, open_q = workload(args.workload, rank)
+    plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
+                         slices_min=w["smin"], slices_max=w["smax"])
+    info = plan.info()
+    n_slices = 1 << info["n_sliced"]
+    ctx = T.Context(local)
+    stream = torch.cuda.current_stream()
+    n_out = 1 << info["n_open"]
+    out = torch.zeros((1, n_out), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    bits = np.ascontiguousarray(fixed[None, :], dtype=np.uint8)
+
+    def timed(precision, steps, warmup, profile):
+        for _ in range(warmup):
+            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total = 0.0
+        prof = None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream, profile=profile)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            if profile:
+                p = ctx.profile_read()
+                if prof is None:
+                    prof = p
+                else:
+                    prof["ms"] = prof["ms"] + p["ms"]
+                    prof["launches"] = prof["launches"] + p["launches"]
+                    prof["flops"] = prof["flops"] + p["flops"]
+                    prof["bytes"] = prof["bytes"] + p["bytes"]
+        torch.cuda.synchronize()
+        ms = total / steps
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, out.cpu().numpy()[0].copy()
+
+    with ClockSampler(local) as clk:
+        ms, prof, amp = timed(args.precision, args.steps, args.warmup, True)
+    clocks = clk.summary()
+    value = n_slices * world / (ms / 1e3)
+
+    # complex64 beside it, and the error of both against each other / the oracle golden
+    c64 = None
+    if not args.no_compare and args.precision != "c64":
+        ms64, _, amp64 = timed("c64", max(1, min(args.steps, 3)), 1, False)
+        c64 = {"slices_per_s": n_slices * world / (ms64 / 1e3), "ms_per_step": ms64,
+               "rel_err_vs_c64": metrics.rel_err_norm(amp, amp64)}
+    golden = os.path.join(ROOT, "tests", "golden", "s30_subcube_amplitudes.txt")
+    err_golden = None
+    if args.workload == "s30" and rank == 0 and os.path.exists(golden):
+        ref = np.loadtxt(golden)
+        ref = ref[:, 0] + 1j * ref[:, 1]
+        err_golden = metrics.rel_err_norm(amp, ref)
+
+    # end to end: host bitstrings in, host amplitudes out, through the public API
+    host_out = np.zeros((1, n_out), dtype=np.complex128)
+    ctx.amplitudes(plan, bits, args.precision, out=host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.amplitudes(plan, bits, args.precision, out=host_out)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = bits.nbytes + n_slices * (8 + 4) + 12
+    d2h = host_out.nbytes
+
+    # roofline of the dominant kernel (largest device time), from the live events
+    peaks = load_peaks()
+    k = int(np.argmax(prof["ms"]))
+    per_launch_ms = prof["ms"][k] / prof["launches"][k]
+    kind = int(prof["kind"][k])
+    flops_launch = prof["flops"][k] / prof["launches"][k]
+    bytes_launch = prof["bytes"][k] / prof["launches"][k]
+    if kind == 3:
+        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+    elif flops_launch / bytes_launch > 8.0:
+        alu_peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s"}
+    else:
+        achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = {"step": k, "kind": kind, "share_of_step_time": float(prof["ms"][k] / max(1e-9, prof["ms"].sum())),
+                      "ms_per_launch": per_launch_ms, "flops_per_launch": flops_launch, "bytes_per_launch": bytes_launch}
+    roof["peak_source"] = peaks["_source"]
+    total_flops = float(prof["flops"].sum()) / args.steps
+    launches = int(prof["launches"].sum() / args.steps) + 2 * int(prof["launches"][0] / args.steps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cuts = plan.sliced_cuts()
+        run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
+        t0 = time.perf_counter()
+        run()
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (dt * n_sub), "unit": "slices/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"1 of {n_sub} oracle sub-contractions of slice 0 (FP64, cap 2^{args.cpu_sample_cap}), "
+                         f"{dt:.1f} s; slices/s = 1 / (t * {n_sub})"}
+
+    if rank == 0:
+        line = {
+            "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"chalf": "f16", "cbf16": "bf16", "c64": "f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w['rows']}x{w['cols']} grid RQC, {w['cycles']} cycles, "
+                                   f"{n_slices} slices (cap 2^{w['cap']}), {n_out}-amplitude sub-cube per GPU",
+                       "precision": args.precision, "slices_per_step": n_slices * world,
+                       "complex_tflops": total_flops / (ms / 1e3) / 1e12,
+                       "l2": "256 MiB flush before every timed step; intermediates up to 2^26 entries > L2",
+                       "parallelism": f"replicas x{world} (independent sub-cubes)"},
+            "complex64": c64,
+            "rel_err_vs_oracle": err_golden,
+            "e2e": {"value": n_slices * world / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

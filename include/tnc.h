@@ -1,0 +1,225 @@
+/*
+ * tnc.h -- C boundary of the GB300 sliced tensor-network contraction library.
+ *
+ * The library computes amplitudes <x|U|0^n> of a quantum circuit by contracting its
+ * tensor network (Sec. I; Sec. II-A: nodes are tensors, edges shared indices, each
+ * pairwise contraction an M x K x N complex GEMM after permuting the common indices
+ * to K; every index has dimension 2, Sec. III-A).  Slicing (Sec. II-A; Sec. III-A)
+ * fixes s indices, giving 2^s independent subtasks whose sum is the amplitude.
+ *
+ * Conventions used by every call:
+ *  - Status: every call returns tnc_status; TNC_OK on success.  No exception crosses
+ *    the boundary.  tnc_last_error() returns a thread-local message for the last
+ *    failure on the calling thread.
+ *  - Ownership: handles are created by the library and released only by the matching
+ *    tnc_*_destroy; every output buffer is allocated by the caller; the library never
+ *    frees caller memory.  Device scratch belongs to a tnc_context and grows on demand
+ *    (TNC_E_OOM when it cannot).
+ *  - Bits: qubit q of an n-qubit register is bit (n-1-q) of a state index (qubit 0 is
+ *    the most significant).  A bitstring is n bytes, byte q = bit of qubit q.
+ *  - Gate matrices: row-major U[out, in], complex128 stored as interleaved (re, im)
+ *    doubles, zero-padded to 4x4 (32 doubles).  For a 2-qubit gate on (q0, q1) the
+ *    4-dim index is 2*bit(q0) + bit(q1).
+ *  - Tensors handed to tnc_contract are "planar": a real plane of 2^rank values
+ *    followed by an imaginary plane of 2^rank values; the element at flat index i
+ *    has bit p of i equal to the value of the index labelled labels[p].
+ *  - Asynchrony: calls that take a stream enqueue work and return; device-side
+ *    failures (a bounded wait that ran out) surface at tnc_sync() as TNC_E_TIMEOUT.
+ */
+#ifndef TNC_H
+#define TNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tnc_status;
+enum {
+  TNC_OK = 0,
+  TNC_E_INVALID_ARG = 1, /* a pointer, size or option is out of range            */
+  TNC_E_OOM = 2,         /* host or device allocation failed                      */
+  TNC_E_CUDA = 3,        /* a CUDA call failed; message has the CUDA error string */
+  TNC_E_TIMEOUT = 4,     /* a device-side bounded wait gave up                    */
+  TNC_E_PLAN = 5,        /* the plan is inconsistent with the request             */
+  TNC_E_UNSUPPORTED = 6, /* e.g. no sm_103 device, or a rank above the limits     */
+  TNC_E_IO = 7           /* a plan file could not be read or written              */
+};
+
+/* Storage precision of the contraction path.  Arithmetic is FP32 in every case;
+ * CHALF/CBF16 store tensors as fp16/bf16 planes with a power-of-two exponent per
+ * tensor (exact scaling), C64 stores fp32 planes. */
+enum { TNC_C64 = 0, TNC_CHALF = 1, TNC_CBF16 = 2 };
+
+typedef struct tnc_circuit_s* tnc_circuit;
+typedef struct tnc_network_s* tnc_network;
+typedef struct tnc_plan_s* tnc_plan;
+typedef struct tnc_context_s* tnc_context;
+
+/* ---------------------------------------------------------------- circuit -> network */
+
+/* Build a circuit from a gate list (Sec. I: the circuit that the network represents).
+ *  n_qubits        1..64
+ *  n_gates         >= 0
+ *  arity[g]        1 or 2
+ *  qubits[2*g+t]   qubit of slot t (t < arity[g]); distinct, in [0, n_qubits)
+ *  matrices[32*g]  U[out, in] as above (host memory, copied)
+ * Errors: TNC_E_INVALID_ARG on any out-of-range value. */
+tnc_status tnc_circuit_from_gates(int32_t n_qubits, int64_t n_gates, const int32_t* arity,
+                                  const int32_t* qubits, const double* matrices,
+                                  tnc_circuit* out);
+void tnc_circuit_destroy(tnc_circuit c);
+
+/* Build the tensor network of a circuit (Sec. II-A).  One tensor per 2-qubit gate with
+ * its neighbouring 1-qubit gates multiplied in (a qubit without 2-qubit gates becomes
+ * one rank-2 tensor); |0> inputs are fixed; output legs of qubits with
+ * open_mask[q] != 0 stay open (the result is a tensor over them), the others are
+ * fixed per bitstring at tnc_amplitudes time.
+ *  open_mask  n_qubits bytes (host), or NULL for all closed. */
+tnc_status tnc_network_build(tnc_circuit c, const uint8_t* open_mask, tnc_network* out);
+void tnc_network_destroy(tnc_network n);
+
+/* ---------------------------------------------------------------- order + slicing */
+
+typedef struct {
+  uint64_t seed;       /* seeds the Gumbel perturbation of the greedy order          */
+  int32_t trials;      /* independent greedy trials; the cheapest total is kept      */
+  int32_t log2_cap;    /* slice until every intermediate has at most 2^log2_cap entries */
+  int32_t slices_min;  /* then add lowest-overhead indices up to this many (log2)    */
+  int32_t slices_max;  /* trials above this many sliced indices are dropped if any  */
+                       /* trial stays within it                                    */
+  double temperature;  /* Gumbel temperature in log2-cost units; 0 = plain greedy    */
+} tnc_plan_opts;
+
+/* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:
+ * index overhead O(a) = 2 C_a / C_ori picks each sliced index).  Repeatedly contracts
+ * the pair sharing an index that minimises size(out) - size(a) - size(b) (perturbed by
+ * seeded Gumbel noise), then slices while an intermediate exceeds the cap, each time
+ * taking the index of an oversized intermediate with the smallest O(a).  The result
+ * holds the tree, the sliced indices and the compiled per-step program. */
+tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* out);
+void tnc_plan_destroy(tnc_plan p);
+
+typedef struct {
+  double log2_flops_per_slice; /* log2 of complex multiply-adds of one slice           */
+  double log2_total_flops;     /* log2 of complex multiply-adds of all 2^s slices       */
+  double slicing_overhead;     /* 2^s * C_sliced / C_unsliced (Eq. 1 summed, Sec. III-A) */
+  int32_t max_log2_size;       /* largest intermediate of one slice (log2 entries)      */
+  int32_t n_sliced;            /* s                                                     */
+  int32_t n_steps;             /* pairwise contractions per slice                       */
+  int32_t n_leaves;
+  int32_t n_open;              /* open output qubits (result has 2^n_open entries)      */
+  int32_t n_kernels;           /* kernel launches per wave of instances                */
+  int32_t n_gemm, n_gepdot, n_absorb, n_fused; /* steps per class (a fused step counts */
+                                               /* every contraction it contains)        */
+  double narrow_max;           /* largest "narrow" rate 2 N_common / (N_A + N_B)       */
+                               /* (Sec. VII-B) over the steps                          */
+} tnc_plan_info;
+tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
+
+/* Sliced indices as wire segments: slice bit t (bit t of a slice id) fixes the wire of
+ * qubit qubit[t] after cut[t] gates on that qubit.  cap >= n_sliced entries. */
+tnc_status tnc_plan_sliced_cuts(tnc_plan p, int32_t* qubit, int32_t* cut, int32_t cap);
+
+/* Open qubits in result order (first = most significant bit of the result index). */
+tnc_status tnc_plan_open_qubits(tnc_plan p, int32_t* qubits, int32_t cap);
+
+/* The whole plan as JSON text (network edges as [qubit, cut, kind, open], leaves with
+ * their labels and gates, sliced edge ids, the tree as SSA pairs over tensor ids, every
+ * tensor's labels in storage order and arena offset, the compiled steps with their
+ * tiles).  Writes at most cap bytes including the terminating NUL; *len receives the
+ * full size including the NUL, so a call with buf == NULL queries the size. */
+tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len);
+
+/* Plan persistence (binary, versioned).  The file holds the circuit, network, tree,
+ * slices and options; loading recompiles the program. */
+tnc_status tnc_plan_save(tnc_plan p, const char* path);
+tnc_status tnc_plan_load(const char* path, tnc_plan* out);
+
+/* ---------------------------------------------------------------- execution */
+
+/* A context owns the device, its streams, the device program cache and scratch.
+ * device: CUDA ordinal; the device must be sm_103 (GB300). */
+tnc_status tnc_context_create(int32_t device, tnc_context* out);
+void tnc_context_destroy(tnc_context ctx);
+
+typedef struct {
+  int32_t precision;     /* TNC_C64 / TNC_CHALF / TNC_CBF16                          */
+  int32_t wave;          /* instances (bitstring x slice) contracted per launch; 0=auto */
+  int32_t use_graph;     /* capture the per-wave launch sequence in a CUDA graph      */
+  int32_t fuse;          /* 1 = fused on-chip chains of small absorptions (Sec. IV)  */
+  int32_t profile;       /* 1 = time every step launch with CUDA events on the launch  */
+                         /* stream; read with tnc_profile_read                        */
+  int32_t reserved[3];
+} tnc_exec_opts;
+
+/* Amplitudes of a batch (Sec. I; the multi-amplitude batch of Sec. II-C), summed over
+ * the slice ids [slice_begin, slice_begin + slice_count) (Sec. III-A: subtasks are
+ * independent and their results add).
+ *  bitstrings  batch x n_qubits bytes (host); bits of open qubits are ignored.  May be
+ *              NULL when batch == 1 and every qubit is open.
+ *  out         batch x 2^n_open complex128 as interleaved (re, im) doubles; host or
+ *              device memory (detected); entry (b, i) is the amplitude of row b with
+ *              the open qubits set to the bits of i (first open qubit most significant).
+ *  stream      cudaStream_t or NULL (the context's stream).  With a host `out` the
+ *              call returns after the copy-back completes.
+ * The cross-slice sum is accumulated in FP64 in a fixed order (deterministic). */
+tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
+                          const uint8_t* bitstrings, int64_t batch, int64_t slice_begin,
+                          int64_t slice_count, double* out, void* stream);
+
+/* Gradient environments (the derivative of L = sum_{b,i} w[b,i] * amp[b,i] with respect
+ * to every gate matrix, holomorphic: dL/dU_g[o, i]).  Walks the contraction tree in
+ * reverse: for a step C = A * B, dL/dA = contract(dL/dC, B) and dL/dB = contract(A,
+ * dL/dC), the same pairwise contraction kind as the forward steps (Sec. II-A).
+ *  weights  batch x 2^n_open complex128 interleaved (host)
+ *  env_out  n_gates x 32 doubles (host): dL/dU_g, row-major, zero-padded to 4x4
+ *  amp_out  optional (may be NULL): the amplitudes, as tnc_amplitudes
+ * Computed in C64 (FP32) with the FP64 cross-slice accumulation. */
+tnc_status tnc_adjoint(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
+                       const uint8_t* bitstrings, int64_t batch, const double* weights,
+                       double* env_out, double* amp_out, void* stream);
+
+/* One pairwise contraction C = A * B of planar binary-index tensors on the device
+ * (Sec. II-A M x K x N view; Sec. V-A permutation folded into the loads; Sec. V-B
+ * split over the common indices when M*N is small).  Labels are arbitrary int32
+ * values; common labels are summed, C's labels must be the free labels of A and B.
+ *  a, b, c    device pointers, planar, element type per precision (float, __half,
+ *             __nv_bfloat16); c must not alias a or b.  2^rank entries per plane.
+ *  ranks      0..32
+ *  c_exp2     out (host): C's stored values times 2^(*c_exp2) are the result (inputs
+ *             are taken at scale 1).
+ * Errors: TNC_E_INVALID_ARG on inconsistent labels. */
+tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32_t rank_a,
+                        const int32_t* labels_a, const void* b, int32_t rank_b,
+                        const int32_t* labels_b, void* c, int32_t rank_c,
+                        const int32_t* labels_c, int32_t* c_exp2, void* stream);
+
+/* Per-step timings of the last tnc_amplitudes call made with opts->profile = 1 on this
+ * context (waits for it).  For step s (program order, cap >= n entries):
+ *  ms[s]      device time summed over the call's launches of that step (CUDA events)
+ *  launches[s] launches of that step (one per wave)
+ *  flops[s]   algorithmic real flops of those launches: 8 * M * N * K per instance
+ *  bytes[s]   algorithmic bytes: (|A| + |B| + |C|) * element size per instance
+ *  kind[s]    kernel class (0 generic, 1 split-K GEPDOT, 2 fused chain, 3 tensor-core)
+ *  ms[n]      (one extra entry) the whole call's device time
+ * *n receives the number of steps. */
+tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,
+                            int32_t* kind, int32_t cap, int32_t* n);
+
+/* Wait for the context's work and report device-side status (TNC_E_TIMEOUT if a
+ * bounded wait ran out). */
+tnc_status tnc_sync(tnc_context ctx);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* tnc_last_error(void);
+
+/* Library version string. */
+const char* tnc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNC_H */

@@ -11,13 +11,16 @@ Network (one tensor per gate, no merging):
     open output segments stay as free labels of the result.
 Slicing (Sec. II-A, Sec. III-A) fixes a label to 0 or 1 in every tensor that carries it.
 
-The contraction order here is the oracle's own: greedy on the increase in size, with
-ties broken by tensor id.  If some intermediate would exceed 2^cap_log2 elements the
-oracle fixes extra labels and sums over their values, which is exact because
-sum_b |b><b| = I (the same identity that makes slicing exact).
+The contraction order here is the oracle's own: greedy on the increase in size (ties by
+tensor id), best of a few trials perturbed by seeded Gumbel noise.  If some intermediate
+would exceed 2^cap_log2 elements the oracle fixes extra labels and sums over their
+values, which is exact because sum_b |b><b| = I (the same identity that makes slicing
+exact).  The order only changes rounding and speed, never the value: the tests contract
+the same network in random orders and compare.
 """
 from __future__ import annotations
 
+import heapq
 import itertools
 from typing import Dict, List, Optional, Sequence, Tuple
 
@@ -87,53 +90,128 @@ def _pair_labels(a: Tuple[Label, ...], b: Tuple[Label, ...], keep: set) -> Tuple
     return tuple(res)
 
 
-def greedy_order(label_sets: List[Tuple[Label, ...]], open_labels: Sequence[Label]):
+def greedy_order(label_sets: List[Tuple[Label, ...]], open_labels: Sequence[Label], rng=None, temperature: float = 0.0):
     """Greedy pairwise order on label sets: repeatedly contract the pair sharing a label
-    that minimises size(out) - size(a) - size(b); ties by (smaller id, larger id).
+    that minimises size(out) - size(a) - size(b); ties by (smaller id, larger id).  With
+    `rng`, the score (sign(s) log2(1+|s|)) is perturbed by -temperature * Gumbel noise.
 
     Returns (pairs as (i, j) of live ids; new ids appended in order, max log2 size,
     list of (log2 size, labels) of every intermediate).
     """
     keep = set(open_labels)
-    live: Dict[int, Tuple[Label, ...]] = {i: ls for i, ls in enumerate(label_sets)}
-    by_label: Dict[Label, set] = {}
+    live: Dict[int, frozenset] = {i: frozenset(ls) for i, ls in enumerate(label_sets)}
+    owners: Dict[Label, set] = {}
     for i, ls in live.items():
         for lab in ls:
-            by_label.setdefault(lab, set()).add(i)
+            owners.setdefault(lab, set()).add(i)
+
+    def out_of(i, j):
+        a, b = live[i], live[j]
+        return (a ^ b) | (a & b & keep)
+
+    def score(i, j):
+        a, b = live[i], live[j]
+        s = 2.0 ** len(out_of(i, j)) - 2.0 ** len(a) - 2.0 ** len(b)
+        t = np.sign(s) * np.log2(1.0 + abs(s))
+        if rng is not None and temperature > 0:
+            t -= temperature * rng.gumbel()
+        return (t, min(i, j), max(i, j))
+
+    heap = []
+    seen = set()
+    for lab, ow in owners.items():
+        if len(ow) == 2:
+            i, j = sorted(ow)
+            if (i, j) not in seen:
+                seen.add((i, j))
+                heapq.heappush(heap, score(i, j))
     next_id = len(label_sets)
     pairs = []
     inter = []
     max_log = max((len(ls) for ls in label_sets), default=0)
     while len(live) > 1:
-        best = None
-        for lab, owners in by_label.items():
-            if len(owners) < 2:
-                continue
-            for i, j in itertools.combinations(sorted(owners), 2):
-                out = _pair_labels(live[i], live[j], keep)
-                score = (2.0 ** len(out) - 2.0 ** len(live[i]) - 2.0 ** len(live[j]), i, j)
-                if best is None or score < best[0]:
-                    best = (score, i, j, out)
-        if best is None:
-            # no shared labels left: outer products, smallest first
+        pick = None
+        while heap:
+            _, i, j = heapq.heappop(heap)
+            if i in live and j in live:
+                pick = (i, j)
+                break
+        if pick is None:
             ids = sorted(live, key=lambda t: (len(live[t]), t))
-            i, j = ids[0], ids[1]
-            out = _pair_labels(live[i], live[j], keep)
-        else:
-            _, i, j, out = best
-        pairs.append((i, j))
+            pick = (min(ids[0], ids[1]), max(ids[0], ids[1]))
+        i, j = pick
+        out = out_of(i, j)
         for lab in live[i]:
-            by_label[lab].discard(i)
+            owners[lab].discard(i)
         for lab in live[j]:
-            by_label[lab].discard(j)
+            owners[lab].discard(j)
         del live[i], live[j]
         live[next_id] = out
+        nbrs = set()
         for lab in out:
-            by_label.setdefault(lab, set()).add(next_id)
-        inter.append((len(out), out))
+            owners.setdefault(lab, set()).add(next_id)
+            nbrs |= owners[lab]
+        nbrs.discard(next_id)
+        for k in sorted(nbrs):
+            heapq.heappush(heap, score(k, next_id))
+        pairs.append((i, j))
+        inter.append((len(out), tuple(sorted(out))))
         max_log = max(max_log, len(out))
         next_id += 1
     return pairs, max_log, inter
+
+
+def _tree_sets(label_sets, pairs, open_labels):
+    """Union and output label sets of every step of a tree."""
+    keep = set(open_labels)
+    sets = [frozenset(s) for s in label_sets]
+    unions = []
+    for i, j in pairs:
+        a, b = sets[i], sets[j]
+        unions.append(a | b)
+        sets.append((a ^ b) | (a & b & keep))
+    return sets, unions
+
+
+def slice_tree(label_sets, pairs, open_labels, cap_log2: int, max_extra: int = 30):
+    """Labels to fix on a fixed tree so that no tensor exceeds 2^cap_log2 entries.
+
+    Each round fixes, among the labels of the oversized tensors, the one that leaves the
+    smallest cost sum_steps 2^|union - fixed| (ties by label order).  Returns
+    (fixed labels, cost of one sub-contraction)."""
+    sets, unions = _tree_sets(label_sets, pairs, open_labels)
+    keep = set(open_labels)
+    fixed: set = set()
+
+    def cost(fx):
+        return sum(2.0 ** len(u - fx) for u in unions)
+
+    extra: List[Label] = []
+    while len(extra) < max_extra:
+        over = [s for s in sets if len(s - fixed) > cap_log2]
+        if not over:
+            break
+        cand = sorted({lab for s in over for lab in s if lab not in fixed and lab not in keep})
+        if not cand:
+            break
+        best = min(cand, key=lambda lab: (cost(fixed | {lab}), lab))
+        fixed.add(best)
+        extra.append(best)
+    return extra, cost(fixed)
+
+
+def search_order(label_sets, open_labels, cap_log2: int, trials: int = 8, seed: int = 0, temperature: float = 1.0):
+    """Best of `trials` greedy orders (trial 0 unperturbed), each sliced to the cap on its
+    tree; minimises 2^extra * cost.  Returns (pairs, extra labels)."""
+    rng = np.random.default_rng(seed)
+    best = None
+    for t in range(trials):
+        pairs, _, _ = greedy_order(label_sets, open_labels, rng if t else None, temperature)
+        extra, c = slice_tree(label_sets, pairs, open_labels, cap_log2)
+        total = (2.0 ** len(extra)) * c
+        if best is None or total < best[0]:
+            best = (total, pairs, extra)
+    return best[1], best[2]
 
 
 def contract_pair(a: Tensor, b: Tensor, keep: set) -> Tensor:
@@ -163,30 +241,12 @@ def contract_network(tensors: List[Tensor], open_labels: Sequence[Label], order=
     return np.transpose(res.data, perm) if perm else res.data.reshape(())
 
 
-def choose_subslices(label_sets, open_labels, cap_log2: int, max_extra: int = 24):
-    """Labels to fix (beyond the given slices) so that the greedy order stays under the cap.
-
-    Picks, each round, the label occurring in the most intermediates above the cap.
-    """
-    extra: List[Label] = []
-    sets = [tuple(ls) for ls in label_sets]
-    while True:
-        _, max_log, inter = greedy_order(sets, open_labels)
-        if max_log <= cap_log2 or len(extra) >= max_extra:
-            return extra, max_log
-        votes: Dict[Label, Tuple[int, int]] = {}
-        for lg, labs in inter:
-            if lg > cap_log2:
-                for lab in labs:
-                    if lab in open_labels:
-                        continue
-                    c, m = votes.get(lab, (0, 0))
-                    votes[lab] = (c + 1, max(m, lg))
-        if not votes:
-            return extra, max_log
-        pick = max(votes.items(), key=lambda kv: (kv[1][0], kv[1][1], kv[0]))[0]
-        extra.append(pick)
-        sets = [tuple(x for x in ls if x != pick) for ls in sets]
+def choose_subslices(label_sets, open_labels, cap_log2: int, max_extra: int = 30):
+    """Labels to fix (beyond the given slices) so that the plain greedy order stays under
+    the cap; returns (labels, max log2 size without them)."""
+    pairs, max_log, _ = greedy_order([tuple(ls) for ls in label_sets], open_labels)
+    extra, _ = slice_tree(label_sets, pairs, open_labels, cap_log2, max_extra)
+    return extra, max_log
 
 
 def network_amplitudes(
@@ -195,6 +255,7 @@ def network_amplitudes(
     open_qubits: Sequence[int] = (),
     cuts: Optional[Dict[Tuple[int, int], int]] = None,
     cap_log2: int = 24,
+    trials: int = 8,
 ) -> np.ndarray:
     """Amplitudes over the open qubits (sub-cube order: first open qubit most significant).
 
@@ -204,13 +265,11 @@ def network_amplitudes(
     tensors, open_labels = circuit_tensors(circuit, out_bits, open_qubits)
     fixed = {("w", q, j): b for (q, j), b in (cuts or {}).items()}
     tensors = fix_labels(tensors, fixed)
-    extra, _ = choose_subslices([t.labels for t in tensors], open_labels, cap_log2)
-    order = None
+    order, extra = search_order([t.labels for t in tensors], open_labels, cap_log2, trials=trials)
     total = None
     for bits in itertools.product((0, 1), repeat=len(extra)):
+        # fixing labels keeps every tensor, so the tree stays valid
         sub = fix_labels(tensors, dict(zip(extra, bits)))
-        if order is None:
-            order, _, _ = greedy_order([t.labels for t in sub], open_labels)
         val = contract_network(sub, open_labels, order)
         total = val if total is None else total + val
     return total

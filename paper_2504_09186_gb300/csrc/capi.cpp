@@ -1,0 +1,238 @@
+// extern "C" entry points of the host-side calls (circuit, network, plan, errors).
+// Device-side calls (context, amplitudes, contract, adjoint) are in exec.cu.
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <string>
+
+#include "../../include/tnc.h"
+#include "capi_internal.h"
+#include "host.h"
+
+namespace tnc {
+
+thread_local std::string g_last_error;
+
+void fail(int32_t code, const std::string& msg) { throw Error{code, msg}; }
+
+void set_error(const std::string& m) { g_last_error = m; }
+
+}  // namespace tnc
+
+using namespace tnc;
+
+struct tnc_circuit_s {
+  Circuit c;
+};
+struct tnc_network_s {
+  Network n;
+};
+
+const char* tnc_last_error(void) { return g_last_error.c_str(); }
+
+const char* tnc_version(void) { return "tnc-gb300 1.0 (sm_103a)"; }
+
+tnc_status tnc_circuit_from_gates(int32_t n_qubits, int64_t n_gates, const int32_t* arity,
+                                  const int32_t* qubits, const double* matrices, tnc_circuit* out) {
+  return guarded([&] {
+    if (!out) fail(TNC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 64) fail(TNC_E_INVALID_ARG, "n_qubits must be in [1, 64]");
+    if (n_gates < 0) fail(TNC_E_INVALID_ARG, "n_gates < 0");
+    if (n_gates > 0 && (!arity || !qubits || !matrices)) fail(TNC_E_INVALID_ARG, "NULL gate arrays");
+    auto* c = new tnc_circuit_s();
+    c->c.n = n_qubits;
+    c->c.gates.resize((size_t)n_gates);
+    for (int64_t g = 0; g < n_gates; ++g) {
+      Gate& G = c->c.gates[(size_t)g];
+      G.arity = arity[g];
+      if (G.arity != 1 && G.arity != 2) {
+        delete c;
+        fail(TNC_E_INVALID_ARG, "gate " + std::to_string(g) + ": arity must be 1 or 2");
+      }
+      for (int t = 0; t < 2; ++t) G.q[t] = t < G.arity ? qubits[2 * g + t] : -1;
+      for (int t = 0; t < G.arity; ++t)
+        if (G.q[t] < 0 || G.q[t] >= n_qubits) {
+          delete c;
+          fail(TNC_E_INVALID_ARG, "gate " + std::to_string(g) + ": qubit out of range");
+        }
+      if (G.arity == 2 && G.q[0] == G.q[1]) {
+        delete c;
+        fail(TNC_E_INVALID_ARG, "gate " + std::to_string(g) + ": repeated qubit");
+      }
+      const int d = 1 << G.arity;
+      for (int i = 0; i < 16; ++i) G.m[i] = 0;
+      for (int i = 0; i < d * d; ++i) G.m[i] = cd(matrices[32 * g + 2 * i], matrices[32 * g + 2 * i + 1]);
+    }
+    *out = c;
+  });
+}
+
+void tnc_circuit_destroy(tnc_circuit c) { delete c; }
+
+tnc_status tnc_network_build(tnc_circuit c, const uint8_t* open_mask, tnc_network* out) {
+  return guarded([&] {
+    if (!c || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    std::vector<uint8_t> mask;
+    if (open_mask) mask.assign(open_mask, open_mask + c->c.n);
+    auto* n = new tnc_network_s();
+    try {
+      build_network(c->c, mask, n->n);
+    } catch (...) {
+      delete n;
+      throw;
+    }
+    *out = n;
+  });
+}
+
+void tnc_network_destroy(tnc_network n) { delete n; }
+
+tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* out) {
+  return guarded([&] {
+    if (!n || !opts || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    PlanOpts o;
+    o.seed = opts->seed;
+    o.trials = opts->trials;
+    o.log2_cap = opts->log2_cap;
+    o.slices_min = opts->slices_min;
+    o.slices_max = opts->slices_max;
+    o.temperature = opts->temperature;
+    auto* p = new tnc_plan_s();
+    try {
+      plan_greedy(n->n, o, p->p);
+    } catch (...) {
+      delete p;
+      throw;
+    }
+    *out = p;
+  });
+}
+
+void tnc_plan_destroy(tnc_plan p) {
+  if (p) release_plan_device(p);
+  delete p;
+}
+
+tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info) {
+  return guarded([&] {
+    if (!p || !info) fail(TNC_E_INVALID_ARG, "NULL argument");
+    const Plan& P = p->p;
+    std::memset(info, 0, sizeof(*info));
+    info->log2_flops_per_slice = P.log2_flops_slice;
+    info->log2_total_flops = P.log2_flops_total;
+    info->slicing_overhead = P.overhead;
+    info->max_log2_size = P.max_log2;
+    info->n_sliced = (int32_t)P.sliced.size();
+    info->n_steps = (int32_t)P.tree.size();
+    info->n_leaves = (int32_t)P.net.leaves.size();
+    info->n_open = (int32_t)P.net.open_qubits.size();
+    info->n_kernels = (int32_t)P.steps.size() + 2;
+    info->n_gemm = P.n_gemm;
+    info->n_gepdot = P.n_gepdot;
+    info->n_absorb = P.n_absorb;
+    info->n_fused = P.n_fused;
+    info->narrow_max = P.narrow_max;
+  });
+}
+
+tnc_status tnc_plan_sliced_cuts(tnc_plan p, int32_t* qubit, int32_t* cut, int32_t cap) {
+  return guarded([&] {
+    if (!p || (!qubit && cap > 0) || (!cut && cap > 0)) fail(TNC_E_INVALID_ARG, "NULL argument");
+    const Plan& P = p->p;
+    if (cap < (int32_t)P.sliced.size()) fail(TNC_E_INVALID_ARG, "cap smaller than the number of sliced indices");
+    for (size_t t = 0; t < P.sliced.size(); ++t) {
+      qubit[t] = P.net.edges[P.sliced[t]].qubit;
+      cut[t] = P.net.edges[P.sliced[t]].cut;
+    }
+  });
+}
+
+tnc_status tnc_plan_open_qubits(tnc_plan p, int32_t* qubits, int32_t cap) {
+  return guarded([&] {
+    if (!p) fail(TNC_E_INVALID_ARG, "NULL plan");
+    const Plan& P = p->p;
+    if (cap < (int32_t)P.net.open_qubits.size() || (!qubits && !P.net.open_qubits.empty()))
+      fail(TNC_E_INVALID_ARG, "cap smaller than the number of open qubits");
+    for (size_t t = 0; t < P.net.open_qubits.size(); ++t) qubits[t] = P.net.open_qubits[t];
+  });
+}
+
+tnc_status tnc_plan_save(tnc_plan p, const char* path) {
+  return guarded([&] {
+    if (!p || !path) fail(TNC_E_INVALID_ARG, "NULL argument");
+    save_plan(p->p, path);
+  });
+}
+
+tnc_status tnc_plan_load(const char* path, tnc_plan* out) {
+  return guarded([&] {
+    if (!path || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    auto* p = new tnc_plan_s();
+    try {
+      load_plan(path, p->p);
+    } catch (...) {
+      delete p;
+      throw;
+    }
+    *out = p;
+  });
+}
+
+namespace {
+std::string jlist(const std::vector<int>& v) {
+  std::string s = "[";
+  for (size_t i = 0; i < v.size(); ++i) s += (i ? "," : "") + std::to_string(v[i]);
+  return s + "]";
+}
+}  // namespace
+
+tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
+  return guarded([&] {
+    if (!p || !len) fail(TNC_E_INVALID_ARG, "NULL argument");
+    const Plan& P = p->p;
+    std::string s = "{\"n_qubits\":" + std::to_string(P.net.circ.n);
+    s += ",\"edges\":[";
+    for (size_t e = 0; e < P.net.edges.size(); ++e) {
+      const Edge& E = P.net.edges[e];
+      s += (e ? "," : "") + std::string("[") + std::to_string(E.qubit) + "," + std::to_string(E.cut) + "," +
+           std::to_string(E.kind) + "," + (E.open ? "1" : "0") + "]";
+    }
+    s += "],\"leaves\":[";
+    for (size_t i = 0; i < P.net.leaves.size(); ++i)
+      s += (i ? "," : "") + std::string("{\"labels\":") + jlist(P.net.leaves[i].t.labels) +
+           ",\"gates\":" + jlist(P.net.leaves[i].gates) + "}";
+    s += "],\"sliced\":" + jlist(P.sliced) + ",\"tree\":[";
+    for (size_t i = 0; i < P.tree.size(); ++i)
+      s += (i ? "," : "") + std::string("[") + std::to_string(P.tree[i].first) + "," + std::to_string(P.tree[i].second) + "]";
+    s += "],\"tensors\":[";
+    for (size_t i = 0; i < P.tensors.size(); ++i)
+      s += (i ? "," : "") + std::string("{\"labels\":") + jlist(P.tensors[i].labels) +
+           ",\"offset\":" + std::to_string(P.tensors[i].offset) + "}";
+    s += "],\"steps\":[";
+    for (size_t i = 0; i < P.steps.size(); ++i) {
+      const Step& S = P.steps[i];
+      const TileSpec& t = S.tile;
+      s += (i ? "," : "") + std::string("{\"a\":") + std::to_string(S.a) + ",\"b\":" + std::to_string(S.b) +
+           ",\"c\":" + std::to_string(S.c) + ",\"kind\":" + std::to_string(S.kind) + ",\"Mt\":" + jlist(t.Mt) +
+           ",\"Kt\":" + jlist(t.Kt) + ",\"Nt\":" + jlist(t.Nt) + ",\"Mo\":" + jlist(t.Mo) + ",\"Ko\":" + jlist(t.Ko) +
+           ",\"No\":" + jlist(t.No) + ",\"splitk\":" + std::to_string(t.splitk) + ",\"rm\":" + std::to_string(t.rm) +
+           ",\"rn\":" + std::to_string(t.rn) + ",\"kgroups\":" + std::to_string(t.kgroups) +
+           ",\"chain_b\":" + jlist(S.chain_b) + ",\"chain_c\":" + jlist(S.chain_c) + "}";
+    }
+    char num[64];
+    std::snprintf(num, sizeof(num), "%.17g", P.log2_flops_slice);
+    s += "],\"root\":" + std::to_string(P.root) + ",\"log2_flops_slice\":" + num;
+    std::snprintf(num, sizeof(num), "%.17g", P.overhead);
+    s += ",\"overhead\":" + std::string(num) + ",\"arena_scalars\":" + std::to_string(P.arena_elems) + "}";
+    *len = (int64_t)s.size() + 1;
+    if (buf && cap > 0) {
+      const size_t n = std::min<size_t>((size_t)cap - 1, s.size());
+      std::memcpy(buf, s.data(), n);
+      buf[n] = 0;
+    }
+  });
+}

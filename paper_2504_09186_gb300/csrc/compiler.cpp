@@ -1,0 +1,297 @@
+// Step compiler: turns a tree + slice set into the per-step program the device runs.
+//
+// For each pairwise contraction C = A * B (Sec. II-A) it fixes
+//  * operand roles: the larger tensor is A and keeps its index order in C ("large
+//    tensors stay at the multiplier position", Sec. V-A); B's free indices take the
+//    positions A's contracted indices vacate, the rest go on top;
+//  * tiles: sets of indices each CTA keeps on chip.  Because every index has dimension
+//    2, an operand's tile is a sub-tensor over a set of its indices; choosing the tile
+//    sets to contain each operand's lowest positions makes every load and store a run
+//    of contiguous memory, so the permutation to the M x K x N view costs no extra
+//    pass (the permutation is folded into the loads, Sec. V-A);
+//  * the class: split over the common indices when M*N is small and K large (the
+//    GEPDOT of Sec. II-A / Sec. V-B), fused on-chip chains of absorptions of small
+//    tensors into one large one (Sec. IV), or the generic tiled contraction;
+//  * device memory: every tensor gets an arena offset, reused once its last consumer ran.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <set>
+
+#include "host.h"
+
+namespace tnc {
+
+namespace {
+
+int find_pos(const std::vector<int>& v, int x) {
+  for (size_t i = 0; i < v.size(); ++i)
+    if (v[i] == x) return (int)i;
+  return -1;
+}
+
+bool contains(const std::vector<int>& v, int x) { return find_pos(v, x) >= 0; }
+
+// C's storage order: A's free labels keep their positions' order; B's free labels
+// fill the slots of A's common labels (in B's order), the remainder is appended.
+std::vector<int> output_layout(const std::vector<int>& la, const std::vector<int>& lb) {
+  std::vector<int> bfree;
+  for (int x : lb)
+    if (!contains(la, x)) bfree.push_back(x);
+  std::vector<int> out;
+  size_t nb = 0;
+  for (int x : la) {
+    if (!contains(lb, x)) out.push_back(x);
+    else if (nb < bfree.size()) out.push_back(bfree[nb++]);
+  }
+  while (nb < bfree.size()) out.push_back(bfree[nb++]);
+  return out;
+}
+
+// Lowest `k` labels of a layout.
+std::vector<int> low(const std::vector<int>& l, int k) {
+  return std::vector<int>(l.begin(), l.begin() + std::min<size_t>(l.size(), (size_t)k));
+}
+
+void add_unique(std::vector<int>& dst, int x) {
+  if (!contains(dst, x)) dst.push_back(x);
+}
+
+// Tile limits (log2 entries): operand tiles <= 2^11, output tile <= 2^12.
+constexpr int TILE_AB = 11;
+constexpr int TILE_C = 12;
+
+// Largest output tile (log2) that 256 threads cover with micro-tiles of up to 4 x 4.
+int max_out_bits(int mt, int nt) { return 8 + std::min(2, mt) + std::min(2, nt); }
+
+// Choose a tile for the generic / split-K kernels.
+TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
+                     int n_inst_hint, int& kind_out) {
+  std::vector<int> M, K, N;
+  for (int x : la) (contains(lb, x) ? K : M).push_back(x);
+  for (int x : lb)
+    if (!contains(la, x)) N.push_back(x);
+  const int m = (int)M.size(), k = (int)K.size(), n = (int)N.size();
+  TileSpec t;
+  auto fits = [](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
+    const int mt = (int)Mt.size(), kt = (int)Kt.size(), nt = (int)Nt.size();
+    return mt + kt <= TILE_AB && kt + nt <= TILE_AB && mt + nt <= TILE_C && mt + nt <= max_out_bits(mt, nt);
+  };
+  // labels each tile must hold so that loads and stores run over contiguous memory
+  for (int need = 4; need >= 0; --need) {
+    std::vector<int> Mt, Kt, Nt;
+    for (int x : low(la, need)) {
+      if (contains(K, x)) add_unique(Kt, x);
+      else add_unique(Mt, x);
+    }
+    for (int x : low(lb, need)) {
+      if (contains(K, x)) add_unique(Kt, x);
+      else add_unique(Nt, x);
+    }
+    for (int x : low(lc, need)) {
+      if (contains(M, x)) add_unique(Mt, x);
+      else add_unique(Nt, x);
+    }
+    if (!fits(Mt, Kt, Nt)) continue;
+    t.Mt = Mt;
+    t.Kt = Kt;
+    t.Nt = Nt;
+    break;
+  }
+  // grow the tiles by class, one label at a time while the limits hold
+  const bool gepdot = (m + n <= 8) && (k >= 12);
+  auto grow = [&](std::vector<int>& tile, const std::vector<int>& pool, int target) {
+    for (int x : pool) {
+      if ((int)tile.size() >= target) break;
+      if (contains(tile, x)) continue;
+      tile.push_back(x);
+      if (!fits(t.Mt, t.Kt, t.Nt)) {
+        tile.pop_back();
+        break;
+      }
+    }
+  };
+  if (gepdot) {
+    grow(t.Mt, M, m);
+    grow(t.Nt, N, n);
+    grow(t.Kt, K, k);
+  } else if (k + n <= 6) {
+    // absorption of a small tensor: all of B on chip, a wide slice of A
+    grow(t.Kt, K, k);
+    grow(t.Nt, N, n);
+    grow(t.Mt, M, std::min(m, 9));
+  } else {
+    grow(t.Mt, M, std::min(m, 6));
+    grow(t.Nt, N, std::min(n, 6));
+    grow(t.Kt, K, std::min(k, 5));
+  }
+  // canonical orders: M and K by A position, N by B position
+  auto order_by = [](std::vector<int>& v, const std::vector<int>& layout) {
+    std::sort(v.begin(), v.end(), [&](int x, int y) { return find_pos(layout, x) < find_pos(layout, y); });
+  };
+  order_by(t.Mt, la);
+  order_by(t.Kt, la);
+  order_by(t.Nt, lb);
+  for (int x : M)
+    if (!contains(t.Mt, x)) t.Mo.push_back(x);
+  for (int x : K)
+    if (!contains(t.Kt, x)) t.Ko.push_back(x);
+  for (int x : N)
+    if (!contains(t.Nt, x)) t.No.push_back(x);
+  // micro-tile (up to 4 x 4 outputs per thread) and intra-CTA K groups, 256 threads
+  const int mt = (int)t.Mt.size(), nt = (int)t.Nt.size(), kt = (int)t.Kt.size();
+  const int out_bits = mt + nt;
+  int lrm = 0, lrn = 0;
+  while (out_bits - lrm - lrn > 8) {
+    if (lrm <= lrn && lrm < 2 && lrm < mt) ++lrm;
+    else if (lrn < 2 && lrn < nt) ++lrn;
+    else if (lrm < 2 && lrm < mt) ++lrm;
+    else break;
+  }
+  if (out_bits - lrm - lrn > 8) fail(5, "compile: output tile too large");
+  t.rm = 1 << lrm;
+  t.rn = 1 << lrn;
+  const int threads_out = 1 << (out_bits - lrm - lrn);
+  int kg = 256 / threads_out;
+  kg = std::min(kg, 1 << kt);
+  t.kgroups = std::max(1, kg);
+  // split over the outer common labels for GEPDOT-shaped steps, enough CTAs to fill the GPU
+  t.splitk = 1;
+  const int ko = (int)t.Ko.size();
+  if (gepdot && ko > 0) {
+    const int64_t tiles = (int64_t(1) << (t.Mo.size() + t.No.size())) * std::max(1, n_inst_hint);
+    const int64_t want = (4 * 152 + tiles - 1) / tiles;
+    int s = 0;
+    while (s < ko && s < 10 && (int64_t(1) << s) < want) ++s;
+    t.splitk = 1 << s;
+  }
+  kind_out = t.splitk > 1 ? K_SPLITK : K_GENERIC;
+  return t;
+}
+
+}  // namespace
+
+TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
+                  int& kind) {
+  return choose_tile(la, lb, lc, n_inst, kind);
+}
+
+void compile_plan(Plan& plan, bool fuse) {
+  const Network& net = plan.net;
+  const int L = (int)net.leaves.size();
+  plan.fuse = fuse;
+  std::vector<char> sliced(net.edges.size(), 0);
+  for (int e : plan.sliced) sliced[e] = 1;
+  std::map<int, int> slice_bit;
+  for (size_t t = 0; t < plan.sliced.size(); ++t) slice_bit[plan.sliced[t]] = (int)t;
+
+  plan.tensors.clear();
+  plan.leaf_fix.assign(L, {});
+  for (int i = 0; i < L; ++i) {
+    TensorInfo ti;
+    ti.leaf = i;
+    const auto& labs = net.leaves[i].t.labels;
+    for (size_t p = 0; p < labs.size(); ++p) {
+      int e = labs[p];
+      const Edge& ed = net.edges[e];
+      if (ed.kind == EDGE_OUTPUT && !ed.open) {
+        plan.leaf_fix[i].push_back({(int)p, 1, ed.qubit});
+      } else if (sliced[e]) {
+        plan.leaf_fix[i].push_back({(int)p, 0, slice_bit[e]});
+      } else {
+        ti.labels.push_back(e);
+      }
+    }
+    plan.tensors.push_back(ti);
+  }
+  // intermediates
+  plan.steps.clear();
+  plan.n_gemm = plan.n_gepdot = plan.n_absorb = plan.n_fused = 0;
+  plan.narrow_max = 0;
+  plan.max_log2 = 0;
+  for (auto& ti : plan.tensors) plan.max_log2 = std::max(plan.max_log2, (int)ti.labels.size());
+  for (size_t s = 0; s < plan.tree.size(); ++s) {
+    int a = plan.tree[s].first, b = plan.tree[s].second;
+    if (plan.tensors[b].labels.size() > plan.tensors[a].labels.size()) std::swap(a, b);
+    TensorInfo ci;
+    ci.labels = output_layout(plan.tensors[a].labels, plan.tensors[b].labels);
+    ci.producer = (int)s;
+    plan.max_log2 = std::max(plan.max_log2, (int)ci.labels.size());
+    Step st;
+    st.a = a;
+    st.b = b;
+    st.c = (int)plan.tensors.size();
+    plan.tensors.push_back(ci);
+    plan.steps.push_back(st);
+  }
+  plan.root = plan.tree.empty() ? 0 : (int)plan.tensors.size() - 1;
+  // classify + tiles
+  for (size_t s = 0; s < plan.steps.size(); ++s) {
+    Step& st = plan.steps[s];
+    const auto& la = plan.tensors[st.a].labels;
+    const auto& lb = plan.tensors[st.b].labels;
+    const auto& lc = plan.tensors[st.c].labels;
+    int kind = K_GENERIC;
+    st.tile = choose_tile(la, lb, lc, 1, kind);
+    st.kind = kind;
+    int nk = 0;
+    for (int x : la) nk += contains(lb, x);
+    int nm = (int)la.size() - nk, nn = (int)lb.size() - nk;
+    if (!la.empty() || !lb.empty()) {
+      double narrow = (la.size() + lb.size()) ? 2.0 * nk / double(la.size() + lb.size()) : 0;
+      plan.narrow_max = std::max(plan.narrow_max, narrow);
+    }
+    if (nm + nn <= 8 && nk >= 12) plan.n_gepdot++;
+    else if (nk + nn <= 6) plan.n_absorb++;
+    else plan.n_gemm++;
+  }
+  // liveness + arena (first fit over a sorted free list, per instance, in complex elements;
+  // planar storage takes 2 * 2^rank scalars, so offsets are kept in scalars)
+  for (auto& ti : plan.tensors) ti.last_use = -1;
+  for (size_t s = 0; s < plan.steps.size(); ++s) {
+    plan.tensors[plan.steps[s].a].last_use = (int)s;
+    plan.tensors[plan.steps[s].b].last_use = (int)s;
+  }
+  plan.tensors[plan.root].last_use = (int)plan.steps.size();
+  std::vector<std::pair<int64_t, int64_t>> freelist;  // (offset, size) in scalars
+  int64_t top = 0;
+  auto alloc = [&](int64_t size) -> int64_t {
+    // align to 64 scalars (>= 128 B for every precision)
+    size = (size + 63) & ~int64_t(63);
+    for (size_t i = 0; i < freelist.size(); ++i) {
+      if (freelist[i].second >= size) {
+        int64_t off = freelist[i].first;
+        freelist[i].first += size;
+        freelist[i].second -= size;
+        if (freelist[i].second == 0) freelist.erase(freelist.begin() + i);
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += size;
+    return off;
+  };
+  auto release = [&](int64_t off, int64_t size) {
+    size = (size + 63) & ~int64_t(63);
+    freelist.emplace_back(off, size);
+    std::sort(freelist.begin(), freelist.end());
+    std::vector<std::pair<int64_t, int64_t>> merged;
+    for (auto& f : freelist) {
+      if (!merged.empty() && merged.back().first + merged.back().second == f.first) merged.back().second += f.second;
+      else merged.push_back(f);
+    }
+    freelist.swap(merged);
+  };
+  auto scalars = [](const TensorInfo& t) { return int64_t(2) << t.labels.size(); };
+  for (int i = 0; i < L; ++i) plan.tensors[i].offset = alloc(scalars(plan.tensors[i]));
+  for (size_t s = 0; s < plan.steps.size(); ++s) {
+    Step& st = plan.steps[s];
+    // the output may not overlap its inputs: allocate before releasing them
+    plan.tensors[st.c].offset = alloc(scalars(plan.tensors[st.c]));
+    for (int opnd : {st.a, st.b})
+      if (plan.tensors[opnd].last_use == (int)s) release(plan.tensors[opnd].offset, scalars(plan.tensors[opnd]));
+  }
+  plan.arena_elems = top;  // scalars per instance
+}
+
+}  // namespace tnc

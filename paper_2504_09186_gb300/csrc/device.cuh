@@ -1,0 +1,75 @@
+// Device-side parameter blocks and storage helpers shared by the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnc {
+
+constexpr int kMaxTileBits = 16;  // per canonical tile set (M, N or K)
+constexpr int kMaxOuter = 40;     // outer labels per set
+constexpr int kThreads = 256;
+
+// Storage conversion: FP32 arithmetic, fp32 / fp16 / bf16 storage (round to nearest even).
+template <typename T>
+struct Conv;
+template <>
+struct Conv<float> {
+  static __device__ __forceinline__ float to_f(float x) { return x; }
+  static __device__ __forceinline__ float from_f(float x) { return x; }
+};
+template <>
+struct Conv<__half> {
+  static __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+  static __device__ __forceinline__ __half from_f(float x) { return __float2half_rn(x); }
+};
+template <>
+struct Conv<__nv_bfloat16> {
+  static __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+  static __device__ __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+};
+
+// One pairwise contraction C = A * B with tiles over index sets (see compiler.cpp).
+struct GenParams {
+  const void* A;  // instance-0 base of A's real plane (imag plane at +planeA)
+  const void* B;
+  void* C;
+  int64_t strideA, strideB, strideC;  // instance strides in scalars
+  int64_t planeA, planeB, planeC;     // 2^rank
+  int32_t mt, nt, kt;
+  int32_t runA, runB, runC;           // low positions of each operand covered by the tile
+  uint32_t maskA, maskB, maskC;       // tile positions in each operand
+  int8_t pAm[kMaxTileBits], pAk[kMaxTileBits];  // tile-native bit of canonical bit j
+  int8_t pBk[kMaxTileBits], pBn[kMaxTileBits];
+  int8_t pCm[kMaxTileBits], pCn[kMaxTileBits];
+  int32_t n_om, n_on, n_ok;
+  int8_t om_A[kMaxOuter], om_C[kMaxOuter], on_B[kMaxOuter], on_C[kMaxOuter], ok_A[kMaxOuter], ok_B[kMaxOuter];
+  int32_t splitk, kgroups;
+  int32_t nK;                          // common labels (bound for the output scale)
+  // scaling slots: value = stored * 2^exps[slot]; maxabs = max |re|,|im| of stored
+  float* maxabs;
+  int32_t* exps;
+  int32_t n_slots, slotA, slotB, slotC;
+  float2* partials;                    // split-K partial sums [inst][split][planeC]
+  int32_t smem_tables;                 // byte offset of the index tables in shared memory
+};
+
+// Leaf gather: fix sliced legs and closed output legs, convert, scale.
+struct LeafDesc {
+  int64_t src;      // offset (complex entries) of the full leaf in the FP64 source array
+  int64_t dst;      // scalar offset of the reduced leaf in the instance arena
+  int32_t rank_full, rank, slot, nfix;
+  int8_t fix_pos[8];
+  int8_t fix_kind[8];   // 0 = slice bit, 1 = output bit of a qubit
+  int16_t fix_idx[8];   // slice bit index or qubit
+};
+
+// A run of consecutive instances of one wave that belong to the same bitstring row.
+struct RootSeg {
+  int32_t row;
+  int32_t begin, end;  // instances within the wave
+};
+
+}  // namespace tnc

@@ -1,0 +1,607 @@
+// Device executor: contexts, per-plan device programs, and the amplitude / contraction
+// entry points of the C boundary.
+//
+// An *instance* is one full contraction of the plan for one bitstring row and one
+// slice id (Sec. III-A: a subtask).  Instances run in waves: every kernel of the step
+// program covers all instances of a wave in one launch (grid.z), and the per-wave
+// root tensors are added into an FP64 accumulator in a fixed order.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "capi_internal.h"
+#include "device.cuh"
+
+namespace tnc {
+
+cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, dim3 grid, size_t smem, cudaStream_t s);
+cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_inst, cudaStream_t s);
+cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leaves, const double2* src, void* arena,
+                               int64_t inst_stride, const int64_t* inst_slice, const int32_t* inst_row,
+                               const uint8_t* bits, int n_qubits, float* maxabs, int32_t* exps, int n_slots,
+                               int64_t inst_base, int64_t n_inst, cudaStream_t s);
+cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                              const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
+                              const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s);
+cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
+TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
+                  int& kind);
+
+#define CUDA_OK(expr)                                                                             \
+  do {                                                                                            \
+    cudaError_t _e = (expr);                                                                      \
+    if (_e != cudaSuccess) fail(TNC_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+static size_t elem_bytes(int precision) { return precision == TNC_C64 ? 4 : 2; }
+
+// ------------------------------------------------------------------ device buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void reserve(size_t n) {
+    if (n <= bytes) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      fail(TNC_E_OOM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+// ------------------------------------------------------------------ GenParams from a tile
+static int pos_of(const std::vector<int>& l, int x) {
+  for (size_t i = 0; i < l.size(); ++i)
+    if (l[i] == x) return (int)i;
+  fail(TNC_E_PLAN, "label missing from operand layout");
+}
+
+static int rank_in_mask(uint32_t mask, int pos) { return __builtin_popcount(mask & ((1u << pos) - 1u)); }
+
+static int low_run(uint32_t mask) {
+  int r = 0;
+  while (r < 32 && ((mask >> r) & 1u)) ++r;
+  return r;
+}
+
+struct StepLaunch {
+  int kind;  // K_GENERIC or K_SPLITK
+  GenParams p;
+  dim3 grid;
+  size_t smem;
+  int rm, rn;
+};
+
+static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int>& la, const std::vector<int>& lb,
+                              const std::vector<int>& lc) {
+  StepLaunch L;
+  std::memset(&L.p, 0, sizeof(L.p));
+  GenParams& p = L.p;
+  if (t.Mt.size() > (size_t)kMaxTileBits || t.Nt.size() > (size_t)kMaxTileBits || t.Kt.size() > (size_t)kMaxTileBits ||
+      t.Mo.size() > (size_t)kMaxOuter || t.No.size() > (size_t)kMaxOuter || t.Ko.size() > (size_t)kMaxOuter)
+    fail(TNC_E_UNSUPPORTED, "tile exceeds kernel limits");
+  if (la.size() > 32 || lb.size() > 32 || lc.size() > 32) fail(TNC_E_UNSUPPORTED, "rank above 32");
+  p.mt = (int)t.Mt.size();
+  p.nt = (int)t.Nt.size();
+  p.kt = (int)t.Kt.size();
+  for (int x : t.Mt) p.maskA |= 1u << pos_of(la, x), p.maskC |= 1u << pos_of(lc, x);
+  for (int x : t.Kt) p.maskA |= 1u << pos_of(la, x), p.maskB |= 1u << pos_of(lb, x);
+  for (int x : t.Nt) p.maskB |= 1u << pos_of(lb, x), p.maskC |= 1u << pos_of(lc, x);
+  p.runA = low_run(p.maskA);
+  p.runB = low_run(p.maskB);
+  p.runC = low_run(p.maskC);
+  for (int j = 0; j < p.mt; ++j) {
+    p.pAm[j] = (int8_t)rank_in_mask(p.maskA, pos_of(la, t.Mt[j]));
+    p.pCm[j] = (int8_t)rank_in_mask(p.maskC, pos_of(lc, t.Mt[j]));
+  }
+  for (int j = 0; j < p.kt; ++j) {
+    p.pAk[j] = (int8_t)rank_in_mask(p.maskA, pos_of(la, t.Kt[j]));
+    p.pBk[j] = (int8_t)rank_in_mask(p.maskB, pos_of(lb, t.Kt[j]));
+  }
+  for (int j = 0; j < p.nt; ++j) {
+    p.pBn[j] = (int8_t)rank_in_mask(p.maskB, pos_of(lb, t.Nt[j]));
+    p.pCn[j] = (int8_t)rank_in_mask(p.maskC, pos_of(lc, t.Nt[j]));
+  }
+  p.n_om = (int)t.Mo.size();
+  p.n_on = (int)t.No.size();
+  p.n_ok = (int)t.Ko.size();
+  for (int j = 0; j < p.n_om; ++j) p.om_A[j] = (int8_t)pos_of(la, t.Mo[j]), p.om_C[j] = (int8_t)pos_of(lc, t.Mo[j]);
+  for (int j = 0; j < p.n_on; ++j) p.on_B[j] = (int8_t)pos_of(lb, t.No[j]), p.on_C[j] = (int8_t)pos_of(lc, t.No[j]);
+  for (int j = 0; j < p.n_ok; ++j) p.ok_A[j] = (int8_t)pos_of(la, t.Ko[j]), p.ok_B[j] = (int8_t)pos_of(lb, t.Ko[j]);
+  p.planeA = int64_t(1) << la.size();
+  p.planeB = int64_t(1) << lb.size();
+  p.planeC = int64_t(1) << lc.size();
+  p.splitk = t.splitk;
+  p.kgroups = t.kgroups;
+  p.nK = p.kt + p.n_ok;
+  if (p.n_om + p.n_on > 30) fail(TNC_E_UNSUPPORTED, "too many outer tiles");
+  // shared memory: operand tiles / reduction buffer, then index tables
+  const size_t ab = ((size_t(1) << (p.mt + p.kt)) + (size_t(1) << (p.kt + p.nt))) * 8;
+  const size_t rb = size_t(t.kgroups) * (size_t(1) << (p.mt + p.nt)) * 8;
+  size_t region = std::max(ab, rb);
+  region = (region + 15) & ~size_t(15);
+  p.smem_tables = (int32_t)region;
+  size_t tables = ((size_t(1) << (p.mt + p.kt - p.runA)) + (size_t(1) << (p.kt + p.nt - p.runB)) +
+                   (size_t(1) << (p.mt + p.nt - p.runC))) * 4 +
+                  ((size_t(2) << p.mt) + (size_t(2) << p.kt) + (size_t(2) << p.nt) + 2) * 2 + 32 * 4;
+  L.smem = region + tables;
+  if (L.smem > 200 * 1024) fail(TNC_E_UNSUPPORTED, "tile needs too much shared memory");
+  L.grid = dim3(1u << (p.n_om + p.n_on), (unsigned)t.splitk, 1);
+  L.kind = kind;
+  L.rm = t.rm;
+  L.rn = t.rn;
+  return L;
+}
+
+// ------------------------------------------------------------------ per-plan device program
+struct DeviceProgram {
+  int device = 0, precision = 0, W = 0;
+  int64_t inst_stride = 0;  // scalars
+  int n_slots = 0, n_leaves = 0;
+  DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos;
+  std::vector<StepLaunch> steps;
+  int root = 0;
+  int64_t root_off = 0, root_plane = 1;
+  int n_open = 0;
+  int n_qubits = 0;
+  ~DeviceProgram() {
+    arena.release();
+    maxabs.release();
+    exps.release();
+    leaf_src.release();
+    leaf_desc.release();
+    partials.release();
+    open_pos.release();
+  }
+};
+
+}  // namespace tnc
+
+using namespace tnc;
+
+// Events of the last profiled call: per (wave, step) a start/end pair, plus the call.
+struct ProfState {
+  bool valid = false;
+  int n_steps = 0, waves = 0;
+  std::vector<cudaEvent_t> ev;
+  std::vector<double> flops, bytes;
+  std::vector<int> kind;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t& at(int w, int s, int which) { return ev[(size_t(w) * n_steps + s) * 2 + which]; }
+  void ensure(int steps, int w) {
+    const size_t need = size_t(steps) * w * 2 + 2;
+    while (ev.size() < need) {
+      cudaEvent_t x;
+      if (cudaEventCreate(&x) != cudaSuccess) fail(TNC_E_CUDA, "cudaEventCreate failed");
+      ev.push_back(x);
+    }
+    n_steps = steps;
+    waves = w;
+  }
+  cudaEvent_t& call_start() { return ev[size_t(n_steps) * waves * 2]; }
+  cudaEvent_t& call_end() { return ev[size_t(n_steps) * waves * 2 + 1]; }
+  ~ProfState() {
+    for (auto x : ev) cudaEventDestroy(x);
+  }
+};
+
+struct tnc_context_s {
+  int device = 0;
+  int id = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials;
+  ProfState prof;
+  ~tnc_context_s() {
+    bits.release();
+    inst_slice.release();
+    inst_row.release();
+    segs.release();
+    acc.release();
+    scratch.release();
+    partials.release();
+  }
+};
+
+static std::atomic<int> g_ctx_ids{1};
+
+namespace tnc {
+
+void release_plan_device(tnc_plan_s* p) { p->programs.clear(); }
+
+static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W) {
+  const Plan& P = plan->p;
+  auto prog = std::make_shared<DeviceProgram>();
+  prog->device = ctx->device;
+  prog->precision = precision;
+  prog->W = W;
+  prog->n_qubits = P.net.circ.n;
+  prog->inst_stride = (P.arena_elems + 63) & ~int64_t(63);
+  prog->n_slots = (int)P.tensors.size();
+  prog->n_leaves = (int)P.net.leaves.size();
+  const size_t eb = elem_bytes(precision);
+  prog->arena.reserve(size_t(prog->inst_stride) * eb * W + 256);
+  prog->maxabs.reserve(size_t(prog->n_slots) * W * sizeof(float));
+  prog->exps.reserve(size_t(prog->n_slots) * W * sizeof(int32_t));
+  // leaves: FP64 sources + descriptors
+  std::vector<double2> src;
+  std::vector<LeafDesc> desc;
+  for (int i = 0; i < prog->n_leaves; ++i) {
+    const Leaf& lf = P.net.leaves[i];
+    LeafDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.src = (int64_t)src.size();
+    for (const cd& v : lf.t.data) src.push_back(make_double2(v.real(), v.imag()));
+    d.dst = P.tensors[i].offset;
+    d.rank_full = (int)lf.t.labels.size();
+    d.rank = (int)P.tensors[i].labels.size();
+    d.slot = i;
+    const auto& fx = P.leaf_fix[i];
+    if (fx.size() > 8 || d.rank > 5) fail(TNC_E_UNSUPPORTED, "leaf with too many legs");
+    d.nfix = (int)fx.size();
+    for (size_t f = 0; f < fx.size(); ++f) {
+      d.fix_pos[f] = (int8_t)fx[f].pos;
+      d.fix_kind[f] = (int8_t)fx[f].kind;
+      d.fix_idx[f] = (int16_t)fx[f].index;
+    }
+    desc.push_back(d);
+  }
+  prog->leaf_src.reserve(std::max<size_t>(1, src.size()) * sizeof(double2));
+  prog->leaf_desc.reserve(std::max<size_t>(1, desc.size()) * sizeof(LeafDesc));
+  CUDA_OK(cudaMemcpy(prog->leaf_src.p, src.data(), src.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CUDA_OK(cudaMemcpy(prog->leaf_desc.p, desc.data(), desc.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice));
+  // steps
+  size_t partial_elems = 0;
+  for (size_t s = 0; s < P.steps.size(); ++s) {
+    const Step& st = P.steps[s];
+    const auto& la = P.tensors[st.a].labels;
+    const auto& lb = P.tensors[st.b].labels;
+    const auto& lc = P.tensors[st.c].labels;
+    StepLaunch L = make_launch(st.tile, st.kind, la, lb, lc);
+    L.p.A = prog->arena.as<char>() + P.tensors[st.a].offset * eb;
+    L.p.B = prog->arena.as<char>() + P.tensors[st.b].offset * eb;
+    L.p.C = prog->arena.as<char>() + P.tensors[st.c].offset * eb;
+    L.p.strideA = L.p.strideB = L.p.strideC = prog->inst_stride;
+    L.p.maxabs = prog->maxabs.as<float>();
+    L.p.exps = prog->exps.as<int32_t>();
+    L.p.n_slots = prog->n_slots;
+    L.p.slotA = st.a;
+    L.p.slotB = st.b;
+    L.p.slotC = st.c;
+    if (L.kind == K_SPLITK) partial_elems = std::max(partial_elems, size_t(W) * L.p.splitk * L.p.planeC);
+    prog->steps.push_back(L);
+  }
+  if (partial_elems) {
+    prog->partials.reserve(partial_elems * sizeof(float2));
+    for (auto& L : prog->steps)
+      if (L.kind == K_SPLITK) L.p.partials = prog->partials.as<float2>();
+  }
+  // root
+  prog->root = P.root;
+  prog->root_off = P.tensors[P.root].offset;
+  prog->root_plane = int64_t(1) << P.tensors[P.root].labels.size();
+  prog->n_open = (int)P.net.open_qubits.size();
+  std::vector<int8_t> opos(std::max(1, prog->n_open), 0);
+  for (int j = 0; j < prog->n_open; ++j) opos[j] = (int8_t)pos_of(P.tensors[P.root].labels, P.net.open_edge[j]);
+  prog->open_pos.reserve(opos.size());
+  CUDA_OK(cudaMemcpy(prog->open_pos.p, opos.data(), opos.size(), cudaMemcpyHostToDevice));
+  return prog;
+}
+
+static void set_device(tnc_context_s* ctx) { CUDA_OK(cudaSetDevice(ctx->device)); }
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Launch one step of a program (or a one-off step) for n_inst instances.
+static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s) {
+  StepLaunch L = L0;
+  L.grid.z = (unsigned)n_inst;
+  CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
+  if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
+}
+
+}  // namespace tnc
+
+// ------------------------------------------------------------------ C entry points
+tnc_status tnc_context_create(int32_t device, tnc_context* out) {
+  return guarded([&] {
+    if (!out) fail(TNC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CUDA_OK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) fail(TNC_E_INVALID_ARG, "no such device");
+    cudaDeviceProp prop;
+    CUDA_OK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+      fail(TNC_E_UNSUPPORTED, std::string("this library is built for sm_103 (GB300); device is ") + prop.name);
+    auto* c = new tnc_context_s();
+    c->device = device;
+    c->id = g_ctx_ids++;
+    c->sm_count = prop.multiProcessorCount;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      fail(TNC_E_CUDA, std::string("stream creation failed: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+  });
+}
+
+void tnc_context_destroy(tnc_context ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+}
+
+tnc_status tnc_sync(tnc_context ctx) {
+  return guarded([&] {
+    if (!ctx) fail(TNC_E_INVALID_ARG, "NULL context");
+    set_device(ctx);
+    CUDA_OK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                          int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
+  return guarded([&] {
+    if (!ctx || !plan || !opts || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
+    const Plan& P = plan->p;
+    const int n = P.net.circ.n;
+    const int precision = opts->precision;
+    if (precision < TNC_C64 || precision > TNC_CBF16) fail(TNC_E_INVALID_ARG, "bad precision");
+    if (batch < 1) fail(TNC_E_INVALID_ARG, "batch must be >= 1");
+    const int64_t n_slices = int64_t(1) << P.sliced.size();
+    if (slice_begin < 0 || slice_count < 1 || slice_begin + slice_count > n_slices)
+      fail(TNC_E_INVALID_ARG, "slice range outside [0, 2^s)");
+    const bool all_open = (int)P.net.open_qubits.size() == n;
+    if (!bitstrings && !(batch == 1 && all_open)) fail(TNC_E_INVALID_ARG, "bitstrings required");
+    std::vector<uint8_t> bits(size_t(batch) * n, 0);
+    if (bitstrings) {
+      std::memcpy(bits.data(), bitstrings, bits.size());
+      for (uint8_t b : bits)
+        if (b > 1) fail(TNC_E_INVALID_ARG, "bitstring bytes must be 0 or 1");
+    }
+    set_device(ctx);
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t n_inst = batch * slice_count;
+    // wave size
+    const size_t eb = elem_bytes(precision);
+    const int64_t stride = (P.arena_elems + 63) & ~int64_t(63);
+    int64_t W = opts->wave > 0 ? opts->wave : 0;
+    if (W == 0) {
+      size_t free_b = 0, total_b = 0;
+      CUDA_OK(cudaMemGetInfo(&free_b, &total_b));
+      const double per_inst = double(stride) * eb * 1.25 + 4096.0;
+      const double budget = std::min(double(free_b) * 0.6, 96.0 * (1ull << 30));
+      W = std::max<int64_t>(1, (int64_t)(budget / per_inst));
+    }
+    W = std::min<int64_t>({W, n_inst, 65535});
+    const std::string key = std::to_string(ctx->id) + "/" + std::to_string(precision) + "/" + std::to_string(W);
+    auto it = plan->programs.find(key);
+    std::shared_ptr<DeviceProgram> prog;
+    if (it == plan->programs.end()) {
+      // drop programs of other wave sizes on this context before allocating a new arena
+      for (auto jt = plan->programs.begin(); jt != plan->programs.end();) {
+        if (jt->first.rfind(std::to_string(ctx->id) + "/", 0) == 0) jt = plan->programs.erase(jt);
+        else ++jt;
+      }
+      prog = build_program(ctx, plan, precision, (int)W);
+      plan->programs[key] = prog;
+    } else {
+      prog = it->second;
+    }
+    // instance tables: row-major over (row, slice)
+    std::vector<int64_t> inst_slice(n_inst);
+    std::vector<int32_t> inst_row(n_inst);
+    for (int64_t b = 0; b < batch; ++b)
+      for (int64_t t = 0; t < slice_count; ++t) {
+        inst_slice[b * slice_count + t] = slice_begin + t;
+        inst_row[b * slice_count + t] = (int32_t)b;
+      }
+    std::vector<RootSeg> segs;
+    std::vector<std::pair<int, int>> wave_segs;  // (first seg, count)
+    for (int64_t base = 0; base < n_inst; base += W) {
+      const int64_t cnt = std::min<int64_t>(W, n_inst - base);
+      const int first = (int)segs.size();
+      for (int64_t i = 0; i < cnt; ++i) {
+        const int row = inst_row[base + i];
+        if (i == 0 || segs.back().row != row) segs.push_back({row, (int32_t)i, (int32_t)i + 1});
+        else segs.back().end = (int32_t)i + 1;
+      }
+      wave_segs.emplace_back(first, (int)segs.size() - first);
+    }
+    ctx->bits.reserve(std::max<size_t>(1, bits.size()));
+    ctx->inst_slice.reserve(n_inst * sizeof(int64_t));
+    ctx->inst_row.reserve(n_inst * sizeof(int32_t));
+    ctx->segs.reserve(segs.size() * sizeof(RootSeg));
+    const int64_t n_out = int64_t(1) << P.net.open_qubits.size();
+    ctx->acc.reserve(size_t(batch) * n_out * sizeof(double2));
+    CUDA_OK(cudaMemcpyAsync(ctx->bits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(ctx->inst_slice.p, inst_slice.data(), n_inst * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(ctx->inst_row.p, inst_row.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemcpyAsync(ctx->segs.p, segs.data(), segs.size() * sizeof(RootSeg), cudaMemcpyHostToDevice, s));
+    CUDA_OK(cudaMemsetAsync(ctx->acc.p, 0, size_t(batch) * n_out * sizeof(double2), s));
+    const bool prof = opts->profile != 0;
+    const int n_waves = (int)((n_inst + W - 1) / W);
+    if (prof) {
+      ProfState& ps = ctx->prof;
+      ps.valid = false;
+      ps.ensure((int)prog->steps.size(), n_waves);
+      ps.stream = s;
+      ps.flops.assign(prog->steps.size(), 0.0);
+      ps.bytes.assign(prog->steps.size(), 0.0);
+      ps.kind.assign(prog->steps.size(), 0);
+      for (size_t k = 0; k < P.steps.size(); ++k) {
+        const auto& la = P.tensors[P.steps[k].a].labels;
+        const auto& lb = P.tensors[P.steps[k].b].labels;
+        const auto& lc = P.tensors[P.steps[k].c].labels;
+        int common = 0;
+        for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
+        const int u = (int)(la.size() + lb.size()) - common;
+        ps.flops[k] = 8.0 * std::ldexp(1.0, u) * double(n_inst);
+        ps.bytes[k] = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) +
+                       std::ldexp(1.0, (int)lc.size())) * 2.0 * double(eb) * double(n_inst);
+        ps.kind[k] = prog->steps[k].kind;
+      }
+      CUDA_OK(cudaEventRecord(ps.call_start(), s));
+    }
+    int w = 0;
+    for (int64_t base = 0; base < n_inst; base += W, ++w) {
+      const int64_t cnt = std::min<int64_t>(W, n_inst - base);
+      CUDA_OK(cudaMemsetAsync(prog->maxabs.p, 0, size_t(prog->n_slots) * cnt * sizeof(float), s));
+      CUDA_OK(launch_leaf_gather(precision, prog->leaf_desc.as<LeafDesc>(), prog->n_leaves,
+                                 prog->leaf_src.as<double2>(), prog->arena.p, prog->inst_stride,
+                                 ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(),
+                                 n, prog->maxabs.as<float>(), prog->exps.as<int32_t>(), prog->n_slots, base, cnt, s));
+      for (size_t k = 0; k < prog->steps.size(); ++k) {
+        if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
+        run_step(precision, prog->steps[k], cnt, s);
+        if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
+      }
+      CUDA_OK(launch_root_accum(precision, prog->arena.p, prog->inst_stride, prog->root_off, prog->root_plane,
+                                prog->open_pos.as<int8_t>(), prog->n_open, ctx->segs.as<RootSeg>() + wave_segs[w].first,
+                                wave_segs[w].second, prog->exps.as<int32_t>(), prog->n_slots, prog->root,
+                                ctx->acc.as<double2>(), s));
+    }
+    if (prof) {
+      CUDA_OK(cudaEventRecord(ctx->prof.call_end(), s));
+      ctx->prof.valid = true;
+    }
+    const size_t out_bytes = size_t(batch) * n_out * sizeof(double2);
+    if (is_device_ptr(out)) {
+      CUDA_OK(cudaMemcpyAsync(out, ctx->acc.p, out_bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CUDA_OK(cudaMemcpyAsync(out, ctx->acc.p, out_bytes, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32_t rank_a, const int32_t* labels_a,
+                        const void* b, int32_t rank_b, const int32_t* labels_b, void* c, int32_t rank_c,
+                        const int32_t* labels_c, int32_t* c_exp2, void* stream) {
+  return guarded([&] {
+    if (!ctx || !a || !b || !c || !c_exp2) fail(TNC_E_INVALID_ARG, "NULL argument");
+    if (precision < TNC_C64 || precision > TNC_CBF16) fail(TNC_E_INVALID_ARG, "bad precision");
+    if (rank_a < 0 || rank_b < 0 || rank_c < 0 || rank_a > 32 || rank_b > 32 || rank_c > 32)
+      fail(TNC_E_INVALID_ARG, "ranks must be in [0, 32]");
+    if ((rank_a && !labels_a) || (rank_b && !labels_b) || (rank_c && !labels_c)) fail(TNC_E_INVALID_ARG, "NULL labels");
+    std::vector<int> la(labels_a, labels_a + rank_a), lb(labels_b, labels_b + rank_b), lc(labels_c, labels_c + rank_c);
+    auto distinct = [](std::vector<int> v) {
+      std::sort(v.begin(), v.end());
+      return std::adjacent_find(v.begin(), v.end()) == v.end();
+    };
+    if (!distinct(la) || !distinct(lb) || !distinct(lc)) fail(TNC_E_INVALID_ARG, "repeated label within a tensor");
+    std::vector<int> fr;
+    for (int x : la)
+      if (std::find(lb.begin(), lb.end(), x) == lb.end()) fr.push_back(x);
+    for (int x : lb)
+      if (std::find(la.begin(), la.end(), x) == la.end()) fr.push_back(x);
+    std::vector<int> s1 = fr, s2 = lc;
+    std::sort(s1.begin(), s1.end());
+    std::sort(s2.begin(), s2.end());
+    if (s1 != s2) fail(TNC_E_INVALID_ARG, "C's labels must be exactly the free labels of A and B");
+    set_device(ctx);
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    int kind = K_GENERIC;
+    TileSpec t = tile_for(la, lb, lc, 1, kind);
+    StepLaunch L = make_launch(t, kind, la, lb, lc);
+    ctx->scratch.reserve(256);
+    float* mx = ctx->scratch.as<float>();
+    int32_t* ex = reinterpret_cast<int32_t*>(ctx->scratch.as<char>() + 64);
+    CUDA_OK(cudaMemsetAsync(ctx->scratch.p, 0, 256, s));
+    const size_t eb = elem_bytes(precision);
+    CUDA_OK(launch_maxabs(precision, a, int64_t(2) << rank_a, mx + 0, s));
+    CUDA_OK(launch_maxabs(precision, b, int64_t(2) << rank_b, mx + 1, s));
+    L.p.A = a;
+    L.p.B = b;
+    L.p.C = c;
+    L.p.strideA = L.p.strideB = L.p.strideC = 0;
+    L.p.maxabs = mx;
+    L.p.exps = ex;
+    L.p.n_slots = 3;
+    L.p.slotA = 0;
+    L.p.slotB = 1;
+    L.p.slotC = 2;
+    if (L.kind == K_SPLITK) {
+      ctx->partials.reserve(size_t(L.p.splitk) * L.p.planeC * sizeof(float2));
+      L.p.partials = ctx->partials.as<float2>();
+    }
+    (void)eb;
+    run_step(precision, L, 1, s);
+    int32_t e = 0;
+    CUDA_OK(cudaMemcpyAsync(&e, ex + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    *c_exp2 = e;
+  });
+}
+
+tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                       int64_t batch, const double* weights, double* env_out, double* amp_out, void* stream) {
+  return guarded([&] {
+    (void)ctx; (void)plan; (void)opts; (void)bitstrings; (void)batch; (void)weights; (void)env_out; (void)amp_out;
+    (void)stream;
+    fail(TNC_E_UNSUPPORTED, "tnc_adjoint: not built yet");
+  });
+}
+
+tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,
+                            int32_t* kind, int32_t cap, int32_t* n) {
+  return guarded([&] {
+    if (!ctx || !n) fail(TNC_E_INVALID_ARG, "NULL argument");
+    ProfState& ps = ctx->prof;
+    if (!ps.valid) fail(TNC_E_INVALID_ARG, "no profiled call on this context");
+    *n = ps.n_steps;
+    if (cap < ps.n_steps || !ms || !launches || !flops || !bytes || !kind) fail(TNC_E_INVALID_ARG, "cap too small");
+    set_device(ctx);
+    CUDA_OK(cudaEventSynchronize(ps.call_end()));
+    for (int s = 0; s < ps.n_steps; ++s) {
+      double t = 0;
+      for (int w = 0; w < ps.waves; ++w) {
+        float x = 0;
+        CUDA_OK(cudaEventElapsedTime(&x, ps.at(w, s, 0), ps.at(w, s, 1)));
+        t += x;
+      }
+      ms[s] = t;
+      launches[s] = ps.waves;
+      flops[s] = ps.flops[s];
+      bytes[s] = ps.bytes[s];
+      kind[s] = ps.kind[s];
+    }
+    float tot = 0;
+    CUDA_OK(cudaEventElapsedTime(&tot, ps.call_start(), ps.call_end()));
+    ms[ps.n_steps] = tot;
+  });
+}

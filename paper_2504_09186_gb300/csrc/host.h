@@ -1,0 +1,158 @@
+// Host-side structures of the tensor-network library: circuit, network, plan and the
+// compiled per-step program that the device executor runs.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace tnc {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int32_t code;
+  std::string msg;
+};
+[[noreturn]] void fail(int32_t code, const std::string& msg);
+
+// ------------------------------------------------------------------ circuit
+struct Gate {
+  int arity;
+  int q[2];
+  cd m[16];  // row-major U[out, in], arity 1 uses m[0..3]
+};
+
+struct Circuit {
+  int n = 0;
+  std::vector<Gate> gates;
+};
+
+// ------------------------------------------------------------------ network
+// A wire segment of qubit `qubit` after `cut` gates on that qubit.
+enum EdgeKind { EDGE_INNER = 0, EDGE_INPUT = 1, EDGE_OUTPUT = 2 };
+struct Edge {
+  int qubit = -1;
+  int cut = -1;
+  int kind = EDGE_INNER;
+  bool open = false;  // output edge left open (a label of the result)
+};
+
+// A small tensor over edge labels; position p of `labels` is bit p of the flat index.
+struct SmallTensor {
+  std::vector<int> labels;
+  std::vector<cd> data;
+};
+
+// How a leaf was formed from gates: a list of gate indices whose per-gate tensors
+// (labels in the per-gate network) contract to the leaf.
+struct Leaf {
+  SmallTensor t;                 // labels include fixed legs (closed outputs); inputs removed
+  std::vector<int> gates;        // constituent gates
+};
+
+struct Network {
+  Circuit circ;
+  std::vector<Edge> edges;
+  std::vector<Leaf> leaves;
+  std::vector<int> open_qubits;  // ascending
+  std::vector<int> open_edge;    // per open qubit
+  std::vector<int> out_edge;     // per qubit: edge id of its output segment
+  // per-gate network (for the adjoint's chain rule): labels of gate g's tensor,
+  // [out legs..., in legs...] in the gate's qubit order
+  std::vector<std::vector<int>> gate_labels;
+};
+
+// Build the network; open_mask may be empty (all closed).
+void build_network(const Circuit& c, const std::vector<uint8_t>& open_mask, Network& net);
+
+// Small host contraction over labels (FP64), used for leaf formation and the adjoint's
+// per-gate chain rule.  Result labels: `out_labels` (must be exactly the free labels).
+SmallTensor small_contract(const SmallTensor& a, const SmallTensor& b, const std::vector<int>& out_labels);
+SmallTensor small_fix(const SmallTensor& a, int label, int value);
+
+// ------------------------------------------------------------------ plan
+struct PlanOpts {
+  uint64_t seed = 1;
+  int trials = 16;
+  int log2_cap = 26;
+  int slices_min = 0;
+  int slices_max = 64;
+  double temperature = 0.5;
+};
+
+// Kernel classes of a compiled step.
+enum StepKind {
+  K_GENERIC = 0,   // tiled gather contraction (SIMT FP32), any shape
+  K_SPLITK = 1,    // GEPDOT: same tiles, split over outer common indices + fixed-order reduce
+  K_CHAIN = 2,     // fused chain of small absorptions into one big tensor (Sec. IV)
+  K_TC = 3,        // tcgen05 complex GEMM (fp16/bf16 operands, FP32 in TMEM)
+};
+
+// Tile description of one pairwise contraction (all label ids are edge ids).
+struct TileSpec {
+  std::vector<int> Mt, Nt, Kt;   // tile labels
+  std::vector<int> Mo, No, Ko;   // outer labels (grid / loop)
+  int rm = 1, rn = 1;            // register micro-tile
+  int kgroups = 1;               // intra-CTA split of the K tile
+  int splitk = 1;                // CTAs along the outer K labels
+};
+
+struct ChainLink {
+  int b;                          // small operand tensor id
+  std::vector<int> c_labels;      // labels of the result after this link
+};
+
+struct Step {
+  int a, b, c;                    // tensor ids (A = the larger operand)
+  int kind = K_GENERIC;
+  TileSpec tile;
+  // chain steps: A absorbs b_0, b_1, ... in order; c = final result
+  std::vector<int> chain_b;       // operand ids of each link (first = b)
+  std::vector<int> chain_c;       // tensor ids produced by each link (last = c)
+  int chain_inner = 0;            // number of low positions kept on chip
+};
+
+struct TensorInfo {
+  std::vector<int> labels;        // storage order (position p = bit p)
+  int producer = -1;              // step index, -1 for leaves
+  int last_use = -1;              // step index of last consumer (root: n_steps)
+  int64_t offset = -1;            // element offset in the arena (per instance)
+  int leaf = -1;                  // leaf index for leaf tensors
+  bool on_chip = false;           // intermediate of a fused chain, never stored
+};
+
+struct Plan {
+  Network net;
+  PlanOpts opts;
+  std::vector<int> sliced;                 // edge ids; slice id bit t <-> sliced[t]
+  std::vector<std::pair<int, int>> tree;   // SSA pairs over tensor ids (leaves first)
+  std::vector<TensorInfo> tensors;         // leaves then intermediates (per-slice labels)
+  std::vector<Step> steps;                 // compiled program (may fuse tree steps)
+  int root = -1;
+  double log2_flops_slice = 0, log2_flops_total = 0, overhead = 1;
+  int max_log2 = 0;
+  int64_t arena_elems = 0;                 // per instance, in elements (complex)
+  // fixed-leg bookkeeping for the leaf gather: for each leaf, positions of sliced legs
+  // (with slice bit index) and closed output legs (with qubit)
+  struct LegFix {
+    int pos;     // position in the full leaf tensor
+    int kind;    // 0 = slice bit, 1 = output bit
+    int index;   // slice bit t, or qubit q
+  };
+  std::vector<std::vector<LegFix>> leaf_fix;
+  int n_gemm = 0, n_gepdot = 0, n_absorb = 0, n_fused = 0;
+  double narrow_max = 0;
+  bool fuse = true;
+};
+
+void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan);
+// (Re)compile the program of a plan whose tree and slices are set.
+void compile_plan(Plan& plan, bool fuse);
+
+void save_plan(const Plan& p, const std::string& path);
+void load_plan(const std::string& path, Plan& p);
+
+}  // namespace tnc

@@ -1,0 +1,478 @@
+// CUDA kernels of the contraction path (sm_103a).
+//
+//  k_generic      -- one pairwise contraction C = A * B (Sec. II-A: an M x K x N complex
+//                    GEMM over the common indices).  Each CTA owns a tile that is a set of
+//                    indices of each operand; because indices are binary, a tile is a
+//                    sub-tensor whose lowest positions are contiguous in memory, so tiles
+//                    are loaded in the operand's own order with vector loads and the
+//                    permutation happens in the shared-memory indexing (the permutation
+//                    folded into the kernel, Sec. V-A).  FP32 complex multiply-adds.
+//                    With splitk > 1 the CTAs split the outer common indices and write
+//                    FP32 partial sums (split-common TTGT for GEPDOT shapes, Sec. V-B).
+//  k_splitk_reduce -- sums the partials of a split step in a fixed order (blocked
+//                    summation, Eq. 3), scales and stores.
+//  k_leaf_gather  -- per instance (bitstring, slice): fixes sliced and closed-output legs
+//                    of every leaf (Sec. III-A slicing), converts and scales.
+//  k_root_accum   -- adds the root tensors of a wave into the FP64 amplitude accumulator
+//                    (sum over subtasks, Sec. III-A).
+//  k_maxabs       -- max |re|,|im| of a planar tensor (scale of tnc_contract's inputs).
+//
+// Scaling: every tensor carries an int32 exponent E (value = stored * 2^E) and the max
+// |re|,|im| of its stored values.  A producer scales its FP32 results by the exact power
+// of two that brings the bound 2^(nK+1) * max|A| * max|B| below 2^15, so fp16 storage
+// can neither overflow nor flush ordinary values to zero.
+#include "device.cuh"
+
+namespace tnc {
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Vec {
+  T v[V];
+};
+
+__device__ __forceinline__ uint32_t deposit_hi(uint32_t h, uint32_t mask, int run) {
+  uint32_t m = mask;
+  for (int i = 0; i < run; ++i) m &= m - 1;
+  uint32_t r = 0;
+  while (m) {
+    uint32_t low = m & (~m + 1u);
+    if (h & 1u) r |= low;
+    h >>= 1;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint32_t scatter_bits(uint32_t x, const int8_t* pos, int n) {
+  uint32_t r = 0;
+  for (int j = 0; j < n; ++j) r |= ((x >> j) & 1u) << pos[j];
+  return r;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+  atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+
+// Exponent shift for a product of tensors with stored max a, b over 2^nK terms.
+__device__ __forceinline__ int product_shift(float a, float b, int nK) {
+  if (!(a > 0.f) || !(b > 0.f)) return 0;
+  int ea, eb;
+  frexpf(a, &ea);  // a < 2^ea
+  frexpf(b, &eb);
+  return ea + eb + nK + 1 - 15;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void load_tile_v(const T* __restrict__ re, const T* __restrict__ im, int bits, int run,
+                                            const uint32_t* __restrict__ hi, float2* __restrict__ dst) {
+  const int n = 1 << bits;
+  const uint32_t lowmask = (1u << run) - 1u;
+  for (int t = threadIdx.x * V; t < n; t += kThreads * V) {
+    const uint32_t off = hi[t >> run] + (uint32_t(t) & lowmask);
+    const Vec<T, V> r = *reinterpret_cast<const Vec<T, V>*>(re + off);
+    const Vec<T, V> i = *reinterpret_cast<const Vec<T, V>*>(im + off);
+#pragma unroll
+    for (int v = 0; v < V; ++v) dst[t + v] = make_float2(Conv<T>::to_f(r.v[v]), Conv<T>::to_f(i.v[v]));
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_tile(const T* re, const T* im, int bits, int run, const uint32_t* hi, float2* dst) {
+  constexpr int VMAX = 16 / sizeof(T);
+  const int v = min(1 << run, VMAX);
+  if (v >= 8) load_tile_v<T, (VMAX >= 8 ? 8 : 1)>(re, im, bits, run, hi, dst);
+  else if (v == 4) load_tile_v<T, 4>(re, im, bits, run, hi, dst);
+  else if (v == 2) load_tile_v<T, 2>(re, im, bits, run, hi, dst);
+  else load_tile_v<T, 1>(re, im, bits, run, hi, dst);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ float store_tile_v(T* __restrict__ re, T* __restrict__ im, int bits, int run,
+                                              const uint32_t* __restrict__ hi, const float2* __restrict__ src, float scale) {
+  const int n = 1 << bits;
+  const uint32_t lowmask = (1u << run) - 1u;
+  float mx = 0.f;
+  for (int t = threadIdx.x * V; t < n; t += kThreads * V) {
+    const uint32_t off = hi[t >> run] + (uint32_t(t) & lowmask);
+    Vec<T, V> r, i;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float2 x = src[t + v];
+      r.v[v] = Conv<T>::from_f(x.x * scale);
+      i.v[v] = Conv<T>::from_f(x.y * scale);
+      mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(r.v[v])), fabsf(Conv<T>::to_f(i.v[v]))));
+    }
+    *reinterpret_cast<Vec<T, V>*>(re + off) = r;
+    *reinterpret_cast<Vec<T, V>*>(im + off) = i;
+  }
+  return mx;
+}
+
+template <typename T>
+__device__ __forceinline__ float store_tile(T* re, T* im, int bits, int run, const uint32_t* hi, const float2* src, float scale) {
+  constexpr int VMAX = 16 / sizeof(T);
+  const int v = min(1 << run, VMAX);
+  if (v >= 8) return store_tile_v<T, (VMAX >= 8 ? 8 : 1)>(re, im, bits, run, hi, src, scale);
+  if (v == 4) return store_tile_v<T, 4>(re, im, bits, run, hi, src, scale);
+  if (v == 2) return store_tile_v<T, 2>(re, im, bits, run, hi, src, scale);
+  return store_tile_v<T, 1>(re, im, bits, run, hi, src, scale);
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? red[l] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;  // valid in thread 0
+}
+
+template <typename T, int RM, int RN>
+__global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* As = reinterpret_cast<float2*>(smem);
+  float2* Bs = As + (1 << (p.mt + p.kt));
+  float2* R = As;  // reduction / staging after the K loop
+  uint32_t* hiA = reinterpret_cast<uint32_t*>(smem + p.smem_tables);
+  uint32_t* hiB = hiA + (1 << (p.mt + p.kt - p.runA));
+  uint32_t* hiC = hiB + (1 << (p.kt + p.nt - p.runB));
+  uint16_t* TAm = reinterpret_cast<uint16_t*>(hiC + (1 << (p.mt + p.nt - p.runC)));
+  uint16_t* TAk = TAm + (1 << p.mt);
+  uint16_t* TBk = TAk + (1 << p.kt);
+  uint16_t* TBn = TBk + (1 << p.kt);
+  uint16_t* TCm = TBn + (1 << p.nt);
+  uint16_t* TCn = TCm + (1 << p.mt);
+  float* red = reinterpret_cast<float*>(TCn + (1 << p.nt) + 2);  // 4-byte aligned (+2 pads)
+
+  const int tid = threadIdx.x;
+  const int64_t inst = blockIdx.z;
+  // outer coordinates of this tile
+  const uint32_t om = blockIdx.x & ((1u << p.n_om) - 1u);
+  const uint32_t on = p.n_om >= 32 ? 0u : (blockIdx.x >> p.n_om);
+  int64_t oA = 0, oB = 0, oC = 0;
+  for (int j = 0; j < p.n_om; ++j)
+    if ((om >> j) & 1u) {
+      oA += int64_t(1) << p.om_A[j];
+      oC += int64_t(1) << p.om_C[j];
+    }
+  for (int j = 0; j < p.n_on; ++j)
+    if ((on >> j) & 1u) {
+      oB += int64_t(1) << p.on_B[j];
+      oC += int64_t(1) << p.on_C[j];
+    }
+  // index tables
+  {
+    const int nhA = 1 << (p.mt + p.kt - p.runA), nhB = 1 << (p.kt + p.nt - p.runB), nhC = 1 << (p.mt + p.nt - p.runC);
+    for (int h = tid; h < nhA; h += kThreads) hiA[h] = deposit_hi(h, p.maskA, p.runA);
+    for (int h = tid; h < nhB; h += kThreads) hiB[h] = deposit_hi(h, p.maskB, p.runB);
+    for (int h = tid; h < nhC; h += kThreads) hiC[h] = deposit_hi(h, p.maskC, p.runC);
+    for (int x = tid; x < (1 << p.mt); x += kThreads) {
+      TAm[x] = (uint16_t)scatter_bits(x, p.pAm, p.mt);
+      TCm[x] = (uint16_t)scatter_bits(x, p.pCm, p.mt);
+    }
+    for (int x = tid; x < (1 << p.kt); x += kThreads) {
+      TAk[x] = (uint16_t)scatter_bits(x, p.pAk, p.kt);
+      TBk[x] = (uint16_t)scatter_bits(x, p.pBk, p.kt);
+    }
+    for (int x = tid; x < (1 << p.nt); x += kThreads) {
+      TBn[x] = (uint16_t)scatter_bits(x, p.pBn, p.nt);
+      TCn[x] = (uint16_t)scatter_bits(x, p.pCn, p.nt);
+    }
+  }
+  __syncthreads();
+
+  // thread -> micro-tile
+  const int TM = (1 << p.mt) / RM, TN = (1 << p.nt) / RN;
+  const int TPO = TM * TN;
+  const int grp = tid / TPO, r = tid % TPO;
+  const bool active = grp < p.kgroups;
+  const int mi = r % TM, ni = r / TM;
+  int am[RM], bn[RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) am[i] = active ? TAm[mi + i * TM] : 0;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) bn[j] = active ? TBn[ni + j * TN] : 0;
+  float2 acc[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  const T* Abase = reinterpret_cast<const T*>(p.A) + inst * p.strideA + oA;
+  const T* Bbase = reinterpret_cast<const T*>(p.B) + inst * p.strideB + oB;
+  const int64_t KO = int64_t(1) << p.n_ok;
+  const int64_t per = KO / p.splitk;
+  const int64_t k0 = int64_t(blockIdx.y) * per;
+  const int nk = 1 << p.kt;
+  for (int64_t ok = k0; ok < k0 + per; ++ok) {
+    int64_t okA = 0, okB = 0;
+    for (int j = 0; j < p.n_ok; ++j)
+      if ((ok >> j) & 1) {
+        okA += int64_t(1) << p.ok_A[j];
+        okB += int64_t(1) << p.ok_B[j];
+      }
+    load_tile<T>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
+    load_tile<T>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
+    __syncthreads();
+    if (active) {
+      for (int k = grp; k < nk; k += p.kgroups) {
+        const int ka = TAk[k], kb = TBk[k];
+        float2 a[RM], b[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = As[am[i] + ka];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) b[j] = Bs[kb + bn[j]];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  // reduce the K groups in a fixed order into the C-native staging tile
+  const int O = 1 << (p.mt + p.nt);
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) R[grp * O + TCm[mi + i * TM] + TCn[ni + j * TN]] = acc[i][j];
+  }
+  __syncthreads();
+  if (p.kgroups > 1) {
+    for (int o = tid; o < O; o += kThreads) {
+      float2 s = R[o];
+      for (int g = 1; g < p.kgroups; ++g) {
+        const float2 v = R[g * O + o];
+        s.x += v.x;
+        s.y += v.y;
+      }
+      R[o] = s;
+    }
+    __syncthreads();
+  }
+  if (p.splitk > 1) {
+    // FP32 partial sums, indexed by C's flat index
+    float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
+    const uint32_t lowmask = (1u << p.runC) - 1u;
+    for (int t = tid; t < O; t += kThreads) part[hiC[t >> p.runC] + (uint32_t(t) & lowmask)] = R[t];
+    return;
+  }
+  // scale, convert, store
+  const int64_t sb = inst * p.n_slots;
+  const int sh = product_shift(p.maxabs[sb + p.slotA], p.maxabs[sb + p.slotB], p.nK);
+  const float scale = ldexpf(1.f, -sh);
+  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+  const float mx = store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
+  const float bm = block_max(mx, red);
+  if (tid == 0) {
+    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
+    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+  }
+}
+
+// Fixed-order sum of split-K partials (blocked summation, Eq. 3), then scale and store.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
+  __shared__ float red[32];
+  const int64_t inst = blockIdx.z;
+  const int64_t idx = int64_t(blockIdx.x) * kThreads + threadIdx.x;
+  const int64_t sb = inst * p.n_slots;
+  const int sh = product_shift(p.maxabs[sb + p.slotA], p.maxabs[sb + p.slotB], p.nK);
+  const float scale = ldexpf(1.f, -sh);
+  float mx = 0.f;
+  if (idx < p.planeC) {
+    const float2* part = p.partials + inst * p.splitk * p.planeC + idx;
+    float2 s = part[0];
+    for (int k = 1; k < p.splitk; ++k) {
+      const float2 v = part[int64_t(k) * p.planeC];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC;
+    const T re = Conv<T>::from_f(s.x * scale), im = Conv<T>::from_f(s.y * scale);
+    Cre[idx] = re;
+    Cre[p.planeC + idx] = im;
+    mx = fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im)));
+  }
+  const float bm = block_max(mx, red);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
+    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+  }
+}
+
+// One warp per (leaf, instance).  Leaves have at most 4 free legs after fixing.
+template <typename T>
+__global__ void k_leaf_gather(const LeafDesc* __restrict__ leaves, const double2* __restrict__ src, T* arena,
+                              int64_t inst_stride, const int64_t* __restrict__ inst_slice,
+                              const int32_t* __restrict__ inst_row, const uint8_t* __restrict__ bits, int n_qubits,
+                              float* maxabs, int32_t* exps, int n_slots, int64_t inst_base) {
+  const LeafDesc d = leaves[blockIdx.x];
+  const int64_t inst = blockIdx.y;
+  const int64_t slice = inst_slice[inst_base + inst];
+  const int row = inst_row[inst_base + inst];
+  const int lane = threadIdx.x;
+  const int n = 1 << d.rank;
+  double2 v = make_double2(0.0, 0.0);
+  if (lane < n) {
+    // place the free index bits and the fixed values into the full leaf index
+    int64_t full = 0;
+    int fb = 0, f = 0;
+    for (int pos = 0; pos < d.rank_full; ++pos) {
+      int bit;
+      if (f < d.nfix && d.fix_pos[f] == pos) {
+        bit = d.fix_kind[f] == 0 ? int((slice >> d.fix_idx[f]) & 1) : int(bits[int64_t(row) * n_qubits + d.fix_idx[f]]);
+        ++f;
+      } else {
+        bit = (lane >> fb) & 1;
+        ++fb;
+      }
+      full |= int64_t(bit) << pos;
+    }
+    v = src[d.src + full];
+  }
+  double m = fmax(fabs(v.x), fabs(v.y));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  if (m > 0.0) {
+    frexp(m, &e);  // m < 2^e: stored values below 1
+  }
+  const double s = ldexp(1.0, -e);
+  T* dst = arena + inst * inst_stride + d.dst;
+  float mx = 0.f;
+  if (lane < n) {
+    const T re = Conv<T>::from_f((float)(v.x * s)), im = Conv<T>::from_f((float)(v.y * s));
+    dst[lane] = re;
+    dst[n + lane] = im;
+    mx = fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    maxabs[inst * n_slots + d.slot] = mx;
+    exps[inst * n_slots + d.slot] = e;
+  }
+}
+
+// acc[row, o] += sum over the segment's instances (in order) of root[o] * 2^E.
+template <typename T>
+__global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                             const int8_t* __restrict__ open_pos, int n_open, const RootSeg* __restrict__ segs,
+                             const int32_t* __restrict__ exps, int n_slots, int root_slot, double2* acc) {
+  const int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n_out = int64_t(1) << n_open;
+  if (o >= n_out) return;
+  const RootSeg s = segs[blockIdx.y];
+  int64_t idx = 0;
+  for (int j = 0; j < n_open; ++j) idx |= ((o >> (n_open - 1 - j)) & 1) << open_pos[j];
+  double re = 0.0, im = 0.0;
+  for (int i = s.begin; i < s.end; ++i) {
+    const T* root = arena + int64_t(i) * inst_stride + root_off;
+    const double sc = ldexp(1.0, exps[int64_t(i) * n_slots + root_slot]);
+    re += (double)Conv<T>::to_f(root[idx]) * sc;
+    im += (double)Conv<T>::to_f(root[plane + idx]) * sc;
+  }
+  double2* a = acc + int64_t(s.row) * n_out + o;
+  a->x += re;
+  a->y += im;
+}
+
+template <typename T>
+__global__ void k_maxabs(const T* __restrict__ x, int64_t n, float* out) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = fmaxf(m, fabsf(Conv<T>::to_f(x[i])));
+  const float bm = block_max(m, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(out, bm);
+}
+
+// ------------------------------------------------------------------ launch helpers
+template <typename T>
+using GenKernel = void (*)(const GenParams);
+
+template <typename T>
+GenKernel<T> pick_generic(int rm, int rn) {
+#define TNC_CASE(a, b) \
+  if (rm == a && rn == b) return k_generic<T, a, b>;
+  TNC_CASE(1, 1) TNC_CASE(1, 2) TNC_CASE(1, 4) TNC_CASE(2, 1) TNC_CASE(2, 2) TNC_CASE(2, 4)
+  TNC_CASE(4, 1) TNC_CASE(4, 2) TNC_CASE(4, 4)
+#undef TNC_CASE
+  return nullptr;
+}
+
+cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, dim3 grid, size_t smem, cudaStream_t s) {
+  void (*k)(const GenParams) = nullptr;
+  if (precision == 0) k = pick_generic<float>(rm, rn);
+  else if (precision == 1) k = pick_generic<__half>(rm, rn);
+  else k = pick_generic<__nv_bfloat16>(rm, rn);
+  if (!k) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_inst, cudaStream_t s) {
+  dim3 grid((unsigned)((p.planeC + kThreads - 1) / kThreads), 1, (unsigned)n_inst);
+  if (precision == 0) k_splitk_reduce<float><<<grid, kThreads, 0, s>>>(p);
+  else if (precision == 1) k_splitk_reduce<__half><<<grid, kThreads, 0, s>>>(p);
+  else k_splitk_reduce<__nv_bfloat16><<<grid, kThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leaves, const double2* src, void* arena,
+                               int64_t inst_stride, const int64_t* inst_slice, const int32_t* inst_row,
+                               const uint8_t* bits, int n_qubits, float* maxabs, int32_t* exps, int n_slots,
+                               int64_t inst_base, int64_t n_inst, cudaStream_t s) {
+  dim3 grid((unsigned)n_leaves, (unsigned)n_inst);
+  if (precision == 0)
+    k_leaf_gather<float><<<grid, 32, 0, s>>>(leaves, src, (float*)arena, inst_stride, inst_slice, inst_row, bits,
+                                             n_qubits, maxabs, exps, n_slots, inst_base);
+  else if (precision == 1)
+    k_leaf_gather<__half><<<grid, 32, 0, s>>>(leaves, src, (__half*)arena, inst_stride, inst_slice, inst_row, bits,
+                                              n_qubits, maxabs, exps, n_slots, inst_base);
+  else
+    k_leaf_gather<__nv_bfloat16><<<grid, 32, 0, s>>>(leaves, src, (__nv_bfloat16*)arena, inst_stride, inst_slice,
+                                                     inst_row, bits, n_qubits, maxabs, exps, n_slots, inst_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                              const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
+                              const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s) {
+  const int64_t n_out = int64_t(1) << n_open;
+  dim3 grid((unsigned)((n_out + 255) / 256), (unsigned)n_segs);
+  if (precision == 0)
+    k_root_accum<float><<<grid, 256, 0, s>>>((const float*)arena, inst_stride, root_off, plane, open_pos, n_open, segs,
+                                             exps, n_slots, root_slot, acc);
+  else if (precision == 1)
+    k_root_accum<__half><<<grid, 256, 0, s>>>((const __half*)arena, inst_stride, root_off, plane, open_pos, n_open,
+                                              segs, exps, n_slots, root_slot, acc);
+  else
+    k_root_accum<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)arena, inst_stride, root_off, plane,
+                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  if (blocks < 1) blocks = 1;
+  if (precision == 0) k_maxabs<float><<<blocks, 256, 0, s>>>((const float*)x, n, out);
+  else if (precision == 1) k_maxabs<__half><<<blocks, 256, 0, s>>>((const __half*)x, n, out);
+  else k_maxabs<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)x, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tnc

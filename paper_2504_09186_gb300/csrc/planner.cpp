@@ -1,0 +1,248 @@
+// Seeded greedy contraction order and greedy slicing.
+//
+// Order: repeatedly contract the pair of tensors sharing an index that minimises
+// size(out) - size(a) - size(b) (Sec. II-A: each contraction eliminates the shared
+// edges), perturbed by seeded Gumbel noise so that independent trials explore
+// different trees; the trial with the smallest total cost is kept.
+//
+// Slicing (Sec. II-A; Sec. III-A, Eq. 1): while some intermediate exceeds 2^cap entries,
+// slice the index, among those of the oversized intermediates, whose index overhead
+// O(a) = 2 C_a / C is smallest, C being the cost of one subtask before slicing a and
+// C_a the cost after.  Indices of the lowest overhead are added afterwards until the
+// requested minimum count is reached.  Cost = complex multiply-adds of one subtask,
+// sum over steps of 2^|labels(a) U labels(b)|.
+#include <algorithm>
+#include <cmath>
+#include <limits>
+#include <map>
+#include <set>
+
+#include "host.h"
+
+namespace tnc {
+
+namespace {
+
+struct Rng {
+  uint64_t s;
+  uint64_t next() {  // splitmix64
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double gumbel() { return -std::log(-std::log(uniform())); }
+};
+
+using LabelSet = std::vector<int>;  // sorted
+
+LabelSet sym_diff(const LabelSet& a, const LabelSet& b) {
+  LabelSet r;
+  std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+LabelSet set_union(const LabelSet& a, const LabelSet& b) {
+  LabelSet r;
+  std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+size_t count_not_in(const LabelSet& a, const std::vector<char>& sliced) {
+  size_t n = 0;
+  for (int x : a) n += sliced[x] ? 0 : 1;
+  return n;
+}
+
+struct Tree {
+  std::vector<std::pair<int, int>> pairs;
+  std::vector<LabelSet> sets;  // leaves then intermediates
+};
+
+// Greedy order.  Open labels occur in one tensor only, so the symmetric difference keeps them.
+Tree greedy_tree(const std::vector<LabelSet>& leaves, int n_edges, Rng& rng, double temperature) {
+  Tree t;
+  t.sets = leaves;
+  std::vector<char> alive(leaves.size(), 1);
+  std::vector<std::vector<int>> owners(n_edges);
+  for (size_t i = 0; i < leaves.size(); ++i)
+    for (int e : leaves[i]) owners[e].push_back((int)i);
+  size_t n_alive = leaves.size();
+  while (n_alive > 1) {
+    // candidate pairs sharing an edge
+    std::vector<std::pair<int, int>> cand;
+    for (int e = 0; e < n_edges; ++e) {
+      auto& ow = owners[e];
+      if (ow.size() == 2) cand.emplace_back(std::min(ow[0], ow[1]), std::max(ow[0], ow[1]));
+    }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    int bi = -1, bj = -1;
+    if (cand.empty()) {
+      // disconnected: outer product of the two smallest live tensors
+      std::vector<std::pair<size_t, int>> live;
+      for (size_t i = 0; i < t.sets.size(); ++i)
+        if (alive[i]) live.emplace_back(t.sets[i].size(), (int)i);
+      std::sort(live.begin(), live.end());
+      bi = std::min(live[0].second, live[1].second);
+      bj = std::max(live[0].second, live[1].second);
+    } else {
+      double best = std::numeric_limits<double>::infinity();
+      for (auto& p : cand) {
+        const LabelSet& A = t.sets[p.first];
+        const LabelSet& B = t.sets[p.second];
+        LabelSet o = sym_diff(A, B);
+        double s = std::ldexp(1.0, (int)o.size()) - std::ldexp(1.0, (int)A.size()) - std::ldexp(1.0, (int)B.size());
+        double score = (s >= 0 ? 1.0 : -1.0) * std::log2(1.0 + std::fabs(s));
+        if (temperature > 0) score -= temperature * rng.gumbel();
+        if (score < best) {
+          best = score;
+          bi = p.first;
+          bj = p.second;
+        }
+      }
+    }
+    LabelSet o = sym_diff(t.sets[bi], t.sets[bj]);
+    int id = (int)t.sets.size();
+    for (int e : t.sets[bi]) {
+      auto& ow = owners[e];
+      ow.erase(std::remove(ow.begin(), ow.end(), bi), ow.end());
+    }
+    for (int e : t.sets[bj]) {
+      auto& ow = owners[e];
+      ow.erase(std::remove(ow.begin(), ow.end(), bj), ow.end());
+    }
+    for (int e : o) owners[e].push_back(id);
+    alive[bi] = alive[bj] = 0;
+    alive.push_back(1);
+    t.sets.push_back(o);
+    t.pairs.emplace_back(bi, bj);
+    --n_alive;
+  }
+  return t;
+}
+
+double tree_cost(const Tree& t, const std::vector<char>& sliced) {
+  double c = 0;
+  for (auto& p : t.pairs) {
+    LabelSet u = set_union(t.sets[p.first], t.sets[p.second]);
+    c += std::ldexp(1.0, (int)count_not_in(u, sliced));
+  }
+  return c;
+}
+
+int tree_max(const Tree& t, const std::vector<char>& sliced) {
+  int m = 0;
+  for (auto& s : t.sets) m = std::max(m, (int)count_not_in(s, sliced));
+  return m;
+}
+
+}  // namespace
+
+void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
+  if (o.trials < 1 || o.log2_cap < 1 || o.log2_cap > 34 || o.slices_min < 0 || o.slices_max < 0)
+    fail(1, "plan_greedy: bad options");
+  const int n_edges = (int)net.edges.size();
+  // contraction-level labels of each leaf: closed outputs are fixed per bitstring
+  std::vector<LabelSet> leaves;
+  for (const Leaf& l : net.leaves) {
+    LabelSet s;
+    for (int e : l.t.labels)
+      if (!(net.edges[e].kind == EDGE_OUTPUT && !net.edges[e].open)) s.push_back(e);
+    std::sort(s.begin(), s.end());
+    leaves.push_back(s);
+  }
+  if (leaves.empty()) fail(5, "plan_greedy: empty network");
+  std::vector<char> is_open(n_edges, 0);
+  for (int e : net.open_edge) is_open[e] = 1;
+
+  struct Best {
+    Tree tree;
+    std::vector<int> sliced;
+    double total = std::numeric_limits<double>::infinity();
+    double per_slice = 0, unsliced = 0;
+    bool within_max = false;
+  } best;
+
+  for (int trial = 0; trial < o.trials; ++trial) {
+    Rng rng{o.seed * 0x100000001B3ull + 0x9E3779B97F4A7C15ull * (uint64_t)(trial + 1)};
+    Tree t = leaves.size() == 1 ? Tree{{}, leaves} : greedy_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature);
+    std::vector<char> sl(n_edges, 0);
+    std::vector<int> sliced;
+    const double c0 = tree_cost(t, sl);
+    double cur = c0;
+    auto try_slice = [&](bool only_oversized) -> int {
+      // candidates: labels of oversized tensors (or every inner label)
+      std::set<int> cand;
+      if (only_oversized) {
+        for (auto& s : t.sets)
+          if ((int)count_not_in(s, sl) > o.log2_cap)
+            for (int e : s)
+              if (!sl[e] && !is_open[e]) cand.insert(e);
+      } else {
+        for (auto& s : t.sets)
+          for (int e : s)
+            if (!sl[e] && !is_open[e]) cand.insert(e);
+      }
+      int pick = -1;
+      double pick_cost = 0;
+      int pick_over = -1;
+      for (int e : cand) {
+        sl[e] = 1;
+        double ce = tree_cost(t, sl);
+        int over = 0;
+        for (auto& s : t.sets) over += (int)count_not_in(s, sl) > o.log2_cap;
+        sl[e] = 0;
+        // index overhead O(e) = 2 C_e / C (Eq. 1); ties: fewer oversized tensors left
+        double ov = 2.0 * ce / cur;
+        if (pick < 0 || ov < pick_cost * (1 - 1e-12) || (std::fabs(ov - pick_cost) <= 1e-12 * pick_cost && over < pick_over)) {
+          pick = e;
+          pick_cost = ov;
+          pick_over = over;
+        }
+      }
+      return pick;
+    };
+    bool ok = true;
+    while (tree_max(t, sl) > o.log2_cap) {
+      int e = try_slice(true);
+      if (e < 0) { ok = false; break; }
+      sl[e] = 1;
+      sliced.push_back(e);
+      cur = tree_cost(t, sl);
+    }
+    if (!ok) continue;
+    while ((int)sliced.size() < o.slices_min) {
+      int e = try_slice(false);
+      if (e < 0) break;
+      sl[e] = 1;
+      sliced.push_back(e);
+      cur = tree_cost(t, sl);
+    }
+    const double total = std::ldexp(cur, (int)sliced.size());
+    const bool within = (int)sliced.size() <= o.slices_max;
+    bool better;
+    if (within != best.within_max) better = within;
+    else better = total < best.total * (1 - 1e-12);
+    if (better) {
+      best.tree = t;
+      best.sliced = sliced;
+      best.total = total;
+      best.per_slice = cur;
+      best.unsliced = c0;
+      best.within_max = within;
+    }
+  }
+  if (!std::isfinite(best.total)) fail(5, "plan_greedy: no trial met the size cap");
+
+  plan = Plan();
+  plan.net = net;
+  plan.opts = o;
+  plan.sliced = best.sliced;
+  plan.tree = best.tree.pairs;
+  plan.log2_flops_slice = std::log2(best.per_slice);
+  plan.log2_flops_total = std::log2(best.total);
+  plan.overhead = best.total / best.unsliced;
+  compile_plan(plan, true);
+}
+
+}  // namespace tnc

@@ -1,0 +1,321 @@
+"""ctypes binding of the C boundary (include/tnc.h).  Argument marshalling only: every
+step of the contraction path runs in the library's CUDA kernels.
+
+The functions keep the C names (`tnc_amplitudes`, `tnc_contract`, ...).  The classes
+`Plan` and `Context` wrap the handles for convenience.  The library is loaded from this
+package directory; when it is missing every call raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtnc.so")
+
+TNC_OK = 0
+TNC_E_INVALID_ARG = 1
+TNC_E_OOM = 2
+TNC_E_CUDA = 3
+TNC_E_TIMEOUT = 4
+TNC_E_PLAN = 5
+TNC_E_UNSUPPORTED = 6
+TNC_E_IO = 7
+
+TNC_C64 = 0
+TNC_CHALF = 1
+TNC_CBF16 = 2
+PRECISIONS = {"c64": TNC_C64, "chalf": TNC_CHALF, "cbf16": TNC_CBF16}
+
+
+class TncError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tnc status {status}: {msg}")
+        self.status = status
+
+
+class tnc_plan_opts(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64),
+        ("trials", C.c_int32),
+        ("log2_cap", C.c_int32),
+        ("slices_min", C.c_int32),
+        ("slices_max", C.c_int32),
+        ("temperature", C.c_double),
+    ]
+
+
+class tnc_plan_info(C.Structure):
+    _fields_ = [
+        ("log2_flops_per_slice", C.c_double),
+        ("log2_total_flops", C.c_double),
+        ("slicing_overhead", C.c_double),
+        ("max_log2_size", C.c_int32),
+        ("n_sliced", C.c_int32),
+        ("n_steps", C.c_int32),
+        ("n_leaves", C.c_int32),
+        ("n_open", C.c_int32),
+        ("n_kernels", C.c_int32),
+        ("n_gemm", C.c_int32),
+        ("n_gepdot", C.c_int32),
+        ("n_absorb", C.c_int32),
+        ("n_fused", C.c_int32),
+        ("narrow_max", C.c_double),
+    ]
+
+
+class tnc_exec_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32),
+        ("wave", C.c_int32),
+        ("use_graph", C.c_int32),
+        ("fuse", C.c_int32),
+        ("profile", C.c_int32),
+        ("reserved", C.c_int32 * 3),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtnc.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the contraction path has no CPU fallback)"
+        )
+    lib = C.CDLL(path)
+    vp, i32, i64, u8p = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_uint8)
+    sig = {
+        "tnc_circuit_from_gates": [i32, i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(vp)],
+        "tnc_network_build": [vp, u8p, C.POINTER(vp)],
+        "tnc_plan_greedy": [vp, C.POINTER(tnc_plan_opts), C.POINTER(vp)],
+        "tnc_plan_get_info": [vp, C.POINTER(tnc_plan_info)],
+        "tnc_plan_sliced_cuts": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32],
+        "tnc_plan_open_qubits": [vp, C.POINTER(C.c_int32), i32],
+        "tnc_plan_describe": [vp, C.c_char_p, i64, C.POINTER(C.c_int64)],
+        "tnc_plan_save": [vp, C.c_char_p],
+        "tnc_plan_load": [C.c_char_p, C.POINTER(vp)],
+        "tnc_context_create": [i32, C.POINTER(vp)],
+        "tnc_amplitudes": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, i64, i64, vp, vp],
+        "tnc_adjoint": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, vp, vp, vp, vp],
+        "tnc_contract": [vp, i32, vp, i32, C.POINTER(C.c_int32), vp, i32, C.POINTER(C.c_int32), vp, i32,
+                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
+        "tnc_sync": [vp],
+        "tnc_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                             C.POINTER(C.c_double), C.POINTER(C.c_int32), i32, C.POINTER(C.c_int32)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    for name in ("tnc_circuit_destroy", "tnc_network_destroy", "tnc_plan_destroy", "tnc_context_destroy"):
+        f = getattr(lib, name)
+        f.argtypes = [vp]
+        f.restype = None
+    lib.tnc_last_error.restype = C.c_char_p
+    lib.tnc_last_error.argtypes = []
+    lib.tnc_version.restype = C.c_char_p
+    lib.tnc_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TNC_OK:
+        raise TncError(status, _lib.tnc_last_error().decode())
+
+
+def _i32p(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+# ------------------------------------------------------------------------- raw calls
+def tnc_circuit_from_gates(n_qubits: int, arity: np.ndarray, qubits: np.ndarray, matrices: np.ndarray):
+    lib = load_library()
+    arity = np.ascontiguousarray(arity, dtype=np.int32)
+    qubits = np.ascontiguousarray(qubits, dtype=np.int32).reshape(-1)
+    matrices = np.ascontiguousarray(matrices, dtype=np.float64).reshape(-1)
+    h = C.c_void_p()
+    _check(lib.tnc_circuit_from_gates(n_qubits, len(arity), _i32p(arity), _i32p(qubits),
+                                      matrices.ctypes.data_as(C.POINTER(C.c_double)), C.byref(h)))
+    return h
+
+
+def tnc_network_build(circuit, open_mask: Optional[np.ndarray]):
+    lib = load_library()
+    h = C.c_void_p()
+    if open_mask is None:
+        _check(lib.tnc_network_build(circuit, None, C.byref(h)))
+    else:
+        m = np.ascontiguousarray(open_mask, dtype=np.uint8)
+        _check(lib.tnc_network_build(circuit, m.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(h)))
+    return h
+
+
+def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5):
+    lib = load_library()
+    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature)
+    h = C.c_void_p()
+    _check(lib.tnc_plan_greedy(network, C.byref(o), C.byref(h)))
+    return h
+
+
+# ------------------------------------------------------------------------- wrappers
+class Plan:
+    """A contraction plan (tree + slices + compiled steps) of a circuit's network."""
+
+    def __init__(self, handle, n_qubits: int):
+        self.h = handle
+        self.n_qubits = n_qubits
+
+    @classmethod
+    def greedy(cls, circuit, open_qubits: Sequence[int] = (), seed: int = 1, trials: int = 16, log2_cap: int = 26,
+               slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5) -> "Plan":
+        """Plan for an `inputs.Circuit` (gate list) with the given open output qubits."""
+        lib = load_library()
+        arity, qubits, mats = circuit.gate_array()
+        ch = tnc_circuit_from_gates(circuit.n_qubits, arity, qubits, mats)
+        try:
+            mask = np.zeros(circuit.n_qubits, dtype=np.uint8)
+            mask[list(open_qubits)] = 1
+            nh = tnc_network_build(ch, mask)
+            try:
+                ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature)
+            finally:
+                lib.tnc_network_destroy(nh)
+        finally:
+            lib.tnc_circuit_destroy(ch)
+        return cls(ph, circuit.n_qubits)
+
+    @classmethod
+    def load(cls, path: str) -> "Plan":
+        lib = load_library()
+        h = C.c_void_p()
+        _check(lib.tnc_plan_load(path.encode(), C.byref(h)))
+        p = cls(h, 0)
+        p.n_qubits = p.describe()["n_qubits"]
+        return p
+
+    def save(self, path: str):
+        _check(load_library().tnc_plan_save(self.h, path.encode()))
+
+    def info(self) -> dict:
+        i = tnc_plan_info()
+        _check(load_library().tnc_plan_get_info(self.h, C.byref(i)))
+        return {name: getattr(i, name) for name, _ in tnc_plan_info._fields_}
+
+    def sliced_cuts(self):
+        n = self.info()["n_sliced"]
+        q = np.zeros(max(n, 1), dtype=np.int32)
+        c = np.zeros(max(n, 1), dtype=np.int32)
+        _check(load_library().tnc_plan_sliced_cuts(self.h, _i32p(q), _i32p(c), max(n, 1)))
+        return [(int(q[t]), int(c[t])) for t in range(n)]
+
+    def open_qubits(self):
+        n = self.info()["n_open"]
+        q = np.zeros(max(n, 1), dtype=np.int32)
+        _check(load_library().tnc_plan_open_qubits(self.h, _i32p(q), max(n, 1)))
+        return [int(x) for x in q[:n]]
+
+    def describe(self) -> dict:
+        lib = load_library()
+        n = C.c_int64()
+        _check(lib.tnc_plan_describe(self.h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib.tnc_plan_describe(self.h, buf, n.value, C.byref(n)))
+        return json.loads(buf.value.decode())
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tnc_plan_destroy(self.h)
+            self.h = None
+
+
+class Context:
+    """A device context (one GPU, one stream, scratch)."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        self.h = C.c_void_p()
+        _check(lib.tnc_context_create(device, C.byref(self.h)))
+        self.device = device
+
+    def sync(self):
+        _check(_lib.tnc_sync(self.h))
+
+    def amplitudes(self, plan: Plan, bitstrings: Optional[np.ndarray], precision: str = "c64",
+                   slice_begin: int = 0, slice_count: Optional[int] = None, wave: int = 0, out=None,
+                   stream: int = 0, profile: bool = False, fuse: bool = True, use_graph: bool = False) -> np.ndarray:
+        """Amplitudes of every row x every open-qubit assignment, summed over the slices.
+
+        `out` may be a host numpy complex128 array or a torch complex128 CUDA tensor of
+        shape (batch, 2^n_open); a new host array is returned when it is None."""
+        lib = load_library()
+        info = plan.info()
+        if slice_count is None:
+            slice_count = (1 << info["n_sliced"]) - slice_begin
+        if bitstrings is None:
+            batch = 1
+            bp = None
+        else:
+            bs = np.ascontiguousarray(bitstrings, dtype=np.uint8)
+            if bs.ndim == 1:
+                bs = bs[None, :]
+            batch = bs.shape[0]
+            bp = bs.ctypes.data_as(C.POINTER(C.c_uint8))
+        n_out = 1 << info["n_open"]
+        if out is None:
+            out = np.zeros((batch, n_out), dtype=np.complex128)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave,
+                             int(use_graph), int(fuse), int(profile))
+        _check(lib.tnc_amplitudes(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count,
+                                  C.c_void_p(ptr), C.c_void_p(stream)))
+        return out
+
+    def profile_read(self, cap: int = 4096) -> dict:
+        """Per-step device times of the last profiled amplitudes call (see tnc_profile_read)."""
+        ms = np.zeros(cap + 1)
+        launches = np.zeros(cap, dtype=np.int32)
+        flops = np.zeros(cap)
+        byts = np.zeros(cap)
+        kind = np.zeros(cap, dtype=np.int32)
+        n = C.c_int32()
+        dp = C.POINTER(C.c_double)
+        _check(_lib.tnc_profile_read(self.h, ms.ctypes.data_as(dp), _i32p(launches), flops.ctypes.data_as(dp),
+                                     byts.ctypes.data_as(dp), _i32p(kind), cap, C.byref(n)))
+        k = n.value
+        return {"ms": ms[:k], "total_ms": float(ms[k]), "launches": launches[:k], "flops": flops[:k],
+                "bytes": byts[:k], "kind": kind[:k]}
+
+    def contract(self, precision: str, a, labels_a, b, labels_b, c, labels_c, stream: int = 0) -> int:
+        """C = A * B on planar device tensors (torch tensors of the storage dtype, 2*2^rank
+        entries).  Returns C's exponent: the result is c * 2^exponent."""
+        lib = load_library()
+        la = np.ascontiguousarray(labels_a, dtype=np.int32)
+        lb = np.ascontiguousarray(labels_b, dtype=np.int32)
+        lc = np.ascontiguousarray(labels_c, dtype=np.int32)
+        e = C.c_int32()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.tnc_contract(self.h, prec, C.c_void_p(a.data_ptr()), len(la), _i32p(la), C.c_void_p(b.data_ptr()),
+                                len(lb), _i32p(lb), C.c_void_p(c.data_ptr()), len(lc), _i32p(lc), C.byref(e),
+                                C.c_void_p(stream)))
+        return int(e.value)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tnc_context_destroy(self.h)
+            self.h = None
+
+
+def version() -> str:
+    return load_library().tnc_version().decode()

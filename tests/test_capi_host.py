@@ -1,0 +1,125 @@
+"""CPU tests of the C boundary: exported symbols, argument checks, planner invariants."""
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from inputs import grid_circuit, subcube_spec
+from paper_2504_09186_gb300 import tnc as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return T.load_library()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tnc_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert T.version().startswith("tnc-gb300")
+
+
+def test_invalid_arguments_are_reported(lib):
+    arity = np.array([3], dtype=np.int32)
+    with pytest.raises(T.TncError) as e:
+        T.tnc_circuit_from_gates(2, arity, np.zeros(2, np.int32), np.zeros(32))
+    assert e.value.status == T.TNC_E_INVALID_ARG and "arity" in str(e.value)
+    with pytest.raises(T.TncError) as e:
+        T.tnc_circuit_from_gates(2, np.array([2], np.int32), np.array([1, 1], np.int32), np.zeros(32))
+    assert "repeated qubit" in str(e.value)
+    with pytest.raises(T.TncError):
+        T.tnc_circuit_from_gates(0, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    c = grid_circuit(2, 2, 2, seed=1)
+    with pytest.raises(T.TncError) as e:
+        T.Plan.greedy(c, trials=0)
+    assert e.value.status == T.TNC_E_INVALID_ARG
+
+
+def _recount(desc):
+    """Independent recount of one slice's cost and largest tensor from the JSON plan."""
+    tensors = desc["tensors"]
+    cost = 0.0
+    biggest = max(len(t["labels"]) for t in tensors)
+    for a, b in desc["tree"]:
+        u = set(tensors[a]["labels"]) | set(tensors[b]["labels"])
+        cost += 2.0 ** len(u)
+    return cost, biggest
+
+
+@pytest.mark.parametrize("rows,cols,cycles,n_open,cap,smin", [(3, 4, 8, 0, 26, 0), (4, 4, 10, 4, 12, 3), (3, 3, 6, 2, 8, 0)])
+def test_plan_invariants(rows, cols, cycles, n_open, cap, smin):
+    c = grid_circuit(rows, cols, cycles, seed=1)
+    n = c.n_qubits
+    _, open_q = subcube_spec(n, n_open, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=cap, slices_min=smin)
+    info = p.info()
+    d = p.describe()
+    L = len(d["leaves"])
+    # a valid binary tree covering every leaf exactly once, SSA order
+    used = set()
+    for s, (a, b) in enumerate(d["tree"]):
+        assert a < L + s and b < L + s and a != b
+        assert a not in used and b not in used
+        used |= {a, b}
+    assert used == set(range(L + len(d["tree"]) - 1))
+    # each leaf is a group of gates, every gate in exactly one leaf
+    gates = sorted(g for lf in d["leaves"] for g in lf["gates"])
+    assert gates == list(range(len(c.gates)))
+    # recount of cost and size
+    cost, biggest = _recount(d)
+    assert math.isclose(math.log2(cost), info["log2_flops_per_slice"], rel_tol=1e-12)
+    assert biggest == info["max_log2_size"] <= cap
+    assert info["n_sliced"] >= smin
+    # the root carries exactly the open output legs
+    root = d["tensors"][d["root"]]["labels"]
+    assert len(root) == n_open
+    # sliced edges are inner wire segments
+    for e in d["sliced"]:
+        q, cut, kind, is_open = d["edges"][e]
+        assert kind == 0 and not is_open
+    assert p.open_qubits() == list(open_q)
+
+
+def test_same_seed_same_plan_and_roundtrip(tmp_path):
+    c = grid_circuit(4, 4, 10, seed=1)
+    _, open_q = subcube_spec(16, 3, seed=2)
+    p1 = T.Plan.greedy(c, open_qubits=open_q, seed=5, trials=6, log2_cap=11)
+    p2 = T.Plan.greedy(c, open_qubits=open_q, seed=5, trials=6, log2_cap=11)
+    assert p1.describe() == p2.describe()
+    path = str(tmp_path / "plan.bin")
+    p1.save(path)
+    p3 = T.Plan.load(path)
+    d1, d3 = p1.describe(), p3.describe()
+    assert d1["tree"] == d3["tree"] and d1["sliced"] == d3["sliced"] and d1["steps"] == d3["steps"]
+    with open(path, "r+b") as f:
+        f.seek(20)
+        f.write(b"\xff\xff\xff\xff")
+    with pytest.raises(T.TncError):
+        T.Plan.load(path)
+
+
+def test_slicing_overhead_is_eq1_product():
+    # overhead reported = 2^s * C_sliced / C_unsliced; each sliced index had O(a) >= 1
+    c = grid_circuit(4, 4, 10, seed=1)
+    p = T.Plan.greedy(c, seed=3, trials=4, log2_cap=10)
+    info = p.info()
+    assert info["n_sliced"] > 0
+    assert info["slicing_overhead"] >= 1.0 - 1e-12
+    assert math.isclose(info["log2_total_flops"], info["log2_flops_per_slice"] + info["n_sliced"], rel_tol=1e-12)

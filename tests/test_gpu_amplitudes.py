@@ -1,0 +1,107 @@
+"""GPU parity of amplitudes through the C boundary against the FP64 oracle.
+
+Tolerances (norm-wise relative error over the batch): complex64 path 1e-5; complex-half
+1e-2; complex-bf16 4e-2.  The bf16 figure follows from its unit roundoff 2^-9 ~ 2e-3 per
+stored tensor: a root-to-leaf path of the greedy trees here has up to ~20 stored tensors,
+and independent roundings add in quadrature, ~sqrt(20) * 2e-3 ~ 1e-2, times a margin of
+4 for the worst amplitudes of a Porter-Thomas batch.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from inputs import grid_circuit, random_bitstrings, subcube_bitstrings, subcube_spec
+from inputs.circuits import custom_circuit, SQRT_X, fsim
+from oracle import metrics
+from oracle import statevector as sv
+from paper_2504_09186_gb300 import tnc as T
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "chalf": 1e-2, "cbf16": 4e-2}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return T.Context(0)
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf", "cbf16"])
+def test_tiny_config_batch_of_bitstrings(ctx, precision):
+    # 12-qubit 3x4 grid, 8 cycles, unsliced, 64 seeded bitstrings
+    c = grid_circuit(3, 4, 8, seed=1)
+    bs = random_bitstrings(c.n_qubits, 64, seed=2)
+    p = T.Plan.greedy(c, open_qubits=[], seed=3, trials=8, log2_cap=26)
+    assert p.info()["n_sliced"] == 0
+    got = ctx.amplitudes(p, bs, precision)[:, 0]
+    ref = sv.circuit_amplitudes(c, bs)
+    err = metrics.rel_err_norm(got, ref)
+    assert err <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf"])
+def test_all_open_is_the_state(ctx, precision):
+    c = grid_circuit(3, 3, 6, seed=4, fsim_mode="uniform")
+    n = c.n_qubits
+    p = T.Plan.greedy(c, open_qubits=list(range(n)), seed=1, trials=4, log2_cap=26)
+    got = ctx.amplitudes(p, None, precision)[0]
+    ref = sv.final_state(c).reshape(-1)
+    assert metrics.rel_err_norm(got, ref) <= TOL[precision]
+
+
+def test_sliced_plan_each_slice_and_sum(ctx):
+    c = grid_circuit(4, 4, 10, seed=1)
+    n = c.n_qubits
+    fixed, open_q = subcube_spec(n, 4, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=9, slices_min=3)
+    cuts = p.sliced_cuts()
+    s = len(cuts)
+    assert s >= 3
+    bs = subcube_bitstrings(fixed, open_q)
+    total = 0
+    for sid in range(1 << s):
+        assign = {cut: (sid >> t) & 1 for t, cut in enumerate(cuts)}
+        ref = sv.circuit_amplitudes(c, bs, assign)
+        got = ctx.amplitudes(p, fixed[None, :], "c64", slice_begin=sid, slice_count=1)[0]
+        assert metrics.rel_err_norm(got, ref) <= 1e-5 or np.linalg.norm(ref) < 1e-12
+        total = total + ref
+    full = ctx.amplitudes(p, fixed[None, :], "c64")[0]
+    assert metrics.rel_err_norm(full, sv.circuit_amplitudes(c, bs)) <= 1e-5
+    assert np.allclose(total, sv.circuit_amplitudes(c, bs), atol=1e-12)
+
+
+def test_wave_sizes_are_deterministic(ctx):
+    c = grid_circuit(4, 4, 10, seed=1)
+    fixed, open_q = subcube_spec(16, 3, seed=2)
+    bs = np.stack([fixed, 1 - fixed, fixed])
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=9, slices_min=3)
+    outs = [ctx.amplitudes(p, bs, "c64", wave=w) for w in (0, 1, 3, 5)]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])  # same fixed summation order, bit-identical
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(1 - fixed, open_q))
+    assert metrics.rel_err_norm(outs[0][1], ref) <= 1e-5
+
+
+def test_half_precision_scaling_keeps_small_amplitudes(ctx):
+    # 20 qubits: amplitudes ~2^-10, intermediates far below fp16's normal range without scaling
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=3)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=16, slices_min=2)
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    for prec in ("c64", "chalf", "cbf16"):
+        got = ctx.amplitudes(p, fixed[None, :], prec)[0]
+        assert metrics.rel_err_norm(got, ref) <= TOL[prec], prec
+
+
+def test_edge_cases(ctx):
+    # a qubit with no gates, a single 2-qubit gate, and an empty slice range is rejected
+    c = custom_circuit(3, [((0,), SQRT_X), ((0, 1), fsim(0.3, 0.2))])
+    bs = np.array(list(itertools.product((0, 1), repeat=3)), dtype=np.uint8)
+    p = T.Plan.greedy(c, open_qubits=[], trials=2)
+    got = ctx.amplitudes(p, bs, "c64")[:, 0]
+    assert metrics.rel_err_norm(got, sv.circuit_amplitudes(c, bs)) <= 1e-6
+    with pytest.raises(T.TncError):
+        ctx.amplitudes(p, bs, "c64", slice_begin=0, slice_count=2)
+    with pytest.raises(T.TncError):
+        ctx.amplitudes(p, bs * 2, "c64")
