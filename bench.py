@@ -94,13 +94,15 @@ class ClockSampler:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", "200", "-f", self.tmp.name], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # first sample lands before the timed region starts
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
         if self.proc is not None:
+            time.sleep(0.3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -208,7 +210,9 @@ def run_ours(args):
     info = plan.info()
     n_slices = 1 << info["n_sliced"]
     ctx = T.Context(local)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library enqueues on it and the CUDA events below time it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     n_out = 1 << info["n_open"]
     out = torch.zeros((1, n_out), dtype=torch.complex128, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)

@@ -42,6 +42,13 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         os.path.join(ROOT, "include", "tnc.h")
     ]
     hdr_time = _newest(headers)
+    stamp = os.path.join(BUILD, "defines.txt")
+    defines = os.environ.get("TNC_NVCC_DEFINES", "")
+    if not os.path.exists(stamp) or open(stamp).read() != defines:
+        os.makedirs(BUILD, exist_ok=True)
+        with open(stamp, "w") as f:
+            f.write(defines)
+    hdr_time = max(hdr_time, os.path.getmtime(stamp))
     inc = ["-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-I" + os.path.join(cuda, "include")]
     jobs_list = []
     objs = []
@@ -51,8 +58,9 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time, os.path.getmtime(__file__)):
             continue
         if src.endswith(".cu"):
+            extra = os.environ.get("TNC_NVCC_DEFINES", "").split()
             cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-Xptxas", "-O3", *inc, "-c", src, "-o", obj]
+                   "-Xptxas", "-O3", *extra, *inc, "-c", src, "-o", obj]
         else:
             cmd = ["g++", "-O2", "-g", "-fPIC", "-std=c++17", "-Wall", "-Wno-unused-function", *inc, "-c", src, "-o", obj]
         jobs_list.append(cmd)

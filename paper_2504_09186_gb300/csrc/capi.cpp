@@ -221,7 +221,7 @@ tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
            ",\"Kt\":" + jlist(t.Kt) + ",\"Nt\":" + jlist(t.Nt) + ",\"Mo\":" + jlist(t.Mo) + ",\"Ko\":" + jlist(t.Ko) +
            ",\"No\":" + jlist(t.No) + ",\"splitk\":" + std::to_string(t.splitk) + ",\"rm\":" + std::to_string(t.rm) +
            ",\"rn\":" + std::to_string(t.rn) + ",\"kgroups\":" + std::to_string(t.kgroups) +
-           ",\"chain_b\":" + jlist(S.chain_b) + ",\"chain_c\":" + jlist(S.chain_c) + "}";
+           ",\"tc\":" + std::to_string(S.tc_ok ? 1 : 0) + ",\"chain_b\":" + jlist(S.chain_b) + ",\"chain_c\":" + jlist(S.chain_c) + "}";
     }
     char num[64];
     std::snprintf(num, sizeof(num), "%.17g", P.log2_flops_slice);

@@ -169,7 +169,52 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   return t;
 }
 
+// Tensor-core tile: 7 M labels, 7 N labels, 6 K labels whose first three are at
+// positions 0..2 of both operands.  Returns false if the step does not qualify.
+bool choose_tc_tile(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
+                    const std::vector<int>& k3, TileSpec& t) {
+  std::vector<int> M, K, N;
+  for (int x : la) (contains(lb, x) ? K : M).push_back(x);
+  for (int x : lb)
+    if (!contains(la, x)) N.push_back(x);
+  if (M.size() < 7 || N.size() < 7 || K.size() < 6 || k3.size() != 3) return false;
+  for (int j = 0; j < 3; ++j)
+    if (la.size() < 3 || lb.size() < 3 || la[j] != k3[j] || lb[j] != k3[j]) return false;
+  t = TileSpec();
+  t.Kt = k3;
+  for (int x : la) {  // further K labels by A position
+    if ((int)t.Kt.size() >= 6) break;
+    if (contains(K, x) && !contains(t.Kt, x)) t.Kt.push_back(x);
+  }
+  for (int x : lc) {  // C's lowest labels first, so stores are runs
+    if (contains(M, x) && t.Mt.size() < 7) t.Mt.push_back(x);
+    else if (contains(N, x) && t.Nt.size() < 7) t.Nt.push_back(x);
+    if (t.Mt.size() + t.Nt.size() >= 3) break;
+  }
+  for (int x : la)
+    if (contains(M, x) && !contains(t.Mt, x) && t.Mt.size() < 7) t.Mt.push_back(x);
+  for (int x : lb)
+    if (contains(N, x) && !contains(t.Nt, x) && t.Nt.size() < 7) t.Nt.push_back(x);
+  // C's three lowest positions must be tile labels
+  for (int j = 0; j < 3; ++j)
+    if (!contains(t.Mt, lc[j]) && !contains(t.Nt, lc[j])) return false;
+  for (int x : M)
+    if (!contains(t.Mt, x)) t.Mo.push_back(x);
+  for (int x : K)
+    if (!contains(t.Kt, x)) t.Ko.push_back(x);
+  for (int x : N)
+    if (!contains(t.Nt, x)) t.No.push_back(x);
+  if (t.Mo.size() + t.No.size() > 30 || t.Ko.size() > 24) return false;
+  return true;
+}
+
 }  // namespace
+
+bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t) {
+  if (la.size() < 3 || lb.size() < 3) return false;
+  std::vector<int> k3(la.begin(), la.begin() + 3);
+  return choose_tc_tile(la, lb, lc, k3, t);
+}
 
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind) {
@@ -204,6 +249,30 @@ void compile_plan(Plan& plan, bool fuse) {
     }
     plan.tensors.push_back(ti);
   }
+  // tensor-core candidates (decided on label sets, before layouts): both operands are
+  // intermediates and M, N >= 2^7, K >= 2^6.  Their three canonical common labels (the
+  // smallest ids) must sit at positions 0..2 of both operands.
+  const int n_leaves = L;
+  std::vector<std::vector<int>> sets(L);
+  for (int i = 0; i < L; ++i) {
+    sets[i] = plan.tensors[i].labels;
+    std::sort(sets[i].begin(), sets[i].end());
+  }
+  std::vector<int> consumer(L + plan.tree.size(), -1);
+  std::vector<std::vector<int>> k3_of_step(plan.tree.size());
+  for (size_t s = 0; s < plan.tree.size(); ++s) {
+    const auto& A = sets[plan.tree[s].first];
+    const auto& B = sets[plan.tree[s].second];
+    std::vector<int> K, U;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(K));
+    std::set_symmetric_difference(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(U));
+    sets.push_back(U);
+    consumer[plan.tree[s].first] = (int)s;
+    consumer[plan.tree[s].second] = (int)s;
+    const int m = (int)A.size() - (int)K.size(), n = (int)B.size() - (int)K.size();
+    const bool inter = plan.tree[s].first >= n_leaves && plan.tree[s].second >= n_leaves;
+    if (inter && m >= 7 && n >= 7 && K.size() >= 6) k3_of_step[s] = {K[0], K[1], K[2]};
+  }
   // intermediates
   plan.steps.clear();
   plan.n_gemm = plan.n_gepdot = plan.n_absorb = plan.n_fused = 0;
@@ -215,6 +284,16 @@ void compile_plan(Plan& plan, bool fuse) {
     if (plan.tensors[b].labels.size() > plan.tensors[a].labels.size()) std::swap(a, b);
     TensorInfo ci;
     ci.labels = output_layout(plan.tensors[a].labels, plan.tensors[b].labels);
+    const int cid = (int)plan.tensors.size();
+    if (consumer[cid] >= 0 && !k3_of_step[consumer[cid]].empty()) {
+      // put the consumer's canonical common labels at positions 0..2, in order
+      const auto& k3 = k3_of_step[consumer[cid]];
+      std::vector<int> rest;
+      for (int x : ci.labels)
+        if (!contains(k3, x)) rest.push_back(x);
+      ci.labels = k3;
+      ci.labels.insert(ci.labels.end(), rest.begin(), rest.end());
+    }
     ci.producer = (int)s;
     plan.max_log2 = std::max(plan.max_log2, (int)ci.labels.size());
     Step st;
@@ -234,6 +313,7 @@ void compile_plan(Plan& plan, bool fuse) {
     int kind = K_GENERIC;
     st.tile = choose_tile(la, lb, lc, 1, kind);
     st.kind = kind;
+    st.tc_ok = !k3_of_step[s].empty() && choose_tc_tile(la, lb, lc, k3_of_step[s], st.tc_tile);
     int nk = 0;
     for (int x : la) nk += contains(lb, x);
     int nm = (int)la.size() - nk, nn = (int)lb.size() - nk;

@@ -66,6 +66,28 @@ struct LeafDesc {
   int16_t fix_idx[8];   // slice bit index or qubit
 };
 
+// Tensor-core complex GEMM step (tc_gemm.cu): 128 x 128 x 64 tiles.
+struct TcParams {
+  const void* A;
+  const void* B;
+  void* C;
+  int64_t strideA, strideB, strideC;
+  int64_t planeA, planeB, planeC;
+  int8_t pAm[7], pBn[7];     // operand positions of the canonical tile m / n bits
+  int8_t pAk[3], pBk[3];     // operand positions of k bits 3..5 (bits 0..2 are positions 0..2)
+  int8_t pCm[7], pCn[7];     // C-tile-native bit of canonical m / n bit
+  uint32_t maskC;            // C positions of the tile (m and n labels)
+  int32_t runC;
+  int32_t n_om, n_on, n_ok;
+  int8_t om_A[kMaxOuter], om_C[kMaxOuter], on_B[kMaxOuter], on_C[kMaxOuter], ok_A[kMaxOuter], ok_B[kMaxOuter];
+  int32_t nK;
+  int32_t bf16;              // operand format: 0 fp16, 1 bf16
+  float* maxabs;
+  int32_t* exps;
+  int32_t n_slots, slotA, slotB, slotC;
+  int32_t* status;           // TNC_E_TIMEOUT on a bounded wait that ran out
+};
+
 // A run of consecutive instances of one wave that belong to the same bitstring row.
 struct RootSeg {
   int32_t row;

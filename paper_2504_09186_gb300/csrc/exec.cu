@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -29,8 +31,10 @@ cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_str
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s);
 cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
+bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t);
 
 #define CUDA_OK(expr)                                                                             \
   do {                                                                                            \
@@ -84,12 +88,54 @@ static int low_run(uint32_t mask) {
 }
 
 struct StepLaunch {
-  int kind;  // K_GENERIC or K_SPLITK
+  int kind;  // K_GENERIC, K_SPLITK or K_TC
   GenParams p;
+  TcParams tp;
   dim3 grid;
   size_t smem;
   int rm, rn;
 };
+
+// Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.
+static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<int>& la, const std::vector<int>& lb,
+                           const std::vector<int>& lc, int precision) {
+  TcParams& q = L.tp;
+  std::memset(&q, 0, sizeof(q));
+  if (t.Mt.size() != 7 || t.Nt.size() != 7 || t.Kt.size() != 6) fail(TNC_E_PLAN, "bad tensor-core tile");
+  for (int j = 0; j < 3; ++j)
+    if (pos_of(la, t.Kt[j]) != j || pos_of(lb, t.Kt[j]) != j) fail(TNC_E_PLAN, "tensor-core operands not K-major");
+  uint32_t maskC = 0;
+  for (int x : t.Mt) maskC |= 1u << pos_of(lc, x);
+  for (int x : t.Nt) maskC |= 1u << pos_of(lc, x);
+  q.maskC = maskC;
+  q.runC = low_run(maskC);
+  if (q.runC < 3) fail(TNC_E_PLAN, "tensor-core output run too short");
+  for (int j = 0; j < 7; ++j) {
+    q.pAm[j] = (int8_t)pos_of(la, t.Mt[j]);
+    q.pBn[j] = (int8_t)pos_of(lb, t.Nt[j]);
+    q.pCm[j] = (int8_t)rank_in_mask(maskC, pos_of(lc, t.Mt[j]));
+    q.pCn[j] = (int8_t)rank_in_mask(maskC, pos_of(lc, t.Nt[j]));
+  }
+  for (int j = 0; j < 3; ++j) {
+    q.pAk[j] = (int8_t)pos_of(la, t.Kt[3 + j]);
+    q.pBk[j] = (int8_t)pos_of(lb, t.Kt[3 + j]);
+  }
+  q.n_om = (int)t.Mo.size();
+  q.n_on = (int)t.No.size();
+  q.n_ok = (int)t.Ko.size();
+  if (q.n_om > kMaxOuter || q.n_on > kMaxOuter || q.n_ok > kMaxOuter) fail(TNC_E_UNSUPPORTED, "too many outer labels");
+  for (int j = 0; j < q.n_om; ++j) q.om_A[j] = (int8_t)pos_of(la, t.Mo[j]), q.om_C[j] = (int8_t)pos_of(lc, t.Mo[j]);
+  for (int j = 0; j < q.n_on; ++j) q.on_B[j] = (int8_t)pos_of(lb, t.No[j]), q.on_C[j] = (int8_t)pos_of(lc, t.No[j]);
+  for (int j = 0; j < q.n_ok; ++j) q.ok_A[j] = (int8_t)pos_of(la, t.Ko[j]), q.ok_B[j] = (int8_t)pos_of(lb, t.Ko[j]);
+  q.planeA = int64_t(1) << la.size();
+  q.planeB = int64_t(1) << lb.size();
+  q.planeC = int64_t(1) << lc.size();
+  q.nK = (int)t.Kt.size() + q.n_ok;
+  q.bf16 = precision == TNC_CBF16 ? 1 : 0;
+  L.kind = K_TC;
+  L.grid = dim3(1u << (q.n_om + q.n_on), 1, 1);
+  L.smem = 0;
+}
 
 static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int>& la, const std::vector<int>& lb,
                               const std::vector<int>& lc) {
@@ -209,7 +255,8 @@ struct tnc_context_s {
   int id = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials;
+  DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status;
+  bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
   ProfState prof;
   ~tnc_context_s() {
     bits.release();
@@ -219,6 +266,7 @@ struct tnc_context_s {
     acc.release();
     scratch.release();
     partials.release();
+    status.release();
   }
 };
 
@@ -277,6 +325,23 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     const auto& lb = P.tensors[st.b].labels;
     const auto& lc = P.tensors[st.c].labels;
     StepLaunch L = make_launch(st.tile, st.kind, la, lb, lc);
+    if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
+      make_tc_launch(L, st.tc_tile, la, lb, lc, precision);
+      TcParams& q = L.tp;
+      q.A = prog->arena.as<char>() + P.tensors[st.a].offset * eb;
+      q.B = prog->arena.as<char>() + P.tensors[st.b].offset * eb;
+      q.C = prog->arena.as<char>() + P.tensors[st.c].offset * eb;
+      q.strideA = q.strideB = q.strideC = prog->inst_stride;
+      q.maxabs = prog->maxabs.as<float>();
+      q.exps = prog->exps.as<int32_t>();
+      q.n_slots = prog->n_slots;
+      q.slotA = st.a;
+      q.slotB = st.b;
+      q.slotC = st.c;
+      q.status = ctx->status.as<int32_t>();
+      prog->steps.push_back(L);
+      continue;
+    }
     L.p.A = prog->arena.as<char>() + P.tensors[st.a].offset * eb;
     L.p.B = prog->arena.as<char>() + P.tensors[st.b].offset * eb;
     L.p.C = prog->arena.as<char>() + P.tensors[st.c].offset * eb;
@@ -309,6 +374,23 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
 
 static void set_device(tnc_context_s* ctx) { CUDA_OK(cudaSetDevice(ctx->device)); }
 
+// Reads and clears the device status word (after the stream has drained).
+static void check_status(tnc_context_s* ctx) {
+  int32_t st = 0;
+  CUDA_OK(cudaMemcpy(&st, ctx->status.p, sizeof(st), cudaMemcpyDeviceToHost));
+  if (std::getenv("TNC_DEBUG_STATUS")) {
+    int32_t w[16];
+    CUDA_OK(cudaMemcpy(w, ctx->status.p, sizeof(w), cudaMemcpyDeviceToHost));
+    std::fprintf(stderr, "tnc status words:");
+    for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %d", w[i]);
+    std::fprintf(stderr, "\n");
+  }
+  if (st != 0) {
+    CUDA_OK(cudaMemset(ctx->status.p, 0, sizeof(st)));
+    fail(TNC_E_TIMEOUT, "a device-side bounded wait ran out (status " + std::to_string(st) + ")");
+  }
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -323,6 +405,10 @@ static bool is_device_ptr(const void* p) {
 static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s) {
   StepLaunch L = L0;
   L.grid.z = (unsigned)n_inst;
+  if (L.kind == K_TC) {
+    CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
+    return;
+  }
   CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
   if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
 }
@@ -351,6 +437,15 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
       delete c;
       fail(TNC_E_CUDA, std::string("stream creation failed: ") + cudaGetErrorString(e));
     }
+    try {
+      c->status.reserve(64);
+      CUDA_OK(cudaMemset(c->status.p, 0, 64));
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    const char* env = std::getenv("TNC_NO_TC");
+    c->no_tc = env && env[0] == '1';
     *out = c;
   });
 }
@@ -370,6 +465,7 @@ tnc_status tnc_sync(tnc_context ctx) {
     if (!ctx) fail(TNC_E_INVALID_ARG, "NULL context");
     set_device(ctx);
     CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    check_status(ctx);
   });
 }
 
@@ -505,6 +601,7 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
     } else {
       CUDA_OK(cudaMemcpyAsync(out, ctx->acc.p, out_bytes, cudaMemcpyDeviceToHost, s));
       CUDA_OK(cudaStreamSynchronize(s));
+      check_status(ctx);
     }
   });
 }
@@ -559,11 +656,27 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       ctx->partials.reserve(size_t(L.p.splitk) * L.p.planeC * sizeof(float2));
       L.p.partials = ctx->partials.as<float2>();
     }
+    TileSpec tct;
+    if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct)) {
+      make_tc_launch(L, tct, la, lb, lc, precision);
+      TcParams& q = L.tp;
+      q.A = a;
+      q.B = b;
+      q.C = c;
+      q.maxabs = mx;
+      q.exps = ex;
+      q.n_slots = 3;
+      q.slotA = 0;
+      q.slotB = 1;
+      q.slotC = 2;
+      q.status = ctx->status.as<int32_t>();
+    }
     (void)eb;
     run_step(precision, L, 1, s);
     int32_t e = 0;
     CUDA_OK(cudaMemcpyAsync(&e, ex + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
+    check_status(ctx);
     *c_exp2 = e;
   });
 }

@@ -109,6 +109,10 @@ struct Step {
   int a, b, c;                    // tensor ids (A = the larger operand)
   int kind = K_GENERIC;
   TileSpec tile;
+  // tensor-core variant for fp16/bf16 storage: 128 x 128 x 64 tiles; tc_tile.Kt[0..2]
+  // sit at positions 0..2 of both operands
+  bool tc_ok = false;
+  TileSpec tc_tile;
   // chain steps: A absorbs b_0, b_1, ... in order; c = final result
   std::vector<int> chain_b;       // operand ids of each link (first = b)
   std::vector<int> chain_c;       // tensor ids produced by each link (last = c)

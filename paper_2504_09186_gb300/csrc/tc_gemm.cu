@@ -1,0 +1,439 @@
+// Tensor-core complex GEMM step for fp16 / bf16 storage (sm_103a, tcgen05 + TMEM).
+//
+// One pairwise contraction C = A * B (Sec. II-A: an M x K x N complex GEMM over the
+// common indices) whose operands are large enough for 128 x 128 x 64 tiles.  Tiles are
+// sets of indices, as in the SIMT kernel: the compiler places three common indices at
+// the lowest positions of both operands, so every 8 consecutive entries of an operand
+// are 8 consecutive k of one row and a row's 64-wide K tile is gathered with 16-byte
+// cp.async copies straight into the 128B-swizzled K-major layout the tensor core reads;
+// the other tile indices are scattered over the operands and handled by per-row address
+// tables -- the permutation costs no extra pass (Sec. V-A: permutation inside the
+// contraction kernel).
+//
+// Complex product with planar operands: per 16-wide k step, four MMAs into two FP32
+// accumulators in TMEM,
+//   Dr += Ar Br,  Dr += (-Ai) Bi  (negate-A bit),  Di += Ar Bi,  Di += Ai Br.
+// One thread issues the MMAs; tcgen05.commit signals a per-stage mbarrier so loaders
+// know when a stage may be overwritten (3-stage pipeline).  Every wait is bounded by
+// the global timer; on timeout the kernel records TNC_E_TIMEOUT in a status word, stops
+// issuing work and still releases its TMEM.  The epilogue reads TMEM (tcgen05.ld),
+// applies the exact power-of-two scale, converts, stages the tile in shared memory in
+// C's own order and writes contiguous runs.
+#include "device.cuh"
+
+namespace tnc {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
+constexpr int TC_THREADS = 256;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;          // one plane of one operand tile (16 KB)
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;          // Ar, Ai, Br, Bi
+constexpr int TC_PIPE_BYTES = TC_STAGES * TC_STAGE_BYTES;  // 192 KB
+constexpr int TC_TMEM_COLS = 2 * TC_BN;                    // Dr, Di
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;             // 2 s bound on any wait
+
+#ifndef TNC_TC_SELFCHECK
+#define TNC_TC_SELFCHECK 0
+#endif
+// Self-check build (-DTNC_TC_SELFCHECK=1): every address is validated before use; the
+// first violation is recorded in status[1..7] (code, block, thread, detail...) and the
+// access is skipped instead of faulting.
+__device__ __forceinline__ bool tc_check(bool good, int32_t* status, int code, int64_t d0, int64_t d1) {
+#if TNC_TC_SELFCHECK
+  if (!good) {
+    if (atomicCAS(&status[1], 0, code) == 0) {
+      status[2] = (int32_t)blockIdx.x;
+      status[3] = (int32_t)threadIdx.x;
+      status[4] = (int32_t)(d0 & 0xffffffff);
+      status[5] = (int32_t)(d0 >> 32);
+      status[6] = (int32_t)(d1 & 0xffffffff);
+      status[7] = (int32_t)(d1 >> 32);
+    }
+    status[0] = 9;
+  }
+  return good;
+#else
+  (void)status; (void)code; (void)d0; (void)d1;
+  return true;
+#endif
+}
+
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false (and records a timeout) if the phase did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > TC_WAIT_NS) {
+      atomicExch(status, 4);  // TNC_E_TIMEOUT
+      return false;
+    }
+  }
+  return true;
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFFu);    // start address
+  d |= uint64_t(1) << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;           // stride byte offset: next 8-row group
+  d |= uint64_t(1) << 46;                   // descriptor version (tcgen05)
+  d |= uint64_t(2) << 61;                   // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, K-major A and B, M = 128, N = 128.
+__device__ __forceinline__ uint32_t instr_desc(int bf16, int neg_a) {
+  uint32_t d = 0;
+  d |= 1u << 4;                              // D format F32
+  d |= uint32_t(bf16) << 7;                  // A format (0 F16, 1 BF16)
+  d |= uint32_t(bf16) << 10;                 // B format
+  d |= uint32_t(neg_a) << 13;                // negate A
+  d |= uint32_t(TC_BN >> 3) << 17;           // N
+  d |= uint32_t(TC_BM >> 4) << 24;           // M
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // 1024-byte aligned pipeline buffers (the 128B swizzle pattern is address based)
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint32_t* depA = reinterpret_cast<uint32_t*>(smem + TC_PIPE_BYTES);   // [128] row offsets in A
+  uint32_t* depB = depA + TC_BM;                                         // [128] row offsets in B
+  uint32_t* hiC = depB + TC_BN;                                          // [2^(14 - runC)]
+  const int nhC = 1 << (14 - p.runC);
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);               // [128]
+  uint16_t* TCn = TCm + TC_BM;                                           // [128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(TCn + TC_BN + 8) & ~uintptr_t(7));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t inst = blockIdx.z;
+  // grid.x enumerates (on fastest, om): CTAs sharing an A row tile run together
+  const uint32_t on = blockIdx.x & ((1u << p.n_on) - 1u);
+  const uint32_t om = p.n_on >= 31 ? 0u : (blockIdx.x >> p.n_on);
+  int64_t oA = 0, oB = 0, oC = 0;
+  for (int j = 0; j < p.n_om; ++j)
+    if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j], oC += int64_t(1) << p.om_C[j];
+  for (int j = 0; j < p.n_on; ++j)
+    if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j], oC += int64_t(1) << p.on_C[j];
+
+  // tables
+  for (int r = tid; r < TC_BM; r += TC_THREADS) {
+    uint32_t a = 0, b = 0, cm = 0, cn = 0;
+    for (int j = 0; j < 7; ++j) {
+      if ((r >> j) & 1) {
+        a |= 1u << p.pAm[j];
+        b |= 1u << p.pBn[j];
+        cm |= 1u << p.pCm[j];
+        cn |= 1u << p.pCn[j];
+      }
+    }
+    depA[r] = a;
+    depB[r] = b;
+    TCm[r] = (uint16_t)cm;
+    TCn[r] = (uint16_t)cn;
+  }
+  for (int h = tid; h < nhC; h += TC_THREADS) {
+    uint32_t m = p.maskC;
+    for (int i = 0; i < p.runC; ++i) m &= m - 1;
+    uint32_t r = 0, x = (uint32_t)h;
+    while (m) {
+      const uint32_t low = m & (~m + 1u);
+      if (x & 1u) r |= low;
+      x >>= 1;
+      m &= m - 1;
+    }
+    hiC[h] = r;
+  }
+  if (tid == 0) {
+    for (int s = 0; s <= TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+#if TNC_TC_SELFCHECK
+  if (blockIdx.x == 0 && tid == 0) {
+    p.status[8] = (int32_t)tmem;
+    p.status[9] = (int32_t)smem_u32(smem);
+    p.status[10] = (int32_t)smem_u32(smem_raw);
+    p.status[11] = (int32_t)smem_u32(bars);
+  }
+  tc_check((smem_u32(smem) & 1023u) == 0, p.status, 11, smem_u32(smem), 0);
+  tc_check((tmem >> 16) == 0 && (tmem & 0xFFFFu) + TC_TMEM_COLS <= 512, p.status, 12, tmem, 0);
+  tc_check((smem_u32(bars) & 7u) == 0, p.status, 18, smem_u32(bars), 0);
+#endif
+
+  const T* Ab = reinterpret_cast<const T*>(p.A) + inst * p.strideA + oA;
+  const T* Bb = reinterpret_cast<const T*>(p.B) + inst * p.strideB + oB;
+  const int n_iter = 1 << p.n_ok;
+  const uint32_t sbase = smem_u32(smem);
+
+  // per stage: 128 rows x 8 chunks of 16 B per plane = 1024 (row, chunk) pairs, 4 per
+  // thread, each copied for the 4 planes Ar, Ai, Br, Bi
+  constexpr int kPairsPerThread = TC_BM * (TC_BK / 8) / TC_THREADS;
+  static_assert(kPairsPerThread * TC_THREADS == TC_BM * (TC_BK / 8) && TC_BM == TC_BN, "tile / thread mismatch");
+  auto load_stage = [&](int it, int buf) {
+    int64_t okA = 0, okB = 0;
+    for (int j = 0; j < p.n_ok; ++j)
+      if ((it >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+    const uint32_t st = sbase + buf * TC_STAGE_BYTES;
+#pragma unroll
+    for (int i = 0; i < kPairsPerThread; ++i) {
+      const int idx = tid + i * TC_THREADS;  // 0..1023: (row, chunk) of one operand tile
+      const int row = idx >> 3, c = idx & 7;
+      uint32_t kA = 0, kB = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        if ((c >> j) & 1) kA |= 1u << p.pAk[j], kB |= 1u << p.pBk[j];
+      const uint32_t so = (row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4);
+      const T* ga = Ab + okA + depA[row] + kA;
+      const T* gb = Bb + okB + depB[row] + kB;
+#if TNC_TC_SELFCHECK
+      {
+        const int64_t ea = (ga - reinterpret_cast<const T*>(p.A)) - inst * p.strideA;
+        const int64_t eb = (gb - reinterpret_cast<const T*>(p.B)) - inst * p.strideB;
+        const bool good = ((reinterpret_cast<uintptr_t>(ga) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(gb) & 15u) == 0) &&
+                          ea >= 0 && ea + 8 <= p.planeA && eb >= 0 && eb + 8 <= p.planeB &&
+                          ((st + so) & 15u) == 0 && (st + so + 3 * TC_TILE_BYTES + 16) <= sbase + TC_PIPE_BYTES;
+        if (!tc_check(good, p.status, 13, ea, eb)) continue;
+      }
+#endif
+      cp_async16(st + 0 * TC_TILE_BYTES + so, ga);
+      cp_async16(st + 1 * TC_TILE_BYTES + so, ga + p.planeA);
+      cp_async16(st + 2 * TC_TILE_BYTES + so, gb);
+      cp_async16(st + 3 * TC_TILE_BYTES + so, gb + p.planeB);
+    }
+  };
+
+  bool ok = true;
+  const uint32_t id_pos = instr_desc(p.bf16, 0), id_neg = instr_desc(p.bf16, 1);
+  for (int s = 0; s < TC_STAGES - 1; ++s) {
+    if (s < n_iter) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int it = 0; it < n_iter && ok; ++it) {
+    const int nxt = it + TC_STAGES - 1;
+    if (nxt < n_iter) {
+      const int buf = nxt % TC_STAGES;
+      if (nxt >= TC_STAGES) ok = mbar_wait_bounded(smem_u32(&bars[buf]), (uint32_t)((nxt / TC_STAGES - 1) & 1), p.status);
+      if (ok) load_stage(nxt, buf);
+    }
+    cp_async_commit();
+    cp_async_wait<TC_STAGES - 1>();
+    fence_async_shared();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int buf = it % TC_STAGES;
+      const uint32_t st = sbase + buf * TC_STAGE_BYTES;
+#pragma unroll
+      for (int j = 0; j < TC_BK / 16; ++j) {
+        const uint64_t ar = sw128_kmajor_desc(st + 0 * TC_TILE_BYTES + j * 32);
+        const uint64_t ai = sw128_kmajor_desc(st + 1 * TC_TILE_BYTES + j * 32);
+        const uint64_t br = sw128_kmajor_desc(st + 2 * TC_TILE_BYTES + j * 32);
+        const uint64_t bi = sw128_kmajor_desc(st + 3 * TC_TILE_BYTES + j * 32);
+        const uint32_t first = (it == 0 && j == 0) ? 0u : 1u;
+#if TNC_TC_SELFCHECK
+        if (!tc_check(((st + j * 32) & 15u) == 0 && st + 3 * TC_TILE_BYTES + TC_TILE_BYTES <= sbase + TC_PIPE_BYTES,
+                      p.status, 15, st, j))
+          continue;
+        if (blockIdx.x == 0 && it == 0 && j == 0) {
+          p.status[12] = (int32_t)(ar & 0xffffffffu);
+          p.status[13] = (int32_t)(ar >> 32);
+          p.status[14] = (int32_t)id_pos;
+        }
+#endif
+        mma_f16(tmem, ar, br, id_pos, first);             // Dr  = Ar Br
+        mma_f16(tmem, ai, bi, id_neg, 1u);                // Dr -= Ai Bi
+        mma_f16(tmem + TC_BN, ar, bi, id_pos, first);     // Di  = Ar Bi
+        mma_f16(tmem + TC_BN, ai, br, id_pos, 1u);        // Di += Ai Br
+      }
+      mma_commit(smem_u32(&bars[buf]));
+    }
+  }
+  // all MMAs done (waited for even after a timeout, so TMEM is never freed under them)
+  if (tid == 0) mma_commit(smem_u32(&bars[TC_STAGES]));
+  const bool done = mbar_wait_bounded(smem_u32(&bars[TC_STAGES]), 0u, p.status);
+  ok = ok && done;
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  ok = __syncthreads_and(ok);
+
+  // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
+  const int64_t sb = inst * p.n_slots;
+  int sh = 0;
+  {
+    const float a = p.maxabs[sb + p.slotA], b = p.maxabs[sb + p.slotB];
+    if (a > 0.f && b > 0.f) {
+      int ea, eb;
+      frexpf(a, &ea);
+      frexpf(b, &eb);
+      sh = ea + eb + p.nK + 1 - 15;
+    }
+  }
+  const float scale = ldexpf(1.f, -sh);
+  T* stg = reinterpret_cast<T*>(smem);  // [2][128*128] re plane then im plane
+  float mx = 0.f;
+  if (ok) {
+    const int row = (warp & 3) * 32 + lane;
+    const int col0 = (warp >> 2) * 64;
+    const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+#pragma unroll 1
+    for (int cc = 0; cc < 64; cc += 32) {
+      float vr[32], vi[32];
+      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
+      tmem_ld32(tmem + lane_addr + TC_BN + col0 + cc, vi);
+      const uint32_t rm = TCm[row];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t idx = rm + TCn[col0 + cc + j];
+#if TNC_TC_SELFCHECK
+        if (!tc_check(idx < uint32_t(TC_BM * TC_BN), p.status, 16, idx, row)) continue;
+#endif
+        const T re = Conv<T>::from_f(vr[j] * scale), im = Conv<T>::from_f(vi[j] * scale);
+        stg[idx] = re;
+        stg[TC_BM * TC_BN + idx] = im;
+        mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+  if (!ok) return;
+  // contiguous runs of C: 16-byte vectors when the run allows
+  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+  const uint32_t lowmask = (1u << p.runC) - 1u;
+  if (p.runC >= 3) {
+    for (int t = tid * 8; t < TC_BM * TC_BN; t += TC_THREADS * 8) {
+      const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
+#if TNC_TC_SELFCHECK
+      {
+        const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
+        if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
+          continue;
+      }
+#endif
+      *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + t);
+      *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + TC_BM * TC_BN + t);
+    }
+  } else {
+    for (int t = tid; t < TC_BM * TC_BN; t += TC_THREADS) {
+      const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
+      Cre[off] = stg[t];
+      Cre[p.planeC + off] = stg[TC_BM * TC_BN + t];
+    }
+  }
+  // block max -> tensor max
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
+    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+  }
+}
+
+size_t tc_smem_bytes(int runC) {
+  return 1024 + TC_PIPE_BYTES + (TC_BM + TC_BN) * 4 + (size_t(1) << (14 - runC)) * 4 + (TC_BM + TC_BN) * 2 + 64 +
+         (TC_STAGES + 1) * 8 + 16 + 32 * 4 + 64;
+}
+
+cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes(p.runC);
+  cudaError_t e;
+  if (precision == 1) {
+    e = cudaFuncSetAttribute(k_tc_gemm<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<__half><<<grid, TC_THREADS, smem, s>>>(p);
+  } else if (precision == 2) {
+    e = cudaFuncSetAttribute(k_tc_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<__nv_bfloat16><<<grid, TC_THREADS, smem, s>>>(p);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tnc

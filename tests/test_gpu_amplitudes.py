@@ -1,10 +1,11 @@
 """GPU parity of amplitudes through the C boundary against the FP64 oracle.
 
-Tolerances (norm-wise relative error over the batch): complex64 path 1e-5; complex-half
-1e-2; complex-bf16 4e-2.  The bf16 figure follows from its unit roundoff 2^-9 ~ 2e-3 per
-stored tensor: a root-to-leaf path of the greedy trees here has up to ~20 stored tensors,
-and independent roundings add in quadrature, ~sqrt(20) * 2e-3 ~ 1e-2, times a margin of
-4 for the worst amplitudes of a Porter-Thomas batch.
+Tolerances (norm-wise relative error over the batch): complex64 path 1e-5 and
+complex-half 1e-2, as required of the two paths.  complex-bf16 has no stated tolerance;
+its bound here is derived: every stored tensor (each leaf and each intermediate) is
+rounded once to bf16 with unit roundoff u = 2^-9, the amplitude is multilinear in the
+stored tensors, so independent relative perturbations of size ~u add in quadrature:
+err ~ u * sqrt(n_stored).  The bound is 4 u sqrt(n_stored).
 """
 import itertools
 
@@ -22,6 +23,11 @@ pytestmark = pytest.mark.gpu
 TOL = {"c64": 1e-5, "chalf": 1e-2, "cbf16": 4e-2}
 
 
+def bf16_bound(plan):
+    info = plan.info()
+    return 4.0 * 2.0 ** -9 * np.sqrt(info["n_leaves"] + info["n_steps"])
+
+
 @pytest.fixture(scope="module")
 def ctx():
     return T.Context(0)
@@ -37,7 +43,8 @@ def test_tiny_config_batch_of_bitstrings(ctx, precision):
     got = ctx.amplitudes(p, bs, precision)[:, 0]
     ref = sv.circuit_amplitudes(c, bs)
     err = metrics.rel_err_norm(got, ref)
-    assert err <= TOL[precision], err
+    tol = bf16_bound(p) if precision == "cbf16" else TOL[precision]
+    assert err <= tol, err
 
 
 @pytest.mark.parametrize("precision", ["c64", "chalf"])
@@ -91,7 +98,8 @@ def test_half_precision_scaling_keeps_small_amplitudes(ctx):
     ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
     for prec in ("c64", "chalf", "cbf16"):
         got = ctx.amplitudes(p, fixed[None, :], prec)[0]
-        assert metrics.rel_err_norm(got, ref) <= TOL[prec], prec
+        tol = bf16_bound(p) if prec == "cbf16" else TOL[prec]
+        assert metrics.rel_err_norm(got, ref) <= tol, prec
 
 
 def test_edge_cases(ctx):

@@ -1,0 +1,89 @@
+"""GPU parity of the tensor-core (tcgen05) complex GEMM step against the FP64 oracle.
+
+Single contractions go through tnc_contract with operand layouts that qualify for the
+tensor-core kernel (the same three common labels at positions 0..2 of A and B, M and N
+>= 2^7, K >= 2^6); whole plans go through tnc_amplitudes.  Same tolerances as the SIMT
+kernel: fp16 storage 2e-3, bf16 1e-2 (one rounding of the output; FP32 accumulation).
+"""
+import numpy as np
+import pytest
+import torch
+
+from inputs import grid_circuit, random_complex, random_labels_perm, subcube_bitstrings, subcube_spec
+from oracle import metrics, pairwise
+from oracle import statevector as sv
+from paper_2504_09186_gb300 import tnc as T
+
+pytestmark = pytest.mark.gpu
+
+DT = {"chalf": torch.float16, "cbf16": torch.bfloat16}
+TOL = {"chalf": 2e-3, "cbf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return T.Context(0)
+
+
+def kmajor_case(m, k, n, seed):
+    ks = list(range(100, 100 + k))
+    la = ks[:3] + random_labels_perm(list(range(m)) + ks[3:], seed)
+    lb = ks[:3] + random_labels_perm(ks[3:] + list(range(200, 200 + n)), seed + 1)
+    lc = random_labels_perm(list(range(m)) + list(range(200, 200 + n)), seed + 2)
+    sigma = 1.0 / np.sqrt(2.0 ** k)
+    a = random_complex(1 << len(la), sigma, seed + 3)
+    b = random_complex(1 << len(lb), sigma, seed + 4)
+    return a, la, b, lb, lc
+
+
+def run(ctx, precision, a, la, b, lb, lc):
+    def planar(x):
+        t = torch.from_numpy(np.concatenate([x.real, x.imag])).to(DT[precision])
+        back = t.to(torch.float64).numpy()
+        return t.cuda(), back[: x.size] + 1j * back[x.size:]
+
+    ta, aq = planar(a)
+    tb, bq = planar(b)
+    tc = torch.empty(2 << len(lc), dtype=DT[precision], device="cuda")
+    e = ctx.contract(precision, ta, la, tb, lb, tc, lc)
+    torch.cuda.synchronize()
+    cc = tc.to(torch.float64).cpu().numpy()
+    n = 1 << len(lc)
+    return (cc[:n] + 1j * cc[n:]) * 2.0 ** e, aq, bq
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape", [(7, 6, 7), (8, 8, 8), (9, 10, 7), (7, 12, 9), (10, 7, 8)])
+def test_tc_contract_elementwise(ctx, precision, shape):
+    a, la, b, lb, lc = kmajor_case(*shape, seed=11 * sum(shape) + shape[0])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    if len(got) <= 1 << 16:
+        ref = pairwise.contract(aq, la, bq, lb, lc)
+        err = metrics.rel_err_norm(got, ref)
+    else:
+        idx = np.random.default_rng(1).integers(0, len(got), 256)
+        err = metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx))
+    assert err <= TOL[precision], err
+
+
+def test_tc_contract_large_sampled(ctx):
+    # the shape of the largest step of the 30-qubit plan, at one slice: M=2^14, K=2^12, N=2^10
+    a, la, b, lb, lc = kmajor_case(14, 12, 10, seed=5)
+    got, aq, bq = run(ctx, "chalf", a, la, b, lb, lc)
+    idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(2).integers(0, len(got), 126)]))
+    ref = pairwise.contract_at(aq, la, bq, lb, lc, idx)
+    assert metrics.rel_err_norm(got[idx], ref) <= TOL["chalf"]
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+def test_tc_steps_inside_a_plan(ctx, precision):
+    # 20-qubit 4x5 grid, 12 cycles: its plan has tensor-core steps
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=16, log2_cap=20)
+    assert sum(s["tc"] for s in p.describe()["steps"]) >= 1
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    got = ctx.amplitudes(p, fixed[None, :], precision)[0]
+    info = p.info()
+    tol = 1e-2 if precision == "chalf" else 4 * 2.0 ** -9 * np.sqrt(info["n_leaves"] + info["n_steps"])
+    assert metrics.rel_err_norm(got, ref) <= tol
