@@ -197,6 +197,29 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
                         const int32_t* labels_b, void* c, int32_t rank_c,
                         const int32_t* labels_c, int32_t* c_exp2, void* stream);
 
+/* The same single contraction as tnc_contract, for callers that cannot allocate device
+ * memory: code running while a stream is being captured into a CUDA graph, real-time
+ * threads that must not take the allocator's locks or implicit device syncs, and
+ * applications whose own pool allocator has already reserved the device's memory.  It
+ * takes no context and allocates nothing: the scratch it needs (a few max/exponent
+ * slots and, for split-over-K shapes, the FP32 partial sums) is one file-scope device
+ * array of 4 MiB that every GPU which loads this library holds until the process exits.
+ * There is no counterpart in the paper; this is an interface choice of this library.
+ *  - Device: the caller's current device; a, b, c must live there.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress); make that first
+ *    call before any stream capture.
+ *  - Arithmetic: always the FP32 SIMT kernels (never the tensor-core kernel).
+ *  - Limit: the split-K partials must fit in 4 MiB - 256 B; the tile policy keeps them
+ *    at most 1024 splits x 256 outputs x 8 B = 2 MiB, and a contraction needing more is
+ *    rejected with TNC_E_INVALID_ARG and a message giving the size it needs.
+ *  - Sharing: every call uses the same array; the slots are cleared on each call, but
+ *    calls that overlap on the GPU (several streams, or several host threads) race on it.
+ *  - stream: cudaStream_t or NULL (the legacy default stream); returns after C is ready.
+ * Other arguments, layouts and errors are those of tnc_contract. */
+tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a, const int32_t* labels_a,
+                                const void* b, int32_t rank_b, const int32_t* labels_b, void* c,
+                                int32_t rank_c, const int32_t* labels_c, int32_t* c_exp2, void* stream);
+
 /* Per-step timings of the last tnc_amplitudes call made with opts->profile = 1 on this
  * context (waits for it).  For step s (program order, cap >= n entries):
  *  ms[s]      device time summed over the call's launches of that step (CUDA events)

@@ -718,3 +718,98 @@ tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, doub
     ms[ps.n_steps] = tot;
   });
 }
+
+// ------------------------------------------------------------------ allocation-free contraction
+// tnc_contract_noalloc: the same single contraction as tnc_contract on the FP32 SIMT kernels
+// (generic tile, or the split-K GEPDOT pair of kernels), for callers that must not allocate
+// device memory.  Its scratch -- the per-operand max/exponent slots and the split-K partial
+// sums -- lives in one file-scope device array instead of a context's cudaMalloc'd buffers.
+namespace tnc {
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // 4 MiB per device, held until exit
+constexpr size_t kNoAllocSlotBytes = 256;                 // maxabs[3], exps[3] at the front
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+std::map<int, void*> g_noalloc_ptr;  // device ordinal -> device address of the array
+
+// Device address of the array on the current device; looked up once per device (the
+// host-side name of a __device__ array is not a device address).
+void* noalloc_scratch(int* device_out) {
+  int dev = -1;
+  CUDA_OK(cudaGetDevice(&dev));
+  *device_out = dev;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_ptr.find(dev);
+  if (it != g_noalloc_ptr.end()) return it->second;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    fail(TNC_E_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch) failed: ") + cudaGetErrorString(e));
+  g_noalloc_ptr[dev] = p;
+  return p;
+}
+}  // namespace
+}  // namespace tnc
+
+tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a, const int32_t* labels_a,
+                                const void* b, int32_t rank_b, const int32_t* labels_b, void* c, int32_t rank_c,
+                                const int32_t* labels_c, int32_t* c_exp2, void* stream) {
+  return guarded([&] {
+    if (!a || !b || !c || !c_exp2) fail(TNC_E_INVALID_ARG, "NULL argument");
+    if (precision < TNC_C64 || precision > TNC_CBF16) fail(TNC_E_INVALID_ARG, "bad precision");
+    if (rank_a < 0 || rank_b < 0 || rank_c < 0 || rank_a > 32 || rank_b > 32 || rank_c > 32)
+      fail(TNC_E_INVALID_ARG, "ranks must be in [0, 32]");
+    if ((rank_a && !labels_a) || (rank_b && !labels_b) || (rank_c && !labels_c)) fail(TNC_E_INVALID_ARG, "NULL labels");
+    std::vector<int> la(labels_a, labels_a + rank_a), lb(labels_b, labels_b + rank_b), lc(labels_c, labels_c + rank_c);
+    auto distinct = [](std::vector<int> v) {
+      std::sort(v.begin(), v.end());
+      return std::adjacent_find(v.begin(), v.end()) == v.end();
+    };
+    if (!distinct(la) || !distinct(lb) || !distinct(lc)) fail(TNC_E_INVALID_ARG, "repeated label within a tensor");
+    std::vector<int> fr;
+    for (int x : la)
+      if (std::find(lb.begin(), lb.end(), x) == lb.end()) fr.push_back(x);
+    for (int x : lb)
+      if (std::find(la.begin(), la.end(), x) == la.end()) fr.push_back(x);
+    std::vector<int> s1 = fr, s2 = lc;
+    std::sort(s1.begin(), s1.end());
+    std::sort(s2.begin(), s2.end());
+    if (s1 != s2) fail(TNC_E_INVALID_ARG, "C's labels must be exactly the free labels of A and B");
+    int dev = -1;
+    char* base = static_cast<char*>(noalloc_scratch(&dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int kind = K_GENERIC;
+    TileSpec t = tile_for(la, lb, lc, 1, kind);
+    StepLaunch L = make_launch(t, kind, la, lb, lc);
+    if (L.kind == K_SPLITK) {
+      const size_t need = size_t(L.p.splitk) * size_t(L.p.planeC) * sizeof(float2);
+      if (need > kNoAllocScratchBytes - kNoAllocSlotBytes)
+        fail(TNC_E_INVALID_ARG, "tnc_contract_noalloc: this contraction needs " + std::to_string(need) +
+                                    " bytes of split-K scratch; the static array holds " +
+                                    std::to_string(kNoAllocScratchBytes - kNoAllocSlotBytes));
+      L.p.partials = reinterpret_cast<float2*>(base + kNoAllocSlotBytes);
+    }
+    float* mx = reinterpret_cast<float*>(base);
+    int32_t* ex = reinterpret_cast<int32_t*>(base + 64);
+    // the slots are shared by every call: clear what must start at zero
+    CUDA_OK(cudaMemsetAsync(base, 0, kNoAllocSlotBytes, s));
+    CUDA_OK(launch_maxabs(precision, a, int64_t(2) << rank_a, mx + 0, s));
+    CUDA_OK(launch_maxabs(precision, b, int64_t(2) << rank_b, mx + 1, s));
+    L.p.A = a;
+    L.p.B = b;
+    L.p.C = c;
+    L.p.strideA = L.p.strideB = L.p.strideC = 0;
+    L.p.maxabs = mx;
+    L.p.exps = ex;
+    L.p.n_slots = 3;
+    L.p.slotA = 0;
+    L.p.slotB = 1;
+    L.p.slotC = 2;
+    run_step(precision, L, 1, s);
+    int32_t e = 0;
+    CUDA_OK(cudaMemcpyAsync(&e, ex + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_OK(cudaStreamSynchronize(s));
+    *c_exp2 = e;
+  });
+}

@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH):
         "tnc_contract": [vp, i32, vp, i32, C.POINTER(C.c_int32), vp, i32, C.POINTER(C.c_int32), vp, i32,
                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
         "tnc_sync": [vp],
+        "tnc_contract_noalloc": [i32, vp, i32, C.POINTER(C.c_int32), vp, i32, C.POINTER(C.c_int32), vp, i32,
+                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
         "tnc_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double),
                              C.POINTER(C.c_double), C.POINTER(C.c_int32), i32, C.POINTER(C.c_int32)],
     }
@@ -315,6 +317,21 @@ class Context:
         if getattr(self, "h", None) and _lib is not None:
             _lib.tnc_context_destroy(self.h)
             self.h = None
+
+
+def tnc_contract_noalloc(precision, a, labels_a, b, labels_b, c, labels_c, stream: int = 0) -> int:
+    """C = A * B without any device allocation (see include/tnc.h).  a, b, c are planar
+    device tensors (torch) on the current device.  Returns C's exponent."""
+    lib = load_library()
+    la = np.ascontiguousarray(labels_a, dtype=np.int32)
+    lb = np.ascontiguousarray(labels_b, dtype=np.int32)
+    lc = np.ascontiguousarray(labels_c, dtype=np.int32)
+    e = C.c_int32()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib.tnc_contract_noalloc(prec, C.c_void_p(a.data_ptr()), len(la), _i32p(la), C.c_void_p(b.data_ptr()),
+                                    len(lb), _i32p(lb), C.c_void_p(c.data_ptr()), len(lc), _i32p(lc), C.byref(e),
+                                    C.c_void_p(stream)))
+    return int(e.value)
 
 
 def version() -> str:
