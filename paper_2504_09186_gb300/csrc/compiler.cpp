@@ -169,32 +169,41 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   return t;
 }
 
-// Tensor-core tile: 7 M labels, 7 N labels, 6 K labels whose first three are at
-// positions 0..2 of both operands.  Returns false if the step does not qualify.
-bool choose_tc_tile(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
-                    const std::vector<int>& k3, TileSpec& t) {
+// Tensor-core tile: 7 row labels from the operand with more free labels (A after an
+// optional swap), 6 or 7 column labels (BN = 64 / 128), 4..6 K labels (BK = 16 / 32 / 64)
+// whose first three are the k3 labels at positions 0..2 of both operands.  Returns false
+// if the step does not qualify.
+bool choose_tc_tile(const std::vector<int>& la0, const std::vector<int>& lb0, const std::vector<int>& lc,
+                    const std::vector<int>& k3, TileSpec& t, bool& swap, int& bn, int& bk) {
   std::vector<int> M, K, N;
-  for (int x : la) (contains(lb, x) ? K : M).push_back(x);
-  for (int x : lb)
-    if (!contains(la, x)) N.push_back(x);
-  if (M.size() < 7 || N.size() < 7 || K.size() < 6 || k3.size() != 3) return false;
+  for (int x : la0) (contains(lb0, x) ? K : M).push_back(x);
+  for (int x : lb0)
+    if (!contains(la0, x)) N.push_back(x);
+  swap = N.size() > M.size();
+  const std::vector<int>& la = swap ? lb0 : la0;
+  const std::vector<int>& lb = swap ? la0 : lb0;
+  if (swap) std::swap(M, N);
+  if (M.size() < 7 || N.size() < 6 || K.size() < 4 || k3.size() != 3) return false;
   for (int j = 0; j < 3; ++j)
     if (la.size() < 3 || lb.size() < 3 || la[j] != k3[j] || lb[j] != k3[j]) return false;
+  bn = N.size() >= 7 ? 128 : 64;
+  bk = K.size() >= 6 ? 64 : (K.size() == 5 ? 32 : 16);
+  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 64 ? 6 : (bk == 32 ? 5 : 4);
   t = TileSpec();
   t.Kt = k3;
   for (int x : la) {  // further K labels by A position
-    if ((int)t.Kt.size() >= 6) break;
+    if (t.Kt.size() >= kt) break;
     if (contains(K, x) && !contains(t.Kt, x)) t.Kt.push_back(x);
   }
   for (int x : lc) {  // C's lowest labels first, so stores are runs
     if (contains(M, x) && t.Mt.size() < 7) t.Mt.push_back(x);
-    else if (contains(N, x) && t.Nt.size() < 7) t.Nt.push_back(x);
+    else if (contains(N, x) && t.Nt.size() < nt) t.Nt.push_back(x);
     if (t.Mt.size() + t.Nt.size() >= 3) break;
   }
   for (int x : la)
     if (contains(M, x) && !contains(t.Mt, x) && t.Mt.size() < 7) t.Mt.push_back(x);
   for (int x : lb)
-    if (contains(N, x) && !contains(t.Nt, x) && t.Nt.size() < 7) t.Nt.push_back(x);
+    if (contains(N, x) && !contains(t.Nt, x) && t.Nt.size() < nt) t.Nt.push_back(x);
   // C's three lowest positions must be tile labels
   for (int j = 0; j < 3; ++j)
     if (!contains(t.Mt, lc[j]) && !contains(t.Nt, lc[j])) return false;
@@ -210,10 +219,11 @@ bool choose_tc_tile(const std::vector<int>& la, const std::vector<int>& lb, cons
 
 }  // namespace
 
-bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t) {
+bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t,
+                 bool& swap, int& bn, int& bk) {
   if (la.size() < 3 || lb.size() < 3) return false;
   std::vector<int> k3(la.begin(), la.begin() + 3);
-  return choose_tc_tile(la, lb, lc, k3, t);
+  return choose_tc_tile(la, lb, lc, k3, t, swap, bn, bk);
 }
 
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
@@ -271,7 +281,7 @@ void compile_plan(Plan& plan, bool fuse) {
     consumer[plan.tree[s].second] = (int)s;
     const int m = (int)A.size() - (int)K.size(), n = (int)B.size() - (int)K.size();
     const bool inter = plan.tree[s].first >= n_leaves && plan.tree[s].second >= n_leaves;
-    if (inter && m >= 7 && n >= 7 && K.size() >= 6) k3_of_step[s] = {K[0], K[1], K[2]};
+    if (inter && std::max(m, n) >= 7 && std::min(m, n) >= 6 && K.size() >= 4) k3_of_step[s] = {K[0], K[1], K[2]};
   }
   // intermediates
   plan.steps.clear();
@@ -313,7 +323,8 @@ void compile_plan(Plan& plan, bool fuse) {
     int kind = K_GENERIC;
     st.tile = choose_tile(la, lb, lc, 1, kind);
     st.kind = kind;
-    st.tc_ok = !k3_of_step[s].empty() && choose_tc_tile(la, lb, lc, k3_of_step[s], st.tc_tile);
+    st.tc_ok = !k3_of_step[s].empty() &&
+               choose_tc_tile(la, lb, lc, k3_of_step[s], st.tc_tile, st.tc_swap, st.tc_bn, st.tc_bk);
     int nk = 0;
     for (int x : la) nk += contains(lb, x);
     int nm = (int)la.size() - nk, nn = (int)lb.size() - nk;

@@ -73,6 +73,7 @@ struct TcParams {
   void* C;
   int64_t strideA, strideB, strideC;
   int64_t planeA, planeB, planeC;
+  int32_t bn, bk;            // tile width (64 / 128) and K tile (16 / 32 / 64)
   int8_t pAm[7], pBn[7];     // operand positions of the canonical tile m / n bits
   int8_t pAk[3], pBk[3];     // operand positions of k bits 3..5 (bits 0..2 are positions 0..2)
   int8_t pCm[7], pCn[7];     // C-tile-native bit of canonical m / n bit
@@ -81,6 +82,8 @@ struct TcParams {
   int32_t n_om, n_on, n_ok;
   int8_t om_A[kMaxOuter], om_C[kMaxOuter], on_B[kMaxOuter], on_C[kMaxOuter], ok_A[kMaxOuter], ok_B[kMaxOuter];
   int32_t nK;
+  int32_t splitk;            // CTAs along the outer K labels; > 1 writes FP32 partials
+  float2* partials;          // [inst][split][planeC]
   int32_t bf16;              // operand format: 0 fp16, 1 bf16
   float* maxabs;
   int32_t* exps;

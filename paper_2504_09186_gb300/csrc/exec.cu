@@ -34,7 +34,8 @@ cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, c
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
-bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t);
+bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t,
+                 bool& swap, int& bn, int& bk);
 
 #define CUDA_OK(expr)                                                                             \
   do {                                                                                            \
@@ -96,29 +97,36 @@ struct StepLaunch {
   int rm, rn;
 };
 
-// Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.
+// Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
+// kernel's A (row side) and B operands (already swapped when the tile asked for it).
+// n_inst sizes the split over the outer common labels: enough CTAs for two waves.
 static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<int>& la, const std::vector<int>& lb,
-                           const std::vector<int>& lc, int precision) {
+                           const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst) {
   TcParams& q = L.tp;
   std::memset(&q, 0, sizeof(q));
-  if (t.Mt.size() != 7 || t.Nt.size() != 7 || t.Kt.size() != 6) fail(TNC_E_PLAN, "bad tensor-core tile");
+  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 64 ? 6 : (bk == 32 ? 5 : 4);
+  if (t.Mt.size() != 7 || t.Nt.size() != nt || t.Kt.size() != kt) fail(TNC_E_PLAN, "bad tensor-core tile");
   for (int j = 0; j < 3; ++j)
     if (pos_of(la, t.Kt[j]) != j || pos_of(lb, t.Kt[j]) != j) fail(TNC_E_PLAN, "tensor-core operands not K-major");
   uint32_t maskC = 0;
   for (int x : t.Mt) maskC |= 1u << pos_of(lc, x);
   for (int x : t.Nt) maskC |= 1u << pos_of(lc, x);
+  q.bn = bn;
+  q.bk = bk;
   q.maskC = maskC;
   q.runC = low_run(maskC);
   if (q.runC < 3) fail(TNC_E_PLAN, "tensor-core output run too short");
   for (int j = 0; j < 7; ++j) {
     q.pAm[j] = (int8_t)pos_of(la, t.Mt[j]);
-    q.pBn[j] = (int8_t)pos_of(lb, t.Nt[j]);
     q.pCm[j] = (int8_t)rank_in_mask(maskC, pos_of(lc, t.Mt[j]));
+  }
+  for (size_t j = 0; j < nt; ++j) {
+    q.pBn[j] = (int8_t)pos_of(lb, t.Nt[j]);
     q.pCn[j] = (int8_t)rank_in_mask(maskC, pos_of(lc, t.Nt[j]));
   }
-  for (int j = 0; j < 3; ++j) {
-    q.pAk[j] = (int8_t)pos_of(la, t.Kt[3 + j]);
-    q.pBk[j] = (int8_t)pos_of(lb, t.Kt[3 + j]);
+  for (size_t j = 3; j < kt; ++j) {
+    q.pAk[j - 3] = (int8_t)pos_of(la, t.Kt[j]);
+    q.pBk[j - 3] = (int8_t)pos_of(lb, t.Kt[j]);
   }
   q.n_om = (int)t.Mo.size();
   q.n_on = (int)t.No.size();
@@ -132,9 +140,47 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   q.planeC = int64_t(1) << lc.size();
   q.nK = (int)t.Kt.size() + q.n_ok;
   q.bf16 = precision == TNC_CBF16 ? 1 : 0;
+  // split over the outer common labels when the tiles alone cannot fill the GPU twice
+  const int64_t tiles = (int64_t(1) << (q.n_om + q.n_on)) * std::max<int64_t>(1, n_inst);
+  int split = 1;
+  while (tiles * split < 2 * 152 && (int64_t(1) << q.n_ok) / (split * 2) >= 4) split *= 2;
+  q.splitk = split;
   L.kind = K_TC;
-  L.grid = dim3(1u << (q.n_om + q.n_on), 1, 1);
+  L.grid = dim3(1u << (q.n_om + q.n_on), (unsigned)split, 1);
   L.smem = 0;
+  // the fixed-order reduction of the partials reuses the SIMT split-K reduce kernel
+  std::memset(&L.p, 0, sizeof(L.p));
+  L.p.planeC = q.planeC;
+  L.p.splitk = split;
+  L.p.nK = q.nK;
+}
+
+// Fills the pointers of a tensor-core launch (and of its reduce, when split).
+static void bind_tc(StepLaunch& L, const void* a, const void* b, void* c, int64_t stride, float* maxabs, int32_t* exps,
+                    int n_slots, int slot_a, int slot_b, int slot_c, int32_t* status, float2* partials) {
+  TcParams& q = L.tp;
+  q.A = a;
+  q.B = b;
+  q.C = c;
+  q.strideA = q.strideB = q.strideC = stride;
+  q.maxabs = maxabs;
+  q.exps = exps;
+  q.n_slots = n_slots;
+  q.slotA = slot_a;
+  q.slotB = slot_b;
+  q.slotC = slot_c;
+  q.status = status;
+  q.partials = partials;
+  GenParams& r = L.p;
+  r.C = c;
+  r.strideC = stride;
+  r.maxabs = maxabs;
+  r.exps = exps;
+  r.n_slots = n_slots;
+  r.slotA = slot_a;
+  r.slotB = slot_b;
+  r.slotC = slot_c;
+  r.partials = partials;
 }
 
 static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int>& la, const std::vector<int>& lb,
@@ -326,19 +372,12 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     const auto& lc = P.tensors[st.c].labels;
     StepLaunch L = make_launch(st.tile, st.kind, la, lb, lc);
     if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
-      make_tc_launch(L, st.tc_tile, la, lb, lc, precision);
-      TcParams& q = L.tp;
-      q.A = prog->arena.as<char>() + P.tensors[st.a].offset * eb;
-      q.B = prog->arena.as<char>() + P.tensors[st.b].offset * eb;
-      q.C = prog->arena.as<char>() + P.tensors[st.c].offset * eb;
-      q.strideA = q.strideB = q.strideC = prog->inst_stride;
-      q.maxabs = prog->maxabs.as<float>();
-      q.exps = prog->exps.as<int32_t>();
-      q.n_slots = prog->n_slots;
-      q.slotA = st.a;
-      q.slotB = st.b;
-      q.slotC = st.c;
-      q.status = ctx->status.as<int32_t>();
+      const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
+      make_tc_launch(L, st.tc_tile, P.tensors[ta].labels, P.tensors[tb].labels, lc, precision, st.tc_bn, st.tc_bk, W);
+      bind_tc(L, prog->arena.as<char>() + P.tensors[ta].offset * eb, prog->arena.as<char>() + P.tensors[tb].offset * eb,
+              prog->arena.as<char>() + P.tensors[st.c].offset * eb, prog->inst_stride, prog->maxabs.as<float>(),
+              prog->exps.as<int32_t>(), prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), nullptr);
+      if (L.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * L.tp.splitk * L.tp.planeC);
       prog->steps.push_back(L);
       continue;
     }
@@ -357,8 +396,10 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   }
   if (partial_elems) {
     prog->partials.reserve(partial_elems * sizeof(float2));
-    for (auto& L : prog->steps)
+    for (auto& L : prog->steps) {
       if (L.kind == K_SPLITK) L.p.partials = prog->partials.as<float2>();
+      if (L.kind == K_TC && L.tp.splitk > 1) L.tp.partials = L.p.partials = prog->partials.as<float2>();
+    }
   }
   // root
   prog->root = P.root;
@@ -407,6 +448,7 @@ static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaSt
   L.grid.z = (unsigned)n_inst;
   if (L.kind == K_TC) {
     CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
+    if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
     return;
   }
   CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
@@ -657,19 +699,17 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       L.p.partials = ctx->partials.as<float2>();
     }
     TileSpec tct;
-    if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct)) {
-      make_tc_launch(L, tct, la, lb, lc, precision);
-      TcParams& q = L.tp;
-      q.A = a;
-      q.B = b;
-      q.C = c;
-      q.maxabs = mx;
-      q.exps = ex;
-      q.n_slots = 3;
-      q.slotA = 0;
-      q.slotB = 1;
-      q.slotC = 2;
-      q.status = ctx->status.as<int32_t>();
+    bool swap = false;
+    int bn = 128, bk = 64;
+    if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct, swap, bn, bk)) {
+      make_tc_launch(L, tct, swap ? lb : la, swap ? la : lb, lc, precision, bn, bk, 1);
+      float2* part = nullptr;
+      if (L.tp.splitk > 1) {
+        ctx->partials.reserve(size_t(L.tp.splitk) * L.tp.planeC * sizeof(float2));
+        part = ctx->partials.as<float2>();
+      }
+      bind_tc(L, swap ? b : a, swap ? a : b, c, 0, mx, ex, 3, swap ? 1 : 0, swap ? 0 : 1, 2, ctx->status.as<int32_t>(),
+              part);
     }
     (void)eb;
     run_step(precision, L, 1, s);

@@ -113,6 +113,8 @@ struct Step {
   // sit at positions 0..2 of both operands
   bool tc_ok = false;
   TileSpec tc_tile;
+  bool tc_swap = false;           // tensor-core rows come from b (b has more free labels)
+  int tc_bn = 128, tc_bk = 64;    // tile width and K tile of the tensor-core kernel
   // chain steps: A absorbs b_0, b_1, ... in order; c = final result
   std::vector<int> chain_b;       // operand ids of each link (first = b)
   std::vector<int> chain_c;       // tensor ids produced by each link (last = c)

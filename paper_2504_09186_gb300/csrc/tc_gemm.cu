@@ -23,13 +23,36 @@
 
 namespace tnc {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
+constexpr int TC_BM = 128;                   // rows of A per tile (TMEM lanes)
 constexpr int TC_THREADS = 256;
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;          // one plane of one operand tile (16 KB)
-constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;          // Ar, Ai, Br, Bi
-constexpr int TC_PIPE_BYTES = TC_STAGES * TC_STAGE_BYTES;  // 192 KB
-constexpr int TC_TMEM_COLS = 2 * TC_BN;                    // Dr, Di
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;             // 2 s bound on any wait
+constexpr int TC_PIPE_BUDGET = 192 * 1024;   // shared memory for the operand pipeline
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s bound on any wait
+
+// Compile-time shape of one tensor-core kernel instance: BN columns (64 or 128), BK-wide
+// K tiles (16, 32 or 64 fp16 = 32, 64 or 128-byte rows, swizzled 32B / 64B / 128B).
+template <int BN, int BK>
+struct TcShape {
+  static constexpr int ROWB = BK * 2;                         // bytes per tile row
+  static constexpr int A_BYTES = TC_BM * ROWB;                // one plane of the A tile
+  static constexpr int B_BYTES = BN * ROWB;                   // one plane of the B tile
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;     // Ar, Ai, Br, Bi
+  static constexpr int STAGES = (TC_PIPE_BUDGET / STAGE) > 8 ? 8 : (TC_PIPE_BUDGET / STAGE);
+  static constexpr int DIST = STAGES - 2;                     // prefetch distance
+  static constexpr int PIPE = STAGES * STAGE;
+  static constexpr int SBO = 8 * ROWB;                        // bytes between 8-row groups
+  static constexpr int LAYOUT = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // SW128 / SW64 / SW32
+  static constexpr int CHUNKS = BK / 8;                        // 16-byte chunks per row
+  static constexpr int TMEM_COLS = 2 * BN;                     // Dr, Di
+  static constexpr int C_BITS = 7 + (BN == 128 ? 7 : 6);       // log2 entries of the C tile
+  static_assert(STAGES >= 3, "pipeline needs at least 3 stages");
+};
+
+// Byte offset of 16-byte chunk c of row r in a swizzled K-major tile with `rowb`-byte rows:
+// the chunk index is XORed with address bits 7.. (the Swizzle<log2(rowb/16), 4, 3> pattern).
+__device__ __forceinline__ uint32_t swz(uint32_t r, uint32_t c, uint32_t rowb) {
+  const uint32_t off = r * rowb + c * 16;
+  return off ^ (((off >> 7) & (rowb / 16 - 1)) << 4);
+}
 
 #ifndef TNC_TC_SELFCHECK
 #define TNC_TC_SELFCHECK 0
@@ -106,25 +129,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return true;
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, swizzled (layout 2 / 4 / 6 = 128B / 64B / 32B),
+// 8-row groups `sbo` bytes apart.
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= uint64_t((saddr >> 4) & 0x3FFFu);    // start address
   d |= uint64_t(1) << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= uint64_t(1024 >> 4) << 32;           // stride byte offset: next 8-row group
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;  // stride byte offset: next 8-row group
   d |= uint64_t(1) << 46;                   // descriptor version (tcgen05)
-  d |= uint64_t(2) << 61;                   // SWIZZLE_128B
+  d |= uint64_t(layout) << 61;              // swizzle mode
   return d;
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulate, K-major A and B, M = 128, N = 128.
-__device__ __forceinline__ uint32_t instr_desc(int bf16, int neg_a) {
+// Instruction descriptor, kind::f16: FP32 accumulate, K-major A and B, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(int bf16, int neg_a, int n) {
   uint32_t d = 0;
   d |= 1u << 4;                              // D format F32
   d |= uint32_t(bf16) << 7;                  // A format (0 F16, 1 BF16)
   d |= uint32_t(bf16) << 10;                 // B format
   d |= uint32_t(neg_a) << 13;                // negate A
-  d |= uint32_t(TC_BN >> 3) << 17;           // N
+  d |= uint32_t(n >> 3) << 17;               // N
   d |= uint32_t(TC_BM >> 4) << 24;           // M
   return d;
 }
@@ -158,19 +182,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <typename T>
+template <typename T, int BN, int BK>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
+  using S = TcShape<BN, BK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // 1024-byte aligned pipeline buffers (the 128B swizzle pattern is address based)
+  // 1024-byte aligned pipeline buffers (the swizzle pattern is address based)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint32_t* depA = reinterpret_cast<uint32_t*>(smem + TC_PIPE_BYTES);   // [128] row offsets in A
-  uint32_t* depB = depA + TC_BM;                                         // [128] row offsets in B
-  uint32_t* hiC = depB + TC_BN;                                          // [2^(14 - runC)]
-  const int nhC = 1 << (14 - p.runC);
+  uint32_t* depA = reinterpret_cast<uint32_t*>(smem + S::PIPE);          // [128] row offsets in A
+  uint32_t* depB = depA + TC_BM;                                         // [BN] row offsets in B
+  uint32_t* hiC = depB + BN;                                             // [2^(C_BITS - runC)]
+  const int nhC = 1 << (S::C_BITS - p.runC);
   uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);               // [128]
-  uint16_t* TCn = TCm + TC_BM;                                           // [128]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(TCn + TC_BN + 8) & ~uintptr_t(7));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_STAGES + 1);
+  uint16_t* TCn = TCm + TC_BM;                                           // [BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S::STAGES + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -183,21 +208,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
     if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j], oC += int64_t(1) << p.om_C[j];
   for (int j = 0; j < p.n_on; ++j)
     if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j], oC += int64_t(1) << p.on_C[j];
+  const int nb = BN == 128 ? 7 : 6;
 
   // tables
   for (int r = tid; r < TC_BM; r += TC_THREADS) {
-    uint32_t a = 0, b = 0, cm = 0, cn = 0;
-    for (int j = 0; j < 7; ++j) {
-      if ((r >> j) & 1) {
-        a |= 1u << p.pAm[j];
-        b |= 1u << p.pBn[j];
-        cm |= 1u << p.pCm[j];
-        cn |= 1u << p.pCn[j];
-      }
-    }
+    uint32_t a = 0, cm = 0;
+    for (int j = 0; j < 7; ++j)
+      if ((r >> j) & 1) a |= 1u << p.pAm[j], cm |= 1u << p.pCm[j];
     depA[r] = a;
-    depB[r] = b;
     TCm[r] = (uint16_t)cm;
+  }
+  for (int r = tid; r < BN; r += TC_THREADS) {
+    uint32_t b = 0, cn = 0;
+    for (int j = 0; j < nb; ++j)
+      if ((r >> j) & 1) b |= 1u << p.pBn[j], cn |= 1u << p.pCn[j];
+    depB[r] = b;
     TCn[r] = (uint16_t)cn;
   }
   for (int h = tid; h < nhC; h += TC_THREADS) {
@@ -213,12 +238,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
     hiC[h] = r;
   }
   if (tid == 0) {
-    for (int s = 0; s <= TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s <= S::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS)
+                 "r"(S::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -227,116 +252,131 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 #if TNC_TC_SELFCHECK
-  if (blockIdx.x == 0 && tid == 0) {
-    p.status[8] = (int32_t)tmem;
-    p.status[9] = (int32_t)smem_u32(smem);
-    p.status[10] = (int32_t)smem_u32(smem_raw);
-    p.status[11] = (int32_t)smem_u32(bars);
-  }
   tc_check((smem_u32(smem) & 1023u) == 0, p.status, 11, smem_u32(smem), 0);
-  tc_check((tmem >> 16) == 0 && (tmem & 0xFFFFu) + TC_TMEM_COLS <= 512, p.status, 12, tmem, 0);
+  tc_check((tmem >> 16) == 0 && (tmem & 0xFFFFu) + S::TMEM_COLS <= 512, p.status, 12, tmem, 0);
   tc_check((smem_u32(bars) & 7u) == 0, p.status, 18, smem_u32(bars), 0);
 #endif
 
   const T* Ab = reinterpret_cast<const T*>(p.A) + inst * p.strideA + oA;
   const T* Bb = reinterpret_cast<const T*>(p.B) + inst * p.strideB + oB;
-  const int n_iter = 1 << p.n_ok;
+  const int n_total = 1 << p.n_ok;
+  const int per = n_total / p.splitk;
+  const int it0 = blockIdx.y * per;
+  const int n_iter = per;
   const uint32_t sbase = smem_u32(smem);
 
-  // per stage: 128 rows x 8 chunks of 16 B per plane = 1024 (row, chunk) pairs, 4 per
-  // thread, each copied for the 4 planes Ar, Ai, Br, Bi
-  constexpr int kPairsPerThread = TC_BM * (TC_BK / 8) / TC_THREADS;
-  static_assert(kPairsPerThread * TC_THREADS == TC_BM * (TC_BK / 8) && TC_BM == TC_BN, "tile / thread mismatch");
+  // per stage: (128 + BN) rows x CHUNKS chunks of 16 B per plane; each (row, chunk) pair is
+  // copied for the real and the imaginary plane
+  constexpr int PAIRS = (TC_BM + BN) * S::CHUNKS;
   auto load_stage = [&](int it, int buf) {
+    const int g = it0 + it;
     int64_t okA = 0, okB = 0;
     for (int j = 0; j < p.n_ok; ++j)
-      if ((it >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
-    const uint32_t st = sbase + buf * TC_STAGE_BYTES;
-#pragma unroll
-    for (int i = 0; i < kPairsPerThread; ++i) {
-      const int idx = tid + i * TC_THREADS;  // 0..1023: (row, chunk) of one operand tile
-      const int row = idx >> 3, c = idx & 7;
-      uint32_t kA = 0, kB = 0;
+      if ((g >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+    const uint32_t st = sbase + buf * S::STAGE;
+    for (int idx = tid; idx < PAIRS; idx += TC_THREADS) {
+      const bool isA = idx < TC_BM * S::CHUNKS;
+      const int li = isA ? idx : idx - TC_BM * S::CHUNKS;
+      const int row = li / S::CHUNKS, c = li % S::CHUNKS;
+      uint32_t kk = 0;
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        if ((c >> j) & 1) kA |= 1u << p.pAk[j], kB |= 1u << p.pBk[j];
-      const uint32_t so = (row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4);
-      const T* ga = Ab + okA + depA[row] + kA;
-      const T* gb = Bb + okB + depB[row] + kB;
+        if ((c >> j) & 1) kk |= 1u << (isA ? p.pAk[j] : p.pBk[j]);
+      const uint32_t so = swz(row, c, S::ROWB);
+      const T* g0 = isA ? (Ab + okA + depA[row] + kk) : (Bb + okB + depB[row] + kk);
+      const int64_t plane = isA ? p.planeA : p.planeB;
+      const uint32_t d0 = st + (isA ? 0u : uint32_t(2 * S::A_BYTES)) + so;
+      const uint32_t d1 = d0 + (isA ? uint32_t(S::A_BYTES) : uint32_t(S::B_BYTES));
 #if TNC_TC_SELFCHECK
       {
-        const int64_t ea = (ga - reinterpret_cast<const T*>(p.A)) - inst * p.strideA;
-        const int64_t eb = (gb - reinterpret_cast<const T*>(p.B)) - inst * p.strideB;
-        const bool good = ((reinterpret_cast<uintptr_t>(ga) & 15u) == 0) && ((reinterpret_cast<uintptr_t>(gb) & 15u) == 0) &&
-                          ea >= 0 && ea + 8 <= p.planeA && eb >= 0 && eb + 8 <= p.planeB &&
-                          ((st + so) & 15u) == 0 && (st + so + 3 * TC_TILE_BYTES + 16) <= sbase + TC_PIPE_BYTES;
-        if (!tc_check(good, p.status, 13, ea, eb)) continue;
+        const int64_t e = isA ? (g0 - reinterpret_cast<const T*>(p.A)) - inst * p.strideA
+                              : (g0 - reinterpret_cast<const T*>(p.B)) - inst * p.strideB;
+        const bool good = ((reinterpret_cast<uintptr_t>(g0) & 15u) == 0) && e >= 0 && e + 8 <= plane &&
+                          (d0 & 15u) == 0 && d1 + 16 <= sbase + S::PIPE;
+        if (!tc_check(good, p.status, 13, e, isA)) continue;
       }
 #endif
-      cp_async16(st + 0 * TC_TILE_BYTES + so, ga);
-      cp_async16(st + 1 * TC_TILE_BYTES + so, ga + p.planeA);
-      cp_async16(st + 2 * TC_TILE_BYTES + so, gb);
-      cp_async16(st + 3 * TC_TILE_BYTES + so, gb + p.planeB);
+      cp_async16(d0, g0);
+      cp_async16(d1, g0 + plane);
     }
   };
 
   bool ok = true;
-  const uint32_t id_pos = instr_desc(p.bf16, 0), id_neg = instr_desc(p.bf16, 1);
-  for (int s = 0; s < TC_STAGES - 1; ++s) {
+  const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
+  for (int s = 0; s < S::DIST; ++s) {
     if (s < n_iter) load_stage(s, s);
     cp_async_commit();
   }
   for (int it = 0; it < n_iter && ok; ++it) {
-    const int nxt = it + TC_STAGES - 1;
+    const int nxt = it + S::DIST;
     if (nxt < n_iter) {
-      const int buf = nxt % TC_STAGES;
-      if (nxt >= TC_STAGES) ok = mbar_wait_bounded(smem_u32(&bars[buf]), (uint32_t)((nxt / TC_STAGES - 1) & 1), p.status);
+      const int buf = nxt % S::STAGES;
+      // the buffer was last read by the MMAs of iteration nxt - STAGES (= it - 2)
+      if (nxt >= S::STAGES)
+        ok = mbar_wait_bounded(smem_u32(&bars[buf]), (uint32_t)((nxt / S::STAGES - 1) & 1), p.status);
       if (ok) load_stage(nxt, buf);
     }
     cp_async_commit();
-    cp_async_wait<TC_STAGES - 1>();
+    cp_async_wait<S::DIST>();
     fence_async_shared();
     ok = __syncthreads_and(ok);
     if (!ok) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int buf = it % TC_STAGES;
-      const uint32_t st = sbase + buf * TC_STAGE_BYTES;
+      const int buf = it % S::STAGES;
+      const uint32_t st = sbase + buf * S::STAGE;
 #pragma unroll
-      for (int j = 0; j < TC_BK / 16; ++j) {
-        const uint64_t ar = sw128_kmajor_desc(st + 0 * TC_TILE_BYTES + j * 32);
-        const uint64_t ai = sw128_kmajor_desc(st + 1 * TC_TILE_BYTES + j * 32);
-        const uint64_t br = sw128_kmajor_desc(st + 2 * TC_TILE_BYTES + j * 32);
-        const uint64_t bi = sw128_kmajor_desc(st + 3 * TC_TILE_BYTES + j * 32);
+      for (int j = 0; j < BK / 16; ++j) {
+        const uint64_t ar = kmajor_desc(st + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t ai = kmajor_desc(st + S::A_BYTES + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t br = kmajor_desc(st + 2 * S::A_BYTES + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t bi = kmajor_desc(st + 2 * S::A_BYTES + S::B_BYTES + j * 32, S::SBO, S::LAYOUT);
         const uint32_t first = (it == 0 && j == 0) ? 0u : 1u;
-#if TNC_TC_SELFCHECK
-        if (!tc_check(((st + j * 32) & 15u) == 0 && st + 3 * TC_TILE_BYTES + TC_TILE_BYTES <= sbase + TC_PIPE_BYTES,
-                      p.status, 15, st, j))
-          continue;
-        if (blockIdx.x == 0 && it == 0 && j == 0) {
-          p.status[12] = (int32_t)(ar & 0xffffffffu);
-          p.status[13] = (int32_t)(ar >> 32);
-          p.status[14] = (int32_t)id_pos;
-        }
-#endif
-        mma_f16(tmem, ar, br, id_pos, first);             // Dr  = Ar Br
-        mma_f16(tmem, ai, bi, id_neg, 1u);                // Dr -= Ai Bi
-        mma_f16(tmem + TC_BN, ar, bi, id_pos, first);     // Di  = Ar Bi
-        mma_f16(tmem + TC_BN, ai, br, id_pos, 1u);        // Di += Ai Br
+        mma_f16(tmem, ar, br, id_pos, first);        // Dr  = Ar Br
+        mma_f16(tmem, ai, bi, id_neg, 1u);           // Dr -= Ai Bi
+        mma_f16(tmem + BN, ar, bi, id_pos, first);   // Di  = Ar Bi
+        mma_f16(tmem + BN, ai, br, id_pos, 1u);      // Di += Ai Br
       }
       mma_commit(smem_u32(&bars[buf]));
     }
   }
   // all MMAs done (waited for even after a timeout, so TMEM is never freed under them)
-  if (tid == 0) mma_commit(smem_u32(&bars[TC_STAGES]));
-  const bool done = mbar_wait_bounded(smem_u32(&bars[TC_STAGES]), 0u, p.status);
+  if (tid == 0) mma_commit(smem_u32(&bars[S::STAGES]));
+  const bool done = mbar_wait_bounded(smem_u32(&bars[S::STAGES]), 0u, p.status);
   ok = ok && done;
   cp_async_wait<0>();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
 
-  // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
   const int64_t sb = inst * p.n_slots;
+  const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+  const int row = (warp & 3) * 32 + lane;
+  const int col0 = (warp >> 2) * (BN / 2);
+  if (p.splitk > 1) {
+    // FP32 partial sums by C's flat index; k_splitk_reduce sums them in a fixed order
+    if (ok) {
+      float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
+      const uint32_t lowmask = (1u << p.runC) - 1u;
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 2; cc += 32) {
+        float vr[32], vi[32];
+        tmem_ld32(tmem + lane_addr + col0 + cc, vr);
+        tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+        const uint32_t rm = TCm[row];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t t = rm + TCn[col0 + cc + j];
+          part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(vr[j], vi[j]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
+    return;
+  }
+  // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
   int sh = 0;
   {
     const float a = p.maxabs[sb + p.slotA], b = p.maxabs[sb + p.slotB];
@@ -348,27 +388,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
     }
   }
   const float scale = ldexpf(1.f, -sh);
-  T* stg = reinterpret_cast<T*>(smem);  // [2][128*128] re plane then im plane
+  constexpr int CT = TC_BM * BN;  // entries of the C tile
+  T* stg = reinterpret_cast<T*>(smem);  // [2][CT] re plane then im plane
   float mx = 0.f;
   if (ok) {
-    const int row = (warp & 3) * 32 + lane;
-    const int col0 = (warp >> 2) * 64;
-    const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
 #pragma unroll 1
-    for (int cc = 0; cc < 64; cc += 32) {
+    for (int cc = 0; cc < BN / 2; cc += 32) {
       float vr[32], vi[32];
       tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-      tmem_ld32(tmem + lane_addr + TC_BN + col0 + cc, vi);
+      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
       const uint32_t rm = TCm[row];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const uint32_t idx = rm + TCn[col0 + cc + j];
 #if TNC_TC_SELFCHECK
-        if (!tc_check(idx < uint32_t(TC_BM * TC_BN), p.status, 16, idx, row)) continue;
+        if (!tc_check(idx < uint32_t(CT), p.status, 16, idx, row)) continue;
 #endif
         const T re = Conv<T>::from_f(vr[j] * scale), im = Conv<T>::from_f(vi[j] * scale);
         stg[idx] = re;
-        stg[TC_BM * TC_BN + idx] = im;
+        stg[CT + idx] = im;
         mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
       }
     }
@@ -376,31 +414,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
   }
   if (!ok) return;
-  // contiguous runs of C: 16-byte vectors when the run allows
+  // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
   T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
   const uint32_t lowmask = (1u << p.runC) - 1u;
-  if (p.runC >= 3) {
-    for (int t = tid * 8; t < TC_BM * TC_BN; t += TC_THREADS * 8) {
-      const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
+  for (int t = tid * 8; t < CT; t += TC_THREADS * 8) {
+    const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
 #if TNC_TC_SELFCHECK
-      {
-        const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
-        if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
-          continue;
-      }
+    {
+      const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
+      if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
+        continue;
+    }
 #endif
-      *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + t);
-      *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + TC_BM * TC_BN + t);
-    }
-  } else {
-    for (int t = tid; t < TC_BM * TC_BN; t += TC_THREADS) {
-      const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
-      Cre[off] = stg[t];
-      Cre[p.planeC + off] = stg[TC_BM * TC_BN + t];
-    }
+    *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + t);
+    *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + t);
   }
   // block max -> tensor max
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -414,26 +444,45 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
   }
 }
 
-size_t tc_smem_bytes(int runC) {
-  return 1024 + TC_PIPE_BYTES + (TC_BM + TC_BN) * 4 + (size_t(1) << (14 - runC)) * 4 + (TC_BM + TC_BN) * 2 + 64 +
-         (TC_STAGES + 1) * 8 + 16 + 32 * 4 + 64;
+template <int BN, int BK>
+size_t tc_smem_bytes_t(int runC) {
+  using S = TcShape<BN, BK>;
+  return 1024 + S::PIPE + (TC_BM + BN) * 4 + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
+         (S::STAGES + 1) * 8 + 16 + 32 * 4 + 64;
+}
+
+template <typename T, int BN, int BK>
+cudaError_t launch_tc_t(const TcParams& p, dim3 grid, cudaStream_t s) {
+  const size_t smem = tc_smem_bytes_t<BN, BK>(p.runC);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<T, BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_gemm<T, BN, BK><<<grid, TC_THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tc_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (p.bn == 128) {
+    if (p.bk == 64) return launch_tc_t<T, 128, 64>(p, grid, s);
+    if (p.bk == 32) return launch_tc_t<T, 128, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tc_t<T, 128, 16>(p, grid, s);
+  } else if (p.bn == 64) {
+    if (p.bk == 64) return launch_tc_t<T, 64, 64>(p, grid, s);
+    if (p.bk == 32) return launch_tc_t<T, 64, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tc_t<T, 64, 16>(p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t tc_smem_bytes(int bn, int bk, int runC) {
+  if (bn == 128) return bk == 64 ? tc_smem_bytes_t<128, 64>(runC) : bk == 32 ? tc_smem_bytes_t<128, 32>(runC) : tc_smem_bytes_t<128, 16>(runC);
+  return bk == 64 ? tc_smem_bytes_t<64, 64>(runC) : bk == 32 ? tc_smem_bytes_t<64, 32>(runC) : tc_smem_bytes_t<64, 16>(runC);
 }
 
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes(p.runC);
-  cudaError_t e;
-  if (precision == 1) {
-    e = cudaFuncSetAttribute(k_tc_gemm<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<__half><<<grid, TC_THREADS, smem, s>>>(p);
-  } else if (precision == 2) {
-    e = cudaFuncSetAttribute(k_tc_gemm<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<__nv_bfloat16><<<grid, TC_THREADS, smem, s>>>(p);
-  } else {
-    return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  if (precision == 1) return launch_tc_bn_bk<__half>(p, grid, s);
+  if (precision == 2) return launch_tc_bn_bk<__nv_bfloat16>(p, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tnc

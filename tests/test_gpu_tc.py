@@ -52,8 +52,13 @@ def run(ctx, precision, a, la, b, lb, lc):
     return (cc[:n] + 1j * cc[n:]) * 2.0 ** e, aq, bq
 
 
+# (m, k, n): 128/64-wide N tiles, 64/32/16-wide K tiles, role swap (m < n), split over K
+SHAPES = [(7, 6, 7), (8, 8, 8), (9, 10, 7), (7, 12, 9), (10, 7, 8), (8, 15, 6), (9, 4, 8), (8, 5, 9),
+          (6, 8, 9), (7, 4, 10), (7, 14, 6)]
+
+
 @pytest.mark.parametrize("precision", ["chalf", "cbf16"])
-@pytest.mark.parametrize("shape", [(7, 6, 7), (8, 8, 8), (9, 10, 7), (7, 12, 9), (10, 7, 8)])
+@pytest.mark.parametrize("shape", SHAPES)
 def test_tc_contract_elementwise(ctx, precision, shape):
     a, la, b, lb, lc = kmajor_case(*shape, seed=11 * sum(shape) + shape[0])
     got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
