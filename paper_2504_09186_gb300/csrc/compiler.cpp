@@ -170,7 +170,7 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
 }
 
 // Tensor-core tile: 7 row labels from the operand with more free labels (A after an
-// optional swap), 6 or 7 column labels (BN = 64 / 128), 4..6 K labels (BK = 16 / 32 / 64)
+// optional swap), 6 or 7 column labels (BN = 64 / 128), 4 or 5 K labels (BK = 16 / 32)
 // whose first three are the k3 labels at positions 0..2 of both operands.  Returns false
 // if the step does not qualify.
 bool choose_tc_tile(const std::vector<int>& la0, const std::vector<int>& lb0, const std::vector<int>& lc,
@@ -187,8 +187,8 @@ bool choose_tc_tile(const std::vector<int>& la0, const std::vector<int>& lb0, co
   for (int j = 0; j < 3; ++j)
     if (la.size() < 3 || lb.size() < 3 || la[j] != k3[j] || lb[j] != k3[j]) return false;
   bn = N.size() >= 7 ? 128 : 64;
-  bk = K.size() >= 6 ? 64 : (K.size() == 5 ? 32 : 16);
-  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 64 ? 6 : (bk == 32 ? 5 : 4);
+  bk = K.size() >= 5 ? 32 : 16;
+  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 32 ? 5 : 4;
   t = TileSpec();
   t.Kt = k3;
   for (int x : la) {  // further K labels by A position

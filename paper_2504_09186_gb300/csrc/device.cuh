@@ -73,7 +73,8 @@ struct TcParams {
   void* C;
   int64_t strideA, strideB, strideC;
   int64_t planeA, planeB, planeC;
-  int32_t bn, bk;            // tile width (64 / 128) and K tile (16 / 32 / 64)
+  int32_t bn, bk;            // tile width (64 / 128) and K tile (16 / 32)
+  int32_t stages;            // 3 = short pipeline (two CTAs per SM), 0 = deepest
   int8_t pAm[7], pBn[7];     // operand positions of the canonical tile m / n bits
   int8_t pAk[3], pBk[3];     // operand positions of k bits 3..5 (bits 0..2 are positions 0..2)
   int8_t pCm[7], pCn[7];     // C-tile-native bit of canonical m / n bit

@@ -104,7 +104,7 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
                            const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst) {
   TcParams& q = L.tp;
   std::memset(&q, 0, sizeof(q));
-  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 64 ? 6 : (bk == 32 ? 5 : 4);
+  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 32 ? 5 : 4;
   if (t.Mt.size() != 7 || t.Nt.size() != nt || t.Kt.size() != kt) fail(TNC_E_PLAN, "bad tensor-core tile");
   for (int j = 0; j < 3; ++j)
     if (pos_of(la, t.Kt[j]) != j || pos_of(lb, t.Kt[j]) != j) fail(TNC_E_PLAN, "tensor-core operands not K-major");
@@ -145,6 +145,8 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   int split = 1;
   while (tiles * split < 2 * 152 && (int64_t(1) << q.n_ok) / (split * 2) >= 4) split *= 2;
   q.splitk = split;
+  // short K loops: a 3-stage pipeline leaves room for two CTAs per SM
+  q.stages = ((int64_t(1) << q.n_ok) / split) <= 3 ? 3 : 0;
   L.kind = K_TC;
   L.grid = dim3(1u << (q.n_om + q.n_on), (unsigned)split, 1);
   L.smem = 0;

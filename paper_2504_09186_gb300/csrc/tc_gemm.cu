@@ -13,10 +13,12 @@
 // Complex product with planar operands: per 16-wide k step, four MMAs into two FP32
 // accumulators in TMEM,
 //   Dr += Ar Br,  Dr += (-Ai) Bi  (negate-A bit),  Di += Ar Bi,  Di += Ai Br.
-// One thread issues the MMAs; tcgen05.commit signals a per-stage mbarrier so loaders
-// know when a stage may be overwritten (3-stage pipeline).  Every wait is bounded by
-// the global timer; on timeout the kernel records TNC_E_TIMEOUT in a status word, stops
-// issuing work and still releases its TMEM.  The epilogue reads TMEM (tcgen05.ld),
+// Warp-specialized pipeline: warps 0..6 gather stages with cp.async, and after their own
+// copies of a stage have landed (cp.async.wait_group) fence them to the async proxy and
+// arrive on the stage's "full" mbarrier; one thread of warp 7 waits on "full", issues the
+// MMAs and commits them to the stage's "empty" mbarrier, which the loaders wait on before
+// reusing the buffer.  Every wait is bounded by the global timer; on timeout the kernel
+// records TNC_E_TIMEOUT in a status word, stops issuing work and still releases its TMEM.  The epilogue reads TMEM (tcgen05.ld),
 // applies the exact power-of-two scale, converts, stages the tile in shared memory in
 // C's own order and writes contiguous runs.
 #include "device.cuh"
@@ -29,23 +31,31 @@ constexpr int TC_PIPE_BUDGET = 192 * 1024;   // shared memory for the operand pi
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s bound on any wait
 
 // Compile-time shape of one tensor-core kernel instance: BN columns (64 or 128), BK-wide
-// K tiles (16, 32 or 64 fp16 = 32, 64 or 128-byte rows, swizzled 32B / 64B / 128B).
-template <int BN, int BK>
+// K tiles (16 or 32 fp16 = 32 or 64-byte rows, swizzled 32B / 64B), NST pipeline stages.
+template <int BN, int BK, int NST>
 struct TcShape {
   static constexpr int ROWB = BK * 2;                         // bytes per tile row
   static constexpr int A_BYTES = TC_BM * ROWB;                // one plane of the A tile
   static constexpr int B_BYTES = BN * ROWB;                   // one plane of the B tile
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;     // Ar, Ai, Br, Bi
-  static constexpr int STAGES = (TC_PIPE_BUDGET / STAGE) > 8 ? 8 : (TC_PIPE_BUDGET / STAGE);
-  static constexpr int DIST = STAGES - 2;                     // prefetch distance
+  static constexpr int STAGES = NST;
+  static constexpr int DIST = NST - 2;                        // loads in flight per loader
   static constexpr int PIPE = STAGES * STAGE;
+  static constexpr int STG = TC_BM * BN * 2 * 2;              // staged C tile (2 planes, 16-bit)
+  static constexpr int REGION = PIPE > STG ? PIPE : STG;
   static constexpr int SBO = 8 * ROWB;                        // bytes between 8-row groups
   static constexpr int LAYOUT = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // SW128 / SW64 / SW32
   static constexpr int CHUNKS = BK / 8;                        // 16-byte chunks per row
   static constexpr int TMEM_COLS = 2 * BN;                     // Dr, Di
   static constexpr int C_BITS = 7 + (BN == 128 ? 7 : 6);       // log2 entries of the C tile
-  static_assert(STAGES >= 3, "pipeline needs at least 3 stages");
+  static_assert(STAGES >= 3 && PIPE <= TC_PIPE_BUDGET, "bad pipeline");
 };
+// deepest pipeline that fits the budget, at most 8 stages
+template <int BN, int BK>
+constexpr int tc_deep_stages() {
+  return (TC_PIPE_BUDGET / (2 * TC_BM * BK * 2 + 2 * BN * BK * 2)) > 8 ? 8
+                                                                       : (TC_PIPE_BUDGET / (2 * TC_BM * BK * 2 + 2 * BN * BK * 2));
+}
 
 // Byte offset of 16-byte chunk c of row r in a swizzled K-major tile with `rowb`-byte rows:
 // the chunk index is XORed with address bits 7.. (the Swizzle<log2(rowb/16), 4, 3> pattern).
@@ -116,6 +126,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
 // Bounded wait; returns false (and records a timeout) if the phase did not complete.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int32_t* status) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -182,20 +195,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <typename T, int BN, int BK>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
-  using S = TcShape<BN, BK>;
+template <typename T, int BN, int BK, int NST>
+__global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(const TcParams p) {
+  using S = TcShape<BN, BK, NST>;
+  constexpr int LOADERS = TC_THREADS - 32;  // warps 0..6 load, warp 7 issues the MMAs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // 1024-byte aligned pipeline buffers (the swizzle pattern is address based)
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint32_t* depA = reinterpret_cast<uint32_t*>(smem + S::PIPE);          // [128] row offsets in A
+  uint32_t* depA = reinterpret_cast<uint32_t*>(smem + S::REGION);        // [128] row offsets in A
   uint32_t* depB = depA + TC_BM;                                         // [BN] row offsets in B
   uint32_t* hiC = depB + BN;                                             // [2^(C_BITS - runC)]
   const int nhC = 1 << (S::C_BITS - p.runC);
   uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);               // [128]
   uint16_t* TCn = TCm + TC_BM;                                           // [BN]
   uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + S::STAGES + 1);
+  uint64_t* full = bars;                    // [NST] loads of a stage have landed
+  uint64_t* empty = bars + NST;             // [NST] MMAs reading a stage have completed
+  uint64_t* done = bars + 2 * NST;          // all MMAs have completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -238,7 +255,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
     hiC[h] = r;
   }
   if (tid == 0) {
-    for (int s = 0; s <= S::STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&full[s]), LOADERS);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -274,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
     for (int j = 0; j < p.n_ok; ++j)
       if ((g >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
     const uint32_t st = sbase + buf * S::STAGE;
-    for (int idx = tid; idx < PAIRS; idx += TC_THREADS) {
+    for (int idx = tid; idx < PAIRS; idx += LOADERS) {
       const bool isA = idx < TC_BM * S::CHUNKS;
       const int li = isA ? idx : idx - TC_BM * S::CHUNKS;
       const int row = li / S::CHUNKS, c = li % S::CHUNKS;
@@ -302,28 +323,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
   };
 
   bool ok = true;
-  const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
-  for (int s = 0; s < S::DIST; ++s) {
-    if (s < n_iter) load_stage(s, s);
-    cp_async_commit();
-  }
-  for (int it = 0; it < n_iter && ok; ++it) {
-    const int nxt = it + S::DIST;
-    if (nxt < n_iter) {
-      const int buf = nxt % S::STAGES;
-      // the buffer was last read by the MMAs of iteration nxt - STAGES (= it - 2)
-      if (nxt >= S::STAGES)
-        ok = mbar_wait_bounded(smem_u32(&bars[buf]), (uint32_t)((nxt / S::STAGES - 1) & 1), p.status);
-      if (ok) load_stage(nxt, buf);
+  if (warp < 7) {
+    // loaders
+    for (int it = 0; it < n_iter && ok; ++it) {
+      const int buf = it % NST;
+      // the buffer was last read by the MMAs of iteration it - NST
+      if (it >= NST) ok = mbar_wait_bounded(smem_u32(&empty[buf]), (uint32_t)((it / NST - 1) & 1), p.status);
+      if (!ok) break;
+      load_stage(it, buf);
+      cp_async_commit();
+      if (it >= S::DIST) {
+        cp_async_wait<S::DIST>();  // own copies of iteration it - DIST have landed
+        fence_async_shared();
+        mbar_arrive(smem_u32(&full[(it - S::DIST) % NST]));
+      }
     }
-    cp_async_commit();
-    cp_async_wait<S::DIST>();
+    cp_async_wait<0>();
     fence_async_shared();
-    ok = __syncthreads_and(ok);
-    if (!ok) break;
-    if (tid == 0) {
+    if (ok)
+      for (int it = n_iter - S::DIST > 0 ? n_iter - S::DIST : 0; it < n_iter; ++it) mbar_arrive(smem_u32(&full[it % NST]));
+  } else if (lane == 0) {
+    // MMA issuer
+    const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
+    for (int it = 0; it < n_iter; ++it) {
+      const int buf = it % NST;
+      if (!mbar_wait_bounded(smem_u32(&full[buf]), (uint32_t)((it / NST) & 1), p.status)) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int buf = it % S::STAGES;
       const uint32_t st = sbase + buf * S::STAGE;
 #pragma unroll
       for (int j = 0; j < BK / 16; ++j) {
@@ -337,14 +365,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
         mma_f16(tmem + BN, ar, bi, id_pos, first);   // Di  = Ar Bi
         mma_f16(tmem + BN, ai, br, id_pos, 1u);      // Di += Ai Br
       }
-      mma_commit(smem_u32(&bars[buf]));
+      mma_commit(smem_u32(&empty[buf]));
     }
+    mma_commit(smem_u32(done));  // arrives once every MMA issued above has completed
   }
   // all MMAs done (waited for even after a timeout, so TMEM is never freed under them)
-  if (tid == 0) mma_commit(smem_u32(&bars[S::STAGES]));
-  const bool done = mbar_wait_bounded(smem_u32(&bars[S::STAGES]), 0u, p.status);
-  ok = ok && done;
-  cp_async_wait<0>();
+  const bool fin = mbar_wait_bounded(smem_u32(done), 0u, p.status);
+  ok = ok && fin;
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
 
@@ -444,39 +471,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const TcParams p) {
   }
 }
 
-template <int BN, int BK>
+template <int BN, int BK, int NST>
 size_t tc_smem_bytes_t(int runC) {
-  using S = TcShape<BN, BK>;
-  return 1024 + S::PIPE + (TC_BM + BN) * 4 + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
-         (S::STAGES + 1) * 8 + 16 + 32 * 4 + 64;
+  using S = TcShape<BN, BK, NST>;
+  return 1024 + S::REGION + (TC_BM + BN) * 4 + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
+         (2 * NST + 1) * 8 + 16 + 32 * 4 + 64;
 }
 
-template <typename T, int BN, int BK>
+template <typename T, int BN, int BK, int NST>
 cudaError_t launch_tc_t(const TcParams& p, dim3 grid, cudaStream_t s) {
-  const size_t smem = tc_smem_bytes_t<BN, BK>(p.runC);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<T, BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = tc_smem_bytes_t<BN, BK, NST>(p.runC);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<T, BN, BK, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_tc_gemm<T, BN, BK><<<grid, TC_THREADS, smem, s>>>(p);
+  k_tc_gemm<T, BN, BK, NST><<<grid, TC_THREADS, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// p.stages: 3 (short K loops: two CTAs share an SM) or 0 (deepest pipeline)
+template <typename T, int BN, int BK>
+cudaError_t launch_tc_st(const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (p.stages == 3) return launch_tc_t<T, BN, BK, 3>(p, grid, s);
+  return launch_tc_t<T, BN, BK, tc_deep_stages<BN, BK>()>(p, grid, s);
 }
 
 template <typename T>
 cudaError_t launch_tc_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
   if (p.bn == 128) {
-    if (p.bk == 64) return launch_tc_t<T, 128, 64>(p, grid, s);
-    if (p.bk == 32) return launch_tc_t<T, 128, 32>(p, grid, s);
-    if (p.bk == 16) return launch_tc_t<T, 128, 16>(p, grid, s);
+    if (p.bk == 32) return launch_tc_st<T, 128, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tc_st<T, 128, 16>(p, grid, s);
   } else if (p.bn == 64) {
-    if (p.bk == 64) return launch_tc_t<T, 64, 64>(p, grid, s);
-    if (p.bk == 32) return launch_tc_t<T, 64, 32>(p, grid, s);
-    if (p.bk == 16) return launch_tc_t<T, 64, 16>(p, grid, s);
+    if (p.bk == 32) return launch_tc_st<T, 64, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tc_st<T, 64, 16>(p, grid, s);
   }
   return cudaErrorInvalidValue;
-}
-
-size_t tc_smem_bytes(int bn, int bk, int runC) {
-  if (bn == 128) return bk == 64 ? tc_smem_bytes_t<128, 64>(runC) : bk == 32 ? tc_smem_bytes_t<128, 32>(runC) : tc_smem_bytes_t<128, 16>(runC);
-  return bk == 64 ? tc_smem_bytes_t<64, 64>(runC) : bk == 32 ? tc_smem_bytes_t<64, 32>(runC) : tc_smem_bytes_t<64, 16>(runC);
 }
 
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s) {
