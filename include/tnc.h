@@ -126,6 +126,12 @@ tnc_status tnc_plan_sliced_cuts(tnc_plan p, int32_t* qubit, int32_t* cut, int32_
 /* Open qubits in result order (first = most significant bit of the result index). */
 tnc_status tnc_plan_open_qubits(tnc_plan p, int32_t* qubits, int32_t cap);
 
+/* Replace the gate matrices of a plan's circuit (same gates, qubits and order; new values),
+ * e.g. for a variational circuit.  The leaf tensors are re-formed on the host; the tree,
+ * slices and compiled program are unchanged, and device programs re-upload the leaves
+ * on their next use.  matrices: n_gates x 32 doubles as in tnc_circuit_from_gates. */
+tnc_status tnc_plan_update_gates(tnc_plan p, int64_t n_gates, const double* matrices);
+
 /* The whole plan as JSON text (network edges as [qubit, cut, kind, open], leaves with
  * their labels and gates, sliced edge ids, the tree as SSA pairs over tensor ids, every
  * tensor's labels in storage order and arena offset, the compiled steps with their
@@ -175,7 +181,8 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts
  * reverse: for a step C = A * B, dL/dA = contract(dL/dC, B) and dL/dB = contract(A,
  * dL/dC), the same pairwise contraction kind as the forward steps (Sec. II-A).
  *  weights  batch x 2^n_open complex128 interleaved (host)
- *  env_out  n_gates x 32 doubles (host): dL/dU_g, row-major, zero-padded to 4x4
+ *  env_out  n_gates x 32 doubles (host): dL/dU_g as d x d row-major complex (d = 2 or 4) in
+ *           the first d*d entries, the layout of the matrices of tnc_circuit_from_gates
  *  amp_out  optional (may be NULL): the amplitudes, as tnc_amplitudes
  * Computed in C64 (FP32) with the FP64 cross-slice accumulation. */
 tnc_status tnc_adjoint(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,

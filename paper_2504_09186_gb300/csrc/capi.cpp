@@ -160,6 +160,22 @@ tnc_status tnc_plan_open_qubits(tnc_plan p, int32_t* qubits, int32_t cap) {
   });
 }
 
+tnc_status tnc_plan_update_gates(tnc_plan p, int64_t n_gates, const double* matrices) {
+  return guarded([&] {
+    if (!p || (!matrices && n_gates > 0)) fail(TNC_E_INVALID_ARG, "NULL argument");
+    Plan& P = p->p;
+    if (n_gates != (int64_t)P.net.circ.gates.size()) fail(TNC_E_INVALID_ARG, "gate count differs from the plan's circuit");
+    std::vector<Gate> gates = P.net.circ.gates;
+    for (int64_t g = 0; g < n_gates; ++g) {
+      const int d = 1 << gates[g].arity;
+      for (int i = 0; i < 16; ++i) gates[g].m[i] = 0;
+      for (int i = 0; i < d * d; ++i) gates[g].m[i] = cd(matrices[32 * g + 2 * i], matrices[32 * g + 2 * i + 1]);
+    }
+    update_gates(P.net, gates);
+    P.gate_version++;
+  });
+}
+
 tnc_status tnc_plan_save(tnc_plan p, const char* path) {
   return guarded([&] {
     if (!p || !path) fail(TNC_E_INVALID_ARG, "NULL argument");

@@ -31,6 +31,10 @@ cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_str
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s);
 cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                                 const int8_t* open_pos, int n_open, const int32_t* inst_row, int64_t inst_base,
+                                 int64_t n_inst, const double2* w, const int32_t* erow, float* maxabs, int32_t* exps,
+                                 int n_slots, int slot, cudaStream_t s);
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
@@ -257,6 +261,7 @@ struct DeviceProgram {
   int64_t root_off = 0, root_plane = 1;
   int n_open = 0;
   int n_qubits = 0;
+  uint64_t leaf_version = 0;
   ~DeviceProgram() {
     arena.release();
     maxabs.release();
@@ -324,6 +329,37 @@ namespace tnc {
 
 void release_plan_device(tnc_plan_s* p) { p->programs.clear(); }
 
+// FP64 leaf sources and gather descriptors; dst[i] = arena offset (scalars) of reduced leaf i.
+// Synchronous copies: callers drain the stream first when buffers may be in use.
+static void upload_leaves(const Plan& P, const std::vector<int64_t>& dst, DevBuf& srcb, DevBuf& descb) {
+  std::vector<double2> src;
+  std::vector<LeafDesc> desc;
+  for (size_t i = 0; i < P.net.leaves.size(); ++i) {
+    const Leaf& lf = P.net.leaves[i];
+    LeafDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.src = (int64_t)src.size();
+    for (const cd& v : lf.t.data) src.push_back(make_double2(v.real(), v.imag()));
+    d.dst = dst[i];
+    d.rank_full = (int)lf.t.labels.size();
+    d.rank = (int)P.tensors[i].labels.size();
+    d.slot = (int)i;
+    const auto& fx = P.leaf_fix[i];
+    if (fx.size() > 8 || d.rank > 5) fail(TNC_E_UNSUPPORTED, "leaf with too many legs");
+    d.nfix = (int)fx.size();
+    for (size_t f = 0; f < fx.size(); ++f) {
+      d.fix_pos[f] = (int8_t)fx[f].pos;
+      d.fix_kind[f] = (int8_t)fx[f].kind;
+      d.fix_idx[f] = (int16_t)fx[f].index;
+    }
+    desc.push_back(d);
+  }
+  srcb.reserve(std::max<size_t>(1, src.size()) * sizeof(double2));
+  descb.reserve(std::max<size_t>(1, desc.size()) * sizeof(LeafDesc));
+  CUDA_OK(cudaMemcpy(srcb.p, src.data(), src.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CUDA_OK(cudaMemcpy(descb.p, desc.data(), desc.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice));
+}
+
 static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W) {
   const Plan& P = plan->p;
   auto prog = std::make_shared<DeviceProgram>();
@@ -339,32 +375,12 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   prog->maxabs.reserve(size_t(prog->n_slots) * W * sizeof(float));
   prog->exps.reserve(size_t(prog->n_slots) * W * sizeof(int32_t));
   // leaves: FP64 sources + descriptors
-  std::vector<double2> src;
-  std::vector<LeafDesc> desc;
-  for (int i = 0; i < prog->n_leaves; ++i) {
-    const Leaf& lf = P.net.leaves[i];
-    LeafDesc d;
-    std::memset(&d, 0, sizeof(d));
-    d.src = (int64_t)src.size();
-    for (const cd& v : lf.t.data) src.push_back(make_double2(v.real(), v.imag()));
-    d.dst = P.tensors[i].offset;
-    d.rank_full = (int)lf.t.labels.size();
-    d.rank = (int)P.tensors[i].labels.size();
-    d.slot = i;
-    const auto& fx = P.leaf_fix[i];
-    if (fx.size() > 8 || d.rank > 5) fail(TNC_E_UNSUPPORTED, "leaf with too many legs");
-    d.nfix = (int)fx.size();
-    for (size_t f = 0; f < fx.size(); ++f) {
-      d.fix_pos[f] = (int8_t)fx[f].pos;
-      d.fix_kind[f] = (int8_t)fx[f].kind;
-      d.fix_idx[f] = (int16_t)fx[f].index;
-    }
-    desc.push_back(d);
+  {
+    std::vector<int64_t> dst(prog->n_leaves);
+    for (int i = 0; i < prog->n_leaves; ++i) dst[i] = P.tensors[i].offset;
+    upload_leaves(P, dst, prog->leaf_src, prog->leaf_desc);
+    prog->leaf_version = P.gate_version;
   }
-  prog->leaf_src.reserve(std::max<size_t>(1, src.size()) * sizeof(double2));
-  prog->leaf_desc.reserve(std::max<size_t>(1, desc.size()) * sizeof(LeafDesc));
-  CUDA_OK(cudaMemcpy(prog->leaf_src.p, src.data(), src.size() * sizeof(double2), cudaMemcpyHostToDevice));
-  CUDA_OK(cudaMemcpy(prog->leaf_desc.p, desc.data(), desc.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice));
   // steps
   size_t partial_elems = 0;
   for (size_t s = 0; s < P.steps.size(); ++s) {
@@ -561,6 +577,13 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       plan->programs[key] = prog;
     } else {
       prog = it->second;
+      if (prog->leaf_version != P.gate_version) {
+        CUDA_OK(cudaStreamSynchronize(s));
+        std::vector<int64_t> dst(prog->n_leaves);
+        for (int i = 0; i < prog->n_leaves; ++i) dst[i] = P.tensors[i].offset;
+        upload_leaves(P, dst, prog->leaf_src, prog->leaf_desc);
+        prog->leaf_version = P.gate_version;
+      }
     }
     // instance tables: row-major over (row, slice)
     std::vector<int64_t> inst_slice(n_inst);
@@ -723,15 +746,6 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
   });
 }
 
-tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
-                       int64_t batch, const double* weights, double* env_out, double* amp_out, void* stream) {
-  return guarded([&] {
-    (void)ctx; (void)plan; (void)opts; (void)bitstrings; (void)batch; (void)weights; (void)env_out; (void)amp_out;
-    (void)stream;
-    fail(TNC_E_UNSUPPORTED, "tnc_adjoint: not built yet");
-  });
-}
-
 tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,
                             int32_t* kind, int32_t cap, int32_t* n) {
   return guarded([&] {
@@ -853,5 +867,235 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
     CUDA_OK(cudaMemcpyAsync(&e, ex + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
     *c_exp2 = e;
+  });
+}
+
+// ------------------------------------------------------------------ adjoint contraction
+// Reverse-mode walk of the contraction tree (complex64 arithmetic, FP64 accumulation over
+// instances).  Forward intermediates are kept (one arena slot each); every tensor X gets
+// an adjoint slot X' = dL/dX.  For a forward step C = A * B the backward steps are
+//   A' = C' * B   (summed over B's free labels, result in A's layout),
+//   B' = A * C'   (summed over A's free labels, result in B's layout),
+// the same pairwise contraction as the forward steps (Sec. II-A).  The leaves' adjoints
+// are read back, placed at their fixed (sliced / output) leg values and summed in FP64;
+// the host then applies the chain rule from leaves to gates.
+tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                       int64_t batch, const double* weights, double* env_out, double* amp_out, void* stream) {
+  return guarded([&] {
+    if (!ctx || !plan || !weights || !env_out) fail(TNC_E_INVALID_ARG, "NULL argument");
+    (void)opts;
+    const Plan& P = plan->p;
+    const int n = P.net.circ.n;
+    if (batch < 1) fail(TNC_E_INVALID_ARG, "batch must be >= 1");
+    const bool all_open = (int)P.net.open_qubits.size() == n;
+    if (!bitstrings && !(batch == 1 && all_open)) fail(TNC_E_INVALID_ARG, "bitstrings required");
+    std::vector<uint8_t> bits(size_t(batch) * n, 0);
+    if (bitstrings) {
+      std::memcpy(bits.data(), bitstrings, bits.size());
+      for (uint8_t b : bits)
+        if (b > 1) fail(TNC_E_INVALID_ARG, "bitstring bytes must be 0 or 1");
+    }
+    set_device(ctx);
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctx->stream;
+    const int T = (int)P.tensors.size();
+    const int L = (int)P.net.leaves.size();
+    const int n_open = (int)P.net.open_qubits.size();
+    const int64_t n_out = int64_t(1) << n_open;
+    const int64_t n_slices = int64_t(1) << P.sliced.size();
+    const int64_t n_inst = batch * n_slices;
+    // arena: forward tensors, then adjoint leaves (contiguous, for one read-back copy), then
+    // the other adjoints; every slot distinct
+    std::vector<int64_t> off(2 * T);
+    int64_t top = 0;
+    auto take = [&](int slot, int rank) {
+      off[slot] = top;
+      top += ((int64_t(2) << rank) + 63) & ~int64_t(63);
+    };
+    for (int t = 0; t < T; ++t) take(t, (int)P.tensors[t].labels.size());
+    const int64_t adj_leaf_begin = top;
+    for (int t = 0; t < L; ++t) take(T + t, (int)P.tensors[t].labels.size());
+    const int64_t adj_leaf_end = top;
+    for (int t = L; t < T; ++t) take(T + t, (int)P.tensors[t].labels.size());
+    const int64_t stride = (top + 63) & ~int64_t(63);
+    size_t free_b = 0, total_b = 0;
+    CUDA_OK(cudaMemGetInfo(&free_b, &total_b));
+    int64_t W = std::max<int64_t>(1, (int64_t)(std::min(double(free_b) * 0.5, 64.0 * (1ull << 30)) / (double(stride) * 4 * 1.1)));
+    W = std::min<int64_t>({W, n_inst, 4096});
+    DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, wdev, erow;
+    arena.reserve(size_t(stride) * 4 * W + 256);
+    maxabs.reserve(size_t(2 * T) * W * sizeof(float));
+    exps.reserve(size_t(2 * T) * W * sizeof(int32_t));
+    {
+      std::vector<int64_t> dst(L);
+      for (int i = 0; i < L; ++i) dst[i] = off[i];
+      upload_leaves(P, dst, leaf_src, leaf_desc);
+    }
+    // launches
+    std::vector<StepLaunch> fwd, bwd;
+    size_t partial_elems = 0;
+    auto bind = [&](StepLaunch& Lh, int sa, int sb, int sc) {
+      char* base = arena.as<char>();
+      Lh.p.A = base + off[sa] * 4;
+      Lh.p.B = base + off[sb] * 4;
+      Lh.p.C = base + off[sc] * 4;
+      Lh.p.strideA = Lh.p.strideB = Lh.p.strideC = stride;
+      Lh.p.n_slots = 2 * T;
+      Lh.p.slotA = sa;
+      Lh.p.slotB = sb;
+      Lh.p.slotC = sc;
+      if (Lh.kind == K_SPLITK) partial_elems = std::max(partial_elems, size_t(W) * Lh.p.splitk * Lh.p.planeC);
+    };
+    for (const Step& st : P.steps) {
+      StepLaunch Lh = make_launch(st.tile, st.kind, P.tensors[st.a].labels, P.tensors[st.b].labels, P.tensors[st.c].labels);
+      bind(Lh, st.a, st.b, st.c);
+      fwd.push_back(Lh);
+    }
+    for (size_t k = P.steps.size(); k-- > 0;) {
+      const Step& st = P.steps[k];
+      const auto& la = P.tensors[st.a].labels;
+      const auto& lb = P.tensors[st.b].labels;
+      const auto& lc = P.tensors[st.c].labels;
+      int kind = K_GENERIC;
+      TileSpec ta = tile_for(lc, lb, la, (int)W, kind);  // A' = C' * B
+      StepLaunch La = make_launch(ta, kind, lc, lb, la);
+      bind(La, T + st.c, st.b, T + st.a);
+      bwd.push_back(La);
+      kind = K_GENERIC;
+      TileSpec tb = tile_for(la, lc, lb, (int)W, kind);  // B' = A * C'
+      StepLaunch Lb = make_launch(tb, kind, la, lc, lb);
+      bind(Lb, st.a, T + st.c, T + st.b);
+      bwd.push_back(Lb);
+    }
+    if (partial_elems) {
+      partials.reserve(partial_elems * sizeof(float2));
+      for (auto* v : {&fwd, &bwd})
+        for (auto& Lh : *v)
+          if (Lh.kind == K_SPLITK) Lh.p.partials = partials.as<float2>();
+    }
+    for (auto* v : {&fwd, &bwd})
+      for (auto& Lh : *v) {
+        Lh.p.maxabs = maxabs.as<float>();
+        Lh.p.exps = exps.as<int32_t>();
+      }
+    const int root = P.root;
+    std::vector<int8_t> opos(std::max(1, n_open), 0);
+    for (int j = 0; j < n_open; ++j) opos[j] = (int8_t)pos_of(P.tensors[root].labels, P.net.open_edge[j]);
+    open_pos.reserve(opos.size());
+    CUDA_OK(cudaMemcpy(open_pos.p, opos.data(), opos.size(), cudaMemcpyHostToDevice));
+    // weights and their per-row exponents (stored cotangents below 1 in magnitude)
+    std::vector<int32_t> er(batch, 0);
+    for (int64_t b = 0; b < batch; ++b) {
+      double m = 0;
+      for (int64_t o = 0; o < n_out; ++o)
+        m = std::max({m, std::fabs(weights[2 * (b * n_out + o)]), std::fabs(weights[2 * (b * n_out + o) + 1])});
+      int ex = 0;
+      if (m > 0) std::frexp(m, &ex);
+      er[b] = ex;
+    }
+    wdev.reserve(size_t(batch) * n_out * sizeof(double2));
+    erow.reserve(size_t(batch) * sizeof(int32_t));
+    CUDA_OK(cudaMemcpy(wdev.p, weights, size_t(batch) * n_out * sizeof(double2), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(erow.p, er.data(), er.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // instance tables (row-major over (row, slice)) and root segments per wave
+    std::vector<int64_t> inst_slice(n_inst);
+    std::vector<int32_t> inst_row(n_inst);
+    for (int64_t b = 0; b < batch; ++b)
+      for (int64_t t = 0; t < n_slices; ++t) {
+        inst_slice[b * n_slices + t] = t;
+        inst_row[b * n_slices + t] = (int32_t)b;
+      }
+    ctx->bits.reserve(std::max<size_t>(1, bits.size()));
+    ctx->inst_slice.reserve(n_inst * sizeof(int64_t));
+    ctx->inst_row.reserve(n_inst * sizeof(int32_t));
+    CUDA_OK(cudaMemcpy(ctx->bits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(ctx->inst_slice.p, inst_slice.data(), n_inst * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(ctx->inst_row.p, inst_row.data(), n_inst * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (amp_out) ctx->acc.reserve(size_t(batch) * n_out * sizeof(double2));
+    if (amp_out) CUDA_OK(cudaMemsetAsync(ctx->acc.p, 0, size_t(batch) * n_out * sizeof(double2), s));
+    // FP64 leaf environments (full leaf tensors, fixed legs included)
+    std::vector<SmallTensor> leaf_env(L);
+    for (int i = 0; i < L; ++i) {
+      leaf_env[i].labels = P.net.leaves[i].t.labels;
+      leaf_env[i].data.assign(P.net.leaves[i].t.data.size(), cd(0, 0));
+    }
+    const int64_t leaf_region = adj_leaf_end - adj_leaf_begin;
+    std::vector<float> host_leaf(size_t(leaf_region) * W);
+    std::vector<int32_t> host_exp(size_t(2 * T) * W);
+    std::vector<RootSeg> segs;
+    for (int64_t base = 0; base < n_inst; base += W) {
+      const int64_t cnt = std::min<int64_t>(W, n_inst - base);
+      CUDA_OK(cudaMemsetAsync(maxabs.p, 0, size_t(2 * T) * cnt * sizeof(float), s));
+      CUDA_OK(launch_leaf_gather(TNC_C64, leaf_desc.as<LeafDesc>(), L, leaf_src.as<double2>(), arena.p, stride,
+                                 ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(), n,
+                                 maxabs.as<float>(), exps.as<int32_t>(), 2 * T, base, cnt, s));
+      for (const StepLaunch& Lh : fwd) run_step(TNC_C64, Lh, cnt, s);
+      if (amp_out) {
+        segs.clear();
+        for (int64_t i = 0; i < cnt; ++i) {
+          const int row = inst_row[base + i];
+          if (i == 0 || segs.back().row != row) segs.push_back({row, (int32_t)i, (int32_t)i + 1});
+          else segs.back().end = (int32_t)i + 1;
+        }
+        ctx->segs.reserve(segs.size() * sizeof(RootSeg));
+        CUDA_OK(cudaMemcpyAsync(ctx->segs.p, segs.data(), segs.size() * sizeof(RootSeg), cudaMemcpyHostToDevice, s));
+        CUDA_OK(launch_root_accum(TNC_C64, arena.p, stride, off[root], int64_t(1) << P.tensors[root].labels.size(),
+                                  open_pos.as<int8_t>(), n_open, ctx->segs.as<RootSeg>(), (int)segs.size(),
+                                  exps.as<int32_t>(), 2 * T, root, ctx->acc.as<double2>(), s));
+      }
+      CUDA_OK(launch_adj_root_init(arena.as<float>(), stride, off[T + root], int64_t(1) << P.tensors[root].labels.size(),
+                                   open_pos.as<int8_t>(), n_open, ctx->inst_row.as<int32_t>(), base, cnt,
+                                   wdev.as<double2>(), erow.as<int32_t>(), maxabs.as<float>(), exps.as<int32_t>(), 2 * T,
+                                   T + root, s));
+      for (const StepLaunch& Lh : bwd) run_step(TNC_C64, Lh, cnt, s);
+      // read back the leaves' adjoints and exponents
+      CUDA_OK(cudaMemcpy2DAsync(host_leaf.data(), size_t(leaf_region) * 4, arena.as<char>() + adj_leaf_begin * 4,
+                                size_t(stride) * 4, size_t(leaf_region) * 4, (size_t)cnt, cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaMemcpyAsync(host_exp.data(), exps.p, size_t(2 * T) * cnt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+      check_status(ctx);
+      for (int64_t i = 0; i < cnt; ++i) {
+        const int64_t g = base + i;
+        const int64_t slice = inst_slice[g];
+        const int row = inst_row[g];
+        for (int l = 0; l < L; ++l) {
+          const int rk = (int)P.tensors[l].labels.size();
+          const int64_t nrk = int64_t(1) << rk;
+          const float* v = host_leaf.data() + size_t(i) * leaf_region + (off[T + l] - adj_leaf_begin);
+          const double sc = std::ldexp(1.0, host_exp[size_t(i) * 2 * T + T + l]);
+          const auto& fx = P.leaf_fix[l];
+          const int rf = (int)P.net.leaves[l].t.labels.size();
+          for (int64_t x = 0; x < nrk; ++x) {
+            int64_t full = 0;
+            int fb = 0;
+            size_t f = 0;
+            for (int pos = 0; pos < rf; ++pos) {
+              int bit;
+              if (f < fx.size() && fx[f].pos == pos) {
+                bit = fx[f].kind == 0 ? int((slice >> fx[f].index) & 1) : int(bits[size_t(row) * n + fx[f].index]);
+                ++f;
+              } else {
+                bit = int((x >> fb) & 1);
+                ++fb;
+              }
+              full |= int64_t(bit) << pos;
+            }
+            leaf_env[l].data[full] += cd(double(v[x]) * sc, double(v[nrk + x]) * sc);
+          }
+        }
+      }
+    }
+    std::vector<std::vector<cd>> genv;
+    gate_envs_from_leaf_envs(P.net, leaf_env, genv);
+    for (size_t g = 0; g < genv.size(); ++g)
+      for (int i = 0; i < 16; ++i) {
+        env_out[32 * g + 2 * i] = genv[g][i].real();
+        env_out[32 * g + 2 * i + 1] = genv[g][i].imag();
+      }
+    if (amp_out) {
+      CUDA_OK(cudaMemcpyAsync(amp_out, ctx->acc.p, size_t(batch) * n_out * sizeof(double2), cudaMemcpyDeviceToHost, s));
+      CUDA_OK(cudaStreamSynchronize(s));
+    }
+    arena.release();
+    partials.release();
   });
 }

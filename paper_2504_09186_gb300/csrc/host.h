@@ -73,6 +73,15 @@ void build_network(const Circuit& c, const std::vector<uint8_t>& open_mask, Netw
 SmallTensor small_contract(const SmallTensor& a, const SmallTensor& b, const std::vector<int>& out_labels);
 SmallTensor small_fix(const SmallTensor& a, int label, int value);
 
+// Replace the gate matrices (same structure) and re-form every leaf.
+void update_gates(Network& net, const std::vector<Gate>& gates);
+
+// Per-gate environments dL/dU_g from leaf environments (dL/d leaf over the leaf's labels):
+// each leaf is multilinear in its gates, so dL/dU_g contracts the leaf environment with the
+// leaf's other gates (and |0> on fixed input legs).  out[g] = d x d row-major [out, in].
+void gate_envs_from_leaf_envs(const Network& net, const std::vector<SmallTensor>& leaf_env,
+                              std::vector<std::vector<cd>>& out);
+
 // ------------------------------------------------------------------ plan
 struct PlanOpts {
   uint64_t seed = 1;
@@ -152,6 +161,7 @@ struct Plan {
   int n_gemm = 0, n_gepdot = 0, n_absorb = 0, n_fused = 0;
   double narrow_max = 0;
   bool fuse = true;
+  uint64_t gate_version = 0;               // bumped whenever the gate matrices change
 };
 
 void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan);

@@ -386,6 +386,47 @@ __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, i
   a->y += im;
 }
 
+// Root cotangent of every instance: dL/droot[o] = w[row, o] (holomorphic derivative of
+// L = sum w * amp), stored as FP32 times 2^-e_row with e_row from the row's largest |w|.
+__global__ void k_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                                const int8_t* __restrict__ open_pos, int n_open, const int32_t* __restrict__ inst_row,
+                                int64_t inst_base, const double2* __restrict__ w, const int32_t* __restrict__ erow,
+                                float* maxabs, int32_t* exps, int n_slots, int slot) {
+  __shared__ float red[32];
+  const int64_t n_out = int64_t(1) << n_open;
+  const int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t inst = blockIdx.y;
+  const int row = inst_row[inst_base + inst];
+  const int e = erow[row];
+  float mx = 0.f;
+  if (o < n_out) {
+    int64_t idx = 0;
+    for (int j = 0; j < n_open; ++j) idx |= ((o >> (n_open - 1 - j)) & 1) << open_pos[j];
+    const double2 v = w[int64_t(row) * n_out + o];
+    float* r = arena + inst * inst_stride + root_off;
+    const float re = (float)ldexp(v.x, -e), im = (float)ldexp(v.y, -e);
+    r[idx] = re;
+    r[plane + idx] = im;
+    mx = fmaxf(fabsf(re), fabsf(im));
+  }
+  const float bm = block_max(mx, red);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&maxabs[inst * n_slots + slot], bm);
+    if (blockIdx.x == 0) exps[inst * n_slots + slot] = e;
+  }
+}
+
+cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
+                                 const int8_t* open_pos, int n_open, const int32_t* inst_row, int64_t inst_base,
+                                 int64_t n_inst, const double2* w, const int32_t* erow, float* maxabs, int32_t* exps,
+                                 int n_slots, int slot, cudaStream_t s) {
+  const int64_t n_out = int64_t(1) << n_open;
+  dim3 grid((unsigned)((n_out + 255) / 256), (unsigned)n_inst);
+  k_adj_root_init<<<grid, 256, 0, s>>>(arena, inst_stride, root_off, plane, open_pos, n_open, inst_row, inst_base, w,
+                                       erow, maxabs, exps, n_slots, slot);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_maxabs(const T* __restrict__ x, int64_t n, float* out) {
   __shared__ float red[32];

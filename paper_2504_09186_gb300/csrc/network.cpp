@@ -7,6 +7,7 @@
 // kept as legs that the device fixes per bitstring, open outputs stay free.
 #include <algorithm>
 #include <map>
+#include <string>
 #include <numeric>
 
 #include "host.h"
@@ -92,6 +93,107 @@ static std::vector<int> free_labels(const std::vector<int>& a, const std::vector
   return out;
 }
 
+// Tensor of one gate over its legs [out legs..., in legs...]: flat bit s = out leg s
+// (bit (arity-1-s) of the matrix row), bit arity+s = in leg s.
+static SmallTensor gate_tensor(const Gate& g, const std::vector<int>& labels) {
+  SmallTensor t;
+  t.labels = labels;
+  const int d = 1 << g.arity;
+  t.data.assign(size_t(d) * d, cd(0, 0));
+  for (int o = 0; o < d; ++o)
+    for (int i = 0; i < d; ++i) {
+      size_t idx = 0;
+      for (int s = 0; s < g.arity; ++s) {
+        idx |= size_t((o >> (g.arity - 1 - s)) & 1) << s;
+        idx |= size_t((i >> (g.arity - 1 - s)) & 1) << (g.arity + s);
+      }
+      t.data[idx] = g.m[o * d + i];
+    }
+  return t;
+}
+
+// Leaf = contraction of its gates (circuit order), then |0> fixed on input legs.
+static SmallTensor form_leaf(const Network& net, const Leaf& lf) {
+  SmallTensor t = gate_tensor(net.circ.gates[lf.gates[0]], net.gate_labels[lf.gates[0]]);
+  for (size_t m = 1; m < lf.gates.size(); ++m) {
+    const SmallTensor u = gate_tensor(net.circ.gates[lf.gates[m]], net.gate_labels[lf.gates[m]]);
+    t = small_contract(t, u, free_labels(t.labels, u.labels));
+  }
+  for (int e : std::vector<int>(t.labels))
+    if (net.edges[e].kind == EDGE_INPUT) t = small_fix(t, e, 0);
+  return t;
+}
+
+void update_gates(Network& net, const std::vector<Gate>& gates) {
+  if (gates.size() != net.circ.gates.size()) fail(1, "update_gates: gate count differs");
+  for (size_t g = 0; g < gates.size(); ++g) {
+    const Gate& a = net.circ.gates[g];
+    if (gates[g].arity != a.arity || gates[g].q[0] != a.q[0] || (a.arity == 2 && gates[g].q[1] != a.q[1]))
+      fail(1, "update_gates: gate " + std::to_string(g) + " changes qubits or arity");
+  }
+  net.circ.gates = gates;
+  for (Leaf& lf : net.leaves)
+    if (!lf.gates.empty()) {
+      SmallTensor t = form_leaf(net, lf);
+      if (t.labels != lf.t.labels) fail(5, "update_gates: leaf labels changed");
+      lf.t = t;
+    }
+}
+
+void gate_envs_from_leaf_envs(const Network& net, const std::vector<SmallTensor>& leaf_env,
+                              std::vector<std::vector<cd>>& out) {
+  out.assign(net.circ.gates.size(), std::vector<cd>(16, cd(0, 0)));
+  const SmallTensor e0{{-1}, {cd(1, 0), cd(0, 0)}};
+  for (size_t li = 0; li < net.leaves.size(); ++li) {
+    const Leaf& lf = net.leaves[li];
+    for (size_t j = 0; j < lf.gates.size(); ++j) {
+      const int gj = lf.gates[j];
+      const std::vector<int>& mine = net.gate_labels[gj];
+      SmallTensor t = leaf_env[li];
+      for (size_t k = 0; k < lf.gates.size(); ++k) {
+        if (k == j) continue;
+        const int gk = lf.gates[k];
+        SmallTensor u = gate_tensor(net.circ.gates[gk], net.gate_labels[gk]);
+        // |0> on the other gate's fixed input legs
+        for (int e : std::vector<int>(u.labels))
+          if (net.edges[e].kind == EDGE_INPUT) u = small_fix(u, e, 0);
+        std::vector<int> keep;
+        for (int x : t.labels)
+          if (std::find(u.labels.begin(), u.labels.end(), x) == u.labels.end() ||
+              std::find(mine.begin(), mine.end(), x) != mine.end())
+            keep.push_back(x);
+        for (int x : u.labels)
+          if (std::find(t.labels.begin(), t.labels.end(), x) == t.labels.end()) keep.push_back(x);
+        t = small_contract(t, u, keep);
+      }
+      // env over the gate's own legs; fixed input legs carry |0>
+      for (int x : mine) {
+        if (std::find(t.labels.begin(), t.labels.end(), x) != t.labels.end()) continue;
+        if (net.edges[x].kind != EDGE_INPUT) fail(5, "chain rule: missing gate leg");
+        SmallTensor v = e0;
+        v.labels = {x};
+        std::vector<int> both = t.labels;
+        both.push_back(x);
+        t = small_contract(t, v, both);
+      }
+      if (t.labels.size() != mine.size()) fail(5, "chain rule: environment labels do not match the gate");
+      const Gate& g = net.circ.gates[gj];
+      const int d = 1 << g.arity;
+      std::vector<int> pos(mine.size());
+      for (size_t s = 0; s < mine.size(); ++s) pos[s] = find_pos(t.labels, mine[s]);
+      for (int o = 0; o < d; ++o)
+        for (int i = 0; i < d; ++i) {
+          size_t idx = 0;
+          for (int s = 0; s < g.arity; ++s) {
+            idx |= size_t((o >> (g.arity - 1 - s)) & 1) << pos[s];
+            idx |= size_t((i >> (g.arity - 1 - s)) & 1) << pos[g.arity + s];
+          }
+          out[gj][o * d + i] += t.data[idx];  // d x d row-major, as the gate matrices
+        }
+    }
+  }
+}
+
 void build_network(const Circuit& c, const std::vector<uint8_t>& open_mask, Network& net) {
   const int n = c.n;
   net = Network();
@@ -112,29 +214,15 @@ void build_network(const Circuit& c, const std::vector<uint8_t>& open_mask, Netw
       net.edges.push_back(e);
     }
   }
-  // per-gate tensors
-  std::vector<SmallTensor> gt(c.gates.size());
+  // per-gate legs: [out legs..., in legs...]
   std::vector<int> pos(n, 0);
   std::vector<std::vector<int>> gates_on(n);
   net.gate_labels.resize(c.gates.size());
   for (size_t gi = 0; gi < c.gates.size(); ++gi) {
     const Gate& g = c.gates[gi];
-    SmallTensor& t = gt[gi];
-    for (int s = 0; s < g.arity; ++s) t.labels.push_back(seg[g.q[s]][pos[g.q[s]] + 1]);
-    for (int s = 0; s < g.arity; ++s) t.labels.push_back(seg[g.q[s]][pos[g.q[s]]]);
-    const int d = 1 << g.arity;
-    t.data.assign(size_t(d) * d, cd(0, 0));
-    for (int o = 0; o < d; ++o)
-      for (int i = 0; i < d; ++i) {
-        // flat bit s = out leg s (bit (arity-1-s) of o), bit arity+s = in leg s
-        size_t idx = 0;
-        for (int s = 0; s < g.arity; ++s) {
-          idx |= size_t((o >> (g.arity - 1 - s)) & 1) << s;
-          idx |= size_t((i >> (g.arity - 1 - s)) & 1) << (g.arity + s);
-        }
-        t.data[idx] = g.m[o * d + i];
-      }
-    net.gate_labels[gi] = t.labels;
+    std::vector<int>& labels = net.gate_labels[gi];
+    for (int s = 0; s < g.arity; ++s) labels.push_back(seg[g.q[s]][pos[g.q[s]] + 1]);
+    for (int s = 0; s < g.arity; ++s) labels.push_back(seg[g.q[s]][pos[g.q[s]]]);
     for (int s = 0; s < g.arity; ++s) {
       gates_on[g.q[s]].push_back((int)gi);
       pos[g.q[s]]++;
@@ -165,16 +253,7 @@ void build_network(const Circuit& c, const std::vector<uint8_t>& open_mask, Netw
   for (auto& kv : members) {
     Leaf leaf;
     leaf.gates = kv.second;  // circuit order
-    SmallTensor t = gt[leaf.gates[0]];
-    for (size_t m = 1; m < leaf.gates.size(); ++m) {
-      const SmallTensor& u = gt[leaf.gates[m]];
-      t = small_contract(t, u, free_labels(t.labels, u.labels));
-    }
-    // fix |0> inputs
-    for (int e : std::vector<int>(t.labels)) {
-      if (net.edges[e].kind == EDGE_INPUT) t = small_fix(t, e, 0);
-    }
-    leaf.t = t;
+    leaf.t = form_leaf(net, leaf);
     net.leaves.push_back(leaf);
   }
   // qubits without any gate: a rank-1 |0> leaf on their single segment

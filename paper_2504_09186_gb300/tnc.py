@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "tnc_plan_open_qubits": [vp, C.POINTER(C.c_int32), i32],
         "tnc_plan_describe": [vp, C.c_char_p, i64, C.POINTER(C.c_int64)],
         "tnc_plan_save": [vp, C.c_char_p],
+        "tnc_plan_update_gates": [vp, i64, C.POINTER(C.c_double)],
         "tnc_plan_load": [C.c_char_p, C.POINTER(vp)],
         "tnc_context_create": [i32, C.POINTER(vp)],
         "tnc_amplitudes": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, i64, i64, vp, vp],
@@ -207,6 +208,19 @@ class Plan:
         p.n_qubits = p.describe()["n_qubits"]
         return p
 
+    def update_gates(self, matrices):
+        """New gate values for the same gates: a list of d x d complex arrays U[out, in]
+        (d = 2 or 4), or the packed (n_gates, 32) float64 layout of the C boundary."""
+        if isinstance(matrices, np.ndarray) and matrices.dtype == np.float64 and matrices.ndim == 2:
+            packed = np.ascontiguousarray(matrices)
+        else:
+            packed = np.zeros((len(matrices), 32))
+            for g, u in enumerate(matrices):
+                flat = np.asarray(u, dtype=np.complex128).reshape(-1)
+                packed[g, 0 : 2 * flat.size : 2] = flat.real
+                packed[g, 1 : 2 * flat.size : 2] = flat.imag
+        _check(load_library().tnc_plan_update_gates(self.h, len(packed), packed.ctypes.data_as(C.POINTER(C.c_double))))
+
     def save(self, path: str):
         _check(load_library().tnc_plan_save(self.h, path.encode()))
 
@@ -283,6 +297,33 @@ class Context:
         _check(lib.tnc_amplitudes(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count,
                                   C.c_void_p(ptr), C.c_void_p(stream)))
         return out
+
+    def adjoint(self, plan: Plan, bitstrings: Optional[np.ndarray], weights: np.ndarray, arities, stream: int = 0):
+        """Gate environments dL/dU_g of L = sum_{b,i} weights[b, i] * amp[b, i] (holomorphic
+        derivative), over all slices.  `arities` lists each gate's arity (1 or 2).  Returns
+        (list of d x d complex128 arrays, amplitudes (batch, 2^n_open))."""
+        lib = load_library()
+        info = plan.info()
+        n_out = 1 << info["n_open"]
+        if bitstrings is None:
+            batch, bp = 1, None
+        else:
+            bs = np.ascontiguousarray(bitstrings, dtype=np.uint8)
+            if bs.ndim == 1:
+                bs = bs[None, :]
+            batch, bp = bs.shape[0], bs.ctypes.data_as(C.POINTER(C.c_uint8))
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128).reshape(batch, n_out))
+        n_gates = len(arities)
+        env = np.zeros((n_gates, 32))
+        amps = np.zeros((batch, n_out), dtype=np.complex128)
+        opts = tnc_exec_opts(TNC_C64, 0, 0, 1, 0)
+        _check(lib.tnc_adjoint(self.h, plan.h, C.byref(opts), bp, batch, C.c_void_p(w.ctypes.data),
+                               C.c_void_p(env.ctypes.data), C.c_void_p(amps.ctypes.data), C.c_void_p(stream)))
+        out = []
+        for g, a in enumerate(arities):
+            d = 1 << int(a)
+            out.append((env[g, 0 : 2 * d * d : 2] + 1j * env[g, 1 : 2 * d * d : 2]).reshape(d, d))
+        return out, amps
 
     def profile_read(self, cap: int = 4096) -> dict:
         """Per-step device times of the last profiled amplitudes call (see tnc_profile_read)."""
