@@ -289,7 +289,7 @@ def run_ours(args):
     kind = int(prof["kind"][k])
     flops_launch = prof["flops"][k] / prof["launches"][k]
     bytes_launch = prof["bytes"][k] / prof["launches"][k]
-    if kind == 3:
+    if kind in (3, 4):
         achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
     elif flops_launch / bytes_launch > 8.0:

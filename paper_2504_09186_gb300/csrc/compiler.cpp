@@ -99,7 +99,7 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     break;
   }
   // grow the tiles by class, one label at a time while the limits hold
-  const bool gepdot = (m + n <= 8) && (k >= 12);
+  const bool gepdot = (m + n <= 10) && (k >= 12);
   auto grow = [&](std::vector<int>& tile, const std::vector<int>& pool, int target) {
     for (int x : pool) {
       if ((int)tile.size() >= target) break;
@@ -259,29 +259,74 @@ void compile_plan(Plan& plan, bool fuse) {
     }
     plan.tensors.push_back(ti);
   }
-  // tensor-core candidates (decided on label sets, before layouts): both operands are
-  // intermediates and M, N >= 2^7, K >= 2^6.  Their three canonical common labels (the
-  // smallest ids) must sit at positions 0..2 of both operands.
+  // Tensor-core steps, decided on label sets from the root down: a step qualifies when both
+  // operands are intermediates, M >= 2^7 rows (the larger operand A), N >= 2^6 columns and
+  // K >= 2^4.  Its tile is Kt (4 or 5 common labels), Mt (7 of A's free labels) and Nt (6, 7
+  // or 8 of B's), and it requires its operands' layouts to start with Kt then Mt (A) / Nt (B):
+  // every operand tile is then one contiguous block, a plain box for the tensor memory
+  // accelerator.  Mt / Nt include the first three labels its own consumer requires of its
+  // output, so the output tile covers the output's lowest positions (contiguous stores).
   const int n_leaves = L;
+  const int n_tree = (int)plan.tree.size();
   std::vector<std::vector<int>> sets(L);
   for (int i = 0; i < L; ++i) {
     sets[i] = plan.tensors[i].labels;
     std::sort(sets[i].begin(), sets[i].end());
   }
-  std::vector<int> consumer(L + plan.tree.size(), -1);
-  std::vector<std::vector<int>> k3_of_step(plan.tree.size());
-  for (size_t s = 0; s < plan.tree.size(); ++s) {
+  for (int s = 0; s < n_tree; ++s) {
     const auto& A = sets[plan.tree[s].first];
     const auto& B = sets[plan.tree[s].second];
-    std::vector<int> K, U;
-    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(K));
+    std::vector<int> U;
     std::set_symmetric_difference(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(U));
     sets.push_back(U);
-    consumer[plan.tree[s].first] = (int)s;
-    consumer[plan.tree[s].second] = (int)s;
-    const int m = (int)A.size() - (int)K.size(), n = (int)B.size() - (int)K.size();
-    const bool inter = plan.tree[s].first >= n_leaves && plan.tree[s].second >= n_leaves;
-    if (inter && std::max(m, n) >= 7 && std::min(m, n) >= 6 && K.size() >= 4) k3_of_step[s] = {K[0], K[1], K[2]};
+  }
+  struct TcDec {
+    bool ok = false;
+    int bn = 128, bk = 32;
+    TileSpec t;
+  };
+  std::vector<TcDec> dec(n_tree);
+  std::vector<std::vector<int>> req(L + n_tree);  // required leading labels of each intermediate
+  for (int s = n_tree - 1; s >= 0; --s) {
+    int a = plan.tree[s].first, b = plan.tree[s].second;
+    if (sets[b].size() > sets[a].size()) std::swap(a, b);  // same roles as the layouts below
+    const auto& A = sets[a];
+    const auto& B = sets[b];
+    std::vector<int> K, M, N;
+    std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(K));
+    std::set_difference(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(M));
+    std::set_difference(B.begin(), B.end(), A.begin(), A.end(), std::back_inserter(N));
+    if (a < n_leaves || b < n_leaves || M.size() < 7 || N.size() < 6 || K.size() < 4) continue;
+    TcDec d;
+    d.ok = true;
+    d.bk = K.size() >= 5 ? 32 : 16;
+    // 256-wide tiles take a whole SM (all TMEM); with one or two K tiles the epilogue
+    // dominates, and 128-wide tiles let two CTAs per SM overlap it
+    const size_t kt0 = d.bk == 32 ? 5 : 4;
+    d.bn = (N.size() >= 8 && K.size() > kt0 + 1) ? 256 : (N.size() >= 7 ? 128 : 64);
+    const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : 6);
+    d.t.Kt.assign(K.begin(), K.begin() + kt);
+    const std::vector<int>& rq = req[n_leaves + s];
+    for (size_t j = 0; j < rq.size() && j < 3; ++j) {
+      if (contains(M, rq[j])) d.t.Mt.push_back(rq[j]);
+      else if (contains(N, rq[j])) d.t.Nt.push_back(rq[j]);
+    }
+    for (int x : M)
+      if (d.t.Mt.size() < 7 && !contains(d.t.Mt, x)) d.t.Mt.push_back(x);
+    for (int x : N)
+      if (d.t.Nt.size() < nt && !contains(d.t.Nt, x)) d.t.Nt.push_back(x);
+    for (int x : M)
+      if (!contains(d.t.Mt, x)) d.t.Mo.push_back(x);
+    for (int x : N)
+      if (!contains(d.t.Nt, x)) d.t.No.push_back(x);
+    for (int x : K)
+      if (!contains(d.t.Kt, x)) d.t.Ko.push_back(x);
+    if (d.t.Mt.size() != 7 || d.t.Nt.size() != nt || d.t.Mo.size() + d.t.No.size() > 30 || d.t.Ko.size() > 24) continue;
+    req[a] = d.t.Kt;
+    req[a].insert(req[a].end(), d.t.Mt.begin(), d.t.Mt.end());
+    req[b] = d.t.Kt;
+    req[b].insert(req[b].end(), d.t.Nt.begin(), d.t.Nt.end());
+    dec[s] = d;
   }
   // intermediates
   plan.steps.clear();
@@ -295,13 +340,12 @@ void compile_plan(Plan& plan, bool fuse) {
     TensorInfo ci;
     ci.labels = output_layout(plan.tensors[a].labels, plan.tensors[b].labels);
     const int cid = (int)plan.tensors.size();
-    if (consumer[cid] >= 0 && !k3_of_step[consumer[cid]].empty()) {
-      // put the consumer's canonical common labels at positions 0..2, in order
-      const auto& k3 = k3_of_step[consumer[cid]];
+    if (!req[cid].empty()) {
+      // the consumer's tensor-core tile labels lead, in order; the rest keep their order
       std::vector<int> rest;
       for (int x : ci.labels)
-        if (!contains(k3, x)) rest.push_back(x);
-      ci.labels = k3;
+        if (!contains(req[cid], x)) rest.push_back(x);
+      ci.labels = req[cid];
       ci.labels.insert(ci.labels.end(), rest.begin(), rest.end());
     }
     ci.producer = (int)s;
@@ -323,8 +367,21 @@ void compile_plan(Plan& plan, bool fuse) {
     int kind = K_GENERIC;
     st.tile = choose_tile(la, lb, lc, 1, kind);
     st.kind = kind;
-    st.tc_ok = !k3_of_step[s].empty() &&
-               choose_tc_tile(la, lb, lc, k3_of_step[s], st.tc_tile, st.tc_swap, st.tc_bn, st.tc_bk);
+    st.tc_ok = dec[s].ok;
+    if (st.tc_ok) {
+      st.tc_tile = dec[s].t;
+      st.tc_swap = false;  // rows come from a (the larger operand)
+      st.tc_bn = dec[s].bn;
+      st.tc_bk = dec[s].bk;
+      // the layouts honour the requirement: operands lead with Kt + Mt / Kt + Nt
+      const size_t kt = st.tc_tile.Kt.size();
+      for (size_t j = 0; j < kt; ++j)
+        if (la[j] != st.tc_tile.Kt[j] || lb[j] != st.tc_tile.Kt[j]) fail(5, "compile: tensor-core K labels not leading");
+      for (size_t j = 0; j < st.tc_tile.Mt.size(); ++j)
+        if (la[kt + j] != st.tc_tile.Mt[j]) fail(5, "compile: tensor-core M labels not leading");
+      for (size_t j = 0; j < st.tc_tile.Nt.size(); ++j)
+        if (lb[kt + j] != st.tc_tile.Nt[j]) fail(5, "compile: tensor-core N labels not leading");
+    }
     int nk = 0;
     for (int x : la) nk += contains(lb, x);
     int nm = (int)la.size() - nk, nn = (int)lb.size() - nk;

@@ -1,6 +1,7 @@
 // Device-side parameter blocks and storage helpers shared by the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -68,16 +69,17 @@ struct LeafDesc {
 
 // Tensor-core complex GEMM step (tc_gemm.cu): 128 x 128 x 64 tiles.
 struct TcParams {
+  CUtensorMap tmA, tmB;      // TMA descriptors of A and B (tensor-memory-accelerator path only)
   const void* A;
   const void* B;
   void* C;
   int64_t strideA, strideB, strideC;
   int64_t planeA, planeB, planeC;
-  int32_t bn, bk;            // tile width (64 / 128) and K tile (16 / 32)
+  int32_t bn, bk;            // tile width (64 / 128 / 256) and K tile (16 / 32)
   int32_t stages;            // 3 = short pipeline (two CTAs per SM), 0 = deepest
-  int8_t pAm[7], pBn[7];     // operand positions of the canonical tile m / n bits
+  int8_t pAm[7], pBn[8];     // operand positions of the canonical tile m / n bits
   int8_t pAk[3], pBk[3];     // operand positions of k bits 3..5 (bits 0..2 are positions 0..2)
-  int8_t pCm[7], pCn[7];     // C-tile-native bit of canonical m / n bit
+  int8_t pCm[7], pCn[8];     // C-tile-native bit of canonical m / n bit
   uint32_t maskC;            // C positions of the tile (m and n labels)
   int32_t runC;
   int32_t n_om, n_on, n_ok;

@@ -18,6 +18,7 @@
 
 #include "capi_internal.h"
 #include "device.cuh"
+#include <cudaTypedefs.h>
 
 namespace tnc {
 
@@ -36,6 +37,7 @@ cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root
                                  int64_t n_inst, const double2* w, const int32_t* erow, float* maxabs, int32_t* exps,
                                  int n_slots, int slot, cudaStream_t s);
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
+cudaError_t launch_tc_tma(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
 bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t,
@@ -108,7 +110,7 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
                            const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst) {
   TcParams& q = L.tp;
   std::memset(&q, 0, sizeof(q));
-  const size_t nt = bn == 128 ? 7 : 6, kt = bk == 32 ? 5 : 4;
+  const size_t nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6), kt = bk == 32 ? 5 : 4;
   if (t.Mt.size() != 7 || t.Nt.size() != nt || t.Kt.size() != kt) fail(TNC_E_PLAN, "bad tensor-core tile");
   for (int j = 0; j < 3; ++j)
     if (pos_of(la, t.Kt[j]) != j || pos_of(lb, t.Kt[j]) != j) fail(TNC_E_PLAN, "tensor-core operands not K-major");
@@ -159,6 +161,79 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   L.p.planeC = q.planeC;
   L.p.splitk = split;
   L.p.nK = q.nK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CUDA_OK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !ptr) fail(TNC_E_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+// 4-D view of a planar 16-bit tensor laid out [Kt (2^kt entries) | rows ...]:
+// (k, row, plane, instance) with a box of 2^kt x box_rows x 1 x 1, swizzled to match the
+// K-major shared-memory layout of the MMA (32B swizzle for 32-byte rows, 64B for 64-byte).
+static void encode_tile_map(CUtensorMap* m, const void* base, int rank, int kt, int box_rows, int64_t inst_stride,
+                            int64_t n_inst) {
+  if ((int64_t(1) << (rank - kt)) < box_rows || rank > 32) fail(TNC_E_PLAN, "tensor map: operand rank out of range");
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) fail(TNC_E_PLAN, "tensor map: base not 16-byte aligned");
+  const int64_t plane = int64_t(1) << rank;
+  const int64_t istr = std::max<int64_t>(inst_stride, 2 * plane);
+  cuuint64_t dims[4] = {cuuint64_t(1) << kt, cuuint64_t(1) << (rank - kt), 2, (cuuint64_t)std::max<int64_t>(1, n_inst)};
+  cuuint64_t strides[3] = {(cuuint64_t(1) << kt) * 2, (cuuint64_t)plane * 2, (cuuint64_t)istr * 2};
+  cuuint32_t box[4] = {1u << kt, (cuuint32_t)box_rows, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = kt == 5 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+  const CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims, strides,
+                                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(TNC_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+}
+
+// Operands already laid out for the TMA kernel: A leads with Kt then 7 of its free labels, B
+// with Kt then 6 or 7 of its free labels, and C's lowest three labels are tile labels.
+static bool tma_tile_from_layout(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
+                                 TileSpec& t, int& bn, int& bk) {
+  std::vector<int> K, M, N;
+  for (int x : la) (std::find(lb.begin(), lb.end(), x) != lb.end() ? K : M).push_back(x);
+  for (int x : lb)
+    if (std::find(la.begin(), la.end(), x) == la.end()) N.push_back(x);
+  if (M.size() < 7 || N.size() < 6 || K.size() < 4) return false;
+  bk = K.size() >= 5 ? 32 : 16;
+  bn = (N.size() >= 8 && K.size() > size_t(bk == 32 ? 6 : 5)) ? 256 : (N.size() >= 7 ? 128 : 64);
+  const size_t kt = bk == 32 ? 5 : 4, nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6);
+  if (la.size() < kt + 7 || lb.size() < kt + nt || lc.size() < 3) return false;
+  auto in = [](const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
+  t = TileSpec();
+  for (size_t j = 0; j < kt; ++j) {
+    if (la[j] != lb[j] || !in(K, la[j])) return false;
+    t.Kt.push_back(la[j]);
+  }
+  for (size_t j = 0; j < 7; ++j) {
+    if (!in(M, la[kt + j])) return false;
+    t.Mt.push_back(la[kt + j]);
+  }
+  for (size_t j = 0; j < nt; ++j) {
+    if (!in(N, lb[kt + j])) return false;
+    t.Nt.push_back(lb[kt + j]);
+  }
+  for (int j = 0; j < 3; ++j)
+    if (!in(t.Mt, lc[j]) && !in(t.Nt, lc[j])) return false;
+  for (int x : M)
+    if (!in(t.Mt, x)) t.Mo.push_back(x);
+  for (int x : N)
+    if (!in(t.Nt, x)) t.No.push_back(x);
+  for (int x : K)
+    if (!in(t.Kt, x)) t.Ko.push_back(x);
+  return t.Mo.size() + t.No.size() <= 30 && t.Ko.size() <= 24;
 }
 
 // Fills the pointers of a tensor-core launch (and of its reduce, when split).
@@ -310,6 +385,7 @@ struct tnc_context_s {
   int sm_count = 0;
   DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status;
   bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
+  bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
   ProfState prof;
   ~tnc_context_s() {
     bits.release();
@@ -395,6 +471,13 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
       bind_tc(L, prog->arena.as<char>() + P.tensors[ta].offset * eb, prog->arena.as<char>() + P.tensors[tb].offset * eb,
               prog->arena.as<char>() + P.tensors[st.c].offset * eb, prog->inst_stride, prog->maxabs.as<float>(),
               prog->exps.as<int32_t>(), prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), nullptr);
+      if (!ctx->no_tma) {
+        // operands are laid out [Kt | Mt/Nt | ...] by the compiler: load tiles with TMA
+        const int kt = st.tc_bk == 32 ? 5 : 4;
+        encode_tile_map(&L.tp.tmA, L.tp.A, (int)P.tensors[ta].labels.size(), kt, 128, prog->inst_stride, W);
+        encode_tile_map(&L.tp.tmB, L.tp.B, (int)P.tensors[tb].labels.size(), kt, st.tc_bn, prog->inst_stride, W);
+        L.kind = K_TMA;
+      }
       if (L.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * L.tp.splitk * L.tp.planeC);
       prog->steps.push_back(L);
       continue;
@@ -416,7 +499,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     prog->partials.reserve(partial_elems * sizeof(float2));
     for (auto& L : prog->steps) {
       if (L.kind == K_SPLITK) L.p.partials = prog->partials.as<float2>();
-      if (L.kind == K_TC && L.tp.splitk > 1) L.tp.partials = L.p.partials = prog->partials.as<float2>();
+      if ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1) L.tp.partials = L.p.partials = prog->partials.as<float2>();
     }
   }
   // root
@@ -464,8 +547,9 @@ static bool is_device_ptr(const void* p) {
 static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s) {
   StepLaunch L = L0;
   L.grid.z = (unsigned)n_inst;
-  if (L.kind == K_TC) {
-    CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
+  if (L.kind == K_TC || L.kind == K_TMA) {
+    if (L.kind == K_TMA) CUDA_OK(launch_tc_tma(precision, L.tp, L.grid, s));
+    else CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
     if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
     return;
   }
@@ -506,6 +590,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     }
     const char* env = std::getenv("TNC_NO_TC");
     c->no_tc = env && env[0] == '1';
+    const char* env2 = std::getenv("TNC_NO_TMA");
+    c->no_tma = env2 && env2[0] == '1';
     *out = c;
   });
 }
@@ -726,7 +812,25 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
     TileSpec tct;
     bool swap = false;
     int bn = 128, bk = 64;
-    if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct, swap, bn, bk)) {
+    const bool tma_a = precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma && tma_tile_from_layout(la, lb, lc, tct, bn, bk);
+    const bool tma_b = !tma_a && precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma &&
+                       tma_tile_from_layout(lb, la, lc, tct, bn, bk);
+    if (tma_a || tma_b) {
+      const std::vector<int>& ra = tma_a ? la : lb;
+      const std::vector<int>& rb = tma_a ? lb : la;
+      make_tc_launch(L, tct, ra, rb, lc, precision, bn, bk, 1);
+      float2* part = nullptr;
+      if (L.tp.splitk > 1) {
+        ctx->partials.reserve(size_t(L.tp.splitk) * L.tp.planeC * sizeof(float2));
+        part = ctx->partials.as<float2>();
+      }
+      bind_tc(L, tma_a ? a : b, tma_a ? b : a, c, 0, mx, ex, 3, tma_a ? 0 : 1, tma_a ? 1 : 0, 2, ctx->status.as<int32_t>(),
+              part);
+      const int kt = bk == 32 ? 5 : 4;
+      encode_tile_map(&L.tp.tmA, L.tp.A, (int)ra.size(), kt, 128, 0, 1);
+      encode_tile_map(&L.tp.tmB, L.tp.B, (int)rb.size(), kt, bn, 0, 1);
+      L.kind = K_TMA;
+    } else if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct, swap, bn, bk)) {
       make_tc_launch(L, tct, swap ? lb : la, swap ? la : lb, lc, precision, bn, bk, 1);
       float2* part = nullptr;
       if (L.tp.splitk > 1) {

@@ -97,7 +97,8 @@ enum StepKind {
   K_GENERIC = 0,   // tiled gather contraction (SIMT FP32), any shape
   K_SPLITK = 1,    // GEPDOT: same tiles, split over outer common indices + fixed-order reduce
   K_CHAIN = 2,     // fused chain of small absorptions into one big tensor (Sec. IV)
-  K_TC = 3,        // tcgen05 complex GEMM (fp16/bf16 operands, FP32 in TMEM)
+  K_TC = 3,        // tcgen05 complex GEMM, cp.async gathered tiles (fp16/bf16, FP32 in TMEM)
+  K_TMA = 4,       // tcgen05 complex GEMM, TMA-loaded tiles (operands laid out [Kt | Mt/Nt | ...])
 };
 
 // Tile description of one pairwise contraction (all label ids are edge ids).

@@ -30,7 +30,7 @@ constexpr int TC_THREADS = 256;
 constexpr int TC_PIPE_BUDGET = 192 * 1024;   // shared memory for the operand pipeline
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s bound on any wait
 
-// Compile-time shape of one tensor-core kernel instance: BN columns (64 or 128), BK-wide
+// Compile-time shape of one tensor-core kernel instance: BN columns (64, 128 or 256), BK-wide
 // K tiles (16 or 32 fp16 = 32 or 64-byte rows, swizzled 32B / 64B), NST pipeline stages.
 template <int BN, int BK, int NST>
 struct TcShape {
@@ -47,7 +47,8 @@ struct TcShape {
   static constexpr int LAYOUT = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // SW128 / SW64 / SW32
   static constexpr int CHUNKS = BK / 8;                        // 16-byte chunks per row
   static constexpr int TMEM_COLS = 2 * BN;                     // Dr, Di
-  static constexpr int C_BITS = 7 + (BN == 128 ? 7 : 6);       // log2 entries of the C tile
+  static constexpr int N_BITS = BN == 256 ? 8 : (BN == 128 ? 7 : 6);
+  static constexpr int C_BITS = 7 + N_BITS;                    // log2 entries of the C tile
   static_assert(STAGES >= 3 && PIPE <= TC_PIPE_BUDGET, "bad pipeline");
 };
 // deepest pipeline that fits the budget, at most 8 stages
@@ -126,6 +127,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// 4-D tiled TMA load (coordinates innermost first) completing on an mbarrier.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
@@ -193,6 +206,116 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Staging-buffer swizzle: 16-byte chunks of each 128-byte group are permuted by higher index
+// bits, so the threads of a warp (one tile row each) do not all hit one bank when rows are
+// far apart in C's order; reads of whole 16-byte chunks stay contiguous.
+__device__ __forceinline__ uint32_t stg_swz(uint32_t idx) {
+  return idx ^ ((((idx >> 7) ^ (idx >> 10) ^ (idx >> 13)) & 7u) << 3);
+}
+
+// Epilogue shared by both tensor-core kernels: TMEM -> registers -> (split: FP32 partials)
+// or (scale, convert, stage in C's own order, contiguous 16-byte stores); frees TMEM.
+template <typename T, int BN, int TMEM_COLS>
+__device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bool ok, unsigned char* smem,
+                                            const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC, float* red,
+                                            int64_t oC, int64_t inst) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t sb = inst * p.n_slots;
+  const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+  const int row = (warp & 3) * 32 + lane;
+  const int col0 = (warp >> 2) * (BN / 2);
+  if (p.splitk > 1) {
+    // FP32 partial sums by C's flat index; k_splitk_reduce sums them in a fixed order
+    if (ok) {
+      float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
+      const uint32_t lowmask = (1u << p.runC) - 1u;
+#pragma unroll 1
+      for (int cc = 0; cc < BN / 2; cc += 32) {
+        float vr[32], vi[32];
+        tmem_ld32(tmem + lane_addr + col0 + cc, vr);
+        tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+        const uint32_t rm = TCm[row];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t t = rm + TCn[col0 + cc + j];
+          part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(vr[j], vi[j]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    return;
+  }
+  // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
+  int sh = 0;
+  {
+    const float a = p.maxabs[sb + p.slotA], b = p.maxabs[sb + p.slotB];
+    if (a > 0.f && b > 0.f) {
+      int ea, eb;
+      frexpf(a, &ea);
+      frexpf(b, &eb);
+      sh = ea + eb + p.nK + 1 - 15;
+    }
+  }
+  const float scale = ldexpf(1.f, -sh);
+  constexpr int CT = TC_BM * BN;  // entries of the C tile
+  T* stg = reinterpret_cast<T*>(smem);  // [2][CT] re plane then im plane
+  float mx = 0.f;
+  if (ok) {
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 2; cc += 32) {
+      float vr[32], vi[32];
+      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
+      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+      const uint32_t rm = TCm[row];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const uint32_t idx = rm + TCn[col0 + cc + j];
+#if TNC_TC_SELFCHECK
+        if (!tc_check(idx < uint32_t(CT), p.status, 16, idx, row)) continue;
+#endif
+        const T re = Conv<T>::from_f(vr[j] * scale), im = Conv<T>::from_f(vi[j] * scale);
+        stg[stg_swz(idx)] = re;
+        stg[CT + stg_swz(idx)] = im;
+        mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (!ok) return;
+  // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
+  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+  const uint32_t lowmask = (1u << p.runC) - 1u;
+  for (int t = tid * 8; t < CT; t += TC_THREADS * 8) {
+    const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
+#if TNC_TC_SELFCHECK
+    {
+      const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
+      if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
+        continue;
+    }
+#endif
+    *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + stg_swz(t));
+    *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + stg_swz(t));
+  }
+  // block max -> tensor max
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
+    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+  }
 }
 
 template <typename T, int BN, int BK, int NST>
@@ -375,100 +498,193 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
 
-  const int64_t sb = inst * p.n_slots;
-  const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
-  const int row = (warp & 3) * 32 + lane;
-  const int col0 = (warp >> 2) * (BN / 2);
-  if (p.splitk > 1) {
-    // FP32 partial sums by C's flat index; k_splitk_reduce sums them in a fixed order
-    if (ok) {
-      float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
-      const uint32_t lowmask = (1u << p.runC) - 1u;
-#pragma unroll 1
-      for (int cc = 0; cc < BN / 2; cc += 32) {
-        float vr[32], vi[32];
-        tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-        tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
-        const uint32_t rm = TCm[row];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const uint32_t t = rm + TCn[col0 + cc + j];
-          part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(vr[j], vi[j]);
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
-    return;
+  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, inst);
+}
+
+// Tensor-memory-accelerator variant: the compiler laid the operands out as [Kt | Mt | ...]
+// and [Kt | Nt | ...], so a stage's A (B) tile is 128 (BN) consecutive rows of 2^kt
+// entries, one 4-D box (k, row, plane, instance) per plane.  One thread issues the four
+// TMA loads of a stage against the "full" mbarrier (expect_tx), one thread issues the
+// MMAs and commits them to "empty"; the TMA swizzle (32B / 64B) writes exactly the K-major
+// layout the MMA descriptors read.
+template <typename T, int BN, int BK, int NST>
+__global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const __grid_constant__ TcParams p) {
+  using S = TcShape<BN, BK, NST>;
+  constexpr int KT = BK == 32 ? 5 : 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::REGION);        // [2^(C_BITS - runC)]
+  const int nhC = 1 << (S::C_BITS - p.runC);
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);               // [128]
+  uint16_t* TCn = TCm + TC_BM;                                           // [BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NST;
+  uint64_t* done = bars + 2 * NST;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t inst = blockIdx.z;
+  const uint32_t on = blockIdx.x & ((1u << p.n_on) - 1u);
+  const uint32_t om = p.n_on >= 31 ? 0u : (blockIdx.x >> p.n_on);
+  int64_t oA = 0, oB = 0, oC = 0;
+  for (int j = 0; j < p.n_om; ++j)
+    if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j], oC += int64_t(1) << p.om_C[j];
+  for (int j = 0; j < p.n_on; ++j)
+    if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j], oC += int64_t(1) << p.on_C[j];
+  constexpr int nb = S::N_BITS;
+  for (int r = tid; r < TC_BM; r += TC_THREADS) {
+    uint32_t cm = 0;
+    for (int j = 0; j < 7; ++j)
+      if ((r >> j) & 1) cm |= 1u << p.pCm[j];
+    TCm[r] = (uint16_t)cm;
   }
-  // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
-  int sh = 0;
-  {
-    const float a = p.maxabs[sb + p.slotA], b = p.maxabs[sb + p.slotB];
-    if (a > 0.f && b > 0.f) {
-      int ea, eb;
-      frexpf(a, &ea);
-      frexpf(b, &eb);
-      sh = ea + eb + p.nK + 1 - 15;
-    }
+  for (int r = tid; r < BN; r += TC_THREADS) {
+    uint32_t cn = 0;
+    for (int j = 0; j < nb; ++j)
+      if ((r >> j) & 1) cn |= 1u << p.pCn[j];
+    TCn[r] = (uint16_t)cn;
   }
-  const float scale = ldexpf(1.f, -sh);
-  constexpr int CT = TC_BM * BN;  // entries of the C tile
-  T* stg = reinterpret_cast<T*>(smem);  // [2][CT] re plane then im plane
-  float mx = 0.f;
-  if (ok) {
-#pragma unroll 1
-    for (int cc = 0; cc < BN / 2; cc += 32) {
-      float vr[32], vi[32];
-      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
-      const uint32_t rm = TCm[row];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t idx = rm + TCn[col0 + cc + j];
-#if TNC_TC_SELFCHECK
-        if (!tc_check(idx < uint32_t(CT), p.status, 16, idx, row)) continue;
-#endif
-        const T re = Conv<T>::from_f(vr[j] * scale), im = Conv<T>::from_f(vi[j] * scale);
-        stg[idx] = re;
-        stg[CT + idx] = im;
-        mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
-      }
+  for (int h = tid; h < nhC; h += TC_THREADS) {
+    uint32_t m = p.maskC;
+    for (int i = 0; i < p.runC; ++i) m &= m - 1;
+    uint32_t r = 0, x = (uint32_t)h;
+    while (m) {
+      const uint32_t low = m & (~m + 1u);
+      if (x & 1u) r |= low;
+      x >>= 1;
+      m &= m - 1;
     }
+    hiC[h] = r;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
-  }
-  if (!ok) return;
-  // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
-  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
-  const uint32_t lowmask = (1u << p.runC) - 1u;
-  for (int t = tid * 8; t < CT; t += TC_THREADS * 8) {
-    const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
-#if TNC_TC_SELFCHECK
-    {
-      const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
-      if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
-        continue;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int n_total = 1 << p.n_ok;
+  const int per = n_total / p.splitk;
+  const int it0 = blockIdx.y * per;
+  const int n_iter = per;
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int it = 0; it < n_iter; ++it) {
+      const int buf = it % NST;
+      if (it >= NST && !mbar_wait_bounded(smem_u32(&empty[buf]), (uint32_t)((it / NST - 1) & 1), p.status)) {
+        ok = false;
+        break;
+      }
+      const int g = it0 + it;
+      int64_t okA = 0, okB = 0;
+      for (int j = 0; j < p.n_ok; ++j)
+        if ((g >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+      const int rowA = (int)((oA + okA) >> KT), rowB = (int)((oB + okB) >> KT);
+      const uint32_t st = sbase + buf * S::STAGE;
+      const uint32_t fb = smem_u32(&full[buf]);
+      mbar_arrive_expect_tx(fb, S::STAGE);
+      tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)inst, fb);
+      tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)inst, fb);
+      tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)inst, fb);
+      tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)inst, fb);
+      issued = it + 1;
     }
-#endif
-    *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + t);
-    *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + t);
+    // copies still in flight land before the CTA may exit (all complete on the normal path)
+    for (int it = issued - NST > 0 ? issued - NST : 0; it < issued; ++it)
+      if (!mbar_wait_bounded(smem_u32(&full[it % NST]), (uint32_t)((it / NST) & 1), p.status)) ok = false;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
+    for (int it = 0; it < n_iter; ++it) {
+      const int buf = it % NST;
+      if (!mbar_wait_bounded(smem_u32(&full[buf]), (uint32_t)((it / NST) & 1), p.status)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t st = sbase + buf * S::STAGE;
+#pragma unroll
+      for (int j = 0; j < BK / 16; ++j) {
+        const uint64_t ar = kmajor_desc(st + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t ai = kmajor_desc(st + S::A_BYTES + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t br = kmajor_desc(st + 2 * S::A_BYTES + j * 32, S::SBO, S::LAYOUT);
+        const uint64_t bi = kmajor_desc(st + 2 * S::A_BYTES + S::B_BYTES + j * 32, S::SBO, S::LAYOUT);
+        const uint32_t first = (it == 0 && j == 0) ? 0u : 1u;
+        mma_f16(tmem, ar, br, id_pos, first);
+        mma_f16(tmem, ai, bi, id_neg, 1u);
+        mma_f16(tmem + BN, ar, bi, id_pos, first);
+        mma_f16(tmem + BN, ai, br, id_pos, 1u);
+      }
+      mma_commit(smem_u32(&empty[buf]));
+    }
+    mma_commit(smem_u32(done));
   }
-  // block max -> tensor max
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) red[warp] = mx;
-  __syncthreads();
-  if (tid == 0) {
-    float m = 0.f;
-    for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
-    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
-    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+  const bool fin = mbar_wait_bounded(smem_u32(done), 0u, p.status);
+  ok = ok && fin;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  ok = __syncthreads_and(ok);
+  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, inst);
+}
+
+template <int BN, int BK, int NST>
+size_t tma_smem_bytes_t(int runC) {
+  using S = TcShape<BN, BK, NST>;
+  return 1024 + S::REGION + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 + (2 * NST + 1) * 8 + 16 +
+         32 * 4 + 64;
+}
+
+template <typename T, int BN, int BK, int NST>
+cudaError_t launch_tma_t(const TcParams& p, dim3 grid, cudaStream_t s) {
+  const size_t smem = tma_smem_bytes_t<BN, BK, NST>(p.runC);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_tma<T, BN, BK, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_tma<T, BN, BK, NST><<<grid, TC_THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, int BN, int BK>
+cudaError_t launch_tma_st(const TcParams& p, dim3 grid, cudaStream_t s) {
+  // 256-wide tiles take all 512 TMEM columns: one CTA per SM, always the deep pipeline
+  if (p.stages == 3 && BN < 256) return launch_tma_t<T, BN, BK, 3>(p, grid, s);
+  return launch_tma_t<T, BN, BK, tc_deep_stages<BN, BK>()>(p, grid, s);
+}
+
+template <typename T>
+cudaError_t launch_tma_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (p.bn == 256) {
+    if (p.bk == 32) return launch_tma_st<T, 256, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tma_st<T, 256, 16>(p, grid, s);
+  } else if (p.bn == 128) {
+    if (p.bk == 32) return launch_tma_st<T, 128, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tma_st<T, 128, 16>(p, grid, s);
+  } else if (p.bn == 64) {
+    if (p.bk == 32) return launch_tma_st<T, 64, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tma_st<T, 64, 16>(p, grid, s);
   }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_tma(int precision, const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (precision == 1) return launch_tma_bn_bk<__half>(p, grid, s);
+  if (precision == 2) return launch_tma_bn_bk<__nv_bfloat16>(p, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int BN, int BK, int NST>

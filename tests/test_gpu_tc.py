@@ -36,6 +36,23 @@ def kmajor_case(m, k, n, seed):
     return a, la, b, lb, lc
 
 
+def tma_case(m, k, n, seed):
+    """Layouts the TMA kernel loads directly: A = [Kt | 7 row labels | rest], B = [Kt | 6-7
+    column labels | rest], C's three lowest labels among the tile labels."""
+    kt = 5 if k >= 5 else 4
+    nt = 8 if (n >= 8 and k > kt + 1) else (7 if n >= 7 else 6)
+    ks = list(range(100, 100 + k))
+    ms = list(range(m))
+    ns = list(range(200, 200 + n))
+    la = ks[:kt] + ms[:7] + random_labels_perm(ms[7:] + ks[kt:], seed)
+    lb = ks[:kt] + ns[:nt] + random_labels_perm(ns[nt:] + ks[kt:], seed + 1)
+    lc = [ns[0], ms[0], ns[1]] + random_labels_perm(ms[1:] + ns[2:], seed + 2)
+    sigma = 1.0 / np.sqrt(2.0 ** k)
+    a = random_complex(1 << len(la), sigma, seed + 3)
+    b = random_complex(1 << len(lb), sigma, seed + 4)
+    return a, la, b, lb, lc
+
+
 def run(ctx, precision, a, la, b, lb, lc):
     def planar(x):
         t = torch.from_numpy(np.concatenate([x.real, x.imag])).to(DT[precision])
@@ -69,6 +86,29 @@ def test_tc_contract_elementwise(ctx, precision, shape):
         idx = np.random.default_rng(1).integers(0, len(got), 256)
         err = metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx))
     assert err <= TOL[precision], err
+
+
+TMA_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (8, 15, 6), (7, 14, 7), (7, 6, 8), (9, 8, 10)]
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+def test_tma_contract(ctx, precision, shape):
+    a, la, b, lb, lc = tma_case(*shape, seed=13 * sum(shape) + shape[2])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    if len(got) <= 1 << 16:
+        err = metrics.rel_err_norm(got, pairwise.contract(aq, la, bq, lb, lc))
+    else:
+        idx = np.random.default_rng(3).integers(0, len(got), 256)
+        err = metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx))
+    assert err <= TOL[precision], err
+
+
+def test_tma_large_sampled(ctx):
+    a, la, b, lb, lc = tma_case(14, 12, 10, seed=6)
+    got, aq, bq = run(ctx, "chalf", a, la, b, lb, lc)
+    idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(4).integers(0, len(got), 126)]))
+    assert metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx)) <= TOL["chalf"]
 
 
 def test_tc_contract_large_sampled(ctx):
