@@ -273,11 +273,12 @@ def run_ours(args):
 
     # end to end: host bitstrings in, host amplitudes out, through the public API
     host_out = np.zeros((1, n_out), dtype=np.complex128)
-    ctx.amplitudes(plan, bits, args.precision, out=host_out)
+    for _ in range(2):  # first call eager, second captures the CUDA graph of the wave
+        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx.amplitudes(plan, bits, args.precision, out=host_out)
+        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True)
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = bits.nbytes + n_slices * (8 + 4) + 12
     d2h = host_out.nbytes
@@ -290,8 +291,10 @@ def run_ours(args):
     flops_launch = prof["flops"][k] / prof["launches"][k]
     bytes_launch = prof["bytes"][k] / prof["launches"][k]
     if kind in (3, 4):
+        # the timed region is well under a second at full clocks: the burst peak applies
         achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_kind": "burst (cuBLAS bf16, measured)", "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"]}
     elif flops_launch / bytes_launch > 8.0:
         alu_peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
@@ -305,7 +308,8 @@ def run_ours(args):
                       "ms_per_launch": per_launch_ms, "flops_per_launch": flops_launch, "bytes_per_launch": bytes_launch}
     roof["peak_source"] = peaks["_source"]
     total_flops = float(prof["flops"].sum()) / args.steps
-    launches = int(prof["launches"].sum() / args.steps) + 2 * int(prof["launches"][0] / args.steps)
+    waves = int(prof["launches"].min() / args.steps)
+    launches = int(prof["launches"].sum() / args.steps) + 2 * waves  # + leaf gather and root sum per wave
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -230,7 +230,7 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
 /* Per-step timings of the last tnc_amplitudes call made with opts->profile = 1 on this
  * context (waits for it).  For step s (program order, cap >= n entries):
  *  ms[s]      device time summed over the call's launches of that step (CUDA events)
- *  launches[s] launches of that step (one per wave)
+ *  launches[s] kernel launches of that step (per wave: 1, or 2 for a split step's reduce)
  *  flops[s]   algorithmic real flops of those launches: 8 * M * N * K per instance
  *  bytes[s]   algorithmic bytes: (|A| + |B| + |C|) * element size per instance
  *  kind[s]    kernel class (0 generic, 1 split-K GEPDOT, 2 fused chain, 3 tensor-core)

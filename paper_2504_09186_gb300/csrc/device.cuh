@@ -100,4 +100,8 @@ struct RootSeg {
   int32_t begin, end;  // instances within the wave
 };
 
+// Raises a kernel's dynamic shared-memory limit once per (kernel, size) instead of on every
+// launch (keeps attribute calls out of CUDA-graph captures after the first, eager launch).
+cudaError_t set_smem_once(const void* kernel, size_t bytes);
+
 }  // namespace tnc

@@ -337,7 +337,11 @@ struct DeviceProgram {
   int n_open = 0;
   int n_qubits = 0;
   uint64_t leaf_version = 0;
+  // CUDA graphs of one wave, keyed by the wave's launch parameters (see tnc_amplitudes)
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, int> graph_seen;
   ~DeviceProgram() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     arena.release();
     maxabs.release();
     exps.release();
@@ -358,7 +362,7 @@ struct ProfState {
   int n_steps = 0, waves = 0;
   std::vector<cudaEvent_t> ev;
   std::vector<double> flops, bytes;
-  std::vector<int> kind;
+  std::vector<int> kind, kernels;  // kernels: launches per wave (2 when a split step reduces)
   cudaStream_t stream = nullptr;
   cudaEvent_t& at(int w, int s, int which) { return ev[(size_t(w) * n_steps + s) * 2 + which]; }
   void ensure(int steps, int w) {
@@ -712,6 +716,7 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       ps.flops.assign(prog->steps.size(), 0.0);
       ps.bytes.assign(prog->steps.size(), 0.0);
       ps.kind.assign(prog->steps.size(), 0);
+      ps.kernels.assign(prog->steps.size(), 1);
       for (size_t k = 0; k < P.steps.size(); ++k) {
         const auto& la = P.tensors[P.steps[k].a].labels;
         const auto& lb = P.tensors[P.steps[k].b].labels;
@@ -723,12 +728,32 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
         ps.bytes[k] = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) +
                        std::ldexp(1.0, (int)lc.size())) * 2.0 * double(eb) * double(n_inst);
         ps.kind[k] = prog->steps[k].kind;
+        const StepLaunch& SL = prog->steps[k];
+        ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
       }
       CUDA_OK(cudaEventRecord(ps.call_start(), s));
     }
     int w = 0;
     for (int64_t base = 0; base < n_inst; base += W, ++w) {
       const int64_t cnt = std::min<int64_t>(W, n_inst - base);
+      // CUDA graph of the wave: the launch sequence depends on the wave's base, size, root
+      // segments and the context's buffers; the first call with a key runs eagerly, later
+      // calls capture once and replay (Sec. III-A subtasks of a wave in one graph launch)
+      std::string gkey;
+      if (opts->use_graph && !prof) {
+        gkey = std::to_string(base) + "/" + std::to_string(cnt) + "/" + std::to_string(wave_segs[w].first) + "/" +
+               std::to_string(wave_segs[w].second) + "/" + std::to_string((uintptr_t)ctx->inst_slice.p) + "/" +
+               std::to_string((uintptr_t)ctx->inst_row.p) + "/" + std::to_string((uintptr_t)ctx->bits.p) + "/" +
+               std::to_string((uintptr_t)ctx->segs.p) + "/" + std::to_string((uintptr_t)ctx->acc.p) + "/" +
+               std::to_string((uintptr_t)s);
+        auto git = prog->graphs.find(gkey);
+        if (git != prog->graphs.end()) {
+          CUDA_OK(cudaGraphLaunch(git->second, s));
+          continue;
+        }
+      }
+      const bool capture = !gkey.empty() && prog->graph_seen[gkey]++ > 0;
+      if (capture) CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       CUDA_OK(cudaMemsetAsync(prog->maxabs.p, 0, size_t(prog->n_slots) * cnt * sizeof(float), s));
       CUDA_OK(launch_leaf_gather(precision, prog->leaf_desc.as<LeafDesc>(), prog->n_leaves,
                                  prog->leaf_src.as<double2>(), prog->arena.p, prog->inst_stride,
@@ -743,6 +768,16 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
                                 prog->open_pos.as<int8_t>(), prog->n_open, ctx->segs.as<RootSeg>() + wave_segs[w].first,
                                 wave_segs[w].second, prog->exps.as<int32_t>(), prog->n_slots, prog->root,
                                 ctx->acc.as<double2>(), s));
+      if (capture) {
+        cudaGraph_t g = nullptr;
+        CUDA_OK(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_OK(ie);
+        prog->graphs[gkey] = ge;
+        CUDA_OK(cudaGraphLaunch(ge, s));
+      }
     }
     if (prof) {
       CUDA_OK(cudaEventRecord(ctx->prof.call_end(), s));
@@ -868,7 +903,7 @@ tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, doub
         t += x;
       }
       ms[s] = t;
-      launches[s] = ps.waves;
+      launches[s] = ps.waves * ps.kernels[s];
       flops[s] = ps.flops[s];
       bytes[s] = ps.bytes[s];
       kind[s] = ps.kind[s];

@@ -21,9 +21,23 @@
 // |re|,|im| of its stored values.  A producer scales its FP32 results by the exact power
 // of two that brings the bound 2^(nK+1) * max|A| * max|B| below 2^15, so fp16 storage
 // can neither overflow nor flush ordinary values to zero.
+#include <map>
+#include <mutex>
+
 #include "device.cuh"
 
 namespace tnc {
+
+cudaError_t set_smem_once(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(kernel);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[kernel] = bytes;
+  return e;
+}
 
 template <typename T, int V>
 struct alignas(sizeof(T) * V) Vec {
@@ -458,7 +472,7 @@ cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, di
   else k = pick_generic<__nv_bfloat16>(rm, rn);
   if (!k) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k), smem);
     if (e != cudaSuccess) return e;
   }
   k<<<grid, kThreads, smem, s>>>(p);

@@ -653,7 +653,7 @@ size_t tma_smem_bytes_t(int runC) {
 template <typename T, int BN, int BK, int NST>
 cudaError_t launch_tma_t(const TcParams& p, dim3 grid, cudaStream_t s) {
   const size_t smem = tma_smem_bytes_t<BN, BK, NST>(p.runC);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_tma<T, BN, BK, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma<T, BN, BK, NST>), smem);
   if (e != cudaSuccess) return e;
   k_tc_tma<T, BN, BK, NST><<<grid, TC_THREADS, smem, s>>>(p);
   return cudaGetLastError();
@@ -697,7 +697,7 @@ size_t tc_smem_bytes_t(int runC) {
 template <typename T, int BN, int BK, int NST>
 cudaError_t launch_tc_t(const TcParams& p, dim3 grid, cudaStream_t s) {
   const size_t smem = tc_smem_bytes_t<BN, BK, NST>(p.runC);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<T, BN, BK, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_gemm<T, BN, BK, NST>), smem);
   if (e != cudaSuccess) return e;
   k_tc_gemm<T, BN, BK, NST><<<grid, TC_THREADS, smem, s>>>(p);
   return cudaGetLastError();

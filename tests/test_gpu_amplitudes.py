@@ -90,6 +90,19 @@ def test_wave_sizes_are_deterministic(ctx):
     assert metrics.rel_err_norm(outs[0][1], ref) <= 1e-5
 
 
+def test_cuda_graph_replay_is_identical(ctx):
+    # several waves; graphs are captured on the second call and replayed afterwards
+    c = grid_circuit(4, 4, 10, seed=1)
+    fixed, open_q = subcube_spec(16, 3, seed=2)
+    bs = np.stack([fixed, 1 - fixed])
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=9, slices_min=3)
+    for prec in ("c64", "chalf"):
+        ref = ctx.amplitudes(p, bs, prec, wave=3)
+        for _ in range(3):
+            got = ctx.amplitudes(p, bs, prec, wave=3, use_graph=True)
+            assert np.array_equal(got, ref)
+
+
 def test_half_precision_scaling_keeps_small_amplitudes(ctx):
     # 20 qubits: amplitudes ~2^-10, intermediates far below fp16's normal range without scaling
     c = grid_circuit(4, 5, 12, seed=1)
