@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the complex64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cap", type=int, default=23, help="log2 size cap of the oracle sample")
+    ap.add_argument("--plan", default="greedy", choices=["greedy", "stem"],
+                    help="greedy: balanced pairwise order; stem: one tensor absorbs leaves (fused chains)")
+    ap.add_argument("--no-fuse", action="store_true", help="run stem absorptions as separate kernels")
     return ap.parse_args()
 
 
@@ -164,7 +167,7 @@ def run_reference(args):
 
     w, circ, fixed, open_q = workload(args.workload, 0)
     plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
-                         slices_min=w["smin"], slices_max=w["smax"])
+                         slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
     cuts = plan.sliced_cuts()
     run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
     for _ in range(args.warmup):
@@ -179,7 +182,8 @@ def run_reference(args):
         "impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 5x6 grid RQC, 14 cycles, 2^6 slices, cap 2^26, 1024-amplitude sub-cube"},
+        "config": {"workload": f"{args.workload}: 5x6 grid RQC, 14 cycles, 2^6 slices, cap 2^26, 1024-amplitude sub-cube",
+                   "plan": args.plan},
         "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores, "kind": "oracle",
                          "sample": f"each step = 1 of {n_sub} oracle sub-contractions of slice 0 (cap 2^{args.cpu_sample_cap}); "
                                    f"slices/s = 1 / (step time * {n_sub})"},
@@ -206,8 +210,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w, circ, fixed, open_q = workload(args.workload, rank)
     plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
-                         slices_min=w["smin"], slices_max=w["smax"])
+                         slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
     info = plan.info()
+    fuse = not args.no_fuse
     n_slices = 1 << info["n_sliced"]
     ctx = T.Context(local)
     # a dedicated stream: the library enqueues on it and the CUDA events below time it
@@ -220,7 +225,7 @@ def run_ours(args):
 
     def timed(precision, steps, warmup, profile):
         for _ in range(warmup):
-            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream)
+            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream, fuse=fuse)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -232,7 +237,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream, profile=profile)
+            ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream, profile=profile, fuse=fuse)
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
@@ -274,11 +279,11 @@ def run_ours(args):
     # end to end: host bitstrings in, host amplitudes out, through the public API
     host_out = np.zeros((1, n_out), dtype=np.complex128)
     for _ in range(2):  # first call eager, second captures the CUDA graph of the wave
-        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True)
+        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True, fuse=fuse)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True)
+        ctx.amplitudes(plan, bits, args.precision, out=host_out, use_graph=True, fuse=fuse)
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = bits.nbytes + n_slices * (8 + 4) + 12
     d2h = host_out.nbytes
@@ -331,6 +336,8 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {w['rows']}x{w['cols']} grid RQC, {w['cycles']} cycles, "
                                    f"{n_slices} slices (cap 2^{w['cap']}), {n_out}-amplitude sub-cube per GPU",
                        "precision": args.precision, "slices_per_step": n_slices * world,
+                       "plan": args.plan, "fused_chains": bool(fuse and info["n_fused"] > 0),
+                       "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"], "sliced_indices": info["n_sliced"],
                        "complex_tflops": total_flops / (ms / 1e3) / 1e12,
                        "l2": "256 MiB flush before every timed step; intermediates up to 2^26 entries > L2",
                        "parallelism": f"replicas x{world} (independent sub-cubes)"},

@@ -91,6 +91,10 @@ typedef struct {
   int32_t slices_max;  /* trials above this many sliced indices are dropped if any  */
                        /* trial stays within it                                    */
   double temperature;  /* Gumbel temperature in log2-cost units; 0 = plain greedy    */
+  int32_t mode;        /* 0: greedy pairwise order (balanced, "multi-stem" trees);     */
+                       /* 1: stem order -- one tensor absorbs neighbouring leaves one  */
+                       /*    at a time (the stem of Sec. II-A), which the fused chains */
+                       /*    of Sec. IV execute on chip                               */
 } tnc_plan_opts;
 
 /* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:
@@ -227,8 +231,9 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
                                 const void* b, int32_t rank_b, const int32_t* labels_b, void* c,
                                 int32_t rank_c, const int32_t* labels_c, int32_t* c_exp2, void* stream);
 
-/* Per-step timings of the last tnc_amplitudes call made with opts->profile = 1 on this
- * context (waits for it).  For step s (program order, cap >= n entries):
+/* Per-launch timings of the last tnc_amplitudes call made with opts->profile = 1 on this
+ * context (waits for it).  Entry s is the s-th launch of the per-wave program (a step, or a
+ * whole fused chain; cap >= n entries):
  *  ms[s]      device time summed over the call's launches of that step (CUDA events)
  *  launches[s] kernel launches of that step (per wave: 1, or 2 for a split step's reduce)
  *  flops[s]   algorithmic real flops of those launches: 8 * M * N * K per instance

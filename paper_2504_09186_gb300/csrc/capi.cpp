@@ -100,6 +100,8 @@ tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* o
     o.slices_min = opts->slices_min;
     o.slices_max = opts->slices_max;
     o.temperature = opts->temperature;
+    o.mode = opts->mode;
+    if (o.mode != 0 && o.mode != 1) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy) or 1 (stem)");
     auto* p = new tnc_plan_s();
     try {
       plan_greedy(n->n, o, p->p);
@@ -237,7 +239,8 @@ tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
            ",\"Kt\":" + jlist(t.Kt) + ",\"Nt\":" + jlist(t.Nt) + ",\"Mo\":" + jlist(t.Mo) + ",\"Ko\":" + jlist(t.Ko) +
            ",\"No\":" + jlist(t.No) + ",\"splitk\":" + std::to_string(t.splitk) + ",\"rm\":" + std::to_string(t.rm) +
            ",\"rn\":" + std::to_string(t.rn) + ",\"kgroups\":" + std::to_string(t.kgroups) +
-           ",\"tc\":" + std::to_string(S.tc_ok ? 1 : 0) + ",\"chain_b\":" + jlist(S.chain_b) + ",\"chain_c\":" + jlist(S.chain_c) + "}";
+           ",\"tc\":" + std::to_string(S.tc_ok ? 1 : 0) + ",\"chain\":" +
+           std::to_string(i < P.step_chain.size() ? P.step_chain[i] : -1) + "}";
     }
     char num[64];
     std::snprintf(num, sizeof(num), "%.17g", P.log2_flops_slice);

@@ -393,6 +393,102 @@ void compile_plan(Plan& plan, bool fuse) {
     else if (nk + nn <= 6) plan.n_absorb++;
     else plan.n_gemm++;
   }
+  // fused chains (Sec. IV): follow the big operand through consecutive absorptions of
+  // small tensors (rank <= 6) while the on-chip label set stays within 2^12 entries.  The
+  // first big operand keeps on chip its four lowest positions (contiguous loads) and every
+  // label the chain contracts; labels brought in by the small tensors join it; the chain's
+  // result must have its three lowest positions on chip (contiguous stores).  A fused
+  // section of n links saves 2(n-1) passes over the big tensor.
+  plan.chains.clear();
+  plan.step_chain.assign(plan.steps.size(), -1);
+  if (fuse) {
+    auto is_link = [&](size_t j) {
+      const Step& st = plan.steps[j];
+      return st.kind == K_GENERIC && !st.tc_ok && plan.tensors[st.b].labels.size() <= 6 &&
+             plan.tensors[st.a].labels.size() >= 10;
+    };
+    constexpr size_t kInnerMax = 12;
+    for (size_t i = 0; i < plan.steps.size(); ++i) {
+      if (plan.step_chain[i] >= 0 || !is_link(i)) continue;
+      const std::vector<int>& A0 = plan.tensors[plan.steps[i].a].labels;
+      std::vector<int> inner0(A0.begin(), A0.begin() + std::min<size_t>(4, A0.size()));
+      std::vector<size_t> links;
+      std::vector<int> best_inner;
+      size_t best_len = 0;
+      for (size_t j = i; j < plan.steps.size(); ++j) {
+        if (!is_link(j) || plan.step_chain[j] >= 0) break;
+        if (j > i && plan.steps[j].a != plan.steps[j - 1].c) break;
+        // tentative inner set with this link's contracted labels of A0 added
+        std::vector<int> cand = inner0;
+        const auto& la = plan.tensors[plan.steps[j].a].labels;
+        const auto& lb = plan.tensors[plan.steps[j].b].labels;
+        for (int x : la)
+          if (contains(lb, x) && contains(A0, x)) add_unique(cand, x);
+        // simulate the on-chip sets
+        std::vector<int> I = cand;
+        size_t mx = I.size();
+        bool ok = true;
+        for (size_t l = i; l <= j && ok; ++l) {
+          const auto& a = plan.tensors[plan.steps[l].a].labels;
+          const auto& b = plan.tensors[plan.steps[l].b].labels;
+          std::vector<int> nI;
+          for (int x : I)
+            if (!contains(b, x)) nI.push_back(x);
+          for (int x : b)
+            if (!contains(a, x)) nI.push_back(x);
+          for (int x : b)
+            if (contains(a, x) && !contains(I, x)) ok = false;  // contracted label not on chip
+          I = nI;
+          mx = std::max(mx, I.size());
+        }
+        if (!ok || mx > kInnerMax) break;
+        inner0 = cand;
+        links.push_back(j);
+        // the result's lowest positions must be on chip
+        const auto& lc = plan.tensors[plan.steps[j].c].labels;
+        bool store_ok = true;
+        for (size_t q = 0; q < std::min<size_t>(3, lc.size()); ++q) store_ok = store_ok && contains(I, lc[q]);
+        if (store_ok && links.size() >= 2) {
+          best_len = links.size();
+          best_inner = inner0;
+        }
+      }
+      if (best_len >= 2) {
+        // widen the on-chip set with A0's untouched low-position labels while every tile of
+        // the chain stays within 2^12 entries (larger tiles amortize each CTA's setup)
+        auto max_tile = [&](const std::vector<int>& in0) {
+          std::vector<int> I = in0;
+          size_t mx = I.size();
+          for (size_t l = 0; l < best_len; ++l) {
+            const auto& a = plan.tensors[plan.steps[links[l]].a].labels;
+            const auto& b = plan.tensors[plan.steps[links[l]].b].labels;
+            std::vector<int> nI;
+            for (int x : I)
+              if (!contains(b, x)) nI.push_back(x);
+            for (int x : b)
+              if (!contains(a, x)) nI.push_back(x);
+            I = nI;
+            mx = std::max(mx, I.size());
+          }
+          return mx;
+        };
+        for (int x : A0) {
+          if (contains(best_inner, x)) continue;
+          best_inner.push_back(x);
+          if (max_tile(best_inner) > kInnerMax) {
+            best_inner.pop_back();
+            break;
+          }
+        }
+        Chain ch;
+        ch.steps.assign(links.begin(), links.begin() + best_len);
+        ch.inner0 = best_inner;
+        for (int sidx : ch.steps) plan.step_chain[sidx] = (int)plan.chains.size();
+        plan.n_fused += (int)best_len;
+        plan.chains.push_back(ch);
+      }
+    }
+  }
   // liveness + arena (first fit over a sorted free list, per instance, in complex elements;
   // planar storage takes 2 * 2^rank scalars, so offsets are kept in scalars)
   for (auto& ti : plan.tensors) ti.last_use = -1;
@@ -440,6 +536,43 @@ void compile_plan(Plan& plan, bool fuse) {
       if (plan.tensors[opnd].last_use == (int)s) release(plan.tensors[opnd].offset, scalars(plan.tensors[opnd]));
   }
   plan.arena_elems = top;  // scalars per instance
+
+  // fused program: a chain runs at its last link, so its inputs (the first large operand
+  // and every small one) stay allocated until its result is; its intermediates take no memory
+  for (auto& ti : plan.tensors) ti.offset_fused = -1;
+  if (plan.chains.empty()) {
+    for (auto& ti : plan.tensors) ti.offset_fused = ti.offset;
+    plan.arena_elems_fused = plan.arena_elems;
+    return;
+  }
+  std::vector<std::vector<int>> unit_in, unit_out;  // execution units in order
+  for (size_t s = 0; s < plan.steps.size(); ++s) {
+    const int ci = plan.step_chain[s];
+    if (ci < 0) {
+      unit_in.push_back({plan.steps[s].a, plan.steps[s].b});
+      unit_out.push_back({plan.steps[s].c});
+      continue;
+    }
+    const Chain& ch = plan.chains[ci];
+    if ((int)s != ch.steps.back()) continue;
+    std::vector<int> ins = {plan.steps[ch.steps.front()].a};
+    for (int sidx : ch.steps) ins.push_back(plan.steps[sidx].b);
+    unit_in.push_back(ins);
+    unit_out.push_back({plan.steps[ch.steps.back()].c});
+  }
+  std::vector<int> last_unit(plan.tensors.size(), -1);
+  for (size_t u = 0; u < unit_in.size(); ++u)
+    for (int t : unit_in[u]) last_unit[t] = (int)u;
+  last_unit[plan.root] = (int)unit_in.size();
+  freelist.clear();
+  top = 0;
+  for (int i = 0; i < L; ++i) plan.tensors[i].offset_fused = alloc(scalars(plan.tensors[i]));
+  for (size_t u = 0; u < unit_in.size(); ++u) {
+    for (int t : unit_out[u]) plan.tensors[t].offset_fused = alloc(scalars(plan.tensors[t]));
+    for (int t : unit_in[u])
+      if (last_unit[t] == (int)u) release(plan.tensors[t].offset_fused, scalars(plan.tensors[t]));
+  }
+  plan.arena_elems_fused = top;
 }
 
 }  // namespace tnc

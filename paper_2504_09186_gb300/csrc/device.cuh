@@ -94,6 +94,35 @@ struct TcParams {
   int32_t* status;           // TNC_E_TIMEOUT on a bounded wait that ran out
 };
 
+// Fused chain of absorptions (Sec. IV): one tile of the big tensor stays on chip while
+// every link contracts it with a small tensor.
+constexpr int kChainMaxBits = 12;  // on-chip tile <= 2^12 complex entries
+struct ChainLink {
+  int64_t g_off;     // arena offset (scalars, instance 0) of the small operand
+  int64_t g_plane;   // 2^rank(small operand)
+  int64_t tab;       // offset of this link's entries in in_tab / g_tab
+  int32_t slot_g, g_size, out_bits, k_bits, n_bits;
+  uint16_t kin[64];  // tile offset of each common-label assignment in the previous tile
+  uint8_t kg[64];    // ... and in the small operand
+  uint8_t gn[64];    // small-operand offset of each free-label assignment (bound only)
+};
+struct ChainParams {
+  const void* arena;
+  int64_t stride;                     // instance stride (scalars)
+  int64_t offA0, planeA0, offC, planeC;
+  uint32_t maskA0, maskC;             // on-chip positions in the first operand / the result
+  int32_t runA0, runC, bits0, bitsC;
+  int32_t n_o;
+  int8_t o_A[kMaxOuter], o_C[kMaxOuter];  // outer (grid) labels: positions in A0 and in C
+  int32_t n_links;
+  const ChainLink* links;
+  const uint16_t* in_tab;             // per link, per output entry: offset in the previous tile
+  const uint8_t* g_tab;               // ... and in the small operand
+  float* maxabs;
+  int32_t* exps;
+  int32_t n_slots, slotA0, slotC;
+};
+
 // A run of consecutive instances of one wave that belong to the same bitstring row.
 struct RootSeg {
   int32_t row;

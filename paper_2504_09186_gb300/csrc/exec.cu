@@ -38,6 +38,7 @@ cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root
                                  int n_slots, int slot, cudaStream_t s);
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 cudaError_t launch_tc_tma(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
+cudaError_t launch_chain(int precision, const ChainParams& p, int64_t n_inst, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
 bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t,
@@ -95,12 +96,14 @@ static int low_run(uint32_t mask) {
 }
 
 struct StepLaunch {
-  int kind;  // K_GENERIC, K_SPLITK or K_TC
+  int kind;  // K_GENERIC, K_SPLITK, K_TC, K_TMA or K_CHAIN
   GenParams p;
   TcParams tp;
+  ChainParams cp;
   dim3 grid;
   size_t smem;
   int rm, rn;
+  double flops = 0, bytes = 0;  // algorithmic, per instance (real flops 8MNK; bytes read + written)
 };
 
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
@@ -330,13 +333,14 @@ struct DeviceProgram {
   int device = 0, precision = 0, W = 0;
   int64_t inst_stride = 0;  // scalars
   int n_slots = 0, n_leaves = 0;
-  DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos;
+  DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links, chain_in, chain_g;
   std::vector<StepLaunch> steps;
   int root = 0;
   int64_t root_off = 0, root_plane = 1;
   int n_open = 0;
   int n_qubits = 0;
   uint64_t leaf_version = 0;
+  std::vector<int64_t> leaf_dst;  // arena offsets of the reduced leaves in this program
   // CUDA graphs of one wave, keyed by the wave's launch parameters (see tnc_amplitudes)
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_seen;
@@ -349,6 +353,9 @@ struct DeviceProgram {
     leaf_desc.release();
     partials.release();
     open_pos.release();
+    chain_links.release();
+    chain_in.release();
+    chain_g.release();
   }
 };
 
@@ -440,14 +447,130 @@ static void upload_leaves(const Plan& P, const std::vector<int64_t>& dst, DevBuf
   CUDA_OK(cudaMemcpy(descb.p, desc.data(), desc.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice));
 }
 
-static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W) {
+// Host-side construction of a fused chain's launch and index tables (see k_chain).
+template <class OffFn>
+static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<ChainLink>& links,
+                                    std::vector<uint16_t>& in_all, std::vector<uint8_t>& g_all, OffFn OFF) {
+  auto pos = [](const std::vector<int>& v, int x) {
+    for (size_t i = 0; i < v.size(); ++i)
+      if (v[i] == x) return (int)i;
+    return -1;
+  };
+  auto order_by = [&](std::vector<int> v, const std::vector<int>& layout) {
+    std::sort(v.begin(), v.end(), [&](int x, int y) { return pos(layout, x) < pos(layout, y); });
+    return v;
+  };
+  StepLaunch L;
+  std::memset(&L.p, 0, sizeof(L.p));
+  std::memset(&L.tp, 0, sizeof(L.tp));
+  std::memset(&L.cp, 0, sizeof(L.cp));
+  L.kind = K_CHAIN;
+  L.smem = 0;
+  L.rm = L.rn = 1;
+  ChainParams& c = L.cp;
+  const Step& first = P.steps[ch.steps.front()];
+  const Step& last = P.steps[ch.steps.back()];
+  const std::vector<int>& la0 = P.tensors[first.a].labels;
+  const std::vector<int>& lcn = P.tensors[last.c].labels;
+  std::vector<int> prev = order_by(ch.inner0, la0);
+  if (prev.size() > (size_t)kChainMaxBits) fail(TNC_E_PLAN, "chain tile too large");
+  for (int x : prev) c.maskA0 |= 1u << pos(la0, x);
+  c.runA0 = low_run(c.maskA0);
+  c.bits0 = (int)prev.size();
+  c.offA0 = OFF(first.a);
+  c.planeA0 = int64_t(1) << la0.size();
+  c.slotA0 = first.a;
+  c.n_links = (int)ch.steps.size();
+  double bytes = double(int64_t(1) << la0.size());
+  for (int sidx : ch.steps) {
+    const Step& st = P.steps[sidx];
+    const std::vector<int>& la = P.tensors[st.a].labels;
+    const std::vector<int>& lg = P.tensors[st.b].labels;
+    const std::vector<int>& lc = P.tensors[st.c].labels;
+    std::vector<int> K, N, cur;
+    for (int x : lg) (pos(la, x) >= 0 ? K : N).push_back(x);
+    for (int x : prev)
+      if (pos(K, x) < 0) cur.push_back(x);
+    for (int x : K)
+      if (pos(prev, x) < 0) fail(TNC_E_PLAN, "chain: contracted label not on chip");
+    cur.insert(cur.end(), N.begin(), N.end());
+    cur = order_by(cur, lc);
+    if (cur.size() > (size_t)kChainMaxBits || K.size() > 6 || N.size() > 6) fail(TNC_E_PLAN, "chain link too large");
+    ChainLink lk;
+    std::memset(&lk, 0, sizeof(lk));
+    lk.g_off = OFF(st.b);
+    lk.g_plane = int64_t(1) << lg.size();
+    lk.g_size = 1 << (int)lg.size();
+    lk.slot_g = st.b;
+    lk.out_bits = (int)cur.size();
+    lk.k_bits = (int)K.size();
+    lk.n_bits = (int)N.size();
+    lk.tab = (int64_t)in_all.size();
+    for (int k = 0; k < (1 << K.size()); ++k) {
+      uint32_t ai = 0, gi = 0;
+      for (size_t j = 0; j < K.size(); ++j)
+        if ((k >> j) & 1) ai |= 1u << pos(prev, K[j]), gi |= 1u << pos(lg, K[j]);
+      lk.kin[k] = (uint16_t)ai;
+      lk.kg[k] = (uint8_t)gi;
+    }
+    for (int n = 0; n < (1 << N.size()); ++n) {
+      uint32_t gi = 0;
+      for (size_t j = 0; j < N.size(); ++j)
+        if ((n >> j) & 1) gi |= 1u << pos(lg, N[j]);
+      lk.gn[n] = (uint8_t)gi;
+    }
+    for (uint32_t x = 0; x < (1u << cur.size()); ++x) {
+      uint32_t ib = 0, gb = 0;
+      for (size_t j = 0; j < cur.size(); ++j) {
+        if (!((x >> j) & 1)) continue;
+        const int pi = pos(prev, cur[j]);
+        if (pi >= 0) ib |= 1u << pi;
+        else gb |= 1u << pos(lg, cur[j]);
+      }
+      in_all.push_back((uint16_t)ib);
+      g_all.push_back((uint8_t)gb);
+    }
+    links.push_back(lk);
+    L.flops += 8.0 * std::ldexp(1.0, (int)(la.size() + N.size()));
+    bytes += std::ldexp(1.0, (int)lg.size());
+    prev = cur;
+  }
+  for (int x : prev) c.maskC |= 1u << pos(lcn, x);
+  c.runC = low_run(c.maskC);
+  c.bitsC = (int)prev.size();
+  c.offC = OFF(last.c);
+  c.planeC = int64_t(1) << lcn.size();
+  c.slotC = last.c;
+  for (int x : la0) {
+    if (pos(ch.inner0, x) >= 0) continue;
+    if (pos(lcn, x) < 0) fail(TNC_E_PLAN, "chain: outer label lost");
+    if (c.n_o >= kMaxOuter) fail(TNC_E_UNSUPPORTED, "chain: too many outer labels");
+    c.o_A[c.n_o] = (int8_t)pos(la0, x);
+    c.o_C[c.n_o] = (int8_t)pos(lcn, x);
+    c.n_o++;
+  }
+  if (c.n_o > 30) fail(TNC_E_UNSUPPORTED, "chain: grid too large");
+  bytes += std::ldexp(1.0, (int)lcn.size());
+  L.bytes = bytes * 2;  // two planes; times the element size by the caller
+  L.grid = dim3(1u << c.n_o, 1, 1);
+  return L;
+}
+
+static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W,
+                                                    bool fuse) {
   const Plan& P = plan->p;
   auto prog = std::make_shared<DeviceProgram>();
   prog->device = ctx->device;
   prog->precision = precision;
   prog->W = W;
   prog->n_qubits = P.net.circ.n;
-  prog->inst_stride = (P.arena_elems + 63) & ~int64_t(63);
+  const bool fused = fuse && !P.chains.empty();
+  prog->inst_stride = ((fused ? P.arena_elems_fused : P.arena_elems) + 63) & ~int64_t(63);
+  auto OFF = [&](int t) {
+    const int64_t o = fused ? P.tensors[t].offset_fused : P.tensors[t].offset;
+    if (o < 0) fail(TNC_E_PLAN, "tensor has no arena slot in this program");
+    return o;
+  };
   prog->n_slots = (int)P.tensors.size();
   prog->n_leaves = (int)P.net.leaves.size();
   const size_t eb = elem_bytes(precision);
@@ -457,23 +580,50 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   // leaves: FP64 sources + descriptors
   {
     std::vector<int64_t> dst(prog->n_leaves);
-    for (int i = 0; i < prog->n_leaves; ++i) dst[i] = P.tensors[i].offset;
+    for (int i = 0; i < prog->n_leaves; ++i) dst[i] = OFF(i);
     upload_leaves(P, dst, prog->leaf_src, prog->leaf_desc);
     prog->leaf_version = P.gate_version;
+    prog->leaf_dst = dst;
   }
   // steps
   size_t partial_elems = 0;
+  std::vector<ChainLink> chain_links;
+  std::vector<uint16_t> chain_in;
+  std::vector<uint8_t> chain_g;
+  std::vector<std::pair<size_t, size_t>> chain_at;  // (launch index, first link index)
   for (size_t s = 0; s < P.steps.size(); ++s) {
     const Step& st = P.steps[s];
     const auto& la = P.tensors[st.a].labels;
     const auto& lb = P.tensors[st.b].labels;
     const auto& lc = P.tensors[st.c].labels;
+    if (fuse && s < P.step_chain.size() && P.step_chain[s] >= 0) {
+      const Chain& ch = P.chains[P.step_chain[s]];
+      if ((int)s != ch.steps.back()) continue;  // the chain runs at its last step
+      const size_t first_link = chain_links.size();
+      StepLaunch L = make_chain_launch(P, ch, chain_links, chain_in, chain_g, OFF);
+      L.cp.stride = prog->inst_stride;
+      L.cp.arena = prog->arena.p;
+      L.cp.maxabs = prog->maxabs.as<float>();
+      L.cp.exps = prog->exps.as<int32_t>();
+      L.cp.n_slots = prog->n_slots;
+      L.bytes *= (double)eb;
+      chain_at.emplace_back(prog->steps.size(), first_link);
+      prog->steps.push_back(L);
+      continue;
+    }
     StepLaunch L = make_launch(st.tile, st.kind, la, lb, lc);
+    {
+      int common = 0;
+      for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
+      L.flops = 8.0 * std::ldexp(1.0, (int)(la.size() + lb.size()) - common);
+      L.bytes = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) + std::ldexp(1.0, (int)lc.size())) *
+                2.0 * double(eb);
+    }
     if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
       const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
       make_tc_launch(L, st.tc_tile, P.tensors[ta].labels, P.tensors[tb].labels, lc, precision, st.tc_bn, st.tc_bk, W);
-      bind_tc(L, prog->arena.as<char>() + P.tensors[ta].offset * eb, prog->arena.as<char>() + P.tensors[tb].offset * eb,
-              prog->arena.as<char>() + P.tensors[st.c].offset * eb, prog->inst_stride, prog->maxabs.as<float>(),
+      bind_tc(L, prog->arena.as<char>() + OFF(ta) * eb, prog->arena.as<char>() + OFF(tb) * eb,
+              prog->arena.as<char>() + OFF(st.c) * eb, prog->inst_stride, prog->maxabs.as<float>(),
               prog->exps.as<int32_t>(), prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), nullptr);
       if (!ctx->no_tma) {
         // operands are laid out [Kt | Mt/Nt | ...] by the compiler: load tiles with TMA
@@ -483,12 +633,19 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
         L.kind = K_TMA;
       }
       if (L.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * L.tp.splitk * L.tp.planeC);
+      {
+        int common = 0;
+        for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
+        L.flops = 8.0 * std::ldexp(1.0, (int)(la.size() + lb.size()) - common);
+        L.bytes = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) + std::ldexp(1.0, (int)lc.size())) *
+                  2.0 * double(eb);
+      }
       prog->steps.push_back(L);
       continue;
     }
-    L.p.A = prog->arena.as<char>() + P.tensors[st.a].offset * eb;
-    L.p.B = prog->arena.as<char>() + P.tensors[st.b].offset * eb;
-    L.p.C = prog->arena.as<char>() + P.tensors[st.c].offset * eb;
+    L.p.A = prog->arena.as<char>() + OFF(st.a) * eb;
+    L.p.B = prog->arena.as<char>() + OFF(st.b) * eb;
+    L.p.C = prog->arena.as<char>() + OFF(st.c) * eb;
     L.p.strideA = L.p.strideB = L.p.strideC = prog->inst_stride;
     L.p.maxabs = prog->maxabs.as<float>();
     L.p.exps = prog->exps.as<int32_t>();
@@ -506,9 +663,24 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
       if ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1) L.tp.partials = L.p.partials = prog->partials.as<float2>();
     }
   }
+  if (!chain_links.empty()) {
+    prog->chain_links.reserve(chain_links.size() * sizeof(ChainLink));
+    prog->chain_in.reserve(chain_in.size() * sizeof(uint16_t));
+    prog->chain_g.reserve(chain_g.size());
+    CUDA_OK(cudaMemcpy(prog->chain_links.p, chain_links.data(), chain_links.size() * sizeof(ChainLink),
+                       cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(prog->chain_in.p, chain_in.data(), chain_in.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(prog->chain_g.p, chain_g.data(), chain_g.size(), cudaMemcpyHostToDevice));
+    for (auto& ca : chain_at) {
+      ChainParams& c = prog->steps[ca.first].cp;
+      c.links = prog->chain_links.as<ChainLink>() + ca.second;
+      c.in_tab = prog->chain_in.as<uint16_t>();
+      c.g_tab = prog->chain_g.as<uint8_t>();
+    }
+  }
   // root
   prog->root = P.root;
-  prog->root_off = P.tensors[P.root].offset;
+  prog->root_off = OFF(P.root);
   prog->root_plane = int64_t(1) << P.tensors[P.root].labels.size();
   prog->n_open = (int)P.net.open_qubits.size();
   std::vector<int8_t> opos(std::max(1, prog->n_open), 0);
@@ -551,6 +723,10 @@ static bool is_device_ptr(const void* p) {
 static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s) {
   StepLaunch L = L0;
   L.grid.z = (unsigned)n_inst;
+  if (L.kind == K_CHAIN) {
+    CUDA_OK(launch_chain(precision, L.cp, n_inst, s));
+    return;
+  }
   if (L.kind == K_TC || L.kind == K_TMA) {
     if (L.kind == K_TMA) CUDA_OK(launch_tc_tma(precision, L.tp, L.grid, s));
     else CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
@@ -644,7 +820,8 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
     const int64_t n_inst = batch * slice_count;
     // wave size
     const size_t eb = elem_bytes(precision);
-    const int64_t stride = (P.arena_elems + 63) & ~int64_t(63);
+    const int64_t stride =
+        ((opts->fuse && !P.chains.empty() ? P.arena_elems_fused : P.arena_elems) + 63) & ~int64_t(63);
     int64_t W = opts->wave > 0 ? opts->wave : 0;
     if (W == 0) {
       size_t free_b = 0, total_b = 0;
@@ -654,7 +831,9 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       W = std::max<int64_t>(1, (int64_t)(budget / per_inst));
     }
     W = std::min<int64_t>({W, n_inst, 65535});
-    const std::string key = std::to_string(ctx->id) + "/" + std::to_string(precision) + "/" + std::to_string(W);
+    const bool fuse = opts->fuse != 0;
+    const std::string key = std::to_string(ctx->id) + "/" + std::to_string(precision) + "/" + std::to_string(W) + "/" +
+                            std::to_string(fuse ? 1 : 0);
     auto it = plan->programs.find(key);
     std::shared_ptr<DeviceProgram> prog;
     if (it == plan->programs.end()) {
@@ -663,15 +842,13 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
         if (jt->first.rfind(std::to_string(ctx->id) + "/", 0) == 0) jt = plan->programs.erase(jt);
         else ++jt;
       }
-      prog = build_program(ctx, plan, precision, (int)W);
+      prog = build_program(ctx, plan, precision, (int)W, fuse);
       plan->programs[key] = prog;
     } else {
       prog = it->second;
       if (prog->leaf_version != P.gate_version) {
         CUDA_OK(cudaStreamSynchronize(s));
-        std::vector<int64_t> dst(prog->n_leaves);
-        for (int i = 0; i < prog->n_leaves; ++i) dst[i] = P.tensors[i].offset;
-        upload_leaves(P, dst, prog->leaf_src, prog->leaf_desc);
+        upload_leaves(P, prog->leaf_dst, prog->leaf_src, prog->leaf_desc);
         prog->leaf_version = P.gate_version;
       }
     }
@@ -717,18 +894,11 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       ps.bytes.assign(prog->steps.size(), 0.0);
       ps.kind.assign(prog->steps.size(), 0);
       ps.kernels.assign(prog->steps.size(), 1);
-      for (size_t k = 0; k < P.steps.size(); ++k) {
-        const auto& la = P.tensors[P.steps[k].a].labels;
-        const auto& lb = P.tensors[P.steps[k].b].labels;
-        const auto& lc = P.tensors[P.steps[k].c].labels;
-        int common = 0;
-        for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
-        const int u = (int)(la.size() + lb.size()) - common;
-        ps.flops[k] = 8.0 * std::ldexp(1.0, u) * double(n_inst);
-        ps.bytes[k] = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) +
-                       std::ldexp(1.0, (int)lc.size())) * 2.0 * double(eb) * double(n_inst);
-        ps.kind[k] = prog->steps[k].kind;
+      for (size_t k = 0; k < prog->steps.size(); ++k) {
         const StepLaunch& SL = prog->steps[k];
+        ps.flops[k] = SL.flops * double(n_inst);
+        ps.bytes[k] = SL.bytes * double(n_inst);
+        ps.kind[k] = SL.kind;
         ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
       }
       CUDA_OK(cudaEventRecord(ps.call_start(), s));

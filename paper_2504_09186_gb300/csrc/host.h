@@ -90,6 +90,7 @@ struct PlanOpts {
   int slices_min = 0;
   int slices_max = 64;
   double temperature = 0.5;
+  int mode = 0;  // 0 greedy, 1 stem
 };
 
 // Kernel classes of a compiled step.
@@ -110,11 +111,6 @@ struct TileSpec {
   int splitk = 1;                // CTAs along the outer K labels
 };
 
-struct ChainLink {
-  int b;                          // small operand tensor id
-  std::vector<int> c_labels;      // labels of the result after this link
-};
-
 struct Step {
   int a, b, c;                    // tensor ids (A = the larger operand)
   int kind = K_GENERIC;
@@ -125,17 +121,21 @@ struct Step {
   TileSpec tc_tile;
   bool tc_swap = false;           // tensor-core rows come from b (b has more free labels)
   int tc_bn = 128, tc_bk = 64;    // tile width and K tile of the tensor-core kernel
-  // chain steps: A absorbs b_0, b_1, ... in order; c = final result
-  std::vector<int> chain_b;       // operand ids of each link (first = b)
-  std::vector<int> chain_c;       // tensor ids produced by each link (last = c)
-  int chain_inner = 0;            // number of low positions kept on chip
+};
+
+// A fused chain (Sec. IV): consecutive absorptions of small tensors into one large
+// tensor executed as one kernel that keeps a tile over the `inner` labels on chip.
+struct Chain {
+  std::vector<int> steps;         // step indices in order (link i's a = link i-1's c)
+  std::vector<int> inner0;        // labels of the first big operand kept on chip
 };
 
 struct TensorInfo {
   std::vector<int> labels;        // storage order (position p = bit p)
   int producer = -1;              // step index, -1 for leaves
   int last_use = -1;              // step index of last consumer (root: n_steps)
-  int64_t offset = -1;            // element offset in the arena (per instance)
+  int64_t offset = -1;            // scalar offset in the arena (per instance), unfused program
+  int64_t offset_fused = -1;      // ... in the fused program (-1: lives on chip inside a chain)
   int leaf = -1;                  // leaf index for leaf tensors
   bool on_chip = false;           // intermediate of a fused chain, never stored
 };
@@ -150,7 +150,8 @@ struct Plan {
   int root = -1;
   double log2_flops_slice = 0, log2_flops_total = 0, overhead = 1;
   int max_log2 = 0;
-  int64_t arena_elems = 0;                 // per instance, in elements (complex)
+  int64_t arena_elems = 0;                 // per instance, in scalars, unfused program
+  int64_t arena_elems_fused = 0;           // per instance, in scalars, fused program
   // fixed-leg bookkeeping for the leaf gather: for each leaf, positions of sliced legs
   // (with slice bit index) and closed output legs (with qubit)
   struct LegFix {
@@ -159,6 +160,8 @@ struct Plan {
     int index;   // slice bit t, or qubit q
   };
   std::vector<std::vector<LegFix>> leaf_fix;
+  std::vector<Chain> chains;               // fused chains (empty when compiled with fuse = false)
+  std::vector<int> step_chain;             // per step: chain index or -1
   int n_gemm = 0, n_gepdot = 0, n_absorb = 0, n_fused = 0;
   double narrow_max = 0;
   bool fuse = true;

@@ -451,6 +451,122 @@ __global__ void k_maxabs(const T* __restrict__ x, int64_t n, float* out) {
   if (threadIdx.x == 0) atomic_max_nonneg(out, bm);
 }
 
+// Fused chain: load a tile of A0 over the on-chip labels, apply every link in FP32 in
+// shared memory (out[x] = sum_k in[in_tab[x] + kin[k]] * g[g_tab[x] + kg[k]]), store the
+// result tile once.  The result is scaled by the power of two that brings the bound
+// sqrt2 * max|A0| * prod_links max_n sum_k |g[k, n]| below 2^15 (|C| cannot exceed it).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* buf1 = buf0 + (1 << kChainMaxBits);
+  float2* gs = buf1 + (1 << kChainMaxBits);                        // [64]
+  uint16_t* kin = reinterpret_cast<uint16_t*>(gs + 64);              // [64]
+  uint8_t* kg = reinterpret_cast<uint8_t*>(kin + 64);                // [64]
+  float* red = reinterpret_cast<float*>(kg + 64);                    // [33]
+  uint32_t* hiA = reinterpret_cast<uint32_t*>(red + 36);             // [2^(bits0 - runA0)]
+  uint32_t* hiC = hiA + (1 << (p.bits0 - p.runA0));                  // [2^(bitsC - runC)]
+  const int tid = threadIdx.x;
+  const int64_t inst = blockIdx.z;
+  const uint32_t o = blockIdx.x;
+  int64_t oA = 0, oC = 0;
+  for (int j = 0; j < p.n_o; ++j)
+    if ((o >> j) & 1u) oA += int64_t(1) << p.o_A[j], oC += int64_t(1) << p.o_C[j];
+  for (int h = tid; h < (1 << (p.bits0 - p.runA0)); h += kThreads) hiA[h] = deposit_hi(h, p.maskA0, p.runA0);
+  for (int h = tid; h < (1 << (p.bitsC - p.runC)); h += kThreads) hiC[h] = deposit_hi(h, p.maskC, p.runC);
+  __syncthreads();
+  const T* base = reinterpret_cast<const T*>(p.arena) + inst * p.stride;
+  const T* A0 = base + p.offA0 + oA;
+  load_tile<T>(A0, A0 + p.planeA0, p.bits0, p.runA0, hiA, buf0);
+  const int64_t sb = inst * p.n_slots;
+  float bound = 1.41421356f * p.maxabs[sb + p.slotA0];
+  int esum = p.exps[sb + p.slotA0];
+  float2* in = buf0;
+  float2* out = buf1;
+  for (int l = 0; l < p.n_links; ++l) {
+    const ChainLink* L = p.links + l;
+    const T* g = base + L->g_off;
+    for (int t = tid; t < L->g_size; t += kThreads) gs[t] = make_float2(Conv<T>::to_f(g[t]), Conv<T>::to_f(g[L->g_plane + t]));
+    const int nk = 1 << L->k_bits;
+    for (int t = tid; t < nk; t += kThreads) {
+      kin[t] = L->kin[t];
+      kg[t] = L->kg[t];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // column norm of the small operand: max over free-label assignments of sum_k |g|
+      float cn = 0.f;
+      for (int n = 0; n < (1 << L->n_bits); ++n) {
+        float s = 0.f;
+        for (int q = 0; q < nk; ++q) {
+          const float2 v = gs[L->gn[n] + kg[q]];
+          s += sqrtf(v.x * v.x + v.y * v.y);
+        }
+        cn = fmaxf(cn, s);
+      }
+      red[32] = cn;
+    }
+    const int nout = 1 << L->out_bits;
+    const uint16_t* itab = p.in_tab + L->tab;
+    const uint8_t* gtab = p.g_tab + L->tab;
+    for (int x = tid; x < nout; x += kThreads) {
+      const int ib = itab[x], gb = gtab[x];
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < nk; ++q) {
+        const float2 a = in[ib + kin[q]];
+        const float2 b = gs[gb + kg[q]];
+        acc.x = fmaf(a.x, b.x, acc.x);
+        acc.x = fmaf(-a.y, b.y, acc.x);
+        acc.y = fmaf(a.x, b.y, acc.y);
+        acc.y = fmaf(a.y, b.x, acc.y);
+      }
+      out[x] = acc;
+    }
+    __syncthreads();
+    bound *= red[32];
+    esum += p.exps[sb + L->slot_g];
+    float2* t = in;
+    in = out;
+    out = t;
+  }
+  int sh = 0;
+  if (bound > 0.f) {
+    frexpf(bound, &sh);  // bound < 2^sh
+    sh -= 15;
+  }
+  const float scale = ldexpf(1.f, -sh);
+  T* C = reinterpret_cast<T*>(const_cast<void*>(p.arena)) + inst * p.stride + p.offC + oC;
+  const float mx = store_tile<T>(C, C + p.planeC, p.bitsC, p.runC, hiC, in, scale);
+  const float bm = block_max(mx, red);
+  if (tid == 0) {
+    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
+    if (blockIdx.x == 0) p.exps[sb + p.slotC] = esum + sh;
+  }
+}
+
+size_t chain_smem_bytes(int bits0, int runA0, int bitsC, int runC) {
+  return (size_t(2) << kChainMaxBits) * 8 + 64 * 8 + 64 * 2 + 64 + 36 * 4 + (size_t(1) << (bits0 - runA0)) * 4 +
+         (size_t(1) << (bitsC - runC)) * 4 + 16;
+}
+
+cudaError_t launch_chain(int precision, const ChainParams& p, int64_t n_inst, cudaStream_t s) {
+  const size_t smem = chain_smem_bytes(p.bits0, p.runA0, p.bitsC, p.runC);
+  dim3 grid(1u << p.n_o, 1, (unsigned)n_inst);
+  cudaError_t e;
+  if (precision == 0) {
+    e = set_smem_once(reinterpret_cast<const void*>(k_chain<float>), smem);
+    if (e == cudaSuccess) k_chain<float><<<grid, kThreads, smem, s>>>(p);
+  } else if (precision == 1) {
+    e = set_smem_once(reinterpret_cast<const void*>(k_chain<__half>), smem);
+    if (e == cudaSuccess) k_chain<__half><<<grid, kThreads, smem, s>>>(p);
+  } else {
+    e = set_smem_once(reinterpret_cast<const void*>(k_chain<__nv_bfloat16>), smem);
+    if (e == cudaSuccess) k_chain<__nv_bfloat16><<<grid, kThreads, smem, s>>>(p);
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launch helpers
 template <typename T>
 using GenKernel = void (*)(const GenParams);

@@ -12,7 +12,7 @@
 namespace tnc {
 
 namespace {
-const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '1'};
+const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '2'};
 
 template <class T>
 void put(std::ofstream& f, const T& v) {
@@ -52,6 +52,7 @@ void save_plan(const Plan& p, const std::string& path) {
   put<int32_t>(f, p.opts.slices_min);
   put<int32_t>(f, p.opts.slices_max);
   put<double>(f, p.opts.temperature);
+  put<int32_t>(f, p.opts.mode);
   put<int32_t>(f, (int32_t)p.sliced.size());
   for (int e : p.sliced) put<int32_t>(f, e);
   put<int32_t>(f, (int32_t)p.tree.size());
@@ -100,6 +101,7 @@ void load_plan(const std::string& path, Plan& p) {
   p.opts.slices_min = get<int32_t>(f);
   p.opts.slices_max = get<int32_t>(f);
   p.opts.temperature = get<double>(f);
+  p.opts.mode = get<int32_t>(f);
   const int32_t ns = get<int32_t>(f);
   if (ns < 0 || ns > 62) fail(7, "corrupt slice count");
   for (int i = 0; i < ns; ++i) {

@@ -121,6 +121,51 @@ Tree greedy_tree(const std::vector<LabelSet>& leaves, int n_edges, Rng& rng, dou
   return t;
 }
 
+// Stem order: one growing tensor absorbs, one at a time, the leaf sharing labels with it
+// that keeps it smallest (Gumbel-perturbed; ties: more shared labels, lower id).  Leaves
+// not connected to the stem are absorbed (outer product) when nothing else is left.
+Tree stem_tree(const std::vector<LabelSet>& leaves, int n_edges, Rng& rng, double temperature, int start) {
+  Tree t;
+  t.sets = leaves;
+  const int L = (int)leaves.size();
+  std::vector<char> used(L, 0);
+  std::vector<std::vector<int>> owners(n_edges);
+  for (int i = 0; i < L; ++i)
+    for (int e : leaves[i]) owners[e].push_back(i);
+  int cur = start;
+  used[start] = 1;
+  for (int step = 1; step < L; ++step) {
+    const LabelSet& S = t.sets[cur];
+    std::vector<int> cand;
+    for (int e : S)
+      for (int o : owners[e])
+        if (o < L && !used[o]) cand.push_back(o);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    int pick = -1;
+    if (cand.empty()) {
+      size_t best = ~size_t(0);
+      for (int i = 0; i < L; ++i)
+        if (!used[i] && leaves[i].size() < best) best = leaves[i].size(), pick = i;
+    } else {
+      double best = std::numeric_limits<double>::infinity();
+      for (int o : cand) {
+        const LabelSet out = sym_diff(S, leaves[o]);
+        LabelSet sh;
+        std::set_intersection(S.begin(), S.end(), leaves[o].begin(), leaves[o].end(), std::back_inserter(sh));
+        double score = (double)out.size() - 0.01 * (double)sh.size();
+        if (temperature > 0) score -= temperature * rng.gumbel();
+        if (score < best) best = score, pick = o;
+      }
+    }
+    used[pick] = 1;
+    t.pairs.emplace_back(cur, pick);
+    t.sets.push_back(sym_diff(S, leaves[pick]));
+    cur = (int)t.sets.size() - 1;
+  }
+  return t;
+}
+
 double tree_cost(const Tree& t, const std::vector<char>& sliced) {
   double c = 0;
   for (auto& p : t.pairs) {
@@ -165,7 +210,11 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
 
   for (int trial = 0; trial < o.trials; ++trial) {
     Rng rng{o.seed * 0x100000001B3ull + 0x9E3779B97F4A7C15ull * (uint64_t)(trial + 1)};
-    Tree t = leaves.size() == 1 ? Tree{{}, leaves} : greedy_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature);
+    Tree t;
+    if (leaves.size() == 1) t = Tree{{}, leaves};
+    else if (o.mode == 1) t = stem_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature,
+                                       (int)(rng.next() % leaves.size()));
+    else t = greedy_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature);
     std::vector<char> sl(n_edges, 0);
     std::vector<int> sliced;
     const double c0 = tree_cost(t, sl);

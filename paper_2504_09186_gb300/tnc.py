@@ -46,6 +46,7 @@ class tnc_plan_opts(C.Structure):
         ("slices_min", C.c_int32),
         ("slices_max", C.c_int32),
         ("temperature", C.c_double),
+        ("mode", C.c_int32),
     ]
 
 
@@ -164,9 +165,9 @@ def tnc_network_build(circuit, open_mask: Optional[np.ndarray]):
     return h
 
 
-def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5):
+def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5, mode=0):
     lib = load_library()
-    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature)
+    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode)
     h = C.c_void_p()
     _check(lib.tnc_plan_greedy(network, C.byref(o), C.byref(h)))
     return h
@@ -182,8 +183,9 @@ class Plan:
 
     @classmethod
     def greedy(cls, circuit, open_qubits: Sequence[int] = (), seed: int = 1, trials: int = 16, log2_cap: int = 26,
-               slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5) -> "Plan":
-        """Plan for an `inputs.Circuit` (gate list) with the given open output qubits."""
+               slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy") -> "Plan":
+        """Plan for an `inputs.Circuit` (gate list) with the given open output qubits.
+        mode: "greedy" (balanced pairwise order) or "stem" (one tensor absorbs leaves)."""
         lib = load_library()
         arity, qubits, mats = circuit.gate_array()
         ch = tnc_circuit_from_gates(circuit.n_qubits, arity, qubits, mats)
@@ -192,7 +194,8 @@ class Plan:
             mask[list(open_qubits)] = 1
             nh = tnc_network_build(ch, mask)
             try:
-                ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature)
+                ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature,
+                                     {"greedy": 0, "stem": 1}[mode])
             finally:
                 lib.tnc_network_destroy(nh)
         finally:

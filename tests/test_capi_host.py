@@ -63,12 +63,13 @@ def _recount(desc):
     return cost, biggest
 
 
+@pytest.mark.parametrize("mode", ["greedy", "stem"])
 @pytest.mark.parametrize("rows,cols,cycles,n_open,cap,smin", [(3, 4, 8, 0, 26, 0), (4, 4, 10, 4, 12, 3), (3, 3, 6, 2, 8, 0)])
-def test_plan_invariants(rows, cols, cycles, n_open, cap, smin):
+def test_plan_invariants(rows, cols, cycles, n_open, cap, smin, mode):
     c = grid_circuit(rows, cols, cycles, seed=1)
     n = c.n_qubits
     _, open_q = subcube_spec(n, n_open, seed=2)
-    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=cap, slices_min=smin)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=cap, slices_min=smin, mode=mode)
     info = p.info()
     d = p.describe()
     L = len(d["leaves"])
@@ -123,3 +124,21 @@ def test_slicing_overhead_is_eq1_product():
     assert info["n_sliced"] > 0
     assert info["slicing_overhead"] >= 1.0 - 1e-12
     assert math.isclose(info["log2_total_flops"], info["log2_flops_per_slice"] + info["n_sliced"], rel_tol=1e-12)
+
+
+def test_stem_plan_is_a_stem_and_fuses():
+    # every step of a stem plan absorbs a leaf into the previous result (Sec. II-A stem)
+    c = grid_circuit(4, 4, 10, seed=1)
+    p = T.Plan.greedy(c, seed=3, trials=4, log2_cap=12, mode="stem")
+    d = p.describe()
+    L = len(d["leaves"])
+    for s, (a, b) in enumerate(d["tree"]):
+        assert min(a, b) < L  # one operand is a leaf
+        if s > 0:
+            assert max(a, b) == L + s - 1  # the other is the previous result
+    chains = {}
+    for i, st in enumerate(d["steps"]):
+        if st["chain"] >= 0:
+            chains.setdefault(st["chain"], []).append(i)
+    assert chains and all(len(v) >= 2 for v in chains.values())
+    assert p.info()["n_fused"] == sum(len(v) for v in chains.values())

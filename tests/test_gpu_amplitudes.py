@@ -126,3 +126,20 @@ def test_edge_cases(ctx):
         ctx.amplitudes(p, bs, "c64", slice_begin=0, slice_count=2)
     with pytest.raises(T.TncError):
         ctx.amplitudes(p, bs * 2, "c64")
+
+
+@pytest.mark.parametrize("rows,cols,cycles,n_open,cap", [(4, 4, 10, 4, 12), (4, 5, 12, 6, 18)])
+def test_stem_plan_fused_chains(ctx, rows, cols, cycles, n_open, cap):
+    # stem order: one tensor absorbs the leaves; long absorb chains run as fused kernels
+    c = grid_circuit(rows, cols, cycles, seed=1)
+    n = c.n_qubits
+    fixed, open_q = subcube_spec(n, n_open, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=cap, mode="stem")
+    info = p.info()
+    assert info["n_fused"] >= 4
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    for prec in ("c64", "chalf"):
+        fused = ctx.amplitudes(p, fixed[None, :], prec, fuse=True)[0]
+        plain = ctx.amplitudes(p, fixed[None, :], prec, fuse=False)[0]
+        assert metrics.rel_err_norm(fused, ref) <= TOL[prec], prec
+        assert metrics.rel_err_norm(plain, ref) <= TOL[prec], prec
