@@ -59,11 +59,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="s30", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="s30", choices=sorted(WORKLOADS) + ["s60", "d20", "sw"],
+                    help="s30 (default) / t12: sliced sub-cube amplitudes; s60: per-slice throughput of the "
+                         "60-qubit circuit; d20: adjoint gradients; sw: single-step contraction sweep")
+    ap.add_argument("--s60-slices", type=int, default=4, help="seeded slice sample of the s60 workload")
+    ap.add_argument("--s60-trials", type=int, default=16, help="planner trials of the s60 workload")
+    ap.add_argument("--s60-c64", type=int, default=2, help="slices of the sample also run in complex64")
+    ap.add_argument("--sw-shapes", default="", help="log2 M,K,N triples 'm,k,n;m,k,n' (default: a fixed set)")
     ap.add_argument("--precision", default="chalf", choices=["chalf", "cbf16", "c64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the complex64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cap", type=int, default=23, help="log2 size cap of the oracle sample")
+    ap.add_argument("--ref-subslices", type=int, default=24, help="oracle sub-slices per reference step")
     ap.add_argument("--plan", default="greedy", choices=["greedy", "stem"],
                     help="greedy: balanced pairwise order; stem: one tensor absorbs leaves (fused chains)")
     ap.add_argument("--no-fuse", action="store_true", help="run stem absorptions as separate kernels")
@@ -138,18 +145,30 @@ class ClockSampler:
 def oracle_sample(circ, fixed, open_q, cuts, cap_log2):
     """Prepare a bounded oracle sample: slice 0 of the plan's slicing (cuts fixed to 0),
     split further by the oracle's own sub-slicing at 2^cap_log2; returns (run, n_sub):
-    `run()` contracts one sub-slice, and a whole slice is n_sub such runs."""
+    `run(i)` contracts sub-slice i, and a whole slice is the n_sub sub-slices."""
     from oracle import network as tn
 
     tensors, open_labels = tn.circuit_tensors(circ, fixed, open_q)
     tensors = tn.fix_labels(tensors, {("w", q, j): 0 for (q, j) in cuts})
     order, extra = tn.search_order([t.labels for t in tensors], open_labels, cap_log2, trials=8)
-    sub = tn.fix_labels(tensors, {lab: 0 for lab in extra})
 
-    def run():
+    def run(i=0):
+        sub = tn.fix_labels(tensors, {lab: (i >> t) & 1 for t, lab in enumerate(extra)})
         return tn.contract_network(sub, open_labels, order)
 
     return run, 2 ** len(extra)
+
+
+def timed_oracle(run, n_sub, min_seconds):
+    """Run sub-slices 0, 1, ... until at least `min_seconds` passed; returns (count, seconds)."""
+    t0 = time.perf_counter()
+    k = 0
+    while k < n_sub:
+        run(k)
+        k += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    return k, time.perf_counter() - t0
 
 
 def cpu_cores():
@@ -170,13 +189,15 @@ def run_reference(args):
                          slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
     cuts = plan.sliced_cuts()
     run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
+    per_step = min(args.ref_subslices, n_sub)
     for _ in range(args.warmup):
-        run()
+        run(0)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        run()
+        for i in range(per_step):
+            run(i)
     dt = (time.perf_counter() - t0) / args.steps
-    value = 1.0 / (dt * n_sub)
+    value = per_step / (dt * n_sub)
     cores = cpu_cores()
     line = {
         "impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": args.gpus,
@@ -185,8 +206,8 @@ def run_reference(args):
         "config": {"workload": f"{args.workload}: 5x6 grid RQC, 14 cycles, 2^6 slices, cap 2^26, 1024-amplitude sub-cube",
                    "plan": args.plan},
         "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores, "kind": "oracle",
-                         "sample": f"each step = 1 of {n_sub} oracle sub-contractions of slice 0 (cap 2^{args.cpu_sample_cap}); "
-                                   f"slices/s = 1 / (step time * {n_sub})"},
+                         "sample": f"each step = sub-slices 0..{per_step - 1} of the {n_sub} oracle sub-contractions of "
+                                   f"slice 0 (FP64, cap 2^{args.cpu_sample_cap}); slices/s = {per_step} / (step time * {n_sub})"},
         "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -320,12 +341,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cuts = plan.sliced_cuts()
         run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
-        t0 = time.perf_counter()
-        run()
-        dt = time.perf_counter() - t0
-        cpu = {"value": 1.0 / (dt * n_sub), "unit": "slices/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"1 of {n_sub} oracle sub-contractions of slice 0 (FP64, cap 2^{args.cpu_sample_cap}), "
-                         f"{dt:.1f} s; slices/s = 1 / (t * {n_sub})"}
+        k, dt = timed_oracle(run, n_sub, 10.0)
+        cpu = {"value": k / (dt * n_sub), "unit": "slices/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"sub-slices 0..{k - 1} of the {n_sub} oracle sub-contractions of slice 0 (FP64, cap "
+                         f"2^{args.cpu_sample_cap}), {dt:.1f} s; slices/s = {k} / (t * {n_sub})"}
 
     if rank == 0:
         line = {
@@ -356,10 +375,212 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- other workloads
+def roofline_of(kind, flops, nbytes, ms, peaks):
+    """Roofline of one kernel launch from its algorithmic flops / bytes and device time."""
+    if kind in (3, 4):
+        r = {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
+    elif flops / max(nbytes, 1.0) > 8.0:
+        alu = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        r = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": alu, "unit": "TFLOP/s"}
+    else:
+        r = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
+
+
+SW_POINTS = [(14, 12, 10), (12, 12, 12), (16, 8, 16), (16, 12, 12), (12, 16, 12), (12, 20, 12), (16, 4, 16),
+             (4, 16, 16), (16, 16, 4), (8, 16, 8), (8, 24, 8), (4, 24, 4), (2, 24, 2), (1, 24, 1), (2, 20, 2)]
+
+
+def sweep_labels(m, k, n, layout, seed):
+    """Index labels of one sweep point.  'random': seeded random axis orders of A, B and C.
+    'arranged': the order the step compiler gives tensor-core steps (K tile labels, then
+    the M / N tile labels, lowest), the rest random."""
+    rng = np.random.default_rng(seed)
+    ms, ks, ns = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
+    perm = lambda v: [int(x) for x in rng.permutation(v)] if v else []
+    if layout == "arranged":
+        kt = 5 if k >= 5 else 4
+        nt = 8 if (n >= 8 and k > kt + 1) else (7 if n >= 7 else 6)
+        return (ks[:kt] + ms[:7] + perm(ms[7:] + ks[kt:]), ks[:kt] + ns[:nt] + perm(ns[nt:] + ks[kt:]),
+                [ns[0], ms[0], ns[1]] + perm(ms[1:] + ns[2:]))
+    return perm(ms + ks), perm(ks + ns), perm(ms + ns)
+
+
+def run_sweep(args):
+    import torch
+
+    from paper_2504_09186_gb300 import tnc as T
+
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    peaks = load_peaks()
+    dt = {"chalf": torch.float16, "cbf16": torch.bfloat16, "c64": torch.float32}
+    pts = [tuple(int(x) for x in s.split(",")) for s in args.sw_shapes.split(";")] if args.sw_shapes else SW_POINTS
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = []
+    for (m, k, n) in pts:
+        layouts = ["arranged", "random"] if (m >= 7 and n >= 6 and k >= 4) else ["random"]
+        for layout in layouts:
+            seed = 1000003 * m + 1009 * k + n + (7 if layout == "random" else 0)
+            la, lb, lc = sweep_labels(m, k, n, layout, seed)
+            for prec in ("chalf", "cbf16", "c64"):
+                if prec == "c64" and (m + k + n > 40 or max(m + k, k + n, m + n) > 28):
+                    continue  # FP32 SIMT path: keep each point under a few seconds
+                if prec == "cbf16" and layout == "random":
+                    continue  # same kernels and rates as chalf
+                g = torch.Generator(device="cuda")
+                g.manual_seed(seed)
+                sig = (2.0 ** -k) ** 0.5 / 2 ** 0.5
+                a = torch.randn(2 << len(la), dtype=dt[prec], device="cuda", generator=g).mul_(sig)
+                b = torch.randn(2 << len(lb), dtype=dt[prec], device="cuda", generator=g).mul_(sig)
+                c = torch.empty(2 << len(lc), dtype=dt[prec], device="cuda")
+                for _ in range(args.warmup):
+                    ctx.contract(prec, a, la, b, lb, c, lc)
+                times = []
+                for _ in range(args.steps):
+                    flush.zero_()
+                    ctx.contract(prec, a, la, b, lb, c, lc)
+                    pr = ctx.profile_read(cap=1)
+                    times.append(float(pr["ms"][0]))
+                ms = statistics.median(times)
+                kind, fl, by = int(pr["kind"][0]), float(pr["flops"][0]), float(pr["bytes"][0])
+                r = roofline_of(kind, fl, by, ms, peaks)
+                out.append({"m": m, "k": k, "n": n, "layout": layout, "precision": prec, "kernel_kind": kind,
+                            "launches": int(pr["launches"][0]), "ms": ms, "tflops": fl / ms / 1e9,
+                            "gbs": by / ms / 1e6, "bound": r["bound"], "frac": r["frac"]})
+                del a, b, c
+                torch.cuda.empty_cache()
+    head = next((p for p in out if (p["m"], p["k"], p["n"], p["layout"], p["precision"]) == (14, 12, 10, "arranged", "chalf")), out[0])
+    line = {"metric": "complex TFLOP/s per contraction step", "value": head["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "sw: single pairwise contractions, log2 (M,K,N) points, complex normal(0, 1/sqrt(K))",
+                       "value_point": [head["m"], head["k"], head["n"], head["layout"], head["precision"]],
+                       "l2": "256 MiB flush before every timed call", "timing": "contraction kernels only (CUDA events)"},
+            "points": out}
+    print(json.dumps(line))
+
+
+def run_s60(args):
+    import torch
+
+    from inputs import grid_circuit, random_bitstrings
+    from paper_2504_09186_gb300 import tnc as T
+
+    torch.cuda.set_device(0)
+    circ = grid_circuit(6, 10, 24, seed=1)
+    bits = random_bitstrings(60, 1, seed=4)
+    t0 = time.perf_counter()
+    plan = T.Plan.greedy(circ, open_qubits=[], seed=3, trials=args.s60_trials, log2_cap=32)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    s = info["n_sliced"]
+    rng = np.random.default_rng(4)
+    space = 1 << min(s, 62)
+    ids = []
+    while len(ids) < args.s60_slices:
+        x = int(rng.integers(0, space))
+        if x not in ids:
+            ids.append(x)
+    ctx = T.Context(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = torch.zeros((1, 1), dtype=torch.complex128, device="cuda")
+    peaks = load_peaks()
+
+    def one(prec, sid, profile):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.amplitudes(plan, bits, prec, slice_begin=sid, slice_count=1, out=out, stream=stream.cuda_stream,
+                       profile=profile)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), complex(out.cpu().numpy()[0, 0])
+
+    for _ in range(max(1, args.warmup)):
+        one("chalf", ids[0], False)
+    with ClockSampler(0) as clk:
+        res = [one("chalf", sid, True) for sid in ids]
+        prof = ctx.profile_read()
+    clocks = clk.summary()
+    ms = [r[0] for r in res]
+    per_slice_s = sum(ms) / len(ms) / 1e3
+    value = 1.0 / per_slice_s
+    k = int(np.argmax(prof["ms"]))
+    roof = roofline_of(int(prof["kind"][k]), prof["flops"][k] / prof["launches"][k], prof["bytes"][k] / prof["launches"][k],
+                       prof["ms"][k] / prof["launches"][k], peaks)
+    roof["traffic"] = None
+    roof["kernel"] = {"step": k, "kind": int(prof["kind"][k]), "share_of_slice_time": float(prof["ms"][k] / prof["ms"].sum())}
+    cmp64 = []
+    for sid, (_, a16) in list(zip(ids, res))[: args.s60_c64]:
+        try:
+            ms64, a64 = one("c64", sid, False)
+            cmp64.append({"slice": sid, "ms": ms64, "rel_err_chalf_vs_c64": abs(a16 - a64) / max(abs(a64), 1e-300)})
+        except Exception as exc:  # a complex64 arena that does not fit is reported, not fatal
+            cmp64.append({"slice": sid, "error": str(exc).splitlines()[0]})
+    line = {"metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 1, "steps": len(ids),
+            "warmup": max(1, args.warmup), "ms_per_step": per_slice_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "s60: 6x10 grid RQC, 24 cycles, cap 2^32 chalf entries, one bitstring; "
+                                   "per-slice time over a seeded slice sample",
+                       "slice_ids": ids, "sliced_indices": s, "plan_trials": args.s60_trials, "plan_seconds": plan_s,
+                       "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"],
+                       "complex_tflops": 8 * 2 ** info["log2_flops_per_slice"] * value / 1e12,
+                       "extrapolated_total_log2_seconds": s - float(np.log2(value))},
+            "per_slice_ms": ms, "complex64": cmp64, "roofline": roof, "clocks": clocks}
+    print(json.dumps(line))
+
+
+def run_d20(args):
+    import torch
+
+    from inputs import grid_circuit, random_bitstrings
+    from paper_2504_09186_gb300 import tnc as T
+
+    torch.cuda.set_device(0)
+    circ = grid_circuit(4, 5, 12, seed=1, fsim_mode="uniform", param_seed=5)
+    bits = random_bitstrings(20, 256, seed=6)
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=256) + 1j * rng.normal(size=256)
+    plan = T.Plan.greedy(circ, open_qubits=[], seed=3, trials=8, log2_cap=20)
+    ar = [len(g.qubits) for g in circ.gates]
+    ctx = T.Context(0)
+    for _ in range(args.warmup):
+        ctx.adjoint(plan, bits, w[:, None], ar)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.adjoint(plan, bits, w[:, None], ar)
+    adj_s = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.amplitudes(plan, bits, "c64")
+    fwd_s = (time.perf_counter() - t0) / args.steps
+    line = {"metric": "gradient evaluations/s", "value": 1.0 / adj_s, "unit": "adjoint calls/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": adj_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "d20: 4x5 grid RQC, 12 cycles, fSim angles U[0,pi], 256 bitstrings, complex64; "
+                                   "one call = amplitudes + gradients w.r.t. every gate (host buffers, wall clock)",
+                       "n_gates": len(ar), "forward_only_ms": fwd_s * 1e3}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload in WORKLOADS:
+            run_reference(args)
+        elif int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the s30/t12 workloads only"}))
+    elif args.workload == "sw":
+        run_sweep(args)
+    elif args.workload == "s60":
+        run_s60(args)
+    elif args.workload == "d20":
+        run_d20(args)
     else:
         run_ours(args)
 

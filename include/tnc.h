@@ -167,7 +167,8 @@ typedef struct {
 
 /* Amplitudes of a batch (Sec. I; the multi-amplitude batch of Sec. II-C), summed over
  * the slice ids [slice_begin, slice_begin + slice_count) (Sec. III-A: subtasks are
- * independent and their results add).
+ * independent and their results add).  Slice id bit t fixes sliced index t; with 63 or
+ * more sliced indices the ids address the slices whose indices 63 and up are 0.
  *  bitstrings  batch x n_qubits bytes (host); bits of open qubits are ignored.  May be
  *              NULL when batch == 1 and every qubit is open.
  *  out         batch x 2^n_open complex128 as interleaved (re, im) doubles; host or
@@ -188,7 +189,8 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts
  *  env_out  n_gates x 32 doubles (host): dL/dU_g as d x d row-major complex (d = 2 or 4) in
  *           the first d*d entries, the layout of the matrices of tnc_circuit_from_gates
  *  amp_out  optional (may be NULL): the amplitudes, as tnc_amplitudes
- * Computed in C64 (FP32) with the FP64 cross-slice accumulation. */
+ * Computed in C64 (FP32) with the FP64 cross-slice accumulation, over every slice of the
+ * plan (TNC_E_UNSUPPORTED above 30 sliced indices). */
 tnc_status tnc_adjoint(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
                        const uint8_t* bitstrings, int64_t batch, const double* weights,
                        double* env_out, double* amp_out, void* stream);
@@ -232,13 +234,15 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
                                 int32_t rank_c, const int32_t* labels_c, int32_t* c_exp2, void* stream);
 
 /* Per-launch timings of the last tnc_amplitudes call made with opts->profile = 1 on this
- * context (waits for it).  Entry s is the s-th launch of the per-wave program (a step, or a
+ * context, or of the last tnc_contract call (always timed: one entry, the contraction's
+ * kernels without the two operand max passes; ms[1] the whole call) (waits for it).  Entry s is the s-th launch of the per-wave program (a step, or a
  * whole fused chain; cap >= n entries):
  *  ms[s]      device time summed over the call's launches of that step (CUDA events)
  *  launches[s] kernel launches of that step (per wave: 1, or 2 for a split step's reduce)
  *  flops[s]   algorithmic real flops of those launches: 8 * M * N * K per instance
  *  bytes[s]   algorithmic bytes: (|A| + |B| + |C|) * element size per instance
- *  kind[s]    kernel class (0 generic, 1 split-K GEPDOT, 2 fused chain, 3 tensor-core)
+ *  kind[s]    kernel class (0 generic, 1 split-K GEPDOT, 2 fused chain, 3 tensor-core with
+ *             cp.async gathers, 4 tensor-core with TMA loads)
  *  ms[n]      (one extra entry) the whole call's device time
  * *n receives the number of steps. */
 tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,

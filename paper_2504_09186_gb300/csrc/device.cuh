@@ -100,11 +100,14 @@ constexpr int kChainMaxBits = 12;  // on-chip tile <= 2^12 complex entries
 struct ChainLink {
   int64_t g_off;     // arena offset (scalars, instance 0) of the small operand
   int64_t g_plane;   // 2^rank(small operand)
-  int64_t tab;       // offset of this link's entries in in_tab / g_tab
   int32_t slot_g, g_size, out_bits, k_bits, n_bits;
   uint16_t kin[64];  // tile offset of each common-label assignment in the previous tile
   uint8_t kg[64];    // ... and in the small operand
   uint8_t gn[64];    // small-operand offset of each free-label assignment (bound only)
+  // output entry x -> (offset in the previous tile, offset in the small operand); both are
+  // bit scatters of x, so they split over x's low and high six bits
+  uint16_t ib_lo[64], ib_hi[64];
+  uint8_t gb_lo[64], gb_hi[64];
 };
 struct ChainParams {
   const void* arena;
@@ -116,8 +119,6 @@ struct ChainParams {
   int8_t o_A[kMaxOuter], o_C[kMaxOuter];  // outer (grid) labels: positions in A0 and in C
   int32_t n_links;
   const ChainLink* links;
-  const uint16_t* in_tab;             // per link, per output entry: offset in the previous tile
-  const uint8_t* g_tab;               // ... and in the small operand
   float* maxabs;
   int32_t* exps;
   int32_t n_slots, slotA0, slotC;

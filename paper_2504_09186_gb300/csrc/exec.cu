@@ -333,7 +333,7 @@ struct DeviceProgram {
   int device = 0, precision = 0, W = 0;
   int64_t inst_stride = 0;  // scalars
   int n_slots = 0, n_leaves = 0;
-  DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links, chain_in, chain_g;
+  DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links;
   std::vector<StepLaunch> steps;
   int root = 0;
   int64_t root_off = 0, root_plane = 1;
@@ -354,8 +354,6 @@ struct DeviceProgram {
     partials.release();
     open_pos.release();
     chain_links.release();
-    chain_in.release();
-    chain_g.release();
   }
 };
 
@@ -449,8 +447,7 @@ static void upload_leaves(const Plan& P, const std::vector<int64_t>& dst, DevBuf
 
 // Host-side construction of a fused chain's launch and index tables (see k_chain).
 template <class OffFn>
-static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<ChainLink>& links,
-                                    std::vector<uint16_t>& in_all, std::vector<uint8_t>& g_all, OffFn OFF) {
+static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<ChainLink>& links, OffFn OFF) {
   auto pos = [](const std::vector<int>& v, int x) {
     for (size_t i = 0; i < v.size(); ++i)
       if (v[i] == x) return (int)i;
@@ -505,7 +502,6 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
     lk.out_bits = (int)cur.size();
     lk.k_bits = (int)K.size();
     lk.n_bits = (int)N.size();
-    lk.tab = (int64_t)in_all.size();
     for (int k = 0; k < (1 << K.size()); ++k) {
       uint32_t ai = 0, gi = 0;
       for (size_t j = 0; j < K.size(); ++j)
@@ -519,16 +515,23 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
         if ((n >> j) & 1) gi |= 1u << pos(lg, N[j]);
       lk.gn[n] = (uint8_t)gi;
     }
-    for (uint32_t x = 0; x < (1u << cur.size()); ++x) {
-      uint32_t ib = 0, gb = 0;
-      for (size_t j = 0; j < cur.size(); ++j) {
-        if (!((x >> j) & 1)) continue;
-        const int pi = pos(prev, cur[j]);
-        if (pi >= 0) ib |= 1u << pi;
-        else gb |= 1u << pos(lg, cur[j]);
+    // bit scatters of x, split over its low and high six bits
+    auto scatter = [&](uint32_t v, int shift, bool want_in) {
+      uint32_t r = 0;
+      for (size_t j = 0; j + shift < cur.size() && j < 6; ++j) {
+        if (!((v >> j) & 1)) continue;
+        const int lab = cur[j + shift];
+        const int pi = pos(prev, lab);
+        if (want_in && pi >= 0) r |= 1u << pi;
+        if (!want_in && pi < 0) r |= 1u << pos(lg, lab);
       }
-      in_all.push_back((uint16_t)ib);
-      g_all.push_back((uint8_t)gb);
+      return r;
+    };
+    for (uint32_t v = 0; v < 64; ++v) {
+      lk.ib_lo[v] = (uint16_t)scatter(v, 0, true);
+      lk.ib_hi[v] = (uint16_t)scatter(v, 6, true);
+      lk.gb_lo[v] = (uint8_t)scatter(v, 0, false);
+      lk.gb_hi[v] = (uint8_t)scatter(v, 6, false);
     }
     links.push_back(lk);
     L.flops += 8.0 * std::ldexp(1.0, (int)(la.size() + N.size()));
@@ -588,8 +591,6 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   // steps
   size_t partial_elems = 0;
   std::vector<ChainLink> chain_links;
-  std::vector<uint16_t> chain_in;
-  std::vector<uint8_t> chain_g;
   std::vector<std::pair<size_t, size_t>> chain_at;  // (launch index, first link index)
   for (size_t s = 0; s < P.steps.size(); ++s) {
     const Step& st = P.steps[s];
@@ -600,7 +601,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
       const Chain& ch = P.chains[P.step_chain[s]];
       if ((int)s != ch.steps.back()) continue;  // the chain runs at its last step
       const size_t first_link = chain_links.size();
-      StepLaunch L = make_chain_launch(P, ch, chain_links, chain_in, chain_g, OFF);
+      StepLaunch L = make_chain_launch(P, ch, chain_links, OFF);
       L.cp.stride = prog->inst_stride;
       L.cp.arena = prog->arena.p;
       L.cp.maxabs = prog->maxabs.as<float>();
@@ -665,18 +666,9 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   }
   if (!chain_links.empty()) {
     prog->chain_links.reserve(chain_links.size() * sizeof(ChainLink));
-    prog->chain_in.reserve(chain_in.size() * sizeof(uint16_t));
-    prog->chain_g.reserve(chain_g.size());
     CUDA_OK(cudaMemcpy(prog->chain_links.p, chain_links.data(), chain_links.size() * sizeof(ChainLink),
                        cudaMemcpyHostToDevice));
-    CUDA_OK(cudaMemcpy(prog->chain_in.p, chain_in.data(), chain_in.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-    CUDA_OK(cudaMemcpy(prog->chain_g.p, chain_g.data(), chain_g.size(), cudaMemcpyHostToDevice));
-    for (auto& ca : chain_at) {
-      ChainParams& c = prog->steps[ca.first].cp;
-      c.links = prog->chain_links.as<ChainLink>() + ca.second;
-      c.in_tab = prog->chain_in.as<uint16_t>();
-      c.g_tab = prog->chain_g.as<uint8_t>();
-    }
+    for (auto& ca : chain_at) prog->steps[ca.first].cp.links = prog->chain_links.as<ChainLink>() + ca.second;
   }
   // root
   prog->root = P.root;
@@ -804,8 +796,10 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
     const int precision = opts->precision;
     if (precision < TNC_C64 || precision > TNC_CBF16) fail(TNC_E_INVALID_ARG, "bad precision");
     if (batch < 1) fail(TNC_E_INVALID_ARG, "batch must be >= 1");
-    const int64_t n_slices = int64_t(1) << P.sliced.size();
-    if (slice_begin < 0 || slice_count < 1 || slice_begin + slice_count > n_slices)
+    // slice ids are int64: with s >= 63 sliced indices the ids [0, 2^63) address the slices
+    // whose higher sliced indices are all 0
+    const int64_t n_slices = P.sliced.size() >= 63 ? INT64_MAX : int64_t(1) << P.sliced.size();
+    if (slice_begin < 0 || slice_count < 1 || slice_count > n_slices - slice_begin)
       fail(TNC_E_INVALID_ARG, "slice range outside [0, 2^s)");
     const bool all_open = (int)P.net.open_qubits.size() == n;
     if (!bitstrings && !(batch == 1 && all_open)) fail(TNC_E_INVALID_ARG, "bitstrings required");
@@ -993,6 +987,11 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
     int kind = K_GENERIC;
     TileSpec t = tile_for(la, lb, lc, 1, kind);
     StepLaunch L = make_launch(t, kind, la, lb, lc);
+    // per-launch events (read with tnc_profile_read): the contraction and the whole call
+    ProfState& ps = ctx->prof;
+    ps.valid = false;
+    ps.ensure(1, 1);
+    CUDA_OK(cudaEventRecord(ps.call_start(), s));
     ctx->scratch.reserve(256);
     float* mx = ctx->scratch.as<float>();
     int32_t* ex = reinterpret_cast<int32_t*>(ctx->scratch.as<char>() + 64);
@@ -1045,8 +1044,19 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       bind_tc(L, swap ? b : a, swap ? a : b, c, 0, mx, ex, 3, swap ? 1 : 0, swap ? 0 : 1, 2, ctx->status.as<int32_t>(),
               part);
     }
-    (void)eb;
+    {
+      int common = 0;
+      for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
+      ps.flops.assign(1, 8.0 * std::ldexp(1.0, rank_a + rank_b - common));
+      ps.bytes.assign(1, (std::ldexp(1.0, rank_a) + std::ldexp(1.0, rank_b) + std::ldexp(1.0, rank_c)) * 2.0 * double(eb));
+      ps.kind.assign(1, L.kind);
+      ps.kernels.assign(1, (L.kind == K_SPLITK || ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1)) ? 2 : 1);
+    }
+    CUDA_OK(cudaEventRecord(ps.at(0, 0, 0), s));
     run_step(precision, L, 1, s);
+    CUDA_OK(cudaEventRecord(ps.at(0, 0, 1), s));
+    CUDA_OK(cudaEventRecord(ps.call_end(), s));
+    ps.valid = true;
     int32_t e = 0;
     CUDA_OK(cudaMemcpyAsync(&e, ex + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CUDA_OK(cudaStreamSynchronize(s));
@@ -1210,6 +1220,7 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
     const int L = (int)P.net.leaves.size();
     const int n_open = (int)P.net.open_qubits.size();
     const int64_t n_out = int64_t(1) << n_open;
+    if (P.sliced.size() > 30) fail(TNC_E_UNSUPPORTED, "tnc_adjoint sums over every slice: at most 30 sliced indices");
     const int64_t n_slices = int64_t(1) << P.sliced.size();
     const int64_t n_inst = batch * n_slices;
     // arena: forward tensors, then adjoint leaves (contiguous, for one read-back copy), then

@@ -345,7 +345,8 @@ __global__ void k_leaf_gather(const LeafDesc* __restrict__ leaves, const double2
     for (int pos = 0; pos < d.rank_full; ++pos) {
       int bit;
       if (f < d.nfix && d.fix_pos[f] == pos) {
-        bit = d.fix_kind[f] == 0 ? int((slice >> d.fix_idx[f]) & 1) : int(bits[int64_t(row) * n_qubits + d.fix_idx[f]]);
+        bit = d.fix_kind[f] == 0 ? (d.fix_idx[f] < 63 ? int((slice >> d.fix_idx[f]) & 1) : 0)
+                                 : int(bits[int64_t(row) * n_qubits + d.fix_idx[f]]);
         ++f;
       } else {
         bit = (lane >> fb) & 1;
@@ -462,8 +463,12 @@ __global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
   float2* buf1 = buf0 + (1 << kChainMaxBits);
   float2* gs = buf1 + (1 << kChainMaxBits);                        // [64]
   uint16_t* kin = reinterpret_cast<uint16_t*>(gs + 64);              // [64]
-  uint8_t* kg = reinterpret_cast<uint8_t*>(kin + 64);                // [64]
-  float* red = reinterpret_cast<float*>(kg + 64);                    // [33]
+  uint16_t* ibl = kin + 64;                                          // [64]
+  uint16_t* ibh = ibl + 64;                                          // [64]
+  uint8_t* kg = reinterpret_cast<uint8_t*>(ibh + 64);                // [64]
+  uint8_t* gbl = kg + 64;                                            // [64]
+  uint8_t* gbh = gbl + 64;                                           // [64]
+  float* red = reinterpret_cast<float*>(gbh + 64);                   // [36]
   uint32_t* hiA = reinterpret_cast<uint32_t*>(red + 36);             // [2^(bits0 - runA0)]
   uint32_t* hiC = hiA + (1 << (p.bits0 - p.runA0));                  // [2^(bitsC - runC)]
   const int tid = threadIdx.x;
@@ -488,9 +493,13 @@ __global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
     const T* g = base + L->g_off;
     for (int t = tid; t < L->g_size; t += kThreads) gs[t] = make_float2(Conv<T>::to_f(g[t]), Conv<T>::to_f(g[L->g_plane + t]));
     const int nk = 1 << L->k_bits;
-    for (int t = tid; t < nk; t += kThreads) {
-      kin[t] = L->kin[t];
-      kg[t] = L->kg[t];
+    if (tid < 64) {
+      kin[tid] = L->kin[tid];
+      kg[tid] = L->kg[tid];
+      ibl[tid] = L->ib_lo[tid];
+      ibh[tid] = L->ib_hi[tid];
+      gbl[tid] = L->gb_lo[tid];
+      gbh[tid] = L->gb_hi[tid];
     }
     __syncthreads();
     if (tid == 0) {
@@ -507,10 +516,8 @@ __global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
       red[32] = cn;
     }
     const int nout = 1 << L->out_bits;
-    const uint16_t* itab = p.in_tab + L->tab;
-    const uint8_t* gtab = p.g_tab + L->tab;
     for (int x = tid; x < nout; x += kThreads) {
-      const int ib = itab[x], gb = gtab[x];
+      const int ib = ibl[x & 63] + ibh[x >> 6], gb = gbl[x & 63] + gbh[x >> 6];
       float2 acc = make_float2(0.f, 0.f);
       for (int q = 0; q < nk; ++q) {
         const float2 a = in[ib + kin[q]];
@@ -545,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
 }
 
 size_t chain_smem_bytes(int bits0, int runA0, int bitsC, int runC) {
-  return (size_t(2) << kChainMaxBits) * 8 + 64 * 8 + 64 * 2 + 64 + 36 * 4 + (size_t(1) << (bits0 - runA0)) * 4 +
+  return (size_t(2) << kChainMaxBits) * 8 + 64 * 8 + 3 * 64 * 2 + 3 * 64 + 36 * 4 + (size_t(1) << (bits0 - runA0)) * 4 +
          (size_t(1) << (bitsC - runC)) * 4 + 16;
 }
 

@@ -103,7 +103,7 @@ void load_plan(const std::string& path, Plan& p) {
   p.opts.temperature = get<double>(f);
   p.opts.mode = get<int32_t>(f);
   const int32_t ns = get<int32_t>(f);
-  if (ns < 0 || ns > 62) fail(7, "corrupt slice count");
+  if (ns < 0 || ns > (int32_t)net.edges.size()) fail(7, "corrupt slice count");
   for (int i = 0; i < ns; ++i) {
     int e = get<int32_t>(f);
     if (e < 0 || e >= (int)net.edges.size()) fail(7, "corrupt sliced edge");
