@@ -77,6 +77,19 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, dist):
+    """The whole job is as slow as its slowest rank: max of a per-rank time over the ranks
+    (NCCL on GPUs, gloo on the host)."""
+    if dist is None:
+        return ms
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name, rank):
     from inputs import grid_circuit, subcube_spec
 
@@ -272,11 +285,7 @@ def run_ours(args):
                     prof["flops"] = prof["flops"] + p["flops"]
                     prof["bytes"] = prof["bytes"] + p["bytes"]
         torch.cuda.synchronize()
-        ms = total / steps
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(total / steps, dist)
         return ms, prof, out.cpu().numpy()[0].copy()
 
     with ClockSampler(local) as clk:
@@ -316,26 +325,17 @@ def run_ours(args):
     kind = int(prof["kind"][k])
     flops_launch = prof["flops"][k] / prof["launches"][k]
     bytes_launch = prof["bytes"][k] / prof["launches"][k]
-    if kind in (3, 4):
+    roof = roofline_of(kind, flops_launch, bytes_launch, per_launch_ms, peaks)
+    if roof["bound"] == "tensor":
         # the timed region is well under a second at full clocks: the burst peak applies
-        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "peak_kind": "burst (cuBLAS bf16, measured)", "frac_of_sustained": achieved / peaks["bf16_tflops_sustained"]}
-    elif flops_launch / bytes_launch > 8.0:
-        alu_peak = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s"}
-    else:
-        achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["frac_of_sustained"] = roof["achieved"] / peaks["bf16_tflops_sustained"]
     roof["traffic"] = None
     roof["kernel"] = {"step": k, "kind": kind, "share_of_step_time": float(prof["ms"][k] / max(1e-9, prof["ms"].sum())),
                       "ms_per_launch": per_launch_ms, "flops_per_launch": flops_launch, "bytes_per_launch": bytes_launch}
     roof["peak_source"] = peaks["_source"]
     total_flops = float(prof["flops"].sum()) / args.steps
     waves = int(prof["launches"].min() / args.steps)
-    launches = int(prof["launches"].sum() / args.steps) + 2 * waves  # + leaf gather and root sum per wave
+    launches = int(prof["launches"].sum() / args.steps) + 3 * waves  # + leaf gather, leaf scales, root sum per wave
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,14 +377,21 @@ def run_ours(args):
 
 # --------------------------------------------------------------------------- other workloads
 def roofline_of(kind, flops, nbytes, ms, peaks):
-    """Roofline of one kernel launch from its algorithmic flops / bytes and device time."""
-    if kind in (3, 4):
-        r = {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
-    elif flops / max(nbytes, 1.0) > 8.0:
-        alu = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        r = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": alu, "unit": "TFLOP/s"}
+    """Roofline of one kernel launch from its algorithmic flops / bytes and device time.
+    Tensor-core kernels (kinds 3-6) are tensor-bound above the machine balance
+    (bf16 peak / HBM bandwidth), SIMT kernels above the FP32-ALU balance; HBM-bound below."""
+    alu = N_SM * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    intensity = flops / max(nbytes, 1.0)
+    tc = kind in (3, 4, 5, 6)
+    if tc and intensity >= peaks["bf16_tflops"] * 1e3 / peaks["hbm_gbs"]:
+        r = {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+             "peak_kind": "burst (cuBLAS bf16, measured)"}
+    elif not tc and intensity >= alu * 1e3 / peaks["hbm_gbs"]:
+        r = {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": alu, "unit": "TFLOP/s",
+             "peak_kind": "152 SMs x 128 FP32 lanes x 2 flops x max SM clock"}
     else:
-        r = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        r = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "peak_kind": "STREAM-style copy, measured"}
     r["frac"] = r["achieved"] / r["peak"]
     return r
 
@@ -396,15 +403,15 @@ SW_POINTS = [(14, 12, 10), (12, 12, 12), (16, 8, 16), (16, 12, 12), (12, 16, 12)
 def sweep_labels(m, k, n, layout, seed):
     """Index labels of one sweep point.  'random': seeded random axis orders of A, B and C.
     'arranged': the order the step compiler gives tensor-core steps (K tile labels, then
-    the M / N tile labels, lowest), the rest random."""
+    the M / N tile labels, lowest; C led by its tile labels, as for a root), the rest random."""
     rng = np.random.default_rng(seed)
     ms, ks, ns = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
     perm = lambda v: [int(x) for x in rng.permutation(v)] if v else []
     if layout == "arranged":
         kt = 5 if k >= 5 else 4
-        nt = 8 if (n >= 8 and k > kt + 1) else (7 if n >= 7 else 6)
+        nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
         return (ks[:kt] + ms[:7] + perm(ms[7:] + ks[kt:]), ks[:kt] + ns[:nt] + perm(ns[nt:] + ks[kt:]),
-                [ns[0], ms[0], ns[1]] + perm(ms[1:] + ns[2:]))
+                ms[:7] + ns[:nt] + perm(ms[7:] + ns[nt:]))
     return perm(ms + ks), perm(ks + ns), perm(ms + ns)
 
 

@@ -118,13 +118,10 @@ def greedy_order(label_sets: List[Tuple[Label, ...]], open_labels: Sequence[Labe
         return (t, min(i, j), max(i, j))
 
     heap = []
-    seen = set()
-    for lab, ow in owners.items():
-        if len(ow) == 2:
-            i, j = sorted(ow)
-            if (i, j) not in seen:
-                seen.add((i, j))
-                heapq.heappush(heap, score(i, j))
+    # candidate pairs in a fixed order, so the seeded noise does not depend on the
+    # process's string-hash seed (label sets are frozensets of tuples with strings)
+    for i, j in sorted({tuple(sorted(ow)) for ow in owners.values() if len(ow) == 2}):
+        heapq.heappush(heap, score(i, j))
     next_id = len(label_sets)
     pairs = []
     inter = []

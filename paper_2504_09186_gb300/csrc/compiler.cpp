@@ -300,10 +300,11 @@ void compile_plan(Plan& plan, bool fuse) {
     TcDec d;
     d.ok = true;
     d.bk = K.size() >= 5 ? 32 : 16;
-    // 256-wide tiles take a whole SM (all TMEM); with one or two K tiles the epilogue
-    // dominates, and 128-wide tiles let two CTAs per SM overlap it
+    // 256-wide tiles take a whole SM (all TMEM) and leave the epilogue exposed; with at
+    // most 8 K tiles the epilogue weighs, and 128-wide tiles run on the persistent kernel,
+    // which overlaps it with the next tile
     const size_t kt0 = d.bk == 32 ? 5 : 4;
-    d.bn = (N.size() >= 8 && K.size() > kt0 + 1) ? 256 : (N.size() >= 7 ? 128 : 64);
+    d.bn = (N.size() >= 8 && K.size() > kt0 + 3) ? 256 : (N.size() >= 7 ? 128 : 64);
     const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : 6);
     d.t.Kt.assign(K.begin(), K.begin() + kt);
     const std::vector<int>& rq = req[n_leaves + s];
@@ -365,7 +366,8 @@ void compile_plan(Plan& plan, bool fuse) {
     const auto& lb = plan.tensors[st.b].labels;
     const auto& lc = plan.tensors[st.c].labels;
     int kind = K_GENERIC;
-    st.tile = choose_tile(la, lb, lc, 1, kind);
+    // split sizing assumes every slice of the plan in flight (see split_instances in exec.cu)
+    st.tile = choose_tile(la, lb, lc, 1 << std::min<int>((int)plan.sliced.size(), 12), kind);
     st.kind = kind;
     st.tc_ok = dec[s].ok;
     if (st.tc_ok) {

@@ -92,6 +92,8 @@ struct TcParams {
   int32_t* exps;
   int32_t n_slots, slotA, slotB, slotC;
   int32_t* status;           // TNC_E_TIMEOUT on a bounded wait that ran out
+  int32_t persistent;        // 1 = persistent TMA kernel (short K loops, no split)
+  int32_t n_inst;            // instances of the launch (persistent kernel: tiles span all)
 };
 
 // Fused chain of absorptions (Sec. IV): one tile of the big tensor stays on chip while
@@ -122,6 +124,22 @@ struct ChainParams {
   float* maxabs;
   int32_t* exps;
   int32_t n_slots, slotA0, slotC;
+};
+
+// Index permutation of a planar binary-index tensor (the transposes of TTGT, Sec. V-A,
+// Sec. V-B): out[y] = in[x] where every label has the same bit in y (at its output
+// position) as in x (at its input position).  Tiles are label sets holding the lowest
+// positions of both layouts, so loads and stores are contiguous runs.
+struct PermParams {
+  const void* in;
+  void* out;
+  int64_t plane;              // 2^rank entries per plane (both tensors)
+  int32_t bits;               // tile labels (<= 12)
+  int32_t run_in, run_out;    // lowest positions of each layout inside the tile
+  uint32_t mask_in, mask_out; // tile positions in each layout
+  uint16_t plo[64], phi[64];  // output-tile index -> input-tile index (low / high 6 bits)
+  int32_t n_o;                // outer labels (one CTA per assignment)
+  int8_t o_in[kMaxOuter], o_out[kMaxOuter];
 };
 
 // A run of consecutive instances of one wave that belong to the same bitstring row.

@@ -27,10 +27,12 @@ cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_in
 cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leaves, const double2* src, void* arena,
                                int64_t inst_stride, const int64_t* inst_slice, const int32_t* inst_row,
                                const uint8_t* bits, int n_qubits, float* maxabs, int32_t* exps, int n_slots,
-                               int64_t inst_base, int64_t n_inst, cudaStream_t s);
+                               int64_t inst_base, int64_t n_inst, double2* leaf_r, cudaStream_t s);
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
-                              const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s);
+                              const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
+                              cudaStream_t s);
+cudaError_t launch_inst_scale(const double2* leaf_r, int n_leaves, int64_t n_inst, double2* c, cudaStream_t s);
 cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                                  const int8_t* open_pos, int n_open, const int32_t* inst_row, int64_t inst_base,
@@ -39,6 +41,7 @@ cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root
 cudaError_t launch_tc_gemm(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 cudaError_t launch_tc_tma(int precision, const TcParams& p, dim3 grid, cudaStream_t s);
 cudaError_t launch_chain(int precision, const ChainParams& p, int64_t n_inst, cudaStream_t s);
+cudaError_t launch_permute(int precision, const PermParams& p, cudaStream_t s);
 TileSpec tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, int n_inst,
                   int& kind);
 bool tc_tile_for(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc, TileSpec& t,
@@ -109,6 +112,10 @@ struct StepLaunch {
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
 // kernel's A (row side) and B operands (already swapped when the tile asked for it).
 // n_inst sizes the split over the outer common labels: enough CTAs for two waves.
+// Instances assumed when a step's split over K is sized: every slice of the plan for one
+// bitstring row (the unit of work of a full-plan call), at most 2^12.
+static int64_t split_instances(const Plan& P) { return int64_t(1) << std::min<size_t>(P.sliced.size(), 12); }
+
 static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<int>& la, const std::vector<int>& lb,
                            const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst) {
   TcParams& q = L.tp;
@@ -149,13 +156,26 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   q.planeC = int64_t(1) << lc.size();
   q.nK = (int)t.Kt.size() + q.n_ok;
   q.bf16 = precision == TNC_CBF16 ? 1 : 0;
-  // split over the outer common labels when the tiles alone cannot fill the GPU twice
   const int64_t tiles = (int64_t(1) << (q.n_om + q.n_on)) * std::max<int64_t>(1, n_inst);
+  const int64_t kit = int64_t(1) << q.n_ok;  // K tiles per output tile
+  // short K loops over many tiles: the persistent TMA kernel overlaps each tile's
+  // epilogue with the next tile's loads and MMAs (two TMEM accumulators: BN <= 128)
+  q.persistent = (bn <= 128 && q.n_ok <= 3 && tiles >= 4 * 152) ? 1 : 0;
+  // otherwise split over the outer common labels: at least two CTAs per SM (every split
+  // keeping at least 4 K tiles), and whole waves (the last one at least 90% busy) when each
+  // split keeps at least 256 K tiles, so the FP32 partial sums cost little
+  auto wave_eff = [](int64_t ctas) {
+    const double w = double(ctas) / 152.0;
+    return w / std::ceil(w);
+  };
   int split = 1;
-  while (tiles * split < 2 * 152 && (int64_t(1) << q.n_ok) / (split * 2) >= 4) split *= 2;
+  if (!q.persistent)
+    while (kit / (split * 2) >= 4 && split < 1024 &&
+           (tiles * split < 2 * 152 || (wave_eff(tiles * split) < 0.9 && kit / (split * 2) >= 256)))
+      split *= 2;
   q.splitk = split;
   // short K loops: a 3-stage pipeline leaves room for two CTAs per SM
-  q.stages = ((int64_t(1) << q.n_ok) / split) <= 3 ? 3 : 0;
+  q.stages = (kit / split) <= 3 ? 3 : 0;
   L.kind = K_TC;
   L.grid = dim3(1u << (q.n_om + q.n_on), (unsigned)split, 1);
   L.smem = 0;
@@ -211,7 +231,9 @@ static bool tma_tile_from_layout(const std::vector<int>& la, const std::vector<i
     if (std::find(la.begin(), la.end(), x) == la.end()) N.push_back(x);
   if (M.size() < 7 || N.size() < 6 || K.size() < 4) return false;
   bk = K.size() >= 5 ? 32 : 16;
-  bn = (N.size() >= 8 && K.size() > size_t(bk == 32 ? 6 : 5)) ? 256 : (N.size() >= 7 ? 128 : 64);
+  // 256-wide tiles (all of TMEM, one CTA per SM) only for K loops of more than 8 K tiles;
+  // shorter loops take 128-wide tiles and the persistent kernel
+  bn = (N.size() >= 8 && K.size() > size_t(bk == 32 ? 8 : 7)) ? 256 : (N.size() >= 7 ? 128 : 64);
   const size_t kt = bk == 32 ? 5 : 4, nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6);
   if (la.size() < kt + 7 || lb.size() < kt + nt || lc.size() < 3) return false;
   auto in = [](const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
@@ -237,6 +259,83 @@ static bool tma_tile_from_layout(const std::vector<int>& la, const std::vector<i
   for (int x : K)
     if (!in(t.Kt, x)) t.Ko.push_back(x);
   return t.Mo.size() + t.No.size() <= 30 && t.Ko.size() <= 24;
+}
+
+// Permutation from layout `lin` to layout `lout` (same label set): the tile holds the six
+// lowest positions of each layout, widened with further input positions up to 12 labels.
+static PermParams make_permute(const std::vector<int>& lin, const std::vector<int>& lout) {
+  PermParams q;
+  std::memset(&q, 0, sizeof(q));
+  const int r = (int)lin.size();
+  std::vector<int> T;
+  auto add = [&](int x) {
+    if (std::find(T.begin(), T.end(), x) == T.end()) T.push_back(x);
+  };
+  for (int j = 0; j < std::min(r, 6); ++j) add(lin[j]);
+  for (int j = 0; j < std::min(r, 6); ++j) add(lout[j]);
+  for (int j = 6; j < r && T.size() < 12; ++j) add(lin[j]);
+  for (int x : T) q.mask_in |= 1u << pos_of(lin, x), q.mask_out |= 1u << pos_of(lout, x);
+  q.bits = (int)T.size();
+  q.run_in = low_run(q.mask_in);
+  q.run_out = low_run(q.mask_out);
+  // tile-native orders: bit i of a tile index is the i-th lowest tile position of the layout
+  std::vector<int> tin = T, tout = T;
+  std::sort(tin.begin(), tin.end(), [&](int x, int y) { return pos_of(lin, x) < pos_of(lin, y); });
+  std::sort(tout.begin(), tout.end(), [&](int x, int y) { return pos_of(lout, x) < pos_of(lout, y); });
+  auto scatter = [&](uint32_t v, int shift) {
+    uint32_t t = 0;
+    for (int j = 0; j < 6 && j + shift < q.bits; ++j)
+      if ((v >> j) & 1u) t |= 1u << pos_of(tin, tout[j + shift]);
+    return (uint16_t)t;
+  };
+  for (uint32_t v = 0; v < 64; ++v) {
+    q.plo[v] = scatter(v, 0);
+    q.phi[v] = scatter(v, 6);
+  }
+  for (int x : lin)
+    if (std::find(T.begin(), T.end(), x) == T.end()) {
+      if (q.n_o >= kMaxOuter) fail(TNC_E_UNSUPPORTED, "permutation: too many outer labels");
+      q.o_in[q.n_o] = (int8_t)pos_of(lin, x);
+      q.o_out[q.n_o] = (int8_t)pos_of(lout, x);
+      ++q.n_o;
+    }
+  q.plane = int64_t(1) << r;
+  return q;
+}
+
+// TTGT layouts for a single contraction whose operands the tensor-core kernels cannot load
+// in place: A' = [Kt | Mt | other M | other K], B' = [Kt | Nt | other N | other K] (the
+// layouts the compiler gives tensor-core steps) and C' = [Mt | Nt | ...].  False when the
+// step is too small for tensor-core tiles.
+static bool ttgt_layouts(const std::vector<int>& la, const std::vector<int>& lb, std::vector<int>& la2,
+                         std::vector<int>& lb2, std::vector<int>& lc2) {
+  std::vector<int> K, M, N;
+  for (int x : la) (std::find(lb.begin(), lb.end(), x) != lb.end() ? K : M).push_back(x);
+  for (int x : lb)
+    if (std::find(la.begin(), la.end(), x) == la.end()) N.push_back(x);
+  if (M.size() < N.size()) return false;  // the caller swaps the operands first
+  if (M.size() < 7 || N.size() < 6 || K.size() < 4) return false;
+  const size_t kt = K.size() >= 5 ? 5 : 4;
+  const size_t nt = (N.size() >= 8 && K.size() > kt + 3) ? 8 : (N.size() >= 7 ? 7 : 6);
+  la2.assign(K.begin(), K.begin() + kt);
+  la2.insert(la2.end(), M.begin(), M.end());
+  la2.insert(la2.end(), K.begin() + kt, K.end());
+  lb2.assign(K.begin(), K.begin() + kt);
+  lb2.insert(lb2.end(), N.begin(), N.end());
+  lb2.insert(lb2.end(), K.begin() + kt, K.end());
+  lc2.assign(M.begin(), M.begin() + 7);
+  lc2.insert(lc2.end(), N.begin(), N.begin() + nt);
+  lc2.insert(lc2.end(), M.begin() + 7, M.end());
+  lc2.insert(lc2.end(), N.begin() + nt, N.end());
+  return true;
+}
+
+// TTGT scratch (A', B', C') must fit in half of the free device memory.
+static bool ttgt_fits(size_t ra, size_t rb, size_t rc, size_t eb) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+  const double need = (std::ldexp(1.0, (int)ra) + std::ldexp(1.0, (int)rb) + std::ldexp(1.0, (int)rc)) * 2.0 * double(eb);
+  return need <= 0.5 * double(free_b);
 }
 
 // Fills the pointers of a tensor-core launch (and of its reduce, when split).
@@ -334,6 +433,7 @@ struct DeviceProgram {
   int64_t inst_stride = 0;  // scalars
   int n_slots = 0, n_leaves = 0;
   DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links;
+  DevBuf leaf_r, inst_c;  // per (instance, leaf) rounding scale and per-instance product
   std::vector<StepLaunch> steps;
   int root = 0;
   int64_t root_off = 0, root_plane = 1;
@@ -354,6 +454,8 @@ struct DeviceProgram {
     partials.release();
     open_pos.release();
     chain_links.release();
+    leaf_r.release();
+    inst_c.release();
   }
 };
 
@@ -392,9 +494,10 @@ struct tnc_context_s {
   int id = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
-  DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status;
+  DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status, ttgt;
   bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
   bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
+  bool no_persist = false;  // TNC_NO_PERSIST=1: short-K TMA steps use one CTA per tile
   ProfState prof;
   ~tnc_context_s() {
     bits.release();
@@ -405,6 +508,7 @@ struct tnc_context_s {
     scratch.release();
     partials.release();
     status.release();
+    ttgt.release();
   }
 };
 
@@ -580,6 +684,8 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   prog->arena.reserve(size_t(prog->inst_stride) * eb * W + 256);
   prog->maxabs.reserve(size_t(prog->n_slots) * W * sizeof(float));
   prog->exps.reserve(size_t(prog->n_slots) * W * sizeof(int32_t));
+  prog->leaf_r.reserve(size_t(std::max(1, prog->n_leaves)) * W * sizeof(double2));
+  prog->inst_c.reserve(size_t(W) * sizeof(double2));
   // leaves: FP64 sources + descriptors
   {
     std::vector<int64_t> dst(prog->n_leaves);
@@ -622,7 +728,12 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     }
     if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
       const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
-      make_tc_launch(L, st.tc_tile, P.tensors[ta].labels, P.tensors[tb].labels, lc, precision, st.tc_bn, st.tc_bk, W);
+      // the split over K follows the plan (its slice count), not the wave size, so results do
+      // not depend on how many instances share a launch; the persistent choice uses the wave
+      make_tc_launch(L, st.tc_tile, P.tensors[ta].labels, P.tensors[tb].labels, lc, precision, st.tc_bn, st.tc_bk,
+                     split_instances(P));
+      L.tp.persistent = (st.tc_bn <= 128 && L.tp.splitk == 1 && L.tp.n_ok <= 3 &&
+                         (int64_t(1) << (L.tp.n_om + L.tp.n_on)) * W >= 4 * 152) ? 1 : 0;
       bind_tc(L, prog->arena.as<char>() + OFF(ta) * eb, prog->arena.as<char>() + OFF(tb) * eb,
               prog->arena.as<char>() + OFF(st.c) * eb, prog->inst_stride, prog->maxabs.as<float>(),
               prog->exps.as<int32_t>(), prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), nullptr);
@@ -632,6 +743,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
         encode_tile_map(&L.tp.tmA, L.tp.A, (int)P.tensors[ta].labels.size(), kt, 128, prog->inst_stride, W);
         encode_tile_map(&L.tp.tmB, L.tp.B, (int)P.tensors[tb].labels.size(), kt, st.tc_bn, prog->inst_stride, W);
         L.kind = K_TMA;
+        if (ctx->no_persist) L.tp.persistent = 0;
       }
       if (L.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * L.tp.splitk * L.tp.planeC);
       {
@@ -720,7 +832,10 @@ static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaSt
     return;
   }
   if (L.kind == K_TC || L.kind == K_TMA) {
-    if (L.kind == K_TMA) CUDA_OK(launch_tc_tma(precision, L.tp, L.grid, s));
+    if (L.kind == K_TMA) {
+      L.tp.n_inst = (int32_t)n_inst;
+      CUDA_OK(launch_tc_tma(precision, L.tp, L.grid, s));
+    }
     else CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
     if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
     return;
@@ -764,6 +879,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->no_tc = env && env[0] == '1';
     const char* env2 = std::getenv("TNC_NO_TMA");
     c->no_tma = env2 && env2[0] == '1';
+    const char* env3 = std::getenv("TNC_NO_PERSIST");
+    c->no_persist = env3 && env3[0] == '1';
     *out = c;
   });
 }
@@ -892,7 +1009,7 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
         const StepLaunch& SL = prog->steps[k];
         ps.flops[k] = SL.flops * double(n_inst);
         ps.bytes[k] = SL.bytes * double(n_inst);
-        ps.kind[k] = SL.kind;
+        ps.kind[k] = (SL.kind == K_TMA && SL.tp.persistent) ? 5 : SL.kind;
         ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
       }
       CUDA_OK(cudaEventRecord(ps.call_start(), s));
@@ -922,16 +1039,18 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       CUDA_OK(launch_leaf_gather(precision, prog->leaf_desc.as<LeafDesc>(), prog->n_leaves,
                                  prog->leaf_src.as<double2>(), prog->arena.p, prog->inst_stride,
                                  ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(),
-                                 n, prog->maxabs.as<float>(), prog->exps.as<int32_t>(), prog->n_slots, base, cnt, s));
+                                 n, prog->maxabs.as<float>(), prog->exps.as<int32_t>(), prog->n_slots, base, cnt,
+                                 prog->leaf_r.as<double2>(), s));
       for (size_t k = 0; k < prog->steps.size(); ++k) {
         if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
         run_step(precision, prog->steps[k], cnt, s);
         if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
       }
+      CUDA_OK(launch_inst_scale(prog->leaf_r.as<double2>(), prog->n_leaves, cnt, prog->inst_c.as<double2>(), s));
       CUDA_OK(launch_root_accum(precision, prog->arena.p, prog->inst_stride, prog->root_off, prog->root_plane,
                                 prog->open_pos.as<int8_t>(), prog->n_open, ctx->segs.as<RootSeg>() + wave_segs[w].first,
                                 wave_segs[w].second, prog->exps.as<int32_t>(), prog->n_slots, prog->root,
-                                ctx->acc.as<double2>(), s));
+                                ctx->acc.as<double2>(), prog->inst_c.as<double2>(), s));
       if (capture) {
         cudaGraph_t g = nullptr;
         CUDA_OK(cudaStreamEndCapture(s, &g));
@@ -1016,6 +1135,9 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
     TileSpec tct;
     bool swap = false;
     int bn = 128, bk = 64;
+    bool ttgt = false;
+    std::vector<int> la2, lb2, lc2;
+    PermParams perm_a, perm_b, perm_c;
     const bool tma_a = precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma && tma_tile_from_layout(la, lb, lc, tct, bn, bk);
     const bool tma_b = !tma_a && precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma &&
                        tma_tile_from_layout(lb, la, lc, tct, bn, bk);
@@ -1034,6 +1156,47 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       encode_tile_map(&L.tp.tmA, L.tp.A, (int)ra.size(), kt, 128, 0, 1);
       encode_tile_map(&L.tp.tmB, L.tp.B, (int)rb.size(), kt, bn, 0, 1);
       L.kind = K_TMA;
+      if (ctx->no_persist) L.tp.persistent = 0;
+    } else if (precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma &&
+               ttgt_layouts(la.size() >= lb.size() ? la : lb, la.size() >= lb.size() ? lb : la, la2, lb2, lc2) &&
+               ttgt_fits(la2.size(), lb2.size(), lc2.size(), eb)) {
+      // TTGT (Sec. V-A, Sec. V-B): permute the operands into the layouts the TMA kernel
+      // loads, contract into a tile-first C, permute C into the requested layout
+      ttgt = true;
+      const bool sw = la.size() < lb.size();
+      const void* ra = sw ? b : a;
+      const void* rb = sw ? a : b;
+      const std::vector<int>& oa = sw ? lb : la;
+      const std::vector<int>& ob = sw ? la : lb;
+      const size_t na = (size_t(2) << la2.size()) * eb, nb2 = (size_t(2) << lb2.size()) * eb,
+                   nc = (size_t(2) << lc2.size()) * eb;
+      ctx->ttgt.reserve(na + nb2 + nc + 1024);
+      char* base = ctx->ttgt.as<char>();
+      char* a2 = base;
+      char* b2 = base + ((na + 255) & ~size_t(255));
+      char* c2 = b2 + ((nb2 + 255) & ~size_t(255));
+      perm_a = make_permute(oa, la2);
+      perm_a.in = ra;
+      perm_a.out = a2;
+      perm_b = make_permute(ob, lb2);
+      perm_b.in = rb;
+      perm_b.out = b2;
+      perm_c = make_permute(lc2, lc);
+      perm_c.in = c2;
+      perm_c.out = c;
+      if (!tma_tile_from_layout(la2, lb2, lc2, tct, bn, bk)) fail(TNC_E_PLAN, "TTGT layouts do not fit the TMA tile");
+      make_tc_launch(L, tct, la2, lb2, lc2, precision, bn, bk, 1);
+      float2* part = nullptr;
+      if (L.tp.splitk > 1) {
+        ctx->partials.reserve(size_t(L.tp.splitk) * L.tp.planeC * sizeof(float2));
+        part = ctx->partials.as<float2>();
+      }
+      bind_tc(L, a2, b2, c2, 0, mx, ex, 3, sw ? 1 : 0, sw ? 0 : 1, 2, ctx->status.as<int32_t>(), part);
+      const int kt = bk == 32 ? 5 : 4;
+      encode_tile_map(&L.tp.tmA, L.tp.A, (int)la2.size(), kt, 128, 0, 1);
+      encode_tile_map(&L.tp.tmB, L.tp.B, (int)lb2.size(), kt, bn, 0, 1);
+      L.kind = K_TMA;
+      if (ctx->no_persist) L.tp.persistent = 0;
     } else if (precision != TNC_C64 && !ctx->no_tc && tc_tile_for(la, lb, lc, tct, swap, bn, bk)) {
       make_tc_launch(L, tct, swap ? lb : la, swap ? la : lb, lc, precision, bn, bk, 1);
       float2* part = nullptr;
@@ -1049,11 +1212,17 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
       ps.flops.assign(1, 8.0 * std::ldexp(1.0, rank_a + rank_b - common));
       ps.bytes.assign(1, (std::ldexp(1.0, rank_a) + std::ldexp(1.0, rank_b) + std::ldexp(1.0, rank_c)) * 2.0 * double(eb));
-      ps.kind.assign(1, L.kind);
+      ps.kind.assign(1, ttgt ? 6 : (L.kind == K_TMA && L.tp.persistent) ? 5 : L.kind);
       ps.kernels.assign(1, (L.kind == K_SPLITK || ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1)) ? 2 : 1);
+      if (ttgt) ps.kernels[0] += 3;
     }
     CUDA_OK(cudaEventRecord(ps.at(0, 0, 0), s));
+    if (ttgt) {
+      CUDA_OK(launch_permute(precision, perm_a, s));
+      CUDA_OK(launch_permute(precision, perm_b, s));
+    }
     run_step(precision, L, 1, s);
+    if (ttgt) CUDA_OK(launch_permute(precision, perm_c, s));
     CUDA_OK(cudaEventRecord(ps.at(0, 0, 1), s));
     CUDA_OK(cudaEventRecord(ps.call_end(), s));
     ps.valid = true;
@@ -1347,7 +1516,7 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
       CUDA_OK(cudaMemsetAsync(maxabs.p, 0, size_t(2 * T) * cnt * sizeof(float), s));
       CUDA_OK(launch_leaf_gather(TNC_C64, leaf_desc.as<LeafDesc>(), L, leaf_src.as<double2>(), arena.p, stride,
                                  ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(), n,
-                                 maxabs.as<float>(), exps.as<int32_t>(), 2 * T, base, cnt, s));
+                                 maxabs.as<float>(), exps.as<int32_t>(), 2 * T, base, cnt, nullptr, s));
       for (const StepLaunch& Lh : fwd) run_step(TNC_C64, Lh, cnt, s);
       if (amp_out) {
         segs.clear();
@@ -1360,7 +1529,7 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
         CUDA_OK(cudaMemcpyAsync(ctx->segs.p, segs.data(), segs.size() * sizeof(RootSeg), cudaMemcpyHostToDevice, s));
         CUDA_OK(launch_root_accum(TNC_C64, arena.p, stride, off[root], int64_t(1) << P.tensors[root].labels.size(),
                                   open_pos.as<int8_t>(), n_open, ctx->segs.as<RootSeg>(), (int)segs.size(),
-                                  exps.as<int32_t>(), 2 * T, root, ctx->acc.as<double2>(), s));
+                                  exps.as<int32_t>(), 2 * T, root, ctx->acc.as<double2>(), nullptr, s));
       }
       CUDA_OK(launch_adj_root_init(arena.as<float>(), stride, off[T + root], int64_t(1) << P.tensors[root].labels.size(),
                                    open_pos.as<int8_t>(), n_open, ctx->inst_row.as<int32_t>(), base, cnt,

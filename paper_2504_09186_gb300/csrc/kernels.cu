@@ -76,7 +76,15 @@ __device__ __forceinline__ int product_shift(float a, float b, int nK) {
   return ea + eb + nK + 1 - 15;
 }
 
-template <typename T, int V>
+// Shared-memory swizzle of a float2 operand tile: the low four index bits (one 128-byte
+// line holds 16 float2) are XORed with index bits 4..7 and 8..11.  A warp reading one
+// entry per tile row hits distinct lines' banks even when the rows are a power of two
+// apart (contiguous K, strided M).  The map is linear over GF(2): the swizzled index of
+// a sum of disjoint bit sets is the XOR of their swizzled parts, so offset tables can be
+// stored swizzled and combined with XOR.
+__device__ __forceinline__ uint32_t sw16(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
+
+template <typename T, int V, bool SW>
 __device__ __forceinline__ void load_tile_v(const T* __restrict__ re, const T* __restrict__ im, int bits, int run,
                                             const uint32_t* __restrict__ hi, float2* __restrict__ dst) {
   const int n = 1 << bits;
@@ -86,18 +94,19 @@ __device__ __forceinline__ void load_tile_v(const T* __restrict__ re, const T* _
     const Vec<T, V> r = *reinterpret_cast<const Vec<T, V>*>(re + off);
     const Vec<T, V> i = *reinterpret_cast<const Vec<T, V>*>(im + off);
 #pragma unroll
-    for (int v = 0; v < V; ++v) dst[t + v] = make_float2(Conv<T>::to_f(r.v[v]), Conv<T>::to_f(i.v[v]));
+    for (int v = 0; v < V; ++v)
+      dst[SW ? sw16(uint32_t(t + v)) : uint32_t(t + v)] = make_float2(Conv<T>::to_f(r.v[v]), Conv<T>::to_f(i.v[v]));
   }
 }
 
-template <typename T>
+template <typename T, bool SW = false>
 __device__ __forceinline__ void load_tile(const T* re, const T* im, int bits, int run, const uint32_t* hi, float2* dst) {
   constexpr int VMAX = 16 / sizeof(T);
   const int v = min(1 << run, VMAX);
-  if (v >= 8) load_tile_v<T, (VMAX >= 8 ? 8 : 1)>(re, im, bits, run, hi, dst);
-  else if (v == 4) load_tile_v<T, 4>(re, im, bits, run, hi, dst);
-  else if (v == 2) load_tile_v<T, 2>(re, im, bits, run, hi, dst);
-  else load_tile_v<T, 1>(re, im, bits, run, hi, dst);
+  if (v >= 8) load_tile_v<T, (VMAX >= 8 ? 8 : 1), SW>(re, im, bits, run, hi, dst);
+  else if (v == 4) load_tile_v<T, 4, SW>(re, im, bits, run, hi, dst);
+  else if (v == 2) load_tile_v<T, 2, SW>(re, im, bits, run, hi, dst);
+  else load_tile_v<T, 1, SW>(re, im, bits, run, hi, dst);
 }
 
 template <typename T, int V>
@@ -184,16 +193,17 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
     for (int h = tid; h < nhA; h += kThreads) hiA[h] = deposit_hi(h, p.maskA, p.runA);
     for (int h = tid; h < nhB; h += kThreads) hiB[h] = deposit_hi(h, p.maskB, p.runB);
     for (int h = tid; h < nhC; h += kThreads) hiC[h] = deposit_hi(h, p.maskC, p.runC);
+    // operand tables are stored swizzled (sw16), the C staging tables plain
     for (int x = tid; x < (1 << p.mt); x += kThreads) {
-      TAm[x] = (uint16_t)scatter_bits(x, p.pAm, p.mt);
+      TAm[x] = (uint16_t)sw16(scatter_bits(x, p.pAm, p.mt));
       TCm[x] = (uint16_t)scatter_bits(x, p.pCm, p.mt);
     }
     for (int x = tid; x < (1 << p.kt); x += kThreads) {
-      TAk[x] = (uint16_t)scatter_bits(x, p.pAk, p.kt);
-      TBk[x] = (uint16_t)scatter_bits(x, p.pBk, p.kt);
+      TAk[x] = (uint16_t)sw16(scatter_bits(x, p.pAk, p.kt));
+      TBk[x] = (uint16_t)sw16(scatter_bits(x, p.pBk, p.kt));
     }
     for (int x = tid; x < (1 << p.nt); x += kThreads) {
-      TBn[x] = (uint16_t)scatter_bits(x, p.pBn, p.nt);
+      TBn[x] = (uint16_t)sw16(scatter_bits(x, p.pBn, p.nt));
       TCn[x] = (uint16_t)scatter_bits(x, p.pCn, p.nt);
     }
   }
@@ -229,17 +239,17 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
         okA += int64_t(1) << p.ok_A[j];
         okB += int64_t(1) << p.ok_B[j];
       }
-    load_tile<T>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
-    load_tile<T>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
+    load_tile<T, true>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
+    load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
     __syncthreads();
     if (active) {
       for (int k = grp; k < nk; k += p.kgroups) {
         const int ka = TAk[k], kb = TBk[k];
         float2 a[RM], b[RN];
 #pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = As[am[i] + ka];
+        for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
 #pragma unroll
-        for (int j = 0; j < RN; ++j) b[j] = Bs[kb + bn[j]];
+        for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
@@ -330,7 +340,8 @@ template <typename T>
 __global__ void k_leaf_gather(const LeafDesc* __restrict__ leaves, const double2* __restrict__ src, T* arena,
                               int64_t inst_stride, const int64_t* __restrict__ inst_slice,
                               const int32_t* __restrict__ inst_row, const uint8_t* __restrict__ bits, int n_qubits,
-                              float* maxabs, int32_t* exps, int n_slots, int64_t inst_base) {
+                              float* maxabs, int32_t* exps, int n_slots, int64_t inst_base, double2* leaf_r,
+                              int n_leaves) {
   const LeafDesc d = leaves[blockIdx.x];
   const int64_t inst = blockIdx.y;
   const int64_t slice = inst_slice[inst_base + inst];
@@ -365,12 +376,28 @@ __global__ void k_leaf_gather(const LeafDesc* __restrict__ leaves, const double2
   const double s = ldexp(1.0, -e);
   T* dst = arena + inst * inst_stride + d.dst;
   float mx = 0.f;
+  // least-squares scale r of the rounded leaf q against the exact one v: v ~ r q.  The
+  // amplitude is linear in every leaf, so multiplying it by the product of the instance's
+  // r removes the coherent part of the storage rounding (the same few gate values round
+  // the same way in every leaf); the rest of the rounding error stays
+  double nr = 0.0, ni = 0.0, dd = 0.0;
   if (lane < n) {
     const T re = Conv<T>::from_f((float)(v.x * s)), im = Conv<T>::from_f((float)(v.y * s));
     dst[lane] = re;
     dst[n + lane] = im;
     mx = fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im)));
+    const double qr = (double)Conv<T>::to_f(re), qi = (double)Conv<T>::to_f(im);
+    const double vr = v.x * s, vi = v.y * s;
+    nr = qr * vr + qi * vi;  // conj(q) * v
+    ni = qr * vi - qi * vr;
+    dd = qr * qr + qi * qi;
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    ni += __shfl_xor_sync(0xffffffffu, ni, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  }
+  if (leaf_r && lane == 0) leaf_r[inst * n_leaves + blockIdx.x] = dd > 0.0 ? make_double2(nr / dd, ni / dd) : make_double2(1.0, 0.0);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) {
     maxabs[inst * n_slots + d.slot] = mx;
@@ -378,27 +405,57 @@ __global__ void k_leaf_gather(const LeafDesc* __restrict__ leaves, const double2
   }
 }
 
-// acc[row, o] += sum over the segment's instances (in order) of root[o] * 2^E.
+// c[i] = product over the leaves (in leaf order) of instance i's leaf scales r.
+__global__ void k_inst_scale(const double2* __restrict__ leaf_r, int n_leaves, int64_t n_inst, double2* c) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  double pr = 1.0, pi = 0.0;
+  for (int l = 0; l < n_leaves; ++l) {
+    const double2 r = leaf_r[i * n_leaves + l];
+    const double t = pr * r.x - pi * r.y;
+    pi = pr * r.y + pi * r.x;
+    pr = t;
+  }
+  c[i] = make_double2(pr, pi);
+}
+
+cudaError_t launch_inst_scale(const double2* leaf_r, int n_leaves, int64_t n_inst, double2* c, cudaStream_t s) {
+  k_inst_scale<<<(unsigned)((n_inst + 127) / 128), 128, 0, s>>>(leaf_r, n_leaves, n_inst, c);
+  return cudaGetLastError();
+}
+
+// acc[row, o] += sum over the segment's instances (in order) of root[o] * 2^E (times the
+// instance's leaf-rounding scale c when given).
 template <typename T>
 __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                              const int8_t* __restrict__ open_pos, int n_open, const RootSeg* __restrict__ segs,
-                             const int32_t* __restrict__ exps, int n_slots, int root_slot, double2* acc) {
+                             const int32_t* __restrict__ exps, int n_slots, int root_slot, double2* acc,
+                             const double2* __restrict__ cfac) {
   const int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n_out = int64_t(1) << n_open;
   if (o >= n_out) return;
   const RootSeg s = segs[blockIdx.y];
   int64_t idx = 0;
   for (int j = 0; j < n_open; ++j) idx |= ((o >> (n_open - 1 - j)) & 1) << open_pos[j];
-  double re = 0.0, im = 0.0;
+  // added one instance at a time, in slice order, onto the running value: the same
+  // association whatever the wave size
+  double2* a = acc + int64_t(s.row) * n_out + o;
+  double re = a->x, im = a->y;
   for (int i = s.begin; i < s.end; ++i) {
     const T* root = arena + int64_t(i) * inst_stride + root_off;
     const double sc = ldexp(1.0, exps[int64_t(i) * n_slots + root_slot]);
-    re += (double)Conv<T>::to_f(root[idx]) * sc;
-    im += (double)Conv<T>::to_f(root[plane + idx]) * sc;
+    const double xr = (double)Conv<T>::to_f(root[idx]) * sc, xi = (double)Conv<T>::to_f(root[plane + idx]) * sc;
+    if (cfac) {
+      const double2 c = cfac[i];
+      re += xr * c.x - xi * c.y;
+      im += xr * c.y + xi * c.x;
+    } else {
+      re += xr;
+      im += xi;
+    }
   }
-  double2* a = acc + int64_t(s.row) * n_out + o;
-  a->x += re;
-  a->y += im;
+  a->x = re;
+  a->y = im;
 }
 
 // Root cotangent of every instance: dL/droot[o] = w[row, o] (holomorphic derivative of
@@ -450,6 +507,83 @@ __global__ void k_maxabs(const T* __restrict__ x, int64_t n, float* out) {
     m = fmaxf(m, fabsf(Conv<T>::to_f(x[i])));
   const float bm = block_max(m, red);
   if (threadIdx.x == 0) atomic_max_nonneg(out, bm);
+}
+
+// Permutation (TTGT transposes): each CTA loads one tile in the input's order with
+// contiguous vector loads, and writes it in the output's order with contiguous vector stores,
+// reading shared memory through the split permutation table.  Values are copied exactly.
+template <typename T, int V>
+__device__ __forceinline__ void store_perm_v(T* __restrict__ re, T* __restrict__ im, int bits, int run,
+                                             const uint32_t* __restrict__ hi, const float2* __restrict__ buf,
+                                             const uint16_t* __restrict__ plo, const uint16_t* __restrict__ phi) {
+  const int n = 1 << bits;
+  const uint32_t lowmask = (1u << run) - 1u;
+  for (int u = threadIdx.x * V; u < n; u += kThreads * V) {
+    const uint32_t off = hi[u >> run] + (uint32_t(u) & lowmask);
+    Vec<T, V> r, i;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int uu = u + v;
+      const float2 x = buf[plo[uu & 63] + phi[uu >> 6]];
+      r.v[v] = Conv<T>::from_f(x.x);
+      i.v[v] = Conv<T>::from_f(x.y);
+    }
+    *reinterpret_cast<Vec<T, V>*>(re + off) = r;
+    *reinterpret_cast<Vec<T, V>*>(im + off) = i;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_permute(const PermParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* buf = reinterpret_cast<float2*>(smem);                          // [2^bits]
+  uint32_t* hiI = reinterpret_cast<uint32_t*>(buf + (1 << p.bits));       // [2^(bits - run_in)]
+  uint32_t* hiO = hiI + (1 << (p.bits - p.run_in));                        // [2^(bits - run_out)]
+  uint16_t* plo = reinterpret_cast<uint16_t*>(hiO + (1 << (p.bits - p.run_out)));  // [64]
+  uint16_t* phi = plo + 64;                                                // [64]
+  const int tid = threadIdx.x;
+  int64_t oI = 0, oO = 0;
+  for (int j = 0; j < p.n_o; ++j)
+    if ((blockIdx.x >> j) & 1u) oI += int64_t(1) << p.o_in[j], oO += int64_t(1) << p.o_out[j];
+  for (int h = tid; h < (1 << (p.bits - p.run_in)); h += kThreads) hiI[h] = deposit_hi(h, p.mask_in, p.run_in);
+  for (int h = tid; h < (1 << (p.bits - p.run_out)); h += kThreads) hiO[h] = deposit_hi(h, p.mask_out, p.run_out);
+  if (tid < 64) {
+    plo[tid] = p.plo[tid];
+    phi[tid] = p.phi[tid];
+  }
+  __syncthreads();
+  const T* in = reinterpret_cast<const T*>(p.in) + oI;
+  load_tile<T>(in, in + p.plane, p.bits, p.run_in, hiI, buf);
+  __syncthreads();
+  T* out = reinterpret_cast<T*>(p.out) + oO;
+  constexpr int VMAX = 16 / sizeof(T);
+  const int v = min(1 << p.run_out, VMAX);
+  if (v >= 8) store_perm_v<T, (VMAX >= 8 ? 8 : 1)>(out, out + p.plane, p.bits, p.run_out, hiO, buf, plo, phi);
+  else if (v == 4) store_perm_v<T, 4>(out, out + p.plane, p.bits, p.run_out, hiO, buf, plo, phi);
+  else if (v == 2) store_perm_v<T, 2>(out, out + p.plane, p.bits, p.run_out, hiO, buf, plo, phi);
+  else store_perm_v<T, 1>(out, out + p.plane, p.bits, p.run_out, hiO, buf, plo, phi);
+}
+
+size_t permute_smem_bytes(const PermParams& p) {
+  return (size_t(1) << p.bits) * 8 + (size_t(1) << (p.bits - p.run_in)) * 4 + (size_t(1) << (p.bits - p.run_out)) * 4 +
+         128 * 2 + 16;
+}
+
+cudaError_t launch_permute(int precision, const PermParams& p, cudaStream_t s) {
+  const size_t smem = permute_smem_bytes(p);
+  const dim3 grid(1u << p.n_o);
+  cudaError_t e;
+  if (precision == 0) {
+    if ((e = set_smem_once(reinterpret_cast<const void*>(k_permute<float>), smem)) != cudaSuccess) return e;
+    k_permute<float><<<grid, kThreads, smem, s>>>(p);
+  } else if (precision == 1) {
+    if ((e = set_smem_once(reinterpret_cast<const void*>(k_permute<__half>), smem)) != cudaSuccess) return e;
+    k_permute<__half><<<grid, kThreads, smem, s>>>(p);
+  } else {
+    if ((e = set_smem_once(reinterpret_cast<const void*>(k_permute<__nv_bfloat16>), smem)) != cudaSuccess) return e;
+    k_permute<__nv_bfloat16><<<grid, kThreads, smem, s>>>(p);
+  }
+  return cudaGetLastError();
 }
 
 // Fused chain: load a tile of A0 over the on-chip labels, apply every link in FP32 in
@@ -613,34 +747,36 @@ cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_in
 cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leaves, const double2* src, void* arena,
                                int64_t inst_stride, const int64_t* inst_slice, const int32_t* inst_row,
                                const uint8_t* bits, int n_qubits, float* maxabs, int32_t* exps, int n_slots,
-                               int64_t inst_base, int64_t n_inst, cudaStream_t s) {
+                               int64_t inst_base, int64_t n_inst, double2* leaf_r, cudaStream_t s) {
   dim3 grid((unsigned)n_leaves, (unsigned)n_inst);
   if (precision == 0)
     k_leaf_gather<float><<<grid, 32, 0, s>>>(leaves, src, (float*)arena, inst_stride, inst_slice, inst_row, bits,
-                                             n_qubits, maxabs, exps, n_slots, inst_base);
+                                             n_qubits, maxabs, exps, n_slots, inst_base, leaf_r, n_leaves);
   else if (precision == 1)
     k_leaf_gather<__half><<<grid, 32, 0, s>>>(leaves, src, (__half*)arena, inst_stride, inst_slice, inst_row, bits,
-                                              n_qubits, maxabs, exps, n_slots, inst_base);
+                                              n_qubits, maxabs, exps, n_slots, inst_base, leaf_r, n_leaves);
   else
     k_leaf_gather<__nv_bfloat16><<<grid, 32, 0, s>>>(leaves, src, (__nv_bfloat16*)arena, inst_stride, inst_slice,
-                                                     inst_row, bits, n_qubits, maxabs, exps, n_slots, inst_base);
+                                                     inst_row, bits, n_qubits, maxabs, exps, n_slots, inst_base, leaf_r,
+                                                     n_leaves);
   return cudaGetLastError();
 }
 
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
-                              const int32_t* exps, int n_slots, int root_slot, double2* acc, cudaStream_t s) {
+                              const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
+                              cudaStream_t s) {
   const int64_t n_out = int64_t(1) << n_open;
   dim3 grid((unsigned)((n_out + 255) / 256), (unsigned)n_segs);
   if (precision == 0)
     k_root_accum<float><<<grid, 256, 0, s>>>((const float*)arena, inst_stride, root_off, plane, open_pos, n_open, segs,
-                                             exps, n_slots, root_slot, acc);
+                                             exps, n_slots, root_slot, acc, cfac);
   else if (precision == 1)
     k_root_accum<__half><<<grid, 256, 0, s>>>((const __half*)arena, inst_stride, root_off, plane, open_pos, n_open,
-                                              segs, exps, n_slots, root_slot, acc);
+                                              segs, exps, n_slots, root_slot, acc, cfac);
   else
     k_root_accum<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)arena, inst_stride, root_off, plane,
-                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc);
+                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc, cfac);
   return cudaGetLastError();
 }
 

@@ -643,6 +643,319 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
   tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, inst);
 }
 
+// Persistent variant of k_tc_tma for short K loops (at most eight K tiles per output tile)
+// over many output tiles.  One CTA per SM walks the tiles of all instances (instance-major,
+// then the tile order of the one-CTA-per-tile launch) with a stride of gridDim.x:
+//   epilogue warps   (BN / 8 of them: four TMEM lane quadrants x 32 columns each) drain
+//                    buffer j & 1 (scale, convert, stage in C's order, store) and release
+//                    it on "tmem empty";
+//   next warp, lane 0   issues the TMA loads of every K tile of its tiles through an
+//                    NST-stage ring ("full" / "empty" mbarriers), running ahead across tiles;
+//   last warp, lane 0   issues the MMAs of the CTA's j-th tile into TMEM accumulator buffer
+//                    j & 1 and commits them to "tmem full" of that buffer,
+// so the epilogue of one tile overlaps the loads and MMAs of the next.  The epilogue threads
+// synchronise on named barrier 1; one of them waits on each mbarrier and shares the
+// outcome, so a timeout ends the loop for all of them together.
+
+template <int BN, int BK>
+struct TcpShape {
+  static constexpr int ROWB = BK * 2;
+  static constexpr int A_BYTES = TC_BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STG = TC_BM * BN * 2 * 2;              // staged C tile (2 planes, 16-bit)
+  static constexpr int NST_FIT = (200 * 1024 - STG) / STAGE;
+  static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
+  static constexpr int PIPE = NST * STAGE;
+  static constexpr int SBO = 8 * ROWB;
+  static constexpr int LAYOUT = BK == 32 ? 4 : 6;             // SW64 / SW32
+  static constexpr int N_BITS = BN == 128 ? 7 : 6;
+  static constexpr int C_BITS = 7 + N_BITS;
+  static constexpr int TMEM_COLS = 4 * BN;                    // two buffers of (Dr, Di)
+  static constexpr int EPI_WARPS = BN / 8;                    // 4 lane quadrants x BN/32
+  static constexpr int EPI_THREADS = EPI_WARPS * 32;
+  static constexpr int THREADS = EPI_THREADS + 64;            // + producer warp + MMA warp
+  static_assert(BN == 64 || BN == 128, "two accumulator buffers need BN <= 128");
+  static_assert(NST >= 3, "pipeline");
+};
+
+template <int N>
+__device__ __forceinline__ void epi_bar() {
+  __syncwarp();
+  asm volatile("barrier.sync 1, %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename T, int BN, int BK>
+__global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist(const __grid_constant__ TcParams p) {
+  using S = TcpShape<BN, BK>;
+  constexpr int KT = BK == 32 ? 5 : 4;
+  constexpr int NST = S::NST;
+  constexpr int CT = TC_BM * BN;  // entries of the C tile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  T* stg = reinterpret_cast<T*>(smem + S::PIPE);                           // [2][CT]
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::PIPE + S::STG);    // [2^(C_BITS - runC)]
+  const int nhC = 1 << (S::C_BITS - p.runC);
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);                  // [128]
+  uint16_t* TCn = TCm + TC_BM;                                              // [BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NST;
+  uint64_t* tfull = bars + 2 * NST;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);                    // [EPI_WARPS]
+  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + S::EPI_WARPS);
+  constexpr int NT = S::THREADS, NE = S::EPI_THREADS;
+  const int prod_warp = S::EPI_WARPS, mma_warp = S::EPI_WARPS + 1;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int nb = S::N_BITS;
+  for (int r = tid; r < TC_BM; r += NT) {
+    uint32_t cm = 0;
+    for (int j = 0; j < 7; ++j)
+      if ((r >> j) & 1) cm |= 1u << p.pCm[j];
+    TCm[r] = (uint16_t)cm;
+  }
+  for (int r = tid; r < BN; r += NT) {
+    uint32_t cn = 0;
+    for (int j = 0; j < nb; ++j)
+      if ((r >> j) & 1) cn |= 1u << p.pCn[j];
+    TCn[r] = (uint16_t)cn;
+  }
+  for (int h = tid; h < nhC; h += NT) {
+    uint32_t m = p.maskC;
+    for (int i = 0; i < p.runC; ++i) m &= m - 1;
+    uint32_t r = 0, x = (uint32_t)h;
+    while (m) {
+      const uint32_t low = m & (~m + 1u);
+      if (x & 1u) r |= low;
+      x >>= 1;
+      m &= m - 1;
+    }
+    hiC[h] = r;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int tile_bits = p.n_om + p.n_on;
+  const int64_t n_tiles = (int64_t(p.n_inst)) << tile_bits;
+  const uint32_t tile_mask = (1u << tile_bits) - 1u;
+  const int k_iters = 1 << p.n_ok;
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
+
+  if (warp == prod_warp) {
+    if (lane == 0) {
+      // TMA producer
+      int64_t g = 0, issued = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int inst = (int)(t >> tile_bits);
+        const uint32_t r = (uint32_t)t & tile_mask;
+        const uint32_t on = r & ((1u << p.n_on) - 1u);
+        const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
+        int64_t oA = 0, oB = 0;
+        for (int j = 0; j < p.n_om; ++j)
+          if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j];
+        for (int j = 0; j < p.n_on; ++j)
+          if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j];
+        for (int it = 0; it < k_iters; ++it, ++g) {
+          const int buf = (int)(g % NST);
+          if (g >= NST && !mbar_wait_bounded(smem_u32(&empty[buf]), (uint32_t)(((g / NST) - 1) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          int64_t okA = 0, okB = 0;
+          for (int j = 0; j < p.n_ok; ++j)
+            if ((it >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+          const int rowA = (int)((oA + okA) >> KT), rowB = (int)((oB + okB) >> KT);
+          const uint32_t st = sbase + buf * S::STAGE;
+          const uint32_t fb = smem_u32(&full[buf]);
+          mbar_arrive_expect_tx(fb, S::STAGE);
+          tma_load_4d(st, &p.tmA, 0, rowA, 0, inst, fb);
+          tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, inst, fb);
+          tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, inst, fb);
+          tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, inst, fb);
+          issued = g + 1;
+        }
+      }
+      // copies still in flight land before the CTA may exit
+      for (int64_t x = issued - NST > 0 ? issued - NST : 0; x < issued; ++x)
+        if (!mbar_wait_bounded(smem_u32(&full[x % NST]), (uint32_t)((x / NST) & 1), p.status)) ok = false;
+    }
+  } else if (warp == mma_warp) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
+      int64_t g = 0;
+      int j = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+        const int b = j & 1;
+        if (j >= 2 && !mbar_wait_bounded(smem_u32(&tempty[b]), (uint32_t)(((j >> 1) - 1) & 1), p.status)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t acc = tmem + uint32_t(b * 2 * BN);
+        for (int it = 0; it < k_iters; ++it, ++g) {
+          const int buf = (int)(g % NST);
+          if (!mbar_wait_bounded(smem_u32(&full[buf]), (uint32_t)((g / NST) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t st = sbase + buf * S::STAGE;
+#pragma unroll
+          for (int jj = 0; jj < BK / 16; ++jj) {
+            const uint64_t ar = kmajor_desc(st + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t ai = kmajor_desc(st + S::A_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t br = kmajor_desc(st + 2 * S::A_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t bi = kmajor_desc(st + 2 * S::A_BYTES + S::B_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint32_t first = (it == 0 && jj == 0) ? 0u : 1u;
+            mma_f16(acc, ar, br, id_pos, first);
+            mma_f16(acc, ai, bi, id_neg, 1u);
+            mma_f16(acc + BN, ar, bi, id_pos, first);
+            mma_f16(acc + BN, ai, br, id_pos, 1u);
+          }
+          mma_commit(smem_u32(&empty[buf]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull[b]));
+      }
+      // every MMA issued above completes before the CTA may free its TMEM
+      mma_commit(smem_u32(done));
+      if (!mbar_wait_bounded(smem_u32(done), 0u, p.status)) ok = false;
+    }
+  } else {
+    // epilogue: thread = one TMEM lane (row) of its warp's quadrant, 32 columns
+    const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+    const int row = (warp & 3) * 32 + lane;
+    const int col0 = (warp >> 2) * 32;
+    const uint32_t lowmask = (1u << p.runC) - 1u;
+    int j = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
+      const int b = j & 1;
+      if (tid == 0) *flag = mbar_wait_bounded(smem_u32(&tfull[b]), (uint32_t)((j >> 1) & 1), p.status) ? 1 : 0;
+      epi_bar<NE>();
+      if (*flag == 0) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int64_t inst = t >> tile_bits;
+      const uint32_t r = (uint32_t)t & tile_mask;
+      const uint32_t on = r & ((1u << p.n_on) - 1u);
+      const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
+      int64_t oC = 0;
+      for (int q = 0; q < p.n_om; ++q)
+        if ((om >> q) & 1u) oC += int64_t(1) << p.om_C[q];
+      for (int q = 0; q < p.n_on; ++q)
+        if ((on >> q) & 1u) oC += int64_t(1) << p.on_C[q];
+      const int64_t sb = inst * p.n_slots;
+      int sh = 0;
+      {
+        const float a = p.maxabs[sb + p.slotA], bb = p.maxabs[sb + p.slotB];
+        if (a > 0.f && bb > 0.f) {
+          int ea, eb;
+          frexpf(a, &ea);
+          frexpf(bb, &eb);
+          sh = ea + eb + p.nK + 1 - 15;
+        }
+      }
+      const float scale = ldexpf(1.f, -sh);
+      const uint32_t acc = tmem + uint32_t(b * 2 * BN);
+      float mx = 0.f;
+      {
+        float vr[32], vi[32];
+        tmem_ld32(acc + lane_addr + col0, vr);
+        tmem_ld32(acc + lane_addr + BN + col0, vi);
+        const uint32_t rm = TCm[row];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const uint32_t idx = rm + TCn[col0 + q];
+          const T re = Conv<T>::from_f(vr[q] * scale), im = Conv<T>::from_f(vi[q] * scale);
+          stg[stg_swz(idx)] = re;
+          stg[CT + stg_swz(idx)] = im;
+          mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      epi_bar<NE>();
+      if (tid == 0) mbar_arrive(smem_u32(&tempty[b]));
+      // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
+      T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+      for (int x = tid * 8; x < CT; x += NE * 8) {
+        const uint32_t off = hiC[x >> p.runC] + (uint32_t(x) & lowmask);
+        *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + stg_swz(x));
+        *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + stg_swz(x));
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) red[warp] = mx;
+      epi_bar<NE>();
+      if (tid == 0) {
+        float m = 0.f;
+        for (int w = 0; w < S::EPI_WARPS; ++w) m = fmaxf(m, red[w]);
+        atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
+        if (r == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
+}
+
+template <int BN, int BK>
+size_t tma_persist_smem_bytes_t(int runC) {
+  using S = TcpShape<BN, BK>;
+  return 1024 + S::PIPE + S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
+         (2 * S::NST + 5) * 8 + 16 + S::EPI_WARPS * 4 + 16 + 64;
+}
+
+static int sm_count_cached() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+  }
+  return n;
+}
+
+template <typename T, int BN, int BK>
+cudaError_t launch_tma_persist_t(const TcParams& p, cudaStream_t s) {
+  const size_t smem = tma_persist_smem_bytes_t<BN, BK>(p.runC);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_persist<T, BN, BK>), smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = int64_t(p.n_inst) << (p.n_om + p.n_on);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count_cached());
+  k_tc_tma_persist<T, BN, BK><<<grid, TcpShape<BN, BK>::THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int BN, int BK, int NST>
 size_t tma_smem_bytes_t(int runC) {
   using S = TcShape<BN, BK, NST>;
@@ -668,6 +981,12 @@ cudaError_t launch_tma_st(const TcParams& p, dim3 grid, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_tma_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (p.persistent && p.splitk == 1 && p.n_inst >= 1) {
+    if (p.bn == 128 && p.bk == 32) return launch_tma_persist_t<T, 128, 32>(p, s);
+    if (p.bn == 128 && p.bk == 16) return launch_tma_persist_t<T, 128, 16>(p, s);
+    if (p.bn == 64 && p.bk == 32) return launch_tma_persist_t<T, 64, 32>(p, s);
+    if (p.bn == 64 && p.bk == 16) return launch_tma_persist_t<T, 64, 16>(p, s);
+  }
   if (p.bn == 256) {
     if (p.bk == 32) return launch_tma_st<T, 256, 32>(p, grid, s);
     if (p.bk == 16) return launch_tma_st<T, 256, 16>(p, grid, s);

@@ -40,7 +40,7 @@ def tma_case(m, k, n, seed):
     """Layouts the TMA kernel loads directly: A = [Kt | 7 row labels | rest], B = [Kt | 6-7
     column labels | rest], C's three lowest labels among the tile labels."""
     kt = 5 if k >= 5 else 4
-    nt = 8 if (n >= 8 and k > kt + 1) else (7 if n >= 7 else 6)
+    nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
     ks = list(range(100, 100 + k))
     ms = list(range(m))
     ns = list(range(200, 200 + n))
@@ -132,3 +132,54 @@ def test_tc_steps_inside_a_plan(ctx, precision):
     info = p.info()
     tol = 1e-2 if precision == "chalf" else 4 * 2.0 ** -9 * np.sqrt(info["n_leaves"] + info["n_steps"])
     assert metrics.rel_err_norm(got, ref) <= tol
+
+
+# Short K loops over >= 4 x 152 output tiles take the persistent TMA kernel (two TMEM
+# accumulators, epilogue overlapped with the next tile): BN = 128 with 16- and 32-wide K
+# tiles, BN = 64; one to eight K tiles per output tile.
+PERSIST_SHAPES = [(12, 4, 12), (14, 5, 10), (12, 6, 12), (17, 7, 7), (16, 8, 8), (17, 4, 6)]
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape", PERSIST_SHAPES)
+def test_tma_persistent_kernel(ctx, precision, shape, monkeypatch):
+    a, la, b, lb, lc = tma_case(*shape, seed=7 * sum(shape) + shape[0])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 5  # the persistent kernel ran
+    # sampled outputs against the oracle, first and last entries included
+    idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(5).integers(0, len(got), 510)]))
+    assert metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx)) <= TOL[precision]
+    # every tile against the one-CTA-per-tile kernel: same MMAs in the same order, same epilogue
+    monkeypatch.setenv("TNC_NO_PERSIST", "1")
+    ctx1 = T.Context(0)
+    ref, _, _ = run(ctx1, precision, a, la, b, lb, lc)
+    assert int(ctx1.profile_read(cap=1)["kind"][0]) == 4
+    assert np.array_equal(got, ref)
+
+
+# Layouts the tensor-core kernels cannot load in place (a free label at the lowest position
+# of each operand): TTGT -- permute into the tensor-core layouts, contract, permute back.
+TTGT_SHAPES = [(8, 6, 7), (9, 8, 8), (10, 5, 6), (7, 10, 9), (12, 4, 12)]
+
+
+def ttgt_case(m, k, n, seed):
+    ms, ks, ns = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
+    la = [ms[0]] + random_labels_perm(ms[1:] + ks, seed)
+    lb = [ns[0]] + random_labels_perm(ks + ns[1:], seed + 1)
+    lc = random_labels_perm(ms + ns, seed + 2)
+    sigma = 1.0 / np.sqrt(2.0 ** k)
+    return random_complex(1 << len(la), sigma, seed + 3), la, random_complex(1 << len(lb), sigma, seed + 4), lb, lc
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape", TTGT_SHAPES)
+def test_ttgt_random_layouts(ctx, precision, shape):
+    a, la, b, lb, lc = ttgt_case(*shape, seed=11 * sum(shape) + shape[1])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 6  # permute, tensor-core GEMM, permute
+    if len(got) <= 1 << 16:
+        err = metrics.rel_err_norm(got, pairwise.contract(aq, la, bq, lb, lc))
+    else:
+        idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(9).integers(0, len(got), 510)]))
+        err = metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx))
+    assert err <= TOL[precision], err
