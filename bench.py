@@ -41,6 +41,32 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 
 
+def measured_traffic(kind, flops_launch):
+    """DRAM bytes (read + write) of one launch of the dominant kernel, from the committed ncu
+    summary: per-instance bytes of a one-instance capture times the launch's instances.  None
+    when the kernel source changed since the capture or the launch is not that contraction."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", "k_tc_tma_bn256_14x12x10_chalf.md")
+    if kind != 4 or not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    get = lambda key: re.search(rf"^{key}: (\S+)$", txt, re.M)
+    vals = {k: get(k) for k in ("traffic_flops_per_instance", "traffic_dram_bytes_per_instance",
+                                 "traffic_kernel_source_sha1")}
+    if not all(vals.values()):
+        return None
+    src = os.path.join(ROOT, "paper_2504_09186_gb300", "csrc", "tc_gemm.cu")
+    if hashlib.sha1(open(src, "rb").read()).hexdigest() != vals["traffic_kernel_source_sha1"].group(1):
+        return None
+    fpi = float(vals["traffic_flops_per_instance"].group(1))
+    inst = flops_launch / fpi
+    if abs(inst - round(inst)) > 1e-9 or round(inst) < 1:
+        return None
+    return float(vals["traffic_dram_bytes_per_instance"].group(1)) * round(inst)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -62,6 +88,7 @@ def parse():
     ap.add_argument("--workload", default="s30", choices=sorted(WORKLOADS) + ["s60", "d20", "sw"],
                     help="s30 (default) / t12: sliced sub-cube amplitudes; s60: per-slice throughput of the "
                          "60-qubit circuit; d20: adjoint gradients; sw: single-step contraction sweep")
+    ap.add_argument("--plan-trials", type=int, default=0, help="planner trials (0: the workload's own)")
     ap.add_argument("--s60-slices", type=int, default=4, help="seeded slice sample of the s60 workload")
     ap.add_argument("--s60-trials", type=int, default=16, help="planner trials of the s60 workload")
     ap.add_argument("--s60-c64", type=int, default=2, help="slices of the sample also run in complex64")
@@ -198,6 +225,8 @@ def run_reference(args):
     from paper_2504_09186_gb300 import tnc as T
 
     w, circ, fixed, open_q = workload(args.workload, 0)
+    if args.plan_trials > 0:
+        w = dict(w, trials=args.plan_trials)
     plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
                          slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
     cuts = plan.sliced_cuts()
@@ -243,6 +272,8 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w, circ, fixed, open_q = workload(args.workload, rank)
+    if args.plan_trials > 0:
+        w = dict(w, trials=args.plan_trials)
     plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
                          slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
     info = plan.info()
@@ -329,10 +360,13 @@ def run_ours(args):
     if roof["bound"] == "tensor":
         # the timed region is well under a second at full clocks: the burst peak applies
         roof["frac_of_sustained"] = roof["achieved"] / peaks["bf16_tflops_sustained"]
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(kind, flops_launch)
     roof["kernel"] = {"step": k, "kind": kind, "share_of_step_time": float(prof["ms"][k] / max(1e-9, prof["ms"].sum())),
                       "ms_per_launch": per_launch_ms, "flops_per_launch": flops_launch, "bytes_per_launch": bytes_launch}
     roof["peak_source"] = peaks["_source"]
+    order = np.argsort(-prof["ms"])[:8]
+    top_steps = [{"step": int(i), "kind": int(prof["kind"][i]), "ms_per_step": float(prof["ms"][i] / args.steps),
+                  "launches_per_step": int(prof["launches"][i] // args.steps)} for i in order]
     total_flops = float(prof["flops"].sum()) / args.steps
     waves = int(prof["launches"].min() / args.steps)
     launches = int(prof["launches"].sum() / args.steps) + 3 * waves  # + leaf gather, leaf scales, root sum per wave
@@ -355,7 +389,7 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {w['rows']}x{w['cols']} grid RQC, {w['cycles']} cycles, "
                                    f"{n_slices} slices (cap 2^{w['cap']}), {n_out}-amplitude sub-cube per GPU",
                        "precision": args.precision, "slices_per_step": n_slices * world,
-                       "plan": args.plan, "fused_chains": bool(fuse and info["n_fused"] > 0),
+                       "plan": args.plan, "plan_trials": w["trials"], "fused_chains": bool(fuse and info["n_fused"] > 0),
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"], "sliced_indices": info["n_sliced"],
                        "complex_tflops": total_flops / (ms / 1e3) / 1e12,
                        "l2": "256 MiB flush before every timed step; intermediates up to 2^26 entries > L2",
@@ -365,6 +399,7 @@ def run_ours(args):
             "e2e": {"value": n_slices * world / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "top_steps": top_steps,
             "roofline": roof,
             "clocks": clocks,
             "cpu_baseline": cpu,

@@ -95,6 +95,10 @@ typedef struct {
                        /* 1: stem order -- one tensor absorbs neighbouring leaves one  */
                        /*    at a time (the stem of Sec. II-A), which the fused chains */
                        /*    of Sec. IV execute on chip                               */
+  int32_t objective;   /* which trial is kept: 0 = fewest complex multiply-adds (the    */
+                       /* cost of Eq. 1); 1 = least modeled GB300 time, summing per step */
+                       /* max(flops / rate, bytes / HBM bandwidth) with the tensor-core */
+                       /* rate for steps large enough for its tiles                   */
 } tnc_plan_opts;
 
 /* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:
@@ -162,7 +166,10 @@ typedef struct {
   int32_t fuse;          /* 1 = fused on-chip chains of small absorptions (Sec. IV)  */
   int32_t profile;       /* 1 = time every step launch with CUDA events on the launch  */
                          /* stream; read with tnc_profile_read                        */
-  int32_t reserved[3];
+  int32_t reserved[3];   /* reserved[0], tnc_adjoint only: device memory (MiB) per instance
+                            for the forward intermediates kept for the backward pass; above
+                            it the largest are recomputed from their children when the
+                            backward pass reaches them (0 = keep all).  Others: 0. */
 } tnc_exec_opts;
 
 /* Amplitudes of a batch (Sec. I; the multi-amplitude batch of Sec. II-C), summed over

@@ -101,6 +101,7 @@ tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* o
     o.slices_max = opts->slices_max;
     o.temperature = opts->temperature;
     o.mode = opts->mode;
+    o.objective = opts->objective;
     if (o.mode != 0 && o.mode != 1) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy) or 1 (stem)");
     auto* p = new tnc_plan_s();
     try {

@@ -1392,15 +1392,76 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
     if (P.sliced.size() > 30) fail(TNC_E_UNSUPPORTED, "tnc_adjoint sums over every slice: at most 30 sliced indices");
     const int64_t n_slices = int64_t(1) << P.sliced.size();
     const int64_t n_inst = batch * n_slices;
-    // arena: forward tensors, then adjoint leaves (contiguous, for one read-back copy), then
-    // the other adjoints; every slot distinct
-    std::vector<int64_t> off(2 * T);
+    // Forward intermediates kept for the backward pass.  Under a memory budget the largest
+    // ones are dropped and recomputed from their two children just before the backward step
+    // that reads them; a dropped tensor's children and its consumer's output stay stored, so
+    // one recomputation (the original forward step) always suffices.
+    auto elems = [&](int t) { return ((int64_t(2) << P.tensors[t].labels.size()) + 63) & ~int64_t(63); };
+    std::vector<int> consumer(T, -1);
+    for (size_t k = 0; k < P.steps.size(); ++k) consumer[P.steps[k].a] = consumer[P.steps[k].b] = (int)k;
+    std::vector<char> dropped(T, 0);
+    const int64_t budget = int64_t(std::max(0, opts ? opts->reserved[0] : 0)) << 20;  // bytes per instance
+    if (budget > 0) {
+      int64_t kept = 0;
+      for (int t = L; t < T; ++t) kept += elems(t) * 4;
+      std::vector<int> cand;
+      for (int t = L; t < T; ++t)
+        if (t != P.root && consumer[t] >= 0) cand.push_back(t);
+      std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) { return elems(x) > elems(y); });
+      for (int x : cand) {
+        if (kept <= budget) break;
+        const Step& px = P.steps[x - L];
+        const int parent = L + consumer[x];
+        if (dropped[px.a] || dropped[px.b] || dropped[parent]) continue;
+        dropped[x] = 1;
+        kept -= elems(x) * 4;
+      }
+    }
+    // arena: kept forward tensors, then a pool for the dropped ones (forward liveness, first
+    // fit; during the backward pass it holds the recomputed operands), then the adjoint
+    // leaves (contiguous, for one read-back copy), then the other adjoints
+    std::vector<int64_t> off(2 * T), off_b(T);
     int64_t top = 0;
     auto take = [&](int slot, int rank) {
       off[slot] = top;
       top += ((int64_t(2) << rank) + 63) & ~int64_t(63);
     };
-    for (int t = 0; t < T; ++t) take(t, (int)P.tensors[t].labels.size());
+    for (int t = 0; t < T; ++t)
+      if (!dropped[t]) take(t, (int)P.tensors[t].labels.size());
+    {
+      const int64_t pool = top;
+      std::vector<std::pair<int64_t, int64_t>> live;  // (offset, size) with end step
+      std::vector<int> dend;
+      int64_t pool_top = 0, biggest = 0;
+      for (int t = L; t < T; ++t) {
+        if (!dropped[t]) continue;
+        const int born = t - L, dies = consumer[t];
+        // first fit among slots whose tenants died before this one is born
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (size_t i = 0; i < live.size(); ++i)
+          if (dend[i] >= born) busy.push_back(live[i]);
+        std::sort(busy.begin(), busy.end());
+        int64_t at = 0;
+        for (auto& b : busy) {
+          if (at + elems(t) <= b.first) break;
+          at = std::max(at, b.first + b.second);
+        }
+        off[t] = pool + at;
+        live.push_back({at, elems(t)});
+        dend.push_back(dies);
+        pool_top = std::max(pool_top, at + elems(t));
+        biggest = std::max(biggest, elems(t));
+      }
+      // backward: a step reads at most two dropped operands, recomputed into two fixed slots
+      int next_slot = 0;
+      for (int t = 0; t < T; ++t) off_b[t] = off[t];
+      for (size_t k = P.steps.size(); k-- > 0;) {
+        next_slot = 0;
+        for (int t : {P.steps[k].a, P.steps[k].b})
+          if (dropped[t]) off_b[t] = pool + (next_slot++) * biggest;
+      }
+      top = pool + std::max(pool_top, 2 * biggest);
+    }
     const int64_t adj_leaf_begin = top;
     for (int t = 0; t < L; ++t) take(T + t, (int)P.tensors[t].labels.size());
     const int64_t adj_leaf_end = top;
@@ -1422,11 +1483,12 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
     // launches
     std::vector<StepLaunch> fwd, bwd;
     size_t partial_elems = 0;
-    auto bind = [&](StepLaunch& Lh, int sa, int sb, int sc) {
+    auto bind = [&](StepLaunch& Lh, int sa, int sb, int sc, bool backward = false) {
       char* base = arena.as<char>();
-      Lh.p.A = base + off[sa] * 4;
-      Lh.p.B = base + off[sb] * 4;
-      Lh.p.C = base + off[sc] * 4;
+      auto at = [&](int slot) { return (backward && slot < T) ? off_b[slot] : off[slot]; };
+      Lh.p.A = base + at(sa) * 4;
+      Lh.p.B = base + at(sb) * 4;
+      Lh.p.C = base + at(sc) * 4;
       Lh.p.strideA = Lh.p.strideB = Lh.p.strideC = stride;
       Lh.p.n_slots = 2 * T;
       Lh.p.slotA = sa;
@@ -1444,15 +1506,25 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
       const auto& la = P.tensors[st.a].labels;
       const auto& lb = P.tensors[st.b].labels;
       const auto& lc = P.tensors[st.c].labels;
+      // dropped operands: rerun their forward step into the backward slots (same kernels,
+      // same inputs: the same values, max and exponent as in the forward pass)
+      for (int t : {st.a, st.b}) {
+        if (!dropped[t]) continue;
+        const Step& pt = P.steps[t - L];
+        StepLaunch Lr = make_launch(pt.tile, pt.kind, P.tensors[pt.a].labels, P.tensors[pt.b].labels,
+                                    P.tensors[pt.c].labels);
+        bind(Lr, pt.a, pt.b, pt.c, true);
+        bwd.push_back(Lr);
+      }
       int kind = K_GENERIC;
       TileSpec ta = tile_for(lc, lb, la, (int)W, kind);  // A' = C' * B
       StepLaunch La = make_launch(ta, kind, lc, lb, la);
-      bind(La, T + st.c, st.b, T + st.a);
+      bind(La, T + st.c, st.b, T + st.a, true);
       bwd.push_back(La);
       kind = K_GENERIC;
       TileSpec tb = tile_for(la, lc, lb, (int)W, kind);  // B' = A * C'
       StepLaunch Lb = make_launch(tb, kind, la, lc, lb);
-      bind(Lb, st.a, T + st.c, T + st.b);
+      bind(Lb, st.a, T + st.c, T + st.b, true);
       bwd.push_back(Lb);
     }
     if (partial_elems) {

@@ -90,7 +90,8 @@ struct PlanOpts {
   int slices_min = 0;
   int slices_max = 64;
   double temperature = 0.5;
-  int mode = 0;  // 0 greedy, 1 stem
+  int mode = 0;       // 0 greedy, 1 stem
+  int objective = 0;  // 0 fewest multiply-adds, 1 least modeled GB300 time
 };
 
 // Kernel classes of a compiled step.

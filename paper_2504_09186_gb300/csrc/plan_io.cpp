@@ -1,5 +1,5 @@
 // Plan persistence.  Binary little-endian file:
-//   "TNCPLAN1", n_qubits, n_gates, gates (arity, q0, q1, 16 complex128), open mask,
+//   "TNCPLAN3", n_qubits, n_gates, gates (arity, q0, q1, 16 complex128), open mask,
 //   options, sliced edge ids, tree pairs, cost summary.
 // Loading rebuilds the network from the stored circuit (the build is deterministic, so
 // edge ids match) and recompiles the step program.
@@ -12,7 +12,7 @@
 namespace tnc {
 
 namespace {
-const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '2'};
+const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '3'};
 
 template <class T>
 void put(std::ofstream& f, const T& v) {
@@ -53,6 +53,7 @@ void save_plan(const Plan& p, const std::string& path) {
   put<int32_t>(f, p.opts.slices_max);
   put<double>(f, p.opts.temperature);
   put<int32_t>(f, p.opts.mode);
+  put<int32_t>(f, p.opts.objective);
   put<int32_t>(f, (int32_t)p.sliced.size());
   for (int e : p.sliced) put<int32_t>(f, e);
   put<int32_t>(f, (int32_t)p.tree.size());
@@ -102,6 +103,7 @@ void load_plan(const std::string& path, Plan& p) {
   p.opts.slices_max = get<int32_t>(f);
   p.opts.temperature = get<double>(f);
   p.opts.mode = get<int32_t>(f);
+  p.opts.objective = get<int32_t>(f);
   const int32_t ns = get<int32_t>(f);
   if (ns < 0 || ns > (int32_t)net.edges.size()) fail(7, "corrupt slice count");
   for (int i = 0; i < ns; ++i) {

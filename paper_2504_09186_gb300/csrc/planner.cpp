@@ -181,6 +181,27 @@ int tree_max(const Tree& t, const std::vector<char>& sliced) {
   return m;
 }
 
+// Modeled GB300 time of one slice (seconds): per step, the larger of its flop time and its
+// HBM time (complex-half storage, 4 bytes per entry); steps large enough for tensor-core
+// tiles (M >= 2^7, N >= 2^6 or the reverse, K >= 2^4) run at the tensor-core rate, the others
+// at the FP32-lane rate.
+double model_time(const Tree& t, const std::vector<char>& sliced) {
+  double tot = 0;
+  for (auto& p : t.pairs) {
+    const LabelSet& A = t.sets[p.first];
+    const LabelSet& B = t.sets[p.second];
+    const int a = (int)count_not_in(A, sliced), b = (int)count_not_in(B, sliced);
+    const int u = (int)count_not_in(set_union(A, B), sliced);
+    const int k = a + b - u, m = a - k, n = b - k;
+    const int c = (int)count_not_in(sym_diff(A, B), sliced);
+    const double flops = 8.0 * std::ldexp(1.0, u);
+    const double bytes = 4.0 * (std::ldexp(1.0, a) + std::ldexp(1.0, b) + std::ldexp(1.0, c));
+    const bool tc = std::max(m, n) >= 7 && std::min(m, n) >= 6 && k >= 4;
+    tot += std::max(flops / (tc ? 1.8e15 : 4.0e13), bytes / 6.5e12);
+  }
+  return tot;
+}
+
 }  // namespace
 
 void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
@@ -204,6 +225,7 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
     Tree tree;
     std::vector<int> sliced;
     double total = std::numeric_limits<double>::infinity();
+    double score = std::numeric_limits<double>::infinity();
     double per_slice = 0, unsliced = 0;
     bool within_max = false;
   } best;
@@ -268,14 +290,16 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       cur = tree_cost(t, sl);
     }
     const double total = std::ldexp(cur, (int)sliced.size());
+    const double score = o.objective == 1 ? std::ldexp(model_time(t, sl), (int)sliced.size()) : total;
     const bool within = (int)sliced.size() <= o.slices_max;
     bool better;
     if (within != best.within_max) better = within;
-    else better = total < best.total * (1 - 1e-12);
+    else better = score < best.score * (1 - 1e-12);
     if (better) {
       best.tree = t;
       best.sliced = sliced;
       best.total = total;
+      best.score = score;
       best.per_slice = cur;
       best.unsliced = c0;
       best.within_max = within;

@@ -239,7 +239,7 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
         const uint32_t rm = TCm[row];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const uint32_t t = rm + TCn[col0 + cc + j];
+          const uint32_t t = stg_swz(rm ^ TCn[col0 + cc + j]);  // the tables hold swizzled offsets
           part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(vr[j], vi[j]);
         }
       }
@@ -274,16 +274,18 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
       const uint32_t rm = TCm[row];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const uint32_t idx = rm + TCn[col0 + cc + j];
+        const uint32_t idx = rm ^ TCn[col0 + cc + j];  // swizzled staging index
 #if TNC_TC_SELFCHECK
         if (!tc_check(idx < uint32_t(CT), p.status, 16, idx, row)) continue;
 #endif
-        const T re = Conv<T>::from_f(vr[j] * scale), im = Conv<T>::from_f(vi[j] * scale);
-        stg[stg_swz(idx)] = re;
-        stg[CT + stg_swz(idx)] = im;
-        mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
+        stg[idx] = Conv<T>::from_f(vr[j] * scale);
+        stg[CT + idx] = Conv<T>::from_f(vi[j] * scale);
+        mx = fmaxf(mx, fmaxf(fabsf(vr[j]), fabsf(vi[j])));
       }
     }
+    // max of the stored values: from the FP32 values, scaled, widened by the largest
+    // rounding step of either 16-bit format so it never falls below the stored maximum
+    mx *= scale * (1.f + 0x1p-8f);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -356,14 +358,14 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
     for (int j = 0; j < 7; ++j)
       if ((r >> j) & 1) a |= 1u << p.pAm[j], cm |= 1u << p.pCm[j];
     depA[r] = a;
-    TCm[r] = (uint16_t)cm;
+    TCm[r] = (uint16_t)stg_swz(cm);  // staging offsets, stored swizzled (stg_swz is linear)
   }
   for (int r = tid; r < BN; r += TC_THREADS) {
     uint32_t b = 0, cn = 0;
     for (int j = 0; j < nb; ++j)
       if ((r >> j) & 1) b |= 1u << p.pBn[j], cn |= 1u << p.pCn[j];
     depB[r] = b;
-    TCn[r] = (uint16_t)cn;
+    TCn[r] = (uint16_t)stg_swz(cn);
   }
   for (int h = tid; h < nhC; h += TC_THREADS) {
     uint32_t m = p.maskC;
@@ -538,13 +540,13 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
     uint32_t cm = 0;
     for (int j = 0; j < 7; ++j)
       if ((r >> j) & 1) cm |= 1u << p.pCm[j];
-    TCm[r] = (uint16_t)cm;
+    TCm[r] = (uint16_t)stg_swz(cm);  // staging offsets, stored swizzled (stg_swz is linear)
   }
   for (int r = tid; r < BN; r += TC_THREADS) {
     uint32_t cn = 0;
     for (int j = 0; j < nb; ++j)
       if ((r >> j) & 1) cn |= 1u << p.pCn[j];
-    TCn[r] = (uint16_t)cn;
+    TCn[r] = (uint16_t)stg_swz(cn);
   }
   for (int h = tid; h < nhC; h += TC_THREADS) {
     uint32_t m = p.maskC;
@@ -645,26 +647,29 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
 
 // Persistent variant of k_tc_tma for short K loops (at most eight K tiles per output tile)
 // over many output tiles.  One CTA per SM walks the tiles of all instances (instance-major,
-// then the tile order of the one-CTA-per-tile launch) with a stride of gridDim.x:
-//   epilogue warps   (BN / 8 of them: four TMEM lane quadrants x 32 columns each) drain
-//                    buffer j & 1 (scale, convert, stage in C's order, store) and release
-//                    it on "tmem empty";
-//   next warp, lane 0   issues the TMA loads of every K tile of its tiles through an
-//                    NST-stage ring ("full" / "empty" mbarriers), running ahead across tiles;
-//   last warp, lane 0   issues the MMAs of the CTA's j-th tile into TMEM accumulator buffer
-//                    j & 1 and commits them to "tmem full" of that buffer,
-// so the epilogue of one tile overlaps the loads and MMAs of the next.  The epilogue threads
-// synchronise on named barrier 1; one of them waits on each mbarrier and shares the
-// outcome, so a timeout ends the loop for all of them together.
-
-template <int BN, int BK>
+// then the tile order of the one-CTA-per-tile launch) with a stride of gridDim.x; its j-th
+// tile uses TMEM accumulator buffer j & 1:
+//   NG epilogue groups (each GW warps: four TMEM lane quadrants x BN/CPW column slices):
+//                    group g drains the CTA's tiles j = g (mod NG) -- scale, convert, stage in
+//                    C's order in its own staging buffer, store -- and releases the buffer
+//                    on "tmem empty".  With two groups (K loops of at most two K tiles) they
+//                    work on consecutive tiles at once, so one group's stores overlap the
+//                    other's staging; longer K loops keep one group and a deeper pipeline;
+//   producer warp, lane 0   issues the TMA loads of every K tile through an NST-stage ring
+//                    ("full" / "empty" mbarriers), running ahead across tiles;
+//   MMA warp, lane 0        issues the MMAs of tile j into buffer j & 1 and commits them to
+//                    "tmem full" of that buffer,
+// so the epilogue of one tile also overlaps the loads and MMAs of the next.  Each group
+// synchronises on its own named barrier; one thread per group waits on each mbarrier and
+// shares the outcome, so a timeout ends the group's loop for all of its threads together.
+template <int BN, int BK, int NG>
 struct TcpShape {
   static constexpr int ROWB = BK * 2;
   static constexpr int A_BYTES = TC_BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STG = TC_BM * BN * 2 * 2;              // staged C tile (2 planes, 16-bit)
-  static constexpr int NST_FIT = (200 * 1024 - STG) / STAGE;
+  static constexpr int STG = TC_BM * BN * 2 * 2;              // one staged C tile (2 planes, 16-bit)
+  static constexpr int NST_FIT = (204 * 1024 - NG * STG) / STAGE;
   static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
   static constexpr int PIPE = NST * STAGE;
   static constexpr int SBO = 8 * ROWB;
@@ -672,32 +677,34 @@ struct TcpShape {
   static constexpr int N_BITS = BN == 128 ? 7 : 6;
   static constexpr int C_BITS = 7 + N_BITS;
   static constexpr int TMEM_COLS = 4 * BN;                    // two buffers of (Dr, Di)
-  static constexpr int EPI_WARPS = BN / 8;                    // 4 lane quadrants x BN/32
-  static constexpr int EPI_THREADS = EPI_WARPS * 32;
-  static constexpr int THREADS = EPI_THREADS + 64;            // + producer warp + MMA warp
+  static constexpr int CPW = NG == 2 ? 64 : 32;               // TMEM columns per epilogue warp
+  static constexpr int GW = 4 * BN / CPW;                     // warps per epilogue group
+  static constexpr int GT = GW * 32;                          // threads per epilogue group
+  static constexpr int THREADS = NG * GT + 64;                // + producer warp + MMA warp
+  static_assert(NG == 1 || NG == 2, "one or two epilogue groups");
   static_assert(BN == 64 || BN == 128, "two accumulator buffers need BN <= 128");
-  static_assert(NST >= 3, "pipeline");
+  static_assert(NST >= 2, "pipeline");
 };
 
 template <int N>
-__device__ __forceinline__ void epi_bar() {
+__device__ __forceinline__ void group_bar(int id) {
   __syncwarp();
-  asm volatile("barrier.sync 1, %0;\n" ::"n"(N) : "memory");
+  asm volatile("barrier.sync %0, %1;\n" ::"r"(id), "n"(N) : "memory");
 }
 
-template <typename T, int BN, int BK>
-__global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist(const __grid_constant__ TcParams p) {
-  using S = TcpShape<BN, BK>;
+template <typename T, int BN, int BK, int NG>
+__global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_persist(const __grid_constant__ TcParams p) {
+  using S = TcpShape<BN, BK, NG>;
   constexpr int KT = BK == 32 ? 5 : 4;
   constexpr int NST = S::NST;
   constexpr int CT = TC_BM * BN;  // entries of the C tile
+  constexpr int NT = S::THREADS, GW = S::GW, GT = S::GT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  T* stg = reinterpret_cast<T*>(smem + S::PIPE);                           // [2][CT]
-  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::PIPE + S::STG);    // [2^(C_BITS - runC)]
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::PIPE + NG * S::STG);  // [2^(C_BITS - runC)]
   const int nhC = 1 << (S::C_BITS - p.runC);
-  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);                  // [128]
-  uint16_t* TCn = TCm + TC_BM;                                              // [BN]
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);                     // [128]
+  uint16_t* TCn = TCm + TC_BM;                                                 // [BN]
   uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
   uint64_t* full = bars;
   uint64_t* empty = bars + NST;
@@ -705,24 +712,23 @@ __global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);                    // [EPI_WARPS]
-  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + S::EPI_WARPS);
-  constexpr int NT = S::THREADS, NE = S::EPI_THREADS;
-  const int prod_warp = S::EPI_WARPS, mma_warp = S::EPI_WARPS + 1;
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);                       // [NG][GW]
+  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + NG * GW);  // [NG]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int prod_warp = NG * GW, mma_warp = NG * GW + 1;
   constexpr int nb = S::N_BITS;
   for (int r = tid; r < TC_BM; r += NT) {
     uint32_t cm = 0;
     for (int j = 0; j < 7; ++j)
       if ((r >> j) & 1) cm |= 1u << p.pCm[j];
-    TCm[r] = (uint16_t)cm;
+    TCm[r] = (uint16_t)stg_swz(cm);  // staging offsets, stored swizzled (stg_swz is linear)
   }
   for (int r = tid; r < BN; r += NT) {
     uint32_t cn = 0;
     for (int j = 0; j < nb; ++j)
       if ((r >> j) & 1) cn |= 1u << p.pCn[j];
-    TCn[r] = (uint16_t)cn;
+    TCn[r] = (uint16_t)stg_swz(cn);
   }
   for (int h = tid; h < nhC; h += NT) {
     uint32_t m = p.maskC;
@@ -848,17 +854,21 @@ __global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist
       if (!mbar_wait_bounded(smem_u32(done), 0u, p.status)) ok = false;
     }
   } else {
-    // epilogue: thread = one TMEM lane (row) of its warp's quadrant, 32 columns
+    // epilogue group gq: thread = one TMEM lane (row) of its warp's quadrant, CPW columns
+    constexpr int CPW = S::CPW;
+    const int gq = warp / GW, lw = warp % GW, gtid = tid - gq * GT;
+    T* stg = reinterpret_cast<T*>(smem + S::PIPE + gq * S::STG);  // [2][CT]
+    float* gred = red + gq * GW;
     const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
     const int row = (warp & 3) * 32 + lane;
-    const int col0 = (warp >> 2) * 32;
+    const int col0 = (lw >> 2) * CPW;
     const uint32_t lowmask = (1u << p.runC) - 1u;
-    int j = 0;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
-      const int b = j & 1;
-      if (tid == 0) *flag = mbar_wait_bounded(smem_u32(&tfull[b]), (uint32_t)((j >> 1) & 1), p.status) ? 1 : 0;
-      epi_bar<NE>();
-      if (*flag == 0) {
+    for (int64_t t = blockIdx.x + int64_t(gq) * gridDim.x, j = gq; t < n_tiles; t += NG * int64_t(gridDim.x), j += NG) {
+      const int b = (int)(j & 1);
+      const uint32_t acc = tmem + uint32_t(b * 2 * BN);
+      if (gtid == 0) flag[gq] = mbar_wait_bounded(smem_u32(&tfull[b]), (uint32_t)((j >> 1) & 1), p.status) ? 1 : 0;
+      group_bar<GT>(1 + gq);
+      if (flag[gq] == 0) {
         ok = false;
         break;
       }
@@ -884,38 +894,38 @@ __global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist
         }
       }
       const float scale = ldexpf(1.f, -sh);
-      const uint32_t acc = tmem + uint32_t(b * 2 * BN);
       float mx = 0.f;
-      {
+      const uint32_t rm = TCm[row];
+#pragma unroll 1
+      for (int cc = 0; cc < CPW; cc += 32) {
         float vr[32], vi[32];
-        tmem_ld32(acc + lane_addr + col0, vr);
-        tmem_ld32(acc + lane_addr + BN + col0, vi);
-        const uint32_t rm = TCm[row];
+        tmem_ld32(acc + lane_addr + col0 + cc, vr);
+        tmem_ld32(acc + lane_addr + BN + col0 + cc, vi);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const uint32_t idx = rm + TCn[col0 + q];
-          const T re = Conv<T>::from_f(vr[q] * scale), im = Conv<T>::from_f(vi[q] * scale);
-          stg[stg_swz(idx)] = re;
-          stg[CT + stg_swz(idx)] = im;
-          mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im))));
+          const uint32_t idx = rm ^ TCn[col0 + cc + q];  // swizzled staging index
+          stg[idx] = Conv<T>::from_f(vr[q] * scale);
+          stg[CT + idx] = Conv<T>::from_f(vi[q] * scale);
+          mx = fmaxf(mx, fmaxf(fabsf(vr[q]), fabsf(vi[q])));
         }
       }
+      mx *= scale * (1.f + 0x1p-8f);  // bound on the stored maximum (see tc_epilogue)
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      epi_bar<NE>();
-      if (tid == 0) mbar_arrive(smem_u32(&tempty[b]));
+      group_bar<GT>(1 + gq);
+      if (gtid == 0) mbar_arrive(smem_u32(&tempty[b]));
       // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
       T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
-      for (int x = tid * 8; x < CT; x += NE * 8) {
+      for (int x = gtid * 8; x < CT; x += GT * 8) {
         const uint32_t off = hiC[x >> p.runC] + (uint32_t(x) & lowmask);
         *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + stg_swz(x));
         *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + stg_swz(x));
       }
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) red[warp] = mx;
-      epi_bar<NE>();
-      if (tid == 0) {
+      if (lane == 0) gred[lw] = mx;
+      group_bar<GT>(1 + gq);
+      if (gtid == 0) {
         float m = 0.f;
-        for (int w = 0; w < S::EPI_WARPS; ++w) m = fmaxf(m, red[w]);
+        for (int w = 0; w < GW; ++w) m = fmaxf(m, gred[w]);
         atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
         if (r == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
       }
@@ -928,11 +938,11 @@ __global__ void __launch_bounds__(TcpShape<BN, BK>::THREADS, 1) k_tc_tma_persist
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
 }
 
-template <int BN, int BK>
+template <int BN, int BK, int NG>
 size_t tma_persist_smem_bytes_t(int runC) {
-  using S = TcpShape<BN, BK>;
-  return 1024 + S::PIPE + S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
-         (2 * S::NST + 5) * 8 + 16 + S::EPI_WARPS * 4 + 16 + 64;
+  using S = TcpShape<BN, BK, NG>;
+  return 1024 + S::PIPE + NG * S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
+         (2 * S::NST + 5) * 8 + 16 + NG * S::GW * 4 + 16 + 64;
 }
 
 static int sm_count_cached() {
@@ -945,15 +955,22 @@ static int sm_count_cached() {
   return n;
 }
 
-template <typename T, int BN, int BK>
-cudaError_t launch_tma_persist_t(const TcParams& p, cudaStream_t s) {
-  const size_t smem = tma_persist_smem_bytes_t<BN, BK>(p.runC);
-  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_persist<T, BN, BK>), smem);
+template <typename T, int BN, int BK, int NG>
+cudaError_t launch_tma_persist_ng(const TcParams& p, cudaStream_t s) {
+  const size_t smem = tma_persist_smem_bytes_t<BN, BK, NG>(p.runC);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_persist<T, BN, BK, NG>), smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = int64_t(p.n_inst) << (p.n_om + p.n_on);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count_cached());
-  k_tc_tma_persist<T, BN, BK><<<grid, TcpShape<BN, BK>::THREADS, smem, s>>>(p);
+  k_tc_tma_persist<T, BN, BK, NG><<<grid, TcpShape<BN, BK, NG>::THREADS, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// two epilogue groups (and a shallower pipeline) for K loops of at most two K tiles
+template <typename T, int BN, int BK>
+cudaError_t launch_tma_persist_t(const TcParams& p, cudaStream_t s) {
+  if (p.n_ok <= 1) return launch_tma_persist_ng<T, BN, BK, 2>(p, s);
+  return launch_tma_persist_ng<T, BN, BK, 1>(p, s);
 }
 
 template <int BN, int BK, int NST>

@@ -47,6 +47,7 @@ class tnc_plan_opts(C.Structure):
         ("slices_max", C.c_int32),
         ("temperature", C.c_double),
         ("mode", C.c_int32),
+        ("objective", C.c_int32),
     ]
 
 
@@ -165,9 +166,10 @@ def tnc_network_build(circuit, open_mask: Optional[np.ndarray]):
     return h
 
 
-def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5, mode=0):
+def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5, mode=0,
+                    objective=0):
     lib = load_library()
-    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode)
+    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode, objective)
     h = C.c_void_p()
     _check(lib.tnc_plan_greedy(network, C.byref(o), C.byref(h)))
     return h
@@ -183,9 +185,12 @@ class Plan:
 
     @classmethod
     def greedy(cls, circuit, open_qubits: Sequence[int] = (), seed: int = 1, trials: int = 16, log2_cap: int = 26,
-               slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy") -> "Plan":
+               slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy",
+               objective: str = "flops") -> "Plan":
         """Plan for an `inputs.Circuit` (gate list) with the given open output qubits.
-        mode: "greedy" (balanced pairwise order) or "stem" (one tensor absorbs leaves)."""
+        mode: "greedy" (balanced pairwise order) or "stem" (one tensor absorbs leaves).
+        objective: which trial is kept -- "flops" (fewest multiply-adds) or "time" (least
+        modeled GB300 time)."""
         lib = load_library()
         arity, qubits, mats = circuit.gate_array()
         ch = tnc_circuit_from_gates(circuit.n_qubits, arity, qubits, mats)
@@ -195,7 +200,7 @@ class Plan:
             nh = tnc_network_build(ch, mask)
             try:
                 ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature,
-                                     {"greedy": 0, "stem": 1}[mode])
+                                     {"greedy": 0, "stem": 1}[mode], {"flops": 0, "time": 1}[objective])
             finally:
                 lib.tnc_network_destroy(nh)
         finally:
@@ -301,10 +306,12 @@ class Context:
                                   C.c_void_p(ptr), C.c_void_p(stream)))
         return out
 
-    def adjoint(self, plan: Plan, bitstrings: Optional[np.ndarray], weights: np.ndarray, arities, stream: int = 0):
+    def adjoint(self, plan: Plan, bitstrings: Optional[np.ndarray], weights: np.ndarray, arities, stream: int = 0,
+                memory_mib: int = 0):
         """Gate environments dL/dU_g of L = sum_{b,i} weights[b, i] * amp[b, i] (holomorphic
         derivative), over all slices.  `arities` lists each gate's arity (1 or 2).  Returns
-        (list of d x d complex128 arrays, amplitudes (batch, 2^n_open))."""
+        (list of d x d complex128 arrays, amplitudes (batch, 2^n_open)).  `memory_mib` > 0 caps
+        the forward intermediates kept per instance; the largest are recomputed instead."""
         lib = load_library()
         info = plan.info()
         n_out = 1 << info["n_open"]
@@ -320,6 +327,7 @@ class Context:
         env = np.zeros((n_gates, 32))
         amps = np.zeros((batch, n_out), dtype=np.complex128)
         opts = tnc_exec_opts(TNC_C64, 0, 0, 1, 0)
+        opts.reserved[0] = int(memory_mib)
         _check(lib.tnc_adjoint(self.h, plan.h, C.byref(opts), bp, batch, C.c_void_p(w.ctypes.data),
                                C.c_void_p(env.ctypes.data), C.c_void_p(amps.ctypes.data), C.c_void_p(stream)))
         out = []

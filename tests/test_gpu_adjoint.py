@@ -111,3 +111,23 @@ def test_autograd_fsim_angles_against_finite_differences(ctx):
         for which, grad in ((0, theta.grad), (1, phi.grad)):
             fd = (loss_at(j, which, h) - loss_at(j, which, -h)) / (2 * h)
             assert abs(float(grad[j]) - fd) <= 1e-4 * max(1.0, abs(fd)), (j, which, float(grad[j]), fd)
+
+
+@pytest.mark.parametrize("sliced", [False, True])
+def test_adjoint_recompute_matches_store_all(ctx, sliced):
+    # a budget below the intermediates' size drops the largest and recomputes them from
+    # their children in the backward pass: same kernels on the same inputs, bit-identical
+    c = grid_circuit(4, 5, 12, seed=1, fsim_mode="uniform", param_seed=5)
+    if sliced:
+        fixed, open_q = subcube_spec(20, 4, seed=3)
+        p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=12, slices_min=2)
+        bs, n_out = fixed[None, :], 16
+    else:
+        p = T.Plan.greedy(c, open_qubits=[], seed=3, trials=8, log2_cap=20)
+        bs, n_out = random_bitstrings(20, 16, seed=6), 1
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=(len(bs), n_out)) + 1j * rng.normal(size=(len(bs), n_out))
+    env0, amps0 = ctx.adjoint(p, bs, w, _arities(c))
+    env1, amps1 = ctx.adjoint(p, bs, w, _arities(c), memory_mib=1)
+    assert np.array_equal(amps0, amps1)
+    assert all(np.array_equal(a, b) for a, b in zip(env0, env1))
