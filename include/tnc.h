@@ -119,11 +119,14 @@ typedef struct {
   int32_t n_steps;             /* pairwise contractions per slice                       */
   int32_t n_leaves;
   int32_t n_open;              /* open output qubits (result has 2^n_open entries)      */
-  int32_t n_kernels;           /* kernel launches per wave of instances                */
+  int32_t n_kernels;           /* kernel launches per wave of instances (steps, leaf    */
+                               /* gather, leaf scales, root sum; split steps add one)   */
   int32_t n_gemm, n_gepdot, n_absorb, n_fused; /* steps per class (a fused step counts */
                                                /* every contraction it contains)        */
   double narrow_max;           /* largest "narrow" rate 2 N_common / (N_A + N_B)       */
                                /* (Sec. VII-B) over the steps                          */
+  double model_seconds_per_slice; /* modeled GB300 time of one slice (the objective = 1 */
+                               /* cost; complex-half storage)                          */
 } tnc_plan_info;
 tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
 

@@ -132,12 +132,13 @@ tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info) {
     info->n_steps = (int32_t)P.tree.size();
     info->n_leaves = (int32_t)P.net.leaves.size();
     info->n_open = (int32_t)P.net.open_qubits.size();
-    info->n_kernels = (int32_t)P.steps.size() + 2;
+    info->n_kernels = (int32_t)P.steps.size() + 3;
     info->n_gemm = P.n_gemm;
     info->n_gepdot = P.n_gepdot;
     info->n_absorb = P.n_absorb;
     info->n_fused = P.n_fused;
     info->narrow_max = P.narrow_max;
+    info->model_seconds_per_slice = P.model_seconds;
   });
 }
 

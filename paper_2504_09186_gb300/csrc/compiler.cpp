@@ -111,19 +111,32 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
       }
     }
   };
+  // common labels by position, alternating between A and B, so that the K tile extends the
+  // contiguous low runs of both operands (with K in A's order only, B's loads could be
+  // short runs)
+  std::vector<int> Kab;
+  {
+    std::vector<int> KB;
+    for (int x : lb)
+      if (contains(K, x)) KB.push_back(x);
+    for (size_t i = 0; i < K.size(); ++i) {
+      add_unique(Kab, K[i]);
+      add_unique(Kab, KB[i]);
+    }
+  }
   if (gepdot) {
     grow(t.Mt, M, m);
     grow(t.Nt, N, n);
-    grow(t.Kt, K, k);
+    grow(t.Kt, Kab, k);
   } else if (k + n <= 6) {
     // absorption of a small tensor: all of B on chip, a wide slice of A
-    grow(t.Kt, K, k);
+    grow(t.Kt, Kab, k);
     grow(t.Nt, N, n);
     grow(t.Mt, M, std::min(m, 9));
   } else {
     grow(t.Mt, M, std::min(m, 6));
     grow(t.Nt, N, std::min(n, 6));
-    grow(t.Kt, K, std::min(k, 5));
+    grow(t.Kt, Kab, std::min(k, 5));
   }
   // canonical orders: M and K by A position, N by B position
   auto order_by = [](std::vector<int>& v, const std::vector<int>& layout) {
@@ -142,6 +155,13 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   const int mt = (int)t.Mt.size(), nt = (int)t.Nt.size(), kt = (int)t.Kt.size();
   const int out_bits = mt + nt;
   int lrm = 0, lrn = 0;
+  if (gepdot) {
+    // few outputs, long K: every thread takes the largest micro-tile (up to 4 x 4) over its
+    // own k values (8 shared-memory loads per 16 complex multiply-adds), the K groups are
+    // summed once at the end
+    lrm = std::min(2, mt);
+    lrn = std::min(2, nt);
+  }
   while (out_bits - lrm - lrn > 8) {
     if (lrm <= lrn && lrm < 2 && lrm < mt) ++lrm;
     else if (lrn < 2 && lrn < nt) ++lrn;
@@ -332,6 +352,7 @@ void compile_plan(Plan& plan, bool fuse) {
   // intermediates
   plan.steps.clear();
   plan.n_gemm = plan.n_gepdot = plan.n_absorb = plan.n_fused = 0;
+  plan.model_seconds = 0;
   plan.narrow_max = 0;
   plan.max_log2 = 0;
   for (auto& ti : plan.tensors) plan.max_log2 = std::max(plan.max_log2, (int)ti.labels.size());
@@ -394,6 +415,7 @@ void compile_plan(Plan& plan, bool fuse) {
     if (nm + nn <= 8 && nk >= 12) plan.n_gepdot++;
     else if (nk + nn <= 6) plan.n_absorb++;
     else plan.n_gemm++;
+    plan.model_seconds += step_model_seconds((int)la.size(), (int)lb.size(), (int)lc.size(), nk);
   }
   // fused chains (Sec. IV): follow the big operand through consecutive absorptions of
   // small tensors (rank <= 6) while the on-chip label set stays within 2^12 entries.  The

@@ -83,6 +83,19 @@ void gate_envs_from_leaf_envs(const Network& net, const std::vector<SmallTensor>
                               std::vector<std::vector<cd>>& out);
 
 // ------------------------------------------------------------------ plan
+// Modeled GB300 time (seconds) of one pairwise contraction of operands with a and b labels,
+// k of them common, and a result with c labels: the larger of its flop time and its HBM time
+// (complex-half storage, 4 bytes per entry).  Steps large enough for tensor-core tiles
+// (M >= 2^7, N >= 2^6 or the reverse, K >= 2^4) run at the tensor-core rate, the others at the
+// FP32-lane rate.
+inline double step_model_seconds(int a, int b, int c, int k) {
+  const int m = a - k, n = b - k;
+  const double flops = 8.0 * std::ldexp(1.0, a + b - k);
+  const double bytes = 4.0 * (std::ldexp(1.0, a) + std::ldexp(1.0, b) + std::ldexp(1.0, c));
+  const bool tc = std::max(m, n) >= 7 && std::min(m, n) >= 6 && k >= 4;
+  return std::max(flops / (tc ? 1.8e15 : 4.0e13), bytes / 6.5e12);
+}
+
 struct PlanOpts {
   uint64_t seed = 1;
   int trials = 16;
@@ -150,6 +163,7 @@ struct Plan {
   std::vector<Step> steps;                 // compiled program (may fuse tree steps)
   int root = -1;
   double log2_flops_slice = 0, log2_flops_total = 0, overhead = 1;
+  double model_seconds = 0;  // modeled GB300 time of one slice (step_model_seconds summed)
   int max_log2 = 0;
   int64_t arena_elems = 0;                 // per instance, in scalars, unfused program
   int64_t arena_elems_fused = 0;           // per instance, in scalars, fused program

@@ -181,10 +181,7 @@ int tree_max(const Tree& t, const std::vector<char>& sliced) {
   return m;
 }
 
-// Modeled GB300 time of one slice (seconds): per step, the larger of its flop time and its
-// HBM time (complex-half storage, 4 bytes per entry); steps large enough for tensor-core
-// tiles (M >= 2^7, N >= 2^6 or the reverse, K >= 2^4) run at the tensor-core rate, the others
-// at the FP32-lane rate.
+// Modeled GB300 time of one slice: step_model_seconds summed over the tree's steps.
 double model_time(const Tree& t, const std::vector<char>& sliced) {
   double tot = 0;
   for (auto& p : t.pairs) {
@@ -192,12 +189,8 @@ double model_time(const Tree& t, const std::vector<char>& sliced) {
     const LabelSet& B = t.sets[p.second];
     const int a = (int)count_not_in(A, sliced), b = (int)count_not_in(B, sliced);
     const int u = (int)count_not_in(set_union(A, B), sliced);
-    const int k = a + b - u, m = a - k, n = b - k;
     const int c = (int)count_not_in(sym_diff(A, B), sliced);
-    const double flops = 8.0 * std::ldexp(1.0, u);
-    const double bytes = 4.0 * (std::ldexp(1.0, a) + std::ldexp(1.0, b) + std::ldexp(1.0, c));
-    const bool tc = std::max(m, n) >= 7 && std::min(m, n) >= 6 && k >= 4;
-    tot += std::max(flops / (tc ? 1.8e15 : 4.0e13), bytes / 6.5e12);
+    tot += step_model_seconds(a, b, c, a + b - u);
   }
   return tot;
 }

@@ -67,6 +67,7 @@ class tnc_plan_info(C.Structure):
         ("n_absorb", C.c_int32),
         ("n_fused", C.c_int32),
         ("narrow_max", C.c_double),
+        ("model_seconds_per_slice", C.c_double),
     ]
 
 

@@ -142,3 +142,15 @@ def test_stem_plan_is_a_stem_and_fuses():
             chains.setdefault(st["chain"], []).append(i)
     assert chains and all(len(v) >= 2 for v in chains.values())
     assert p.info()["n_fused"] == sum(len(v) for v in chains.values())
+
+
+def test_plan_objectives_pick_their_own_minimum():
+    # same seed and trials: the same candidate trees; each objective keeps its own minimum
+    c = grid_circuit(4, 5, 12, seed=1)
+    _, open_q = subcube_spec(20, 6, seed=2)
+    kw = dict(open_qubits=open_q, seed=4, trials=24, log2_cap=14, slices_min=2)
+    pf = T.Plan.greedy(c, objective="flops", **kw).info()
+    pt = T.Plan.greedy(c, objective="time", **kw).info()
+    assert pt["model_seconds_per_slice"] * 2 ** pt["n_sliced"] <= pf["model_seconds_per_slice"] * 2 ** pf["n_sliced"] * (1 + 1e-12)
+    assert pf["log2_total_flops"] <= pt["log2_total_flops"] + 1e-12
+    assert pf["model_seconds_per_slice"] > 0
