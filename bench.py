@@ -438,7 +438,8 @@ SW_POINTS = [(14, 12, 10), (12, 12, 12), (16, 8, 16), (16, 12, 12), (12, 16, 12)
 def sweep_labels(m, k, n, layout, seed):
     """Index labels of one sweep point.  'random': seeded random axis orders of A, B and C.
     'arranged': the order the step compiler gives tensor-core steps (K tile labels, then
-    the M / N tile labels, lowest; C led by its tile labels, as for a root), the rest random."""
+    the M / N tile labels, lowest; C led by three tile columns, then the tile rows, then the
+    other tile columns), the rest random."""
     rng = np.random.default_rng(seed)
     ms, ks, ns = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
     perm = lambda v: [int(x) for x in rng.permutation(v)] if v else []
@@ -446,7 +447,7 @@ def sweep_labels(m, k, n, layout, seed):
         kt = 5 if k >= 5 else 4
         nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
         return (ks[:kt] + ms[:7] + perm(ms[7:] + ks[kt:]), ks[:kt] + ns[:nt] + perm(ns[nt:] + ks[kt:]),
-                ms[:7] + ns[:nt] + perm(ms[7:] + ns[nt:]))
+                ns[:3] + ms[:7] + ns[3:nt] + perm(ms[7:] + ns[nt:]))
     return perm(ms + ks), perm(ks + ns), perm(ms + ns)
 
 

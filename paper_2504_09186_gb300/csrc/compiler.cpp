@@ -303,6 +303,7 @@ void compile_plan(Plan& plan, bool fuse) {
   struct TcDec {
     bool ok = false;
     int bn = 128, bk = 32;
+    int rows = -1;  // operand whose free labels are the tile rows (TMEM lanes)
     TileSpec t;
   };
   std::vector<TcDec> dec(n_tree);
@@ -316,9 +317,23 @@ void compile_plan(Plan& plan, bool fuse) {
     std::set_intersection(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(K));
     std::set_difference(A.begin(), A.end(), B.begin(), B.end(), std::back_inserter(M));
     std::set_difference(B.begin(), B.end(), A.begin(), A.end(), std::back_inserter(N));
+    const std::vector<int>& rq = req[n_leaves + s];
+    // roles: the result's leading labels (its consumer's requirement) should be tile
+    // columns, so that each thread's TMEM row holds runs of consecutive result entries and
+    // the epilogue can store them directly; swap rows and columns when most of the first
+    // three are free labels of the larger operand
+    {
+      int in_m = 0, in_n = 0;
+      for (size_t j = 0; j < rq.size() && j < 3; ++j) in_m += contains(M, rq[j]), in_n += contains(N, rq[j]);
+      if (in_m > in_n && N.size() >= 7 && M.size() >= 6) {
+        std::swap(a, b);
+        std::swap(M, N);
+      }
+    }
     if (a < n_leaves || b < n_leaves || M.size() < 7 || N.size() < 6 || K.size() < 4) continue;
     TcDec d;
     d.ok = true;
+    d.rows = a;
     d.bk = K.size() >= 5 ? 32 : 16;
     // 256-wide tiles take a whole SM (all TMEM) and leave the epilogue exposed; with at
     // most 8 K tiles the epilogue weighs, and 128-wide tiles run on the persistent kernel,
@@ -327,10 +342,11 @@ void compile_plan(Plan& plan, bool fuse) {
     d.bn = (N.size() >= 8 && K.size() > kt0 + 3) ? 256 : (N.size() >= 7 ? 128 : 64);
     const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : 6);
     d.t.Kt.assign(K.begin(), K.begin() + kt);
-    const std::vector<int>& rq = req[n_leaves + s];
-    for (size_t j = 0; j < rq.size() && j < 3; ++j) {
-      if (contains(M, rq[j])) d.t.Mt.push_back(rq[j]);
-      else if (contains(N, rq[j])) d.t.Nt.push_back(rq[j]);
+    // the result's leading labels first, in their order: the lowest result positions are
+    // then the lowest canonical column / row bits (runs per thread, adjacent rows per warp)
+    for (size_t j = 0; j < rq.size(); ++j) {
+      if (contains(M, rq[j]) && d.t.Mt.size() < 7) d.t.Mt.push_back(rq[j]);
+      else if (contains(N, rq[j]) && d.t.Nt.size() < nt) d.t.Nt.push_back(rq[j]);
     }
     for (int x : M)
       if (d.t.Mt.size() < 7 && !contains(d.t.Mt, x)) d.t.Mt.push_back(x);
@@ -393,17 +409,19 @@ void compile_plan(Plan& plan, bool fuse) {
     st.tc_ok = dec[s].ok;
     if (st.tc_ok) {
       st.tc_tile = dec[s].t;
-      st.tc_swap = false;  // rows come from a (the larger operand)
+      st.tc_swap = dec[s].rows != st.a;  // rows from b when the roles were swapped
       st.tc_bn = dec[s].bn;
       st.tc_bk = dec[s].bk;
       // the layouts honour the requirement: operands lead with Kt + Mt / Kt + Nt
+      const auto& lr = st.tc_swap ? lb : la;
+      const auto& lcol = st.tc_swap ? la : lb;
       const size_t kt = st.tc_tile.Kt.size();
       for (size_t j = 0; j < kt; ++j)
-        if (la[j] != st.tc_tile.Kt[j] || lb[j] != st.tc_tile.Kt[j]) fail(5, "compile: tensor-core K labels not leading");
+        if (lr[j] != st.tc_tile.Kt[j] || lcol[j] != st.tc_tile.Kt[j]) fail(5, "compile: tensor-core K labels not leading");
       for (size_t j = 0; j < st.tc_tile.Mt.size(); ++j)
-        if (la[kt + j] != st.tc_tile.Mt[j]) fail(5, "compile: tensor-core M labels not leading");
+        if (lr[kt + j] != st.tc_tile.Mt[j]) fail(5, "compile: tensor-core M labels not leading");
       for (size_t j = 0; j < st.tc_tile.Nt.size(); ++j)
-        if (lb[kt + j] != st.tc_tile.Nt[j]) fail(5, "compile: tensor-core N labels not leading");
+        if (lcol[kt + j] != st.tc_tile.Nt[j]) fail(5, "compile: tensor-core N labels not leading");
     }
     int nk = 0;
     for (int x : la) nk += contains(lb, x);

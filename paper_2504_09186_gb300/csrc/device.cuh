@@ -93,6 +93,8 @@ struct TcParams {
   int32_t n_slots, slotA, slotB, slotC;
   int32_t* status;           // TNC_E_TIMEOUT on a bounded wait that ran out
   int32_t persistent;        // 1 = persistent TMA kernel (short K loops, no split)
+  int32_t direct;            // 1 = C's three lowest positions are tile columns 0..2: each
+                             //     thread stores runs of 8 columns straight from registers
   int32_t n_inst;            // instances of the launch (persistent kernel: tiles span all)
 };
 

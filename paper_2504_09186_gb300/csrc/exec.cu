@@ -132,6 +132,11 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   q.maskC = maskC;
   q.runC = low_run(maskC);
   if (q.runC < 3) fail(TNC_E_PLAN, "tensor-core output run too short");
+  // direct epilogue: tile columns 0..2 at C positions 0..2 (runs of 8 per thread) and row 0
+  // at position 3, so lanes write whole 32-byte sectors (scattered 16-byte halves of sectors
+  // measured slower than staging)
+  q.direct = (pos_of(lc, t.Nt[0]) == 0 && pos_of(lc, t.Nt[1]) == 1 && pos_of(lc, t.Nt[2]) == 2 &&
+              pos_of(lc, t.Mt[0]) == 3) ? 1 : 0;
   for (int j = 0; j < 7; ++j) {
     q.pAm[j] = (int8_t)pos_of(la, t.Mt[j]);
     q.pCm[j] = (int8_t)rank_in_mask(maskC, pos_of(lc, t.Mt[j]));
@@ -305,7 +310,7 @@ static PermParams make_permute(const std::vector<int>& lin, const std::vector<in
 
 // TTGT layouts for a single contraction whose operands the tensor-core kernels cannot load
 // in place: A' = [Kt | Mt | other M | other K], B' = [Kt | Nt | other N | other K] (the
-// layouts the compiler gives tensor-core steps) and C' = [Mt | Nt | ...].  False when the
+// layouts the compiler gives tensor-core steps) and C' = [3 of Nt | Mt | ...].  False when the
 // step is too small for tensor-core tiles.
 static bool ttgt_layouts(const std::vector<int>& la, const std::vector<int>& lb, std::vector<int>& la2,
                          std::vector<int>& lb2, std::vector<int>& lc2) {
@@ -323,10 +328,13 @@ static bool ttgt_layouts(const std::vector<int>& la, const std::vector<int>& lb,
   lb2.assign(K.begin(), K.begin() + kt);
   lb2.insert(lb2.end(), N.begin(), N.end());
   lb2.insert(lb2.end(), K.begin() + kt, K.end());
-  lc2.assign(M.begin(), M.begin() + 7);
-  lc2.insert(lc2.end(), N.begin(), N.begin() + nt);
+  // C' leads with three tile columns, then the tile rows: each thread stores runs of 8
+  // columns straight from registers (the direct epilogue) and the 32 rows of a warp are
+  // adjacent, so one warp store covers a contiguous 512-byte block
+  lc2.assign(N.begin(), N.begin() + 3);
+  lc2.insert(lc2.end(), M.begin(), M.begin() + 7);
+  lc2.insert(lc2.end(), N.begin() + 3, N.end());
   lc2.insert(lc2.end(), M.begin() + 7, M.end());
-  lc2.insert(lc2.end(), N.begin() + nt, N.end());
   return true;
 }
 

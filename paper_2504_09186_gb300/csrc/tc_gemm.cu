@@ -208,6 +208,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Eight 16-bit values, one 16-byte store.
+template <typename T>
+struct alignas(16) Vec8 {
+  T v[8];
+};
+
 // Staging-buffer swizzle: 16-byte chunks of each 128-byte group are permuted by higher index
 // bits, so the threads of a warp (one tile row each) do not all hit one bank when rows are
 // far apart in C's order; reads of whole 16-byte chunks stay contiguous.
@@ -265,7 +271,33 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   constexpr int CT = TC_BM * BN;  // entries of the C tile
   T* stg = reinterpret_cast<T*>(smem);  // [2][CT] re plane then im plane
   float mx = 0.f;
-  if (ok) {
+  if (ok && p.direct) {
+    // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores from registers
+    T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+    const uint32_t lowmask = (1u << p.runC) - 1u;
+    const uint32_t rm = TCm[row];
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 2; cc += 32) {
+      float vr[32], vi[32];
+      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
+      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint32_t t = stg_swz(rm ^ TCn[col0 + cc + 8 * g]);  // C-tile index, low 3 bits 0
+        const uint32_t off = hiC[t >> p.runC] + (t & lowmask);
+        Vec8<T> r8, i8;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          r8.v[v] = Conv<T>::from_f(vr[8 * g + v] * scale);
+          i8.v[v] = Conv<T>::from_f(vi[8 * g + v] * scale);
+          mx = fmaxf(mx, fmaxf(fabsf(vr[8 * g + v]), fabsf(vi[8 * g + v])));
+        }
+        *reinterpret_cast<Vec8<T>*>(Cre + off) = r8;
+        *reinterpret_cast<Vec8<T>*>(Cre + p.planeC + off) = i8;
+      }
+    }
+    mx *= scale * (1.f + 0x1p-8f);
+  } else if (ok) {
 #pragma unroll 1
     for (int cc = 0; cc < BN / 2; cc += 32) {
       float vr[32], vi[32];
@@ -296,7 +328,7 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
   T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
   const uint32_t lowmask = (1u << p.runC) - 1u;
-  for (int t = tid * 8; t < CT; t += TC_THREADS * 8) {
+  for (int t = tid * 8; t < (p.direct ? 0 : CT); t += TC_THREADS * 8) {
     const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
 #if TNC_TC_SELFCHECK
     {
@@ -896,6 +928,44 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       const float scale = ldexpf(1.f, -sh);
       float mx = 0.f;
       const uint32_t rm = TCm[row];
+      T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+      if (p.direct) {
+        // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores straight
+        // from registers, no staging; one barrier per tile (TMEM release and block max)
+#pragma unroll 1
+        for (int cc = 0; cc < CPW; cc += 32) {
+          float vr[32], vi[32];
+          tmem_ld32(acc + lane_addr + col0 + cc, vr);
+          tmem_ld32(acc + lane_addr + BN + col0 + cc, vi);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const uint32_t x = stg_swz(rm ^ TCn[col0 + cc + 8 * g]);  // C-tile index, low 3 bits 0
+            const uint32_t off = hiC[x >> p.runC] + (x & lowmask);
+            Vec8<T> r8, i8;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              r8.v[v] = Conv<T>::from_f(vr[8 * g + v] * scale);
+              i8.v[v] = Conv<T>::from_f(vi[8 * g + v] * scale);
+              mx = fmaxf(mx, fmaxf(fabsf(vr[8 * g + v]), fabsf(vi[8 * g + v])));
+            }
+            *reinterpret_cast<Vec8<T>*>(Cre + off) = r8;
+            *reinterpret_cast<Vec8<T>*>(Cre + p.planeC + off) = i8;
+          }
+        }
+        mx *= scale * (1.f + 0x1p-8f);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) gred[lw] = mx;
+        group_bar<GT>(1 + gq);
+        if (gtid == 0) {
+          mbar_arrive(smem_u32(&tempty[b]));
+          float m = 0.f;
+          for (int w = 0; w < GW; ++w) m = fmaxf(m, gred[w]);
+          atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
+          if (r == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+        }
+        continue;
+      }
 #pragma unroll 1
       for (int cc = 0; cc < CPW; cc += 32) {
         float vr[32], vi[32];
@@ -914,7 +984,6 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       group_bar<GT>(1 + gq);
       if (gtid == 0) mbar_arrive(smem_u32(&tempty[b]));
       // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
-      T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
       for (int x = gtid * 8; x < CT; x += GT * 8) {
         const uint32_t off = hiC[x >> p.runC] + (uint32_t(x) & lowmask);
         *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + stg_swz(x));

@@ -36,9 +36,10 @@ def kmajor_case(m, k, n, seed):
     return a, la, b, lb, lc
 
 
-def tma_case(m, k, n, seed):
+def tma_case(m, k, n, seed, direct=False):
     """Layouts the TMA kernel loads directly: A = [Kt | 7 row labels | rest], B = [Kt | 6-7
-    column labels | rest], C's three lowest labels among the tile labels."""
+    column labels | rest], C's three lowest labels among the tile labels (direct: the first
+    three tile columns in order, so the epilogue stores from registers without staging)."""
     kt = 5 if k >= 5 else 4
     nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
     ks = list(range(100, 100 + k))
@@ -46,7 +47,10 @@ def tma_case(m, k, n, seed):
     ns = list(range(200, 200 + n))
     la = ks[:kt] + ms[:7] + random_labels_perm(ms[7:] + ks[kt:], seed)
     lb = ks[:kt] + ns[:nt] + random_labels_perm(ns[nt:] + ks[kt:], seed + 1)
-    lc = [ns[0], ms[0], ns[1]] + random_labels_perm(ms[1:] + ns[2:], seed + 2)
+    if direct:
+        lc = ns[:3] + ms[:5] + random_labels_perm(ms[5:] + ns[3:], seed + 2)
+    else:
+        lc = [ns[0], ms[0], ns[1]] + random_labels_perm(ms[1:] + ns[2:], seed + 2)
     sigma = 1.0 / np.sqrt(2.0 ** k)
     a = random_complex(1 << len(la), sigma, seed + 3)
     b = random_complex(1 << len(lb), sigma, seed + 4)
@@ -94,7 +98,7 @@ TMA_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (8, 15, 6
 @pytest.mark.parametrize("precision", ["chalf", "cbf16"])
 @pytest.mark.parametrize("shape", TMA_SHAPES)
 def test_tma_contract(ctx, precision, shape):
-    a, la, b, lb, lc = tma_case(*shape, seed=13 * sum(shape) + shape[2])
+    a, la, b, lb, lc = tma_case(*shape, seed=13 * sum(shape) + shape[2], direct=shape[0] % 2 == 1)
     got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
     if len(got) <= 1 << 16:
         err = metrics.rel_err_norm(got, pairwise.contract(aq, la, bq, lb, lc))
@@ -140,10 +144,13 @@ def test_tc_steps_inside_a_plan(ctx, precision):
 PERSIST_SHAPES = [(12, 4, 12), (14, 5, 10), (12, 6, 12), (17, 7, 7), (16, 8, 8), (17, 4, 6)]
 
 
+@pytest.mark.parametrize("direct", [False, True])
 @pytest.mark.parametrize("precision", ["chalf", "cbf16"])
 @pytest.mark.parametrize("shape", PERSIST_SHAPES)
-def test_tma_persistent_kernel(ctx, precision, shape, monkeypatch):
-    a, la, b, lb, lc = tma_case(*shape, seed=7 * sum(shape) + shape[0])
+def test_tma_persistent_kernel(ctx, precision, shape, direct, monkeypatch):
+    # direct: C's lowest labels are the first tile columns, so both kernels store from
+    # registers; otherwise through the staging buffer
+    a, la, b, lb, lc = tma_case(*shape, seed=7 * sum(shape) + shape[0], direct=direct)
     got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
     assert int(ctx.profile_read(cap=1)["kind"][0]) == 5  # the persistent kernel ran
     # sampled outputs against the oracle, first and last entries included
