@@ -273,6 +273,7 @@ void compile_plan(Plan& plan, bool fuse) {
         plan.leaf_fix[i].push_back({(int)p, 1, ed.qubit});
       } else if (sliced[e]) {
         plan.leaf_fix[i].push_back({(int)p, 0, slice_bit[e]});
+        if (slice_bit[e] < 64) ti.dep |= uint64_t(1) << slice_bit[e];
       } else {
         ti.labels.push_back(e);
       }
@@ -387,6 +388,8 @@ void compile_plan(Plan& plan, bool fuse) {
       ci.labels.insert(ci.labels.end(), rest.begin(), rest.end());
     }
     ci.producer = (int)s;
+    // tree-like reuse (Sec. III-B): a result depends on the sliced indices its subtree fixes
+    ci.dep = plan.tensors[a].dep | plan.tensors[b].dep;
     plan.max_log2 = std::max(plan.max_log2, (int)ci.labels.size());
     Step st;
     st.a = a;

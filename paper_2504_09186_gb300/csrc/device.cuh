@@ -32,6 +32,35 @@ struct Conv<__nv_bfloat16> {
   static __device__ __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
 };
 
+// Tree-like reuse across slices (Sec. III-B).  Instances of a wave are row-major over
+// (bitstring row, slice id) with s slice bits per row.  A step whose result depends only on
+// the sliced indices in dep_c runs once per assignment of those indices: launch index z =
+// row << popcount(dep_c) | assignment.  It writes the instance whose other slice bits are 0,
+// and reads each operand at its own such instance (dep_a, dep_b are subsets of dep_c).
+// s < 0: identity (every instance computed).
+struct InstMap {
+  int32_t s;
+  uint32_t dep_c, dep_a, dep_b;
+};
+struct Inst3 {
+  int64_t c, a, b;
+};
+__device__ __forceinline__ Inst3 map_inst(int64_t z, const InstMap& m) {
+  if (m.s < 0) return Inst3{z, z, z};
+  const int nd = __popc(m.dep_c);
+  const int64_t row = z >> nd;
+  uint32_t asg = (uint32_t)(z & ((int64_t(1) << nd) - 1));
+  uint32_t slice = 0, msk = m.dep_c;
+  while (msk) {
+    const uint32_t low = msk & (~msk + 1u);
+    if (asg & 1u) slice |= low;
+    asg >>= 1;
+    msk &= msk - 1;
+  }
+  const int64_t base = row << m.s;
+  return Inst3{base | slice, base | (slice & m.dep_a), base | (slice & m.dep_b)};
+}
+
 // One pairwise contraction C = A * B with tiles over index sets (see compiler.cpp).
 struct GenParams {
   const void* A;  // instance-0 base of A's real plane (imag plane at +planeA)
@@ -55,6 +84,7 @@ struct GenParams {
   int32_t n_slots, slotA, slotB, slotC;
   float2* partials;                    // split-K partial sums [inst][split][planeC]
   int32_t smem_tables;                 // byte offset of the index tables in shared memory
+  InstMap im;                          // launch index -> instances (tree-like reuse)
 };
 
 // Leaf gather: fix sliced legs and closed output legs, convert, scale.
@@ -95,7 +125,8 @@ struct TcParams {
   int32_t persistent;        // 1 = persistent TMA kernel (short K loops, no split)
   int32_t direct;            // 1 = C's three lowest positions are tile columns 0..2: each
                              //     thread stores runs of 8 columns straight from registers
-  int32_t n_inst;            // instances of the launch (persistent kernel: tiles span all)
+  int32_t n_inst;            // launch indices (persistent kernel: tiles span all)
+  InstMap im;                // launch index -> instances (tree-like reuse)
 };
 
 // Fused chain of absorptions (Sec. IV): one tile of the big tensor stays on chip while

@@ -31,7 +31,7 @@ cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leav
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
-                              cudaStream_t s);
+                              InstMap rm, cudaStream_t s);
 cudaError_t launch_inst_scale(const double2* leaf_r, int n_leaves, int64_t n_inst, double2* c, cudaStream_t s);
 cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
@@ -442,6 +442,8 @@ struct DeviceProgram {
   int n_slots = 0, n_leaves = 0;
   DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links;
   DevBuf leaf_r, inst_c;  // per (instance, leaf) rounding scale and per-instance product
+  InstMap root_map{-1, 0, 0, 0};  // instance holding each slice's root (tree-like reuse)
+  bool reuse_ok = false;          // the step maps above are set (waves of whole rows)
   std::vector<StepLaunch> steps;
   int root = 0;
   int64_t root_off = 0, root_plane = 1;
@@ -506,6 +508,7 @@ struct tnc_context_s {
   bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
   bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
   bool no_persist = false;  // TNC_NO_PERSIST=1: short-K TMA steps use one CTA per tile
+  bool no_reuse = false;    // TNC_NO_REUSE=1: every step runs for every (row, slice)
   ProfState prof;
   ~tnc_context_s() {
     bits.release();
@@ -790,6 +793,29 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
                        cudaMemcpyHostToDevice));
     for (auto& ca : chain_at) prog->steps[ca.first].cp.links = prog->chain_links.as<ChainLink>() + ca.second;
   }
+  // tree-like reuse across slices (Sec. III-B): a step runs once per assignment of the sliced
+  // indices its result depends on.  Needs waves of whole rows (all 2^s slices of a bitstring)
+  // and launches that map one to one onto the plan's steps (no fused chains); a call uses the
+  // maps only when it covers every slice (see tnc_amplitudes).
+  {
+    const int sbits = (int)P.sliced.size();
+    const bool reuse = !ctx->no_reuse && sbits >= 1 && sbits <= 20 && W % (int64_t(1) << sbits) == 0 &&
+                       chain_links.empty() && prog->steps.size() == P.steps.size();
+    for (size_t si = 0; si < prog->steps.size(); ++si) {
+      StepLaunch& L = prog->steps[si];
+      InstMap m{-1, 0, 0, 0};
+      if (reuse) {
+        const Step& st = P.steps[si];
+        const bool tcs = (L.kind == K_TC || L.kind == K_TMA) && st.tc_swap;
+        const int ta = tcs ? st.b : st.a, tb = tcs ? st.a : st.b;
+        m = InstMap{sbits, (uint32_t)P.tensors[st.c].dep, (uint32_t)P.tensors[ta].dep, (uint32_t)P.tensors[tb].dep};
+      }
+      L.p.im = m;
+      L.tp.im = m;
+    }
+    prog->reuse_ok = reuse;
+    prog->root_map = reuse ? InstMap{sbits, (uint32_t)P.tensors[P.root].dep, 0, 0} : InstMap{-1, 0, 0, 0};
+  }
   // root
   prog->root = P.root;
   prog->root_off = OFF(P.root);
@@ -832,24 +858,35 @@ static bool is_device_ptr(const void* p) {
 }
 
 // Launch one step of a program (or a one-off step) for n_inst instances.
-static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s) {
+// Launch indices of a step over a wave of n_inst instances: every instance, or with
+// tree-like reuse one per (row, assignment of the result's sliced indices).
+static int64_t launch_count(const InstMap& m, int64_t n_inst) {
+  if (m.s < 0) return n_inst;
+  return (n_inst >> m.s) << __builtin_popcount(m.dep_c);
+}
+
+static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaStream_t s, bool reuse = false) {
   StepLaunch L = L0;
-  L.grid.z = (unsigned)n_inst;
+  if (!reuse) L.p.im = L.tp.im = InstMap{-1, 0, 0, 0};
   if (L.kind == K_CHAIN) {
+    L.grid.z = (unsigned)n_inst;
     CUDA_OK(launch_chain(precision, L.cp, n_inst, s));
     return;
   }
-  if (L.kind == K_TC || L.kind == K_TMA) {
+  const bool tc = L.kind == K_TC || L.kind == K_TMA;
+  const int64_t nz = launch_count(tc ? L.tp.im : L.p.im, n_inst);
+  L.grid.z = (unsigned)nz;
+  if (tc) {
     if (L.kind == K_TMA) {
-      L.tp.n_inst = (int32_t)n_inst;
+      L.tp.n_inst = (int32_t)nz;
       CUDA_OK(launch_tc_tma(precision, L.tp, L.grid, s));
     }
     else CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
-    if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
+    if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, nz, s));
     return;
   }
   CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
-  if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, n_inst, s));
+  if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, nz, s));
 }
 
 }  // namespace tnc
@@ -889,6 +926,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->no_tma = env2 && env2[0] == '1';
     const char* env3 = std::getenv("TNC_NO_PERSIST");
     c->no_persist = env3 && env3[0] == '1';
+    const char* env4 = std::getenv("TNC_NO_REUSE");
+    c->no_reuse = env4 && env4[0] == '1';
     *out = c;
   });
 }
@@ -1004,6 +1043,8 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
     CUDA_OK(cudaMemsetAsync(ctx->acc.p, 0, size_t(batch) * n_out * sizeof(double2), s));
     const bool prof = opts->profile != 0;
     const int n_waves = (int)((n_inst + W - 1) / W);
+    // tree-like reuse needs instances laid out as whole rows of every slice
+    const bool reuse = prog->reuse_ok && slice_begin == 0 && slice_count == (int64_t(1) << P.sliced.size());
     if (prof) {
       ProfState& ps = ctx->prof;
       ps.valid = false;
@@ -1015,8 +1056,10 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       ps.kernels.assign(prog->steps.size(), 1);
       for (size_t k = 0; k < prog->steps.size(); ++k) {
         const StepLaunch& SL = prog->steps[k];
-        ps.flops[k] = SL.flops * double(n_inst);
-        ps.bytes[k] = SL.bytes * double(n_inst);
+        const bool tcs = SL.kind == K_TC || SL.kind == K_TMA;
+        const double nz = reuse ? double(launch_count(tcs ? SL.tp.im : SL.p.im, n_inst)) : double(n_inst);
+        ps.flops[k] = SL.flops * nz;  // what runs: reused results are computed once
+        ps.bytes[k] = SL.bytes * nz;
         ps.kind[k] = (SL.kind == K_TMA && SL.tp.persistent) ? 5 : SL.kind;
         ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
       }
@@ -1034,7 +1077,7 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
                std::to_string(wave_segs[w].second) + "/" + std::to_string((uintptr_t)ctx->inst_slice.p) + "/" +
                std::to_string((uintptr_t)ctx->inst_row.p) + "/" + std::to_string((uintptr_t)ctx->bits.p) + "/" +
                std::to_string((uintptr_t)ctx->segs.p) + "/" + std::to_string((uintptr_t)ctx->acc.p) + "/" +
-               std::to_string((uintptr_t)s);
+               std::to_string((uintptr_t)s) + "/" + std::to_string(reuse ? 1 : 0);
         auto git = prog->graphs.find(gkey);
         if (git != prog->graphs.end()) {
           CUDA_OK(cudaGraphLaunch(git->second, s));
@@ -1051,14 +1094,15 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
                                  prog->leaf_r.as<double2>(), s));
       for (size_t k = 0; k < prog->steps.size(); ++k) {
         if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
-        run_step(precision, prog->steps[k], cnt, s);
+        run_step(precision, prog->steps[k], cnt, s, reuse);
         if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
       }
       CUDA_OK(launch_inst_scale(prog->leaf_r.as<double2>(), prog->n_leaves, cnt, prog->inst_c.as<double2>(), s));
       CUDA_OK(launch_root_accum(precision, prog->arena.p, prog->inst_stride, prog->root_off, prog->root_plane,
                                 prog->open_pos.as<int8_t>(), prog->n_open, ctx->segs.as<RootSeg>() + wave_segs[w].first,
                                 wave_segs[w].second, prog->exps.as<int32_t>(), prog->n_slots, prog->root,
-                                ctx->acc.as<double2>(), prog->inst_c.as<double2>(), s));
+                                ctx->acc.as<double2>(), prog->inst_c.as<double2>(),
+                                reuse ? prog->root_map : InstMap{-1, 0, 0, 0}, s));
       if (capture) {
         cudaGraph_t g = nullptr;
         CUDA_OK(cudaStreamEndCapture(s, &g));
@@ -1609,7 +1653,8 @@ tnc_status tnc_adjoint(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts
         CUDA_OK(cudaMemcpyAsync(ctx->segs.p, segs.data(), segs.size() * sizeof(RootSeg), cudaMemcpyHostToDevice, s));
         CUDA_OK(launch_root_accum(TNC_C64, arena.p, stride, off[root], int64_t(1) << P.tensors[root].labels.size(),
                                   open_pos.as<int8_t>(), n_open, ctx->segs.as<RootSeg>(), (int)segs.size(),
-                                  exps.as<int32_t>(), 2 * T, root, ctx->acc.as<double2>(), nullptr, s));
+                                  exps.as<int32_t>(), 2 * T, root, ctx->acc.as<double2>(), nullptr, InstMap{-1, 0, 0, 0},
+                                  s));
       }
       CUDA_OK(launch_adj_root_init(arena.as<float>(), stride, off[T + root], int64_t(1) << P.tensors[root].labels.size(),
                                    open_pos.as<int8_t>(), n_open, ctx->inst_row.as<int32_t>(), base, cnt,

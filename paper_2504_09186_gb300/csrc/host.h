@@ -152,6 +152,7 @@ struct TensorInfo {
   int64_t offset_fused = -1;      // ... in the fused program (-1: lives on chip inside a chain)
   int leaf = -1;                  // leaf index for leaf tensors
   bool on_chip = false;           // intermediate of a fused chain, never stored
+  uint64_t dep = 0;               // sliced indices (slice-id bits) its values depend on
 };
 
 struct Plan {

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   float* red = reinterpret_cast<float*>(TCn + (1 << p.nt) + 2);  // 4-byte aligned (+2 pads)
 
   const int tid = threadIdx.x;
-  const int64_t inst = blockIdx.z;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
   // outer coordinates of this tile
   const uint32_t om = blockIdx.x & ((1u << p.n_om) - 1u);
   const uint32_t on = p.n_om >= 32 ? 0u : (blockIdx.x >> p.n_om);
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
 #pragma unroll
     for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  const T* Abase = reinterpret_cast<const T*>(p.A) + inst * p.strideA + oA;
-  const T* Bbase = reinterpret_cast<const T*>(p.B) + inst * p.strideB + oB;
+  const T* Abase = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
+  const T* Bbase = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
   const int64_t KO = int64_t(1) << p.n_ok;
   const int64_t per = KO / p.splitk;
   const int64_t k0 = int64_t(blockIdx.y) * per;
@@ -286,21 +286,21 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   }
   if (p.splitk > 1) {
     // FP32 partial sums, indexed by C's flat index
-    float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
+    float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
     const uint32_t lowmask = (1u << p.runC) - 1u;
     for (int t = tid; t < O; t += kThreads) part[hiC[t >> p.runC] + (uint32_t(t) & lowmask)] = R[t];
     return;
   }
   // scale, convert, store
-  const int64_t sb = inst * p.n_slots;
-  const int sh = product_shift(p.maxabs[sb + p.slotA], p.maxabs[sb + p.slotB], p.nK);
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
+  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
   const float scale = ldexpf(1.f, -sh);
-  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+  T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
   const float mx = store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
   const float bm = block_max(mx, red);
   if (tid == 0) {
-    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
-    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+    atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
+    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
 }
 
@@ -308,21 +308,21 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
   __shared__ float red[32];
-  const int64_t inst = blockIdx.z;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
   const int64_t idx = int64_t(blockIdx.x) * kThreads + threadIdx.x;
-  const int64_t sb = inst * p.n_slots;
-  const int sh = product_shift(p.maxabs[sb + p.slotA], p.maxabs[sb + p.slotB], p.nK);
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
+  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
   const float scale = ldexpf(1.f, -sh);
   float mx = 0.f;
   if (idx < p.planeC) {
-    const float2* part = p.partials + inst * p.splitk * p.planeC + idx;
+    const float2* part = p.partials + int64_t(blockIdx.z) * p.splitk * p.planeC + idx;
     float2 s = part[0];
     for (int k = 1; k < p.splitk; ++k) {
       const float2 v = part[int64_t(k) * p.planeC];
       s.x += v.x;
       s.y += v.y;
     }
-    T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC;
+    T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC;
     const T re = Conv<T>::from_f(s.x * scale), im = Conv<T>::from_f(s.y * scale);
     Cre[idx] = re;
     Cre[p.planeC + idx] = im;
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
   }
   const float bm = block_max(mx, red);
   if (threadIdx.x == 0) {
-    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
-    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+    atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
+    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
 }
 
@@ -430,7 +430,7 @@ template <typename T>
 __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                              const int8_t* __restrict__ open_pos, int n_open, const RootSeg* __restrict__ segs,
                              const int32_t* __restrict__ exps, int n_slots, int root_slot, double2* acc,
-                             const double2* __restrict__ cfac) {
+                             const double2* __restrict__ cfac, InstMap rm) {
   const int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n_out = int64_t(1) << n_open;
   if (o >= n_out) return;
@@ -442,8 +442,11 @@ __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, i
   double2* a = acc + int64_t(s.row) * n_out + o;
   double re = a->x, im = a->y;
   for (int i = s.begin; i < s.end; ++i) {
-    const T* root = arena + int64_t(i) * inst_stride + root_off;
-    const double sc = ldexp(1.0, exps[int64_t(i) * n_slots + root_slot]);
+    // the root of a slice is stored at the instance that keeps only the slice bits it
+    // depends on (tree-like reuse); the leaf-rounding scale is per instance
+    const int64_t ir = rm.s < 0 ? int64_t(i) : ((int64_t(i) >> rm.s << rm.s) | (int64_t(i) & int64_t(rm.dep_c)));
+    const T* root = arena + ir * inst_stride + root_off;
+    const double sc = ldexp(1.0, exps[ir * n_slots + root_slot]);
     const double xr = (double)Conv<T>::to_f(root[idx]) * sc, xi = (double)Conv<T>::to_f(root[plane + idx]) * sc;
     if (cfac) {
       const double2 c = cfac[i];
@@ -765,18 +768,18 @@ cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leav
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
-                              cudaStream_t s) {
+                              InstMap rm, cudaStream_t s) {
   const int64_t n_out = int64_t(1) << n_open;
   dim3 grid((unsigned)((n_out + 255) / 256), (unsigned)n_segs);
   if (precision == 0)
     k_root_accum<float><<<grid, 256, 0, s>>>((const float*)arena, inst_stride, root_off, plane, open_pos, n_open, segs,
-                                             exps, n_slots, root_slot, acc, cfac);
+                                             exps, n_slots, root_slot, acc, cfac, rm);
   else if (precision == 1)
     k_root_accum<__half><<<grid, 256, 0, s>>>((const __half*)arena, inst_stride, root_off, plane, open_pos, n_open,
-                                              segs, exps, n_slots, root_slot, acc, cfac);
+                                              segs, exps, n_slots, root_slot, acc, cfac, rm);
   else
     k_root_accum<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)arena, inst_stride, root_off, plane,
-                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc, cfac);
+                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc, cfac, rm);
   return cudaGetLastError();
 }
 

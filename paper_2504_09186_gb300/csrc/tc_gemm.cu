@@ -226,16 +226,16 @@ __device__ __forceinline__ uint32_t stg_swz(uint32_t idx) {
 template <typename T, int BN, int TMEM_COLS>
 __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bool ok, unsigned char* smem,
                                             const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC, float* red,
-                                            int64_t oC, int64_t inst) {
+                                            int64_t oC, const Inst3 I) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t sb = inst * p.n_slots;
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
   const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
   const int row = (warp & 3) * 32 + lane;
   const int col0 = (warp >> 2) * (BN / 2);
   if (p.splitk > 1) {
     // FP32 partial sums by C's flat index; k_splitk_reduce sums them in a fixed order
     if (ok) {
-      float2* part = p.partials + (inst * p.splitk + blockIdx.y) * p.planeC + oC;
+      float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
       const uint32_t lowmask = (1u << p.runC) - 1u;
 #pragma unroll 1
       for (int cc = 0; cc < BN / 2; cc += 32) {
@@ -259,7 +259,7 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   // epilogue: TMEM -> registers -> scaled, converted, staged in C-native order -> global
   int sh = 0;
   {
-    const float a = p.maxabs[sb + p.slotA], b = p.maxabs[sb + p.slotB];
+    const float a = p.maxabs[sa + p.slotA], b = p.maxabs[sbb + p.slotB];
     if (a > 0.f && b > 0.f) {
       int ea, eb;
       frexpf(a, &ea);
@@ -273,7 +273,7 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   float mx = 0.f;
   if (ok && p.direct) {
     // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores from registers
-    T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+    T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
     const uint32_t lowmask = (1u << p.runC) - 1u;
     const uint32_t rm = TCm[row];
 #pragma unroll 1
@@ -326,13 +326,13 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   }
   if (!ok) return;
   // contiguous runs of C: 16-byte vectors (the compiler guarantees runC >= 3)
-  T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+  T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
   const uint32_t lowmask = (1u << p.runC) - 1u;
   for (int t = tid * 8; t < (p.direct ? 0 : CT); t += TC_THREADS * 8) {
     const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
 #if TNC_TC_SELFCHECK
     {
-      const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - inst * p.strideC;
+      const int64_t ec = (Cre + off - reinterpret_cast<T*>(p.C)) - I.c * p.strideC;
       if (!tc_check(((reinterpret_cast<uintptr_t>(Cre + off) & 15u) == 0) && ec >= 0 && ec + 8 <= p.planeC, p.status, 17, ec, t))
         continue;
     }
@@ -347,8 +347,8 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   if (tid == 0) {
     float m = 0.f;
     for (int w = 0; w < TC_THREADS / 32; ++w) m = fmaxf(m, red[w]);
-    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
-    if (blockIdx.x == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
 }
 
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
   float* red = reinterpret_cast<float*>(tmem_slot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t inst = blockIdx.z;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
   // grid.x enumerates (on fastest, om): CTAs sharing an A row tile run together
   const uint32_t on = blockIdx.x & ((1u << p.n_on) - 1u);
   const uint32_t om = p.n_on >= 31 ? 0u : (blockIdx.x >> p.n_on);
@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
   tc_check((smem_u32(bars) & 7u) == 0, p.status, 18, smem_u32(bars), 0);
 #endif
 
-  const T* Ab = reinterpret_cast<const T*>(p.A) + inst * p.strideA + oA;
-  const T* Bb = reinterpret_cast<const T*>(p.B) + inst * p.strideB + oB;
+  const T* Ab = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
+  const T* Bb = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
   const int n_total = 1 << p.n_ok;
   const int per = n_total / p.splitk;
   const int it0 = blockIdx.y * per;
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
       const uint32_t d1 = d0 + (isA ? uint32_t(S::A_BYTES) : uint32_t(S::B_BYTES));
 #if TNC_TC_SELFCHECK
       {
-        const int64_t e = isA ? (g0 - reinterpret_cast<const T*>(p.A)) - inst * p.strideA
-                              : (g0 - reinterpret_cast<const T*>(p.B)) - inst * p.strideB;
+        const int64_t e = isA ? (g0 - reinterpret_cast<const T*>(p.A)) - I.a * p.strideA
+                              : (g0 - reinterpret_cast<const T*>(p.B)) - I.b * p.strideB;
         const bool good = ((reinterpret_cast<uintptr_t>(g0) & 15u) == 0) && e >= 0 && e + 8 <= plane &&
                           (d0 & 15u) == 0 && d1 + 16 <= sbase + S::PIPE;
         if (!tc_check(good, p.status, 13, e, isA)) continue;
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_gemm(cons
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
 
-  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, inst);
+  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, I);
 }
 
 // Tensor-memory-accelerator variant: the compiler laid the operands out as [Kt | Mt | ...]
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
   float* red = reinterpret_cast<float*>(tmem_slot + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t inst = blockIdx.z;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
   const uint32_t on = blockIdx.x & ((1u << p.n_on) - 1u);
   const uint32_t om = p.n_on >= 31 ? 0u : (blockIdx.x >> p.n_on);
   int64_t oA = 0, oB = 0, oC = 0;
@@ -634,10 +634,10 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
       const uint32_t st = sbase + buf * S::STAGE;
       const uint32_t fb = smem_u32(&full[buf]);
       mbar_arrive_expect_tx(fb, S::STAGE);
-      tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)inst, fb);
-      tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)inst, fb);
-      tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)inst, fb);
-      tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)inst, fb);
+      tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)I.a, fb);
+      tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)I.a, fb);
+      tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)I.b, fb);
+      tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)I.b, fb);
       issued = it + 1;
     }
     // copies still in flight land before the CTA may exit (all complete on the normal path)
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
   ok = ok && fin;
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
-  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, inst);
+  tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, I);
 }
 
 // Persistent variant of k_tc_tma for short K loops (at most eight K tiles per output tile)
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       // TMA producer
       int64_t g = 0, issued = 0;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int inst = (int)(t >> tile_bits);
+        const Inst3 It = map_inst(t >> tile_bits, p.im);
         const uint32_t r = (uint32_t)t & tile_mask;
         const uint32_t on = r & ((1u << p.n_on) - 1u);
         const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
@@ -831,10 +831,10 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
           const uint32_t st = sbase + buf * S::STAGE;
           const uint32_t fb = smem_u32(&full[buf]);
           mbar_arrive_expect_tx(fb, S::STAGE);
-          tma_load_4d(st, &p.tmA, 0, rowA, 0, inst, fb);
-          tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, inst, fb);
-          tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, inst, fb);
-          tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, inst, fb);
+          tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)It.a, fb);
+          tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)It.a, fb);
+          tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)It.b, fb);
+          tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)It.b, fb);
           issued = g + 1;
         }
       }
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int64_t inst = t >> tile_bits;
+      const Inst3 It = map_inst(t >> tile_bits, p.im);
       const uint32_t r = (uint32_t)t & tile_mask;
       const uint32_t on = r & ((1u << p.n_on) - 1u);
       const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
@@ -914,10 +914,10 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
         if ((om >> q) & 1u) oC += int64_t(1) << p.om_C[q];
       for (int q = 0; q < p.n_on; ++q)
         if ((on >> q) & 1u) oC += int64_t(1) << p.on_C[q];
-      const int64_t sb = inst * p.n_slots;
+      const int64_t sa = It.a * p.n_slots, sbb = It.b * p.n_slots, sc = It.c * p.n_slots;
       int sh = 0;
       {
-        const float a = p.maxabs[sb + p.slotA], bb = p.maxabs[sb + p.slotB];
+        const float a = p.maxabs[sa + p.slotA], bb = p.maxabs[sbb + p.slotB];
         if (a > 0.f && bb > 0.f) {
           int ea, eb;
           frexpf(a, &ea);
@@ -928,7 +928,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       const float scale = ldexpf(1.f, -sh);
       float mx = 0.f;
       const uint32_t rm = TCm[row];
-      T* Cre = reinterpret_cast<T*>(p.C) + inst * p.strideC + oC;
+      T* Cre = reinterpret_cast<T*>(p.C) + It.c * p.strideC + oC;
       if (p.direct) {
         // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores straight
         // from registers, no staging; one barrier per tile (TMEM release and block max)
@@ -961,8 +961,8 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
           mbar_arrive(smem_u32(&tempty[b]));
           float m = 0.f;
           for (int w = 0; w < GW; ++w) m = fmaxf(m, gred[w]);
-          atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
-          if (r == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+          atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+          if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
         }
         continue;
       }
@@ -995,8 +995,8 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       if (gtid == 0) {
         float m = 0.f;
         for (int w = 0; w < GW; ++w) m = fmaxf(m, gred[w]);
-        atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sb + p.slotC]), __float_as_uint(m));
-        if (r == 0) p.exps[sb + p.slotC] = p.exps[sb + p.slotA] + p.exps[sb + p.slotB] + sh;
+        atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+        if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
       }
     }
   }

@@ -143,3 +143,24 @@ def test_stem_plan_fused_chains(ctx, rows, cols, cycles, n_open, cap):
         plain = ctx.amplitudes(p, fixed[None, :], prec, fuse=False)[0]
         assert metrics.rel_err_norm(fused, ref) <= TOL[prec], prec
         assert metrics.rel_err_norm(plain, ref) <= TOL[prec], prec
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf"])
+def test_tree_reuse_across_slices_is_bit_identical(ctx, precision, monkeypatch):
+    # steps whose subtree fixes no sliced index (or only some) run once per assignment of the
+    # indices they depend on (Sec. III-B tree-like reuse); the values cannot change
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=3)
+    bs = np.stack([fixed, 1 - fixed])
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=14, slices_min=4)
+    assert p.info()["n_sliced"] >= 4
+    got = ctx.amplitudes(p, bs, precision, profile=True)
+    flops_reuse = ctx.profile_read()["flops"].sum()
+    monkeypatch.setenv("TNC_NO_REUSE", "1")
+    ctx1 = T.Context(0)
+    ref = ctx1.amplitudes(p, bs, precision, profile=True)
+    flops_all = ctx1.profile_read()["flops"].sum()
+    assert np.array_equal(got, ref)
+    assert flops_reuse < flops_all  # some steps ran fewer times
+    exact = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    assert metrics.rel_err_norm(got[0], exact) <= TOL[precision]
