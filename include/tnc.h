@@ -96,9 +96,10 @@ typedef struct {
                        /*    at a time (the stem of Sec. II-A), which the fused chains */
                        /*    of Sec. IV execute on chip                               */
   int32_t objective;   /* which trial is kept: 0 = fewest complex multiply-adds (the    */
-                       /* cost of Eq. 1); 1 = least modeled GB300 time, summing per step */
-                       /* max(flops / rate, bytes / HBM bandwidth) with the tensor-core */
-                       /* rate for steps large enough for its tiles                   */
+                       /* cost of Eq. 1); 1 = least modeled GB300 time of a call over   */
+                       /* every slice: per step max(flops / rate, bytes / HBM bandwidth)*/
+                       /* (tensor-core rate for steps large enough for its tiles) times */
+                       /* the times it runs under tree-like reuse (Sec. III-B)          */
 } tnc_plan_opts;
 
 /* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:
@@ -125,8 +126,8 @@ typedef struct {
                                                /* every contraction it contains)        */
   double narrow_max;           /* largest "narrow" rate 2 N_common / (N_A + N_B)       */
                                /* (Sec. VII-B) over the steps                          */
-  double model_seconds_per_slice; /* modeled GB300 time of one slice (the objective = 1 */
-                               /* cost; complex-half storage)                          */
+  double model_seconds_per_slice; /* modeled GB300 time of a call over every slice,    */
+                               /* divided by 2^s (the objective = 1 cost; complex-half) */
 } tnc_plan_info;
 tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
 

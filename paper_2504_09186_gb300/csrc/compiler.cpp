@@ -436,7 +436,10 @@ void compile_plan(Plan& plan, bool fuse) {
     if (nm + nn <= 8 && nk >= 12) plan.n_gepdot++;
     else if (nk + nn <= 6) plan.n_absorb++;
     else plan.n_gemm++;
-    plan.model_seconds += step_model_seconds((int)la.size(), (int)lb.size(), (int)lc.size(), nk);
+    // per slice, averaged over a call on every slice with tree-like reuse (a step runs once
+    // per assignment of the sliced indices its result depends on)
+    plan.model_seconds += step_model_seconds((int)la.size(), (int)lb.size(), (int)lc.size(), nk) *
+                          std::ldexp(1.0, __builtin_popcountll(plan.tensors[st.c].dep) - (int)plan.sliced.size());
   }
   // fused chains (Sec. IV): follow the big operand through consecutive absorptions of
   // small tensors (rank <= 6) while the on-chip label set stays within 2^12 entries.  The

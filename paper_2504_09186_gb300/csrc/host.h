@@ -84,16 +84,17 @@ void gate_envs_from_leaf_envs(const Network& net, const std::vector<SmallTensor>
 
 // ------------------------------------------------------------------ plan
 // Modeled GB300 time (seconds) of one pairwise contraction of operands with a and b labels,
-// k of them common, and a result with c labels: the larger of its flop time and its HBM time
-// (complex-half storage, 4 bytes per entry).  Steps large enough for tensor-core tiles
-// (M >= 2^7, N >= 2^6 or the reverse, K >= 2^4) run at the tensor-core rate, the others at the
-// FP32-lane rate.
+// k of them common, and a result with c labels: the larger of its flop time and its memory
+// time (complex-half storage, 4 bytes per entry), at the rates this library's kernels reach
+// on GB300.  Steps large enough for tensor-core tiles (M >= 2^7, N >= 2^6 or the reverse,
+// K >= 2^4): 1.8 PF/s and 4.5 TB/s (the tensor-core GEMM and its direct epilogue).  Others:
+// the FP32-lane rate of 40 TF/s and 1.5 TB/s (the SIMT tiled kernels).
 inline double step_model_seconds(int a, int b, int c, int k) {
   const int m = a - k, n = b - k;
   const double flops = 8.0 * std::ldexp(1.0, a + b - k);
   const double bytes = 4.0 * (std::ldexp(1.0, a) + std::ldexp(1.0, b) + std::ldexp(1.0, c));
   const bool tc = std::max(m, n) >= 7 && std::min(m, n) >= 6 && k >= 4;
-  return std::max(flops / (tc ? 1.8e15 : 4.0e13), bytes / 6.5e12);
+  return tc ? std::max(flops / 1.8e15, bytes / 4.5e12) : std::max(flops / 4.0e13, bytes / 1.5e12);
 }
 
 struct PlanOpts {

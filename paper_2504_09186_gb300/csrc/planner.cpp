@@ -181,16 +181,25 @@ int tree_max(const Tree& t, const std::vector<char>& sliced) {
   return m;
 }
 
-// Modeled GB300 time of one slice: step_model_seconds summed over the tree's steps.
-double model_time(const Tree& t, const std::vector<char>& sliced) {
+// Modeled GB300 time of a call over all 2^s slices of one bitstring row: step_model_seconds
+// of every step times the number of times it runs under tree-like reuse (Sec. III-B), one
+// per assignment of the sliced indices its subtree fixes.
+double model_time(const Tree& t, const std::vector<char>& sliced, const std::vector<int>& sliced_list) {
+  std::vector<uint64_t> dep(t.sets.size(), 0);
+  const size_t n_leaves = t.sets.size() - t.pairs.size();
+  for (size_t i = 0; i < n_leaves; ++i)
+    for (size_t j = 0; j < sliced_list.size() && j < 64; ++j)
+      if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), sliced_list[j])) dep[i] |= uint64_t(1) << j;
   double tot = 0;
-  for (auto& p : t.pairs) {
+  for (size_t k = 0; k < t.pairs.size(); ++k) {
+    const auto& p = t.pairs[k];
     const LabelSet& A = t.sets[p.first];
     const LabelSet& B = t.sets[p.second];
     const int a = (int)count_not_in(A, sliced), b = (int)count_not_in(B, sliced);
     const int u = (int)count_not_in(set_union(A, B), sliced);
     const int c = (int)count_not_in(sym_diff(A, B), sliced);
-    tot += step_model_seconds(a, b, c, a + b - u);
+    dep[n_leaves + k] = dep[p.first] | dep[p.second];
+    tot += step_model_seconds(a, b, c, a + b - u) * std::ldexp(1.0, __builtin_popcountll(dep[n_leaves + k]));
   }
   return tot;
 }
@@ -283,7 +292,7 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       cur = tree_cost(t, sl);
     }
     const double total = std::ldexp(cur, (int)sliced.size());
-    const double score = o.objective == 1 ? std::ldexp(model_time(t, sl), (int)sliced.size()) : total;
+    const double score = o.objective == 1 ? model_time(t, sl, sliced) : total;
     const bool within = (int)sliced.size() <= o.slices_max;
     bool better;
     if (within != best.within_max) better = within;
