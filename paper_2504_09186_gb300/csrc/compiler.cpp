@@ -73,9 +73,13 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     if (!contains(la, x)) N.push_back(x);
   const int m = (int)M.size(), k = (int)K.size(), n = (int)N.size();
   TileSpec t;
-  auto fits = [](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
+  // GEPDOT steps (few outputs, long K) are bound by memory latency: operand tiles of 2^12
+  // entries double the bytes each CTA has in flight per K step
+  const bool gepdot = (m + n <= 10) && (k >= 12);
+  const int tile_ab = gepdot ? TILE_AB + 1 : TILE_AB;
+  auto fits = [tile_ab](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
     const int mt = (int)Mt.size(), kt = (int)Kt.size(), nt = (int)Nt.size();
-    return mt + kt <= TILE_AB && kt + nt <= TILE_AB && mt + nt <= TILE_C && mt + nt <= max_out_bits(mt, nt);
+    return mt + kt <= tile_ab && kt + nt <= tile_ab && mt + nt <= TILE_C && mt + nt <= max_out_bits(mt, nt);
   };
   // labels each tile must hold so that loads and stores run over contiguous memory
   for (int need = 4; need >= 0; --need) {
@@ -99,7 +103,6 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     break;
   }
   // grow the tiles by class, one label at a time while the limits hold
-  const bool gepdot = (m + n <= 10) && (k >= 12);
   auto grow = [&](std::vector<int>& tile, const std::vector<int>& pool, int target) {
     for (int x : pool) {
       if ((int)tile.size() >= target) break;
