@@ -164,3 +164,20 @@ def test_tree_reuse_across_slices_is_bit_identical(ctx, precision, monkeypatch):
     assert flops_reuse < flops_all  # some steps ran fewer times
     exact = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
     assert metrics.rel_err_norm(got[0], exact) <= TOL[precision]
+
+
+def test_sharded_slices_with_gpu_chunks(ctx, tmp_path):
+    # chunks of consecutive slice ids through the library, every chunk verified by rerun
+    # (the GPU sums are deterministic, so the rerun must be bit-identical)
+    from paper_2504_09186_gb300 import shard
+
+    c = grid_circuit(4, 4, 10, seed=1)
+    fixed, open_q = subcube_spec(16, 3, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=9, slices_min=4)
+    n = 1 << p.info()["n_sliced"]
+    run = shard.gpu_chunk(ctx, p, fixed[None, :], "c64")
+    spec = shard.ShardSpec(n_slices=n, chunk=4)
+    got = shard.run_rank(spec, run, shard.CheckpointStore(str(tmp_path), 0), verify_fraction=1.0)
+    full = ctx.amplitudes(p, fixed[None, :], "c64")
+    assert np.allclose(got, full, rtol=1e-12, atol=1e-15)
+    assert metrics.rel_err_norm(got[0], sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))) <= 1e-5
