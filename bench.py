@@ -95,6 +95,8 @@ def parse():
     ap.add_argument("--sw-shapes", default="", help="log2 M,K,N triples 'm,k,n;m,k,n' (default: a fixed set)")
     ap.add_argument("--precision", default="chalf", choices=["chalf", "cbf16", "c64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the complex64 comparison run")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run the heuristic tile configurations (no timing of the tensor-core steps first)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cap", type=int, default=23, help="log2 size cap of the oracle sample")
     ap.add_argument("--ref-subslices", type=int, default=24, help="oracle sub-slices per reference step")
@@ -288,6 +290,13 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     bits = np.ascontiguousarray(fixed[None, :], dtype=np.uint8)
 
+    # tile configurations of the tensor-core steps chosen by timing (setup, untimed)
+    tune = None
+    if not args.no_autotune and args.precision != "c64":
+        t0 = time.perf_counter()
+        tune = ctx.autotune(plan, bits, args.precision, fuse=fuse)
+        tune["setup_s"] = time.perf_counter() - t0
+
     def timed(precision, steps, warmup, profile):
         for _ in range(warmup):
             ctx.amplitudes(plan, bits, precision, out=out, stream=stream.cuda_stream, fuse=fuse)
@@ -393,7 +402,8 @@ def run_ours(args):
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"], "sliced_indices": info["n_sliced"],
                        "complex_tflops": total_flops / (ms / 1e3) / 1e12,
                        "l2": "256 MiB flush before every timed step; intermediates up to 2^26 entries > L2",
-                       "parallelism": f"replicas x{world} (independent sub-cubes)"},
+                       "parallelism": f"replicas x{world} (independent sub-cubes)",
+                       "autotune": tune},
             "complex64": c64,
             "rel_err_vs_oracle": err_golden,
             "e2e": {"value": n_slices * world / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": h2d,
@@ -543,6 +553,11 @@ def run_s60(args):
         e1.synchronize()
         return e0.elapsed_time(e1), complex(out.cpu().numpy()[0, 0])
 
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = ctx.autotune(plan, bits, "chalf", slice_begin=ids[0], slice_count=1)
+        tune["setup_s"] = time.perf_counter() - t0
     for _ in range(max(1, args.warmup)):
         one("chalf", ids[0], False)
     with ClockSampler(0) as clk:
@@ -572,7 +587,7 @@ def run_s60(args):
                        "slice_ids": ids, "sliced_indices": s, "plan_trials": args.s60_trials, "plan_seconds": plan_s,
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"],
                        "complex_tflops": 8 * 2 ** info["log2_flops_per_slice"] * value / 1e12,
-                       "extrapolated_total_log2_seconds": s - float(np.log2(value))},
+                       "extrapolated_total_log2_seconds": s - float(np.log2(value)), "autotune": tune},
             "per_slice_ms": ms, "complex64": cmp64, "roofline": roof, "clocks": clocks}
     print(json.dumps(line))
 

@@ -260,6 +260,64 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
 tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,
                             int32_t* kind, int32_t cap, int32_t* n);
 
+/* ---------------------------------------------------------------- autotuner */
+
+/* Tile configurations of the tensor-core steps, chosen by timing (the step compiler's
+ * configurations of Sec. IV and V, measured instead of predicted).  A tensor-core step's
+ * admissible configurations are the ones its compiled operand layouts support:
+ *  - tile widths of 256, 128 or 64 columns, at most the compiled width (a narrower tile
+ *    loads a prefix of the compiled column labels; the rest become outer labels);
+ *  - the persistent kernel (width <= 128, at most 3 outer common labels);
+ *  - splits over the outer common labels, powers of two whose FP32 partial sums fit the
+ *    program's partial-sum buffer;
+ *  - a three-stage or a deep operand pipeline.
+ * Every configuration computes the same contraction.  A different split changes only how
+ * the FP32 partial sums are grouped.  For a fixed cache, results stay deterministic. */
+typedef struct {
+  int32_t steps_tuned;     /* tensor-core steps whose configurations were timed          */
+  int32_t steps_changed;   /* steps now running a configuration other than the heuristics'*/
+  int32_t candidates;      /* configurations timed                                       */
+  int32_t reserved0;
+  double seconds_default;  /* sum over the tuned steps of one launch, heuristic configs  */
+  double seconds_tuned;    /* the same with the chosen configurations                     */
+  double reserved[4];
+} tnc_tune_info;
+
+/* Runs tnc_amplitudes(ctx, p, opts, bitstrings, batch, slice_begin, slice_count) once,
+ * discarding the result.  It then times the admissible configurations of every TMA
+ * tensor-core step of the program that call used:
+ *  - each at the call's wave size, on the call's stream;
+ *  - one untimed launch, then 3 timed launches (23 when a launch is under 0.2 ms).
+ * A step takes the fastest configuration only if it beats the heuristics by 3% or more.
+ * The choice is recorded in a process-wide cache keyed by the step's shape:
+ *  - precision;
+ *  - operand and result ranks;
+ *  - compiled tile width and depth;
+ *  - outer label counts;
+ *  - epilogue kind;
+ *  - instances per launch.
+ * Programs built later take cached choices for steps of the same shape.  The tuned program
+ * runs the chosen configurations from the next call on.
+ *  info  may be NULL.
+ * Errors: those of tnc_amplitudes.  Skipped without an error: C64 plans, and contexts
+ * with TNC_NO_TC or TNC_NO_TMA set (they have no TMA steps). */
+tnc_status tnc_autotune(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
+                        const uint8_t* bitstrings, int64_t batch, int64_t slice_begin,
+                        int64_t slice_count, tnc_tune_info* info);
+
+/* The process-wide cache as a text file: the line "tnc-tune 1", then one line per shape:
+ *   key bn persistent split stages
+ *  - split: 0 means the heuristics;
+ *  - stages: 0 heuristics, 1 deep, 3 three stages.
+ * Save writes a temporary file and renames it into place.  Load merges the file's entries
+ * into the cache; it changes nothing when any line is malformed.
+ * Errors: TNC_E_INVALID_ARG (NULL path), TNC_E_IO (unreadable, unwritable or malformed).
+ * Neither needs a GPU. */
+tnc_status tnc_tune_save(const char* path);
+tnc_status tnc_tune_load(const char* path);
+void tnc_tune_clear(void);
+int64_t tnc_tune_size(void);
+
 /* Wait for the context's work and report device-side status (TNC_E_TIMEOUT if a
  * bounded wait ran out). */
 tnc_status tnc_sync(tnc_context ctx);

@@ -107,6 +107,7 @@ struct StepLaunch {
   size_t smem;
   int rm, rn;
   double flops = 0, bytes = 0;  // algorithmic, per instance (real flops 8MNK; bytes read + written)
+  int plan_step = -1;           // the plan step a tensor-core launch runs
 };
 
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
@@ -117,7 +118,8 @@ struct StepLaunch {
 static int64_t split_instances(const Plan& P) { return int64_t(1) << std::min<size_t>(P.sliced.size(), 12); }
 
 static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<int>& la, const std::vector<int>& lb,
-                           const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst) {
+                           const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst,
+                           int force_split = 0) {
   TcParams& q = L.tp;
   std::memset(&q, 0, sizeof(q));
   const size_t nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6), kt = bk == 32 ? 5 : 4;
@@ -174,7 +176,12 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
     return w / std::ceil(w);
   };
   int split = 1;
-  if (!q.persistent)
+  if (force_split > 0) {
+    // a tuned split (1 <= split <= K tiles; the caller decides about the persistent kernel)
+    if (force_split > kit || (force_split & (force_split - 1))) fail(TNC_E_PLAN, "bad tensor-core split");
+    q.persistent = 0;
+    split = force_split;
+  } else if (!q.persistent)
     while (kit / (split * 2) >= 4 && split < 1024 &&
            (tiles * split < 2 * 152 || (wave_eff(tiles * split) < 0.9 && kit / (split * 2) >= 256)))
       split *= 2;
@@ -438,6 +445,7 @@ static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int
 // ------------------------------------------------------------------ per-plan device program
 struct DeviceProgram {
   int device = 0, precision = 0, W = 0;
+  bool fused = false;       // chains fused: tensors at their fused-arena offsets
   int64_t inst_stride = 0;  // scalars
   int n_slots = 0, n_leaves = 0;
   DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links;
@@ -674,6 +682,99 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
   return L;
 }
 
+// ------------------------------------------------------------------ tensor-core step configurations
+// What the tuner may choose for a tensor-core step.  Every choice computes the same
+// contraction; only the split over K changes the grouping of the FP32 sums.
+struct TcChoice {
+  int bn = 0;          // tile width 64, 128 or 256, at most the compiled one (a prefix of Nt)
+  int persistent = 0;  // one CTA per SM walking the tiles (BN <= 128, no split, <= 3 outer K labels)
+  int split = 0;       // split over the outer common labels; 0: the heuristics of make_tc_launch
+  int stages = 0;      // pipeline (BN < 256): 0 heuristics, 3 three stages (two CTAs per SM), 1 deep
+};
+
+// Process-wide cache of tuned choices keyed by step shape: tnc_autotune fills it,
+// build_program reads it, tnc_tune_save / tnc_tune_load keep it in a text file.
+static std::mutex g_tune_mu;
+static std::map<std::string, TcChoice> g_tune;
+
+static bool tune_lookup(const std::string& key, TcChoice* ch) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *ch = it->second;
+  return true;
+}
+
+// Shape of a tensor-core step as the tuner sees it: precision, operand and result ranks,
+// compiled tile width and depth, outer label counts of the heuristic launch `D`, direct
+// epilogue, and the instances one launch covers.
+static std::string tune_key(int precision, const Plan& P, const Step& st, const StepLaunch& D, int64_t nz) {
+  const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
+  char buf[192];
+  std::snprintf(buf, sizeof buf, "p%d.a%zu.b%zu.c%zu.bn%d.bk%d.om%d.on%d.ok%d.d%d.z%lld", precision,
+                P.tensors[ta].labels.size(), P.tensors[tb].labels.size(), P.tensors[st.c].labels.size(), st.tc_bn,
+                st.tc_bk, D.tp.n_om, D.tp.n_on, D.tp.n_ok, D.tp.direct, (long long)nz);
+  return buf;
+}
+
+static int64_t prog_off(const Plan& P, const DeviceProgram* prog, int t) {
+  const int64_t o = prog->fused ? P.tensors[t].offset_fused : P.tensors[t].offset;
+  if (o < 0) fail(TNC_E_PLAN, "tensor has no arena slot in this program");
+  return o;
+}
+
+// Tensor-core launch of plan step `si` in `prog` with configuration `ch` (nullptr: the
+// heuristics of make_tc_launch and the wave-size rule for the persistent kernel).  The split
+// over K is sized from the plan's slice count, not the wave size, so results do not depend on
+// how many instances share a launch.
+static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const DeviceProgram* prog, int si,
+                            const TcChoice* ch) {
+  const Step& st = P.steps[si];
+  const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
+  const auto& la = P.tensors[ta].labels;
+  const auto& lb = P.tensors[tb].labels;
+  const auto& lc = P.tensors[st.c].labels;
+  TileSpec t = st.tc_tile;
+  int bn = st.tc_bn;
+  if (ch && ch->bn && ch->bn < bn) {
+    // a narrower tile loads a prefix of B's tile labels (B is laid out [Kt | Nt | ...]); the
+    // rest become the lowest outer labels
+    if (ch->bn != 64 && ch->bn != 128) fail(TNC_E_PLAN, "bad tuned tile width");
+    const size_t nt = ch->bn == 128 ? 7 : 6;
+    t.No.insert(t.No.begin(), t.Nt.begin() + nt, t.Nt.end());
+    t.Nt.resize(nt);
+    bn = ch->bn;
+  }
+  StepLaunch L;
+  std::memset(&L.cp, 0, sizeof(L.cp));
+  L.rm = L.rn = 0;
+  L.plan_step = si;
+  make_tc_launch(L, t, la, lb, lc, prog->precision, bn, st.tc_bk, split_instances(P), ch ? ch->split : 0);
+  const bool can_persist = bn <= 128 && L.tp.splitk == 1 && L.tp.n_ok <= 3;
+  L.tp.persistent =
+      (ch ? ch->persistent != 0 : (int64_t(1) << (L.tp.n_om + L.tp.n_on)) * prog->W >= 4 * 152) && can_persist ? 1 : 0;
+  if (ch && ch->stages) L.tp.stages = ch->stages == 3 ? 3 : 0;
+  const size_t eb = elem_bytes(prog->precision);
+  char* arena = prog->arena.as<char>();
+  bind_tc(L, arena + prog_off(P, prog, ta) * eb, arena + prog_off(P, prog, tb) * eb,
+          arena + prog_off(P, prog, st.c) * eb, prog->inst_stride, prog->maxabs.as<float>(), prog->exps.as<int32_t>(),
+          prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), prog->partials.as<float2>());
+  if (!ctx->no_tma) {
+    // operands are laid out [Kt | Mt/Nt | ...] by the compiler: load tiles with TMA
+    const int kt = st.tc_bk == 32 ? 5 : 4;
+    encode_tile_map(&L.tp.tmA, L.tp.A, (int)la.size(), kt, 128, prog->inst_stride, prog->W);
+    encode_tile_map(&L.tp.tmB, L.tp.B, (int)lb.size(), kt, bn, prog->inst_stride, prog->W);
+    L.kind = K_TMA;
+    if (ctx->no_persist) L.tp.persistent = 0;
+  }
+  int common = 0;
+  for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
+  L.flops = 8.0 * std::ldexp(1.0, (int)(la.size() + lb.size()) - common);
+  L.bytes =
+      (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) + std::ldexp(1.0, (int)lc.size())) * 2.0 * double(eb);
+  return L;
+}
+
 static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W,
                                                     bool fuse) {
   const Plan& P = plan->p;
@@ -683,12 +784,13 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   prog->W = W;
   prog->n_qubits = P.net.circ.n;
   const bool fused = fuse && !P.chains.empty();
+  prog->fused = fused;
   prog->inst_stride = ((fused ? P.arena_elems_fused : P.arena_elems) + 63) & ~int64_t(63);
-  auto OFF = [&](int t) {
-    const int64_t o = fused ? P.tensors[t].offset_fused : P.tensors[t].offset;
-    if (o < 0) fail(TNC_E_PLAN, "tensor has no arena slot in this program");
-    return o;
-  };
+  auto OFF = [&](int t) { return prog_off(P, prog.get(), t); };
+  // tree-like reuse across slices (see the step maps below) needs waves of whole rows and no
+  // fused chains
+  const int sbits = (int)P.sliced.size();
+  const bool reuse_shape = !ctx->no_reuse && sbits >= 1 && sbits <= 20 && W % (int64_t(1) << sbits) == 0 && !fused;
   prog->n_slots = (int)P.tensors.size();
   prog->n_leaves = (int)P.net.leaves.size();
   const size_t eb = elem_bytes(precision);
@@ -738,33 +840,22 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
                 2.0 * double(eb);
     }
     if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
-      const int ta = st.tc_swap ? st.b : st.a, tb = st.tc_swap ? st.a : st.b;
-      // the split over K follows the plan (its slice count), not the wave size, so results do
-      // not depend on how many instances share a launch; the persistent choice uses the wave
-      make_tc_launch(L, st.tc_tile, P.tensors[ta].labels, P.tensors[tb].labels, lc, precision, st.tc_bn, st.tc_bk,
-                     split_instances(P));
-      L.tp.persistent = (st.tc_bn <= 128 && L.tp.splitk == 1 && L.tp.n_ok <= 3 &&
-                         (int64_t(1) << (L.tp.n_om + L.tp.n_on)) * W >= 4 * 152) ? 1 : 0;
-      bind_tc(L, prog->arena.as<char>() + OFF(ta) * eb, prog->arena.as<char>() + OFF(tb) * eb,
-              prog->arena.as<char>() + OFF(st.c) * eb, prog->inst_stride, prog->maxabs.as<float>(),
-              prog->exps.as<int32_t>(), prog->n_slots, ta, tb, st.c, ctx->status.as<int32_t>(), nullptr);
-      if (!ctx->no_tma) {
-        // operands are laid out [Kt | Mt/Nt | ...] by the compiler: load tiles with TMA
-        const int kt = st.tc_bk == 32 ? 5 : 4;
-        encode_tile_map(&L.tp.tmA, L.tp.A, (int)P.tensors[ta].labels.size(), kt, 128, prog->inst_stride, W);
-        encode_tile_map(&L.tp.tmB, L.tp.B, (int)P.tensors[tb].labels.size(), kt, st.tc_bn, prog->inst_stride, W);
-        L.kind = K_TMA;
-        if (ctx->no_persist) L.tp.persistent = 0;
+      StepLaunch T = tc_launch(ctx, P, prog.get(), (int)s, nullptr);
+      if (T.kind == K_TMA) {
+        // a configuration tuned for this shape (tnc_autotune) replaces the heuristics
+        const int64_t nz = reuse_shape ? (int64_t(W) >> sbits) << __builtin_popcount((uint32_t)P.tensors[st.c].dep) : W;
+        TcChoice ch;
+        if (tune_lookup(tune_key(precision, P, st, T, nz), &ch)) {
+          try {
+            T = tc_launch(ctx, P, prog.get(), (int)s, &ch);
+          } catch (const Error&) {
+            // a cached choice this step's layouts cannot take (a hand-edited cache file):
+            // the heuristics stay
+          }
+        }
       }
-      if (L.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * L.tp.splitk * L.tp.planeC);
-      {
-        int common = 0;
-        for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
-        L.flops = 8.0 * std::ldexp(1.0, (int)(la.size() + lb.size()) - common);
-        L.bytes = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) + std::ldexp(1.0, (int)lc.size())) *
-                  2.0 * double(eb);
-      }
-      prog->steps.push_back(L);
+      if (T.tp.splitk > 1) partial_elems = std::max(partial_elems, size_t(W) * T.tp.splitk * T.tp.planeC);
+      prog->steps.push_back(T);
       continue;
     }
     L.p.A = prog->arena.as<char>() + OFF(st.a) * eb;
@@ -798,9 +889,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   // and launches that map one to one onto the plan's steps (no fused chains); a call uses the
   // maps only when it covers every slice (see tnc_amplitudes).
   {
-    const int sbits = (int)P.sliced.size();
-    const bool reuse = !ctx->no_reuse && sbits >= 1 && sbits <= 20 && W % (int64_t(1) << sbits) == 0 &&
-                       chain_links.empty() && prog->steps.size() == P.steps.size();
+    const bool reuse = reuse_shape && chain_links.empty() && prog->steps.size() == P.steps.size();
     for (size_t si = 0; si < prog->steps.size(); ++si) {
       StepLaunch& L = prog->steps[si];
       InstMap m{-1, 0, 0, 0};
@@ -951,9 +1040,16 @@ tnc_status tnc_sync(tnc_context ctx) {
   });
 }
 
-tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
-                          int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
-  return guarded([&] {
+// The program a call of tnc_amplitudes ran, and whether its steps used tree-like reuse.
+struct AmpRun {
+  std::shared_ptr<DeviceProgram> prog;
+  bool reuse = false;
+  cudaStream_t stream = nullptr;
+};
+
+static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                             int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
+  {
     if (!ctx || !plan || !opts || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
     const Plan& P = plan->p;
     const int n = P.net.circ.n;
@@ -1126,7 +1222,215 @@ tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* o
       CUDA_OK(cudaStreamSynchronize(s));
       check_status(ctx);
     }
+    return AmpRun{prog, reuse, s};
+  }
+}
+
+tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                          int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
+  return guarded([&] { run_amplitudes(ctx, plan, opts, bitstrings, batch, slice_begin, slice_count, out, stream); });
+}
+
+// Times every admissible configuration of each TMA tensor-core step of `prog` at its wave
+// size (inputs: the arena as the last wave left it), installs the fastest and records it in
+// the cache under the step's shape.
+static void tune_program(tnc_context_s* ctx, const Plan& P, DeviceProgram* prog, bool reuse, cudaStream_t s,
+                         tnc_tune_info* info) {
+  const int64_t W = prog->W;
+  const int sbits = (int)P.sliced.size();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_OK(cudaEventCreate(&e0));
+  CUDA_OK(cudaEventCreate(&e1));
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  // mean device time of one launch: 3 timed launches after one untimed, 20 more when short
+  auto time_launch = [&](const StepLaunch& L) {
+    auto timed = [&](int reps) {
+      CUDA_OK(cudaEventRecord(e0, s));
+      for (int i = 0; i < reps; ++i) run_step(prog->precision, L, W, s, reuse);
+      CUDA_OK(cudaEventRecord(e1, s));
+      CUDA_OK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+      return double(ms) * 1e-3 / reps;
+    };
+    run_step(prog->precision, L, W, s, reuse);
+    double t = timed(3);
+    if (t < 2e-4) t = timed(20);
+    return t;
+  };
+  // steps of one shape share a cache entry, so they are tuned together: a configuration's
+  // time is the sum over the steps of that shape
+  std::map<std::string, std::vector<size_t>> groups;
+  std::vector<std::string> order;
+  for (size_t k = 0; k < prog->steps.size(); ++k) {
+    const StepLaunch& cur = prog->steps[k];
+    if (cur.kind != K_TMA || cur.plan_step < 0) continue;
+    const Step& st = P.steps[cur.plan_step];
+    const StepLaunch D = tc_launch(ctx, P, prog, cur.plan_step, nullptr);
+    const int64_t nz = reuse ? (W >> sbits) << __builtin_popcount((uint32_t)P.tensors[st.c].dep) : W;
+    const std::string key = tune_key(prog->precision, P, st, D, nz);
+    if (!groups.count(key)) order.push_back(key);
+    groups[key].push_back(k);
+  }
+  int tuned = 0, changed = 0, cands = 0;
+  double t_default = 0, t_tuned = 0;
+  for (const std::string& key : order) {
+    const std::vector<size_t>& ks = groups[key];
+    // the launch of step k with choice c (nullptr: heuristics), keeping its instance map
+    auto launch_of = [&](size_t k, const TcChoice* c) {
+      StepLaunch L = tc_launch(ctx, P, prog, prog->steps[k].plan_step, c);
+      L.p.im = L.tp.im = prog->steps[k].tp.im;
+      return L;
+    };
+    // a choice the layouts cannot take (e.g. an output run shorter than 3 once the tile is
+    // narrower) is rejected on the host, before anything is launched
+    auto group_time = [&](const TcChoice* c) {
+      std::vector<StepLaunch> ls;
+      try {
+        for (size_t k : ks) ls.push_back(launch_of(k, c));
+      } catch (const Error&) {
+        if (!c) throw;
+        return HUGE_VAL;
+      }
+      double t = 0;
+      for (const StepLaunch& L : ls) t += time_launch(L);
+      return t;
+    };
+    const StepLaunch D = launch_of(ks[0], nullptr);
+    const int tc_bn = P.steps[D.plan_step].tc_bn;
+    // candidates: every tile width down to 64, the persistent kernel where it applies, and
+    // splits (powers of two up to the program's partial-sum buffer) with either pipeline depth
+    std::vector<TcChoice> cc;
+    for (int bn = tc_bn; bn >= 64; bn /= 2) {
+      if (bn <= 128 && D.tp.n_ok <= 3 && !ctx->no_persist) cc.push_back(TcChoice{bn, 1, 1, 0});
+      const int64_t kit = int64_t(1) << D.tp.n_ok;
+      for (int64_t sp = 1; sp <= std::min<int64_t>(kit, 1024); sp *= 2) {
+        if (sp > 1 && size_t(W) * sp * D.tp.planeC * sizeof(float2) > prog->partials.bytes) break;
+        if (sp > 1 && kit / sp < 2) break;
+        if (bn == 256) {
+          cc.push_back(TcChoice{bn, 0, (int)sp, 0});
+        } else {
+          cc.push_back(TcChoice{bn, 0, (int)sp, 1});
+          if (kit / sp <= 8) cc.push_back(TcChoice{bn, 0, (int)sp, 3});
+        }
+      }
+    }
+    const double td = group_time(nullptr);
+    double best_t = td;
+    TcChoice best;
+    bool have = false;
+    for (const TcChoice& c : cc) {
+      const double t = group_time(&c);
+      ++cands;
+      if (t < best_t) best_t = t, best = c, have = true;
+    }
+    tuned += (int)ks.size();
+    t_default += td;
+    // keep the heuristics unless a choice is clearly faster (3%: timing noise)
+    const bool take = have && best_t < 0.97 * td;
+    for (size_t k : ks) prog->steps[k] = launch_of(k, take ? &best : nullptr);
+    t_tuned += take ? best_t : td;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (take) {
+      changed += (int)ks.size();
+      g_tune[key] = best;
+    } else {
+      g_tune.erase(key);
+    }
+  }
+  // captured waves hold the old launch parameters
+  for (auto& kv : prog->graphs) cudaGraphExecDestroy(kv.second);
+  prog->graphs.clear();
+  prog->graph_seen.clear();
+  CUDA_OK(cudaStreamSynchronize(s));
+  check_status(ctx);
+  if (info) {
+    info->steps_tuned = tuned;
+    info->steps_changed = changed;
+    info->candidates = cands;
+    info->seconds_default = t_default;
+    info->seconds_tuned = t_tuned;
+  }
+}
+
+tnc_status tnc_autotune(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                        int64_t batch, int64_t slice_begin, int64_t slice_count, tnc_tune_info* info) {
+  return guarded([&] {
+    if (!ctx || !plan || !opts) fail(TNC_E_INVALID_ARG, "NULL argument");
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (batch < 1) fail(TNC_E_INVALID_ARG, "batch must be >= 1");
+    const int64_t n_out = int64_t(1) << plan->p.net.open_qubits.size();
+    std::vector<double> out(size_t(batch) * n_out * 2);
+    AmpRun r = run_amplitudes(ctx, plan, opts, bitstrings, batch, slice_begin, slice_count, out.data(), nullptr);
+    tune_program(ctx, plan->p, r.prog.get(), r.reuse, r.stream, info);
   });
+}
+
+tnc_status tnc_tune_save(const char* path) {
+  return guarded([&] {
+    if (!path) fail(TNC_E_INVALID_ARG, "NULL path");
+    std::string text = "tnc-tune 1\n";
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (const auto& kv : g_tune)
+        text += kv.first + " " + std::to_string(kv.second.bn) + " " + std::to_string(kv.second.persistent) + " " +
+                std::to_string(kv.second.split) + " " + std::to_string(kv.second.stages) + "\n";
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) fail(TNC_E_IO, std::string("cannot write ") + tmp);
+    const bool ok = std::fwrite(text.data(), 1, text.size(), f) == text.size();
+    if (std::fclose(f) != 0 || !ok) fail(TNC_E_IO, std::string("cannot write ") + tmp);
+    if (std::rename(tmp.c_str(), path) != 0) fail(TNC_E_IO, std::string("cannot rename to ") + path);
+  });
+}
+
+tnc_status tnc_tune_load(const char* path) {
+  return guarded([&] {
+    if (!path) fail(TNC_E_INVALID_ARG, "NULL path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) fail(TNC_E_IO, std::string("cannot read ") + path);
+    std::map<std::string, TcChoice> got;
+    char line[512];
+    bool header = false, bad = false;
+    while (std::fgets(line, sizeof line, f)) {
+      if (!header) {
+        header = std::strncmp(line, "tnc-tune 1", 10) == 0;
+        if (!header) bad = true;
+        if (bad) break;
+        continue;
+      }
+      char key[256];
+      TcChoice c;
+      if (std::sscanf(line, "%255s %d %d %d %d", key, &c.bn, &c.persistent, &c.split, &c.stages) != 5 ||
+          (c.bn != 64 && c.bn != 128 && c.bn != 256) || (c.persistent != 0 && c.persistent != 1) || c.split < 0 ||
+          c.split > 1024 || (c.split & (c.split - 1)) || (c.stages != 0 && c.stages != 1 && c.stages != 3)) {
+        bad = true;
+        break;
+      }
+      got[key] = c;
+    }
+    std::fclose(f);
+    if (bad || !header) fail(TNC_E_IO, std::string("not a tuning cache: ") + path);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : got) g_tune[kv.first] = kv.second;
+  });
+}
+
+void tnc_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+}
+
+int64_t tnc_tune_size(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int64_t)g_tune.size();
 }
 
 tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32_t rank_a, const int32_t* labels_a,

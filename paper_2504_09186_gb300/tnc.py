@@ -71,6 +71,18 @@ class tnc_plan_info(C.Structure):
     ]
 
 
+class tnc_tune_info(C.Structure):
+    _fields_ = [
+        ("steps_tuned", C.c_int32),
+        ("steps_changed", C.c_int32),
+        ("candidates", C.c_int32),
+        ("reserved0", C.c_int32),
+        ("seconds_default", C.c_double),
+        ("seconds_tuned", C.c_double),
+        ("reserved", C.c_double * 4),
+    ]
+
+
 class tnc_exec_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32),
@@ -118,6 +130,9 @@ def load_library(path: str = LIB_PATH):
                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
         "tnc_profile_read": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_double),
                              C.POINTER(C.c_double), C.POINTER(C.c_int32), i32, C.POINTER(C.c_int32)],
+        "tnc_autotune": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, i64, i64, C.POINTER(tnc_tune_info)],
+        "tnc_tune_save": [C.c_char_p],
+        "tnc_tune_load": [C.c_char_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -127,6 +142,10 @@ def load_library(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = [vp]
         f.restype = None
+    lib.tnc_tune_clear.argtypes = []
+    lib.tnc_tune_clear.restype = None
+    lib.tnc_tune_size.argtypes = []
+    lib.tnc_tune_size.restype = C.c_int64
     lib.tnc_last_error.restype = C.c_char_p
     lib.tnc_last_error.argtypes = []
     lib.tnc_version.restype = C.c_char_p
@@ -307,6 +326,28 @@ class Context:
                                   C.c_void_p(ptr), C.c_void_p(stream)))
         return out
 
+    def autotune(self, plan: Plan, bitstrings: Optional[np.ndarray], precision: str = "chalf",
+                 slice_begin: int = 0, slice_count: Optional[int] = None, wave: int = 0, fuse: bool = True) -> dict:
+        """Time the admissible configurations of every tensor-core step of the program this
+        call shape uses and keep the fastest (tnc_autotune).  Returns the tuning counts."""
+        lib = load_library()
+        info = plan.info()
+        if slice_count is None:
+            slice_count = (1 << info["n_sliced"]) - slice_begin
+        if bitstrings is None:
+            batch, bp = 1, None
+        else:
+            bs = np.ascontiguousarray(bitstrings, dtype=np.uint8)
+            if bs.ndim == 1:
+                bs = bs[None, :]
+            batch, bp = bs.shape[0], bs.ctypes.data_as(C.POINTER(C.c_uint8))
+        opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave, 0,
+                             int(fuse), 0)
+        ti = tnc_tune_info()
+        _check(lib.tnc_autotune(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count, C.byref(ti)))
+        return {k: getattr(ti, k) for k in ("steps_tuned", "steps_changed", "candidates", "seconds_default",
+                                             "seconds_tuned")}
+
     def adjoint(self, plan: Plan, bitstrings: Optional[np.ndarray], weights: np.ndarray, arities, stream: int = 0,
                 memory_mib: int = 0):
         """Gate environments dL/dU_g of L = sum_{b,i} weights[b, i] * amp[b, i] (holomorphic
@@ -389,3 +430,21 @@ def tnc_contract_noalloc(precision, a, labels_a, b, labels_b, c, labels_c, strea
 
 def version() -> str:
     return load_library().tnc_version().decode()
+
+
+def tune_save(path: str) -> None:
+    """Write the process-wide tuning cache to `path` (tnc_tune_save)."""
+    _check(load_library().tnc_tune_save(path.encode()))
+
+
+def tune_load(path: str) -> None:
+    """Merge the tuning cache file at `path` into the process-wide cache (tnc_tune_load)."""
+    _check(load_library().tnc_tune_load(path.encode()))
+
+
+def tune_clear() -> None:
+    load_library().tnc_tune_clear()
+
+
+def tune_size() -> int:
+    return int(load_library().tnc_tune_size())

@@ -154,3 +154,35 @@ def test_plan_objectives_pick_their_own_minimum():
     assert pt["model_seconds_per_slice"] * 2 ** pt["n_sliced"] <= pf["model_seconds_per_slice"] * 2 ** pf["n_sliced"] * (1 + 1e-12)
     assert pf["log2_total_flops"] <= pt["log2_total_flops"] + 1e-12
     assert pf["model_seconds_per_slice"] > 0
+
+
+def test_tuning_cache_file_roundtrip_and_rejection(tmp_path):
+    """The autotuner's cache file: load merges entries, save writes them back in key order,
+    and a malformed file is rejected without changing the cache."""
+    T.load_library()
+    T.tune_clear()
+    assert T.tune_size() == 0
+    src = tmp_path / "tune.txt"
+    src.write_text("tnc-tune 1\n"
+                   "p1.a30.b28.c26.bn256.bk32.om3.on2.ok10.d1.z4096 128 1 1 0\n"
+                   "p2.a20.b18.c16.bn128.bk16.om1.on1.ok6.d0.z64 64 0 4 3\n")
+    T.tune_load(str(src))
+    assert T.tune_size() == 2
+    out = tmp_path / "saved.txt"
+    T.tune_save(str(out))
+    assert out.read_text() == src.read_text()
+    for bad in ("tnc-tune 2\n",                                   # unknown version
+                "tnc-tune 1\nkey 96 0 1 0\n",                     # tile width not 64/128/256
+                "tnc-tune 1\nkey 128 0 3 0\n",                    # split not a power of two
+                "tnc-tune 1\nkey 128 2 1 0\n",                    # persistent not 0/1
+                "tnc-tune 1\nkey 128 0 1 2\n",                    # unknown pipeline depth
+                "tnc-tune 1\nkey 128 0\n"):                       # short line
+        f = tmp_path / "bad.txt"
+        f.write_text(bad)
+        with pytest.raises(T.TncError):
+            T.tune_load(str(f))
+        assert T.tune_size() == 2
+    with pytest.raises(T.TncError):
+        T.tune_load(str(tmp_path / "missing.txt"))
+    T.tune_clear()
+    assert T.tune_size() == 0

@@ -54,3 +54,37 @@ def test_s30_all_slices_against_statevector(s30):
     f_ref = metrics.xeb_weighted(p_ref, p_ref, 30)
     f_half = metrics.xeb_weighted(p_ref, np.abs(half) ** 2, 30)
     assert abs(f_half - f_ref) <= 0.01 * abs(f_ref)
+
+
+@pytest.fixture
+def clean_tuning_cache():
+    T.load_library()
+    T.tune_clear()
+    yield
+    T.tune_clear()
+
+
+def test_s30_autotuned_against_statevector(s30, tmp_path, clean_tuning_cache):
+    """Tile configurations chosen by timing keep parity, runs stay deterministic, and a
+    program built later from the saved cache runs the same configurations bit for bit."""
+    _, fixed, p = s30
+    ctx = T.Context(0)
+    ref = _golden()
+    info = ctx.autotune(p, fixed[None, :], "chalf")
+    assert info["steps_tuned"] > 0 and info["candidates"] >= info["steps_tuned"]
+    assert info["seconds_tuned"] <= info["seconds_default"] * (1 + 1e-9)
+    tuned = ctx.amplitudes(p, fixed[None, :], "chalf")[0]
+    assert np.array_equal(tuned, ctx.amplitudes(p, fixed[None, :], "chalf")[0])
+    assert metrics.rel_err_norm(tuned, ref) <= 1e-2
+    p_ref = np.abs(ref) ** 2
+    f_ref = metrics.xeb_weighted(p_ref, p_ref, 30)
+    assert abs(metrics.xeb_weighted(p_ref, np.abs(tuned) ** 2, 30) - f_ref) <= 0.01 * abs(f_ref)
+    path = tmp_path / "tune.txt"
+    T.tune_save(str(path))
+    n = T.tune_size()
+    assert n <= info["steps_changed"]
+    T.tune_clear()
+    T.tune_load(str(path))
+    assert T.tune_size() == n
+    ctx2 = T.Context(0)  # a new context builds its own program from the cache
+    assert np.array_equal(ctx2.amplitudes(p, fixed[None, :], "chalf")[0], tuned)
