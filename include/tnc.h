@@ -147,7 +147,8 @@ tnc_status tnc_plan_update_gates(tnc_plan p, int64_t n_gates, const double* matr
 /* The whole plan as JSON text (network edges as [qubit, cut, kind, open], leaves with
  * their labels and gates, sliced edge ids, the tree as SSA pairs over tensor ids, every
  * tensor's labels in storage order and arena offset, the compiled steps with their
- * tiles).  Writes at most cap bytes including the terminating NUL; *len receives the
+ * tiles; a tensor-core step also has "tc_tile": its row / column roles ("swap": rows from
+ * operand b), tile width and depth and label sets).  Writes at most cap bytes including the terminating NUL; *len receives the
  * full size including the NUL, so a call with buf == NULL queries the size. */
 tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len);
 
@@ -267,7 +268,8 @@ tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, doub
  * admissible configurations are the ones its compiled operand layouts support:
  *  - tile widths of 256, 128 or 64 columns, at most the compiled width (a narrower tile
  *    loads a prefix of the compiled column labels; the rest become outer labels);
- *  - the persistent kernel (width <= 128, at most 3 outer common labels);
+ *  - the persistent kernels (width <= 128 with two TMEM buffers; width 256 with the direct
+ *    epilogue, one TMEM buffer handed back once drained into registers);
  *  - splits over the outer common labels, powers of two whose FP32 partial sums fit the
  *    program's partial-sum buffer;
  *  - a three-stage or a deep operand pipeline.
@@ -287,8 +289,9 @@ typedef struct {
  * discarding the result.  It then times the admissible configurations of every TMA
  * tensor-core step of the program that call used:
  *  - each at the call's wave size, on the call's stream;
- *  - one untimed launch, then 3 timed launches (23 when a launch is under 0.2 ms).
- * A step takes the fastest configuration only if it beats the heuristics by 3% or more.
+ *  - one untimed launch, then 3 timed launches (23 when a launch is under 0.2 ms);
+ *  - all configurations of a step in turn, three rounds, each keeping its fastest round.
+ * A step takes the fastest configuration only if it beats the heuristics by 5% or more.
  * The choice is recorded in a process-wide cache keyed by the step's shape:
  *  - precision;
  *  - operand and result ranks;

@@ -242,7 +242,15 @@ tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
            ",\"No\":" + jlist(t.No) + ",\"splitk\":" + std::to_string(t.splitk) + ",\"rm\":" + std::to_string(t.rm) +
            ",\"rn\":" + std::to_string(t.rn) + ",\"kgroups\":" + std::to_string(t.kgroups) +
            ",\"tc\":" + std::to_string(S.tc_ok ? 1 : 0) + ",\"chain\":" +
-           std::to_string(i < P.step_chain.size() ? P.step_chain[i] : -1) + "}";
+           std::to_string(i < P.step_chain.size() ? P.step_chain[i] : -1);
+      if (S.tc_ok) {
+        const TileSpec& u = S.tc_tile;
+        s += ",\"tc_tile\":{\"swap\":" + std::to_string(S.tc_swap ? 1 : 0) + ",\"bn\":" + std::to_string(S.tc_bn) +
+             ",\"bk\":" + std::to_string(S.tc_bk) + ",\"Mt\":" + jlist(u.Mt) + ",\"Kt\":" + jlist(u.Kt) +
+             ",\"Nt\":" + jlist(u.Nt) + ",\"Mo\":" + jlist(u.Mo) + ",\"Ko\":" + jlist(u.Ko) + ",\"No\":" + jlist(u.No) +
+             "}";
+      }
+      s += "}";
     }
     char num[64];
     std::snprintf(num, sizeof(num), "%.17g", P.log2_flops_slice);

@@ -312,6 +312,22 @@ void compile_plan(Plan& plan, bool fuse) {
   };
   std::vector<TcDec> dec(n_tree);
   std::vector<std::vector<int>> req(L + n_tree);  // required leading labels of each intermediate
+  // Which operand of intermediate t's producer contributes label x (0: the tree node's first,
+  // 1: its second), and whether that producer can take the labels from that operand as its
+  // tile columns: from the smaller operand as is, from the larger one by swapping roles,
+  // which needs 7 row labels from the other side (the role rule below).
+  auto side_of = [&](int t, int x) { return contains(sets[plan.tree[t - n_leaves].first], x) ? 0 : 1; };
+  auto columns_ok = [&](int t, int sd) {
+    const auto& P0 = sets[plan.tree[t - n_leaves].first];
+    const auto& P1 = sets[plan.tree[t - n_leaves].second];
+    const int larger = P1.size() > P0.size() ? 1 : 0;
+    if (sd != larger) return true;
+    std::vector<int> Kp;
+    std::set_intersection(P0.begin(), P0.end(), P1.begin(), P1.end(), std::back_inserter(Kp));
+    const size_t free_larger = (larger ? P1.size() : P0.size()) - Kp.size();
+    const size_t free_smaller = (larger ? P0.size() : P1.size()) - Kp.size();
+    return free_smaller >= 7 && free_larger >= 6;
+  };
   for (int s = n_tree - 1; s >= 0; --s) {
     int a = plan.tree[s].first, b = plan.tree[s].second;
     if (sets[b].size() > sets[a].size()) std::swap(a, b);  // same roles as the layouts below
@@ -345,7 +361,39 @@ void compile_plan(Plan& plan, bool fuse) {
     const size_t kt0 = d.bk == 32 ? 5 : 4;
     d.bn = (N.size() >= 8 && K.size() > kt0 + 3) ? 256 : (N.size() >= 7 ? 128 : 64);
     const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : 6);
-    d.t.Kt.assign(K.begin(), K.begin() + kt);
+    // K-tile order: Kt[0..3] become the lowest positions of both operands, i.e. of both
+    // producers' results.  A producer stores its tiles straight from registers (direct
+    // epilogue) when its result's positions 0..2 are tile columns and position 3 a tile row:
+    // three labels from one of its operands, the fourth from the other.  Take such labels
+    // for both producers where K allows it, else for the larger operand's producer.
+    std::vector<int> Kord = K;
+    {
+      int best = -1;
+      std::vector<int> pick;
+      for (int both = 1; both >= 0 && best < 0; --both)
+        for (int sa = 0; sa < 2; ++sa)
+          for (int sb = 0; sb < 2; ++sb) {
+            if (!both && sb == 1) continue;
+            std::vector<int> g, opp;
+            for (int x : K) {
+              const int xa = side_of(a, x), xb = side_of(b, x);
+              if (xa == sa && (!both || xb == sb)) g.push_back(x);
+              else if (xa != sa && (!both || xb != sb)) opp.push_back(x);
+            }
+            if (g.size() < 3 || opp.empty()) continue;
+            const int score = (columns_ok(a, sa) ? 1 : 0) + (both && columns_ok(b, sb) ? 1 : 0);
+            if (score > best) {
+              best = score;
+              pick = {g[0], g[1], g[2], opp[0]};
+            }
+          }
+      if (best >= 0) {
+        Kord = pick;
+        for (int x : K)
+          if (!contains(pick, x)) Kord.push_back(x);
+      }
+    }
+    d.t.Kt.assign(Kord.begin(), Kord.begin() + kt);
     // the result's leading labels first, in their order: the lowest result positions are
     // then the lowest canonical column / row bits (runs per thread, adjacent rows per warp)
     for (size_t j = 0; j < rq.size(); ++j) {
@@ -360,7 +408,7 @@ void compile_plan(Plan& plan, bool fuse) {
       if (!contains(d.t.Mt, x)) d.t.Mo.push_back(x);
     for (int x : N)
       if (!contains(d.t.Nt, x)) d.t.No.push_back(x);
-    for (int x : K)
+    for (int x : Kord)
       if (!contains(d.t.Kt, x)) d.t.Ko.push_back(x);
     if (d.t.Mt.size() != 7 || d.t.Nt.size() != nt || d.t.Mo.size() + d.t.No.size() > 30 || d.t.Ko.size() > 24) continue;
     req[a] = d.t.Kt;

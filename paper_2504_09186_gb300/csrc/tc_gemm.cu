@@ -208,6 +208,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Two values converted as Conv<T>::from_f does, packed low-first (the byte order of two
+// consecutive entries in memory).
+template <typename T>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  const T x = Conv<T>::from_f(a), y = Conv<T>::from_f(b);
+  uint16_t ux, uy;
+  memcpy(&ux, &x, 2);
+  memcpy(&uy, &y, 2);
+  return uint32_t(ux) | (uint32_t(uy) << 16);
+}
+
 // Eight 16-bit values, one 16-byte store.
 template <typename T>
 struct alignas(16) Vec8 {
@@ -1007,6 +1030,298 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
 }
 
+// Persistent variant for 256-wide tiles with the direct epilogue (tile columns 0..2 at C
+// positions 0..2, row 0 at position 3).  The two accumulators of a 128 x 256 tile take all
+// 512 TMEM columns, so there is one buffer.  The epilogue drains it into registers (each
+// thread: one row, 128 columns of Dr and of Di, scaled and converted to 16-bit pairs, 128
+// registers), hands TMEM back to the MMA warp at once, and stores from registers while the
+// next tile's MMAs run.  The producer runs ahead through the ring, so the next tile's loads
+// are in flight during the drain.  Warps 0..7: epilogue (TMEM lane quadrant warp & 3,
+// column half warp >> 2); warp 8: TMA producer; warp 9: MMA issuer.
+template <int BK>
+struct TcwShape {
+  static constexpr int BN = 256;
+  static constexpr int ROWB = BK * 2;
+  static constexpr int A_BYTES = TC_BM * ROWB;
+  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int NST = (192 * 1024) / STAGE > 8 ? 8 : (192 * 1024) / STAGE;
+  static constexpr int PIPE = NST * STAGE;
+  static constexpr int SBO = 8 * ROWB;
+  static constexpr int LAYOUT = BK == 32 ? 4 : 6;  // SW64 / SW32
+  static constexpr int C_BITS = 15;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int EW = 8;                     // epilogue warps
+  static constexpr int THREADS = EW * 32 + 64;     // + producer warp + MMA warp
+  static constexpr int HOLD = 64;                  // columns per thread held in registers
+  static_assert(NST >= 3, "pipeline");
+};
+
+template <typename T, int BK>
+__global__ void __launch_bounds__(TcwShape<BK>::THREADS, 1) k_tc_tma_wide(const __grid_constant__ TcParams p) {
+  using S = TcwShape<BK>;
+  constexpr int BN = 256, KT = BK == 32 ? 5 : 4, NST = S::NST, NT = S::THREADS, ET = S::EW * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::PIPE);  // [2^(C_BITS - runC)]
+  const int nhC = 1 << (S::C_BITS - p.runC);
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);       // [128]
+  uint16_t* TCn = TCm + TC_BM;                                   // [256]
+  uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NST;
+  uint64_t* tfull = bars + 2 * NST;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* done = tempty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);                   // [EW]
+  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + S::EW);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int prod_warp = S::EW, mma_warp = S::EW + 1;
+  for (int r = tid; r < TC_BM; r += NT) {
+    uint32_t cm = 0;
+    for (int j = 0; j < 7; ++j)
+      if ((r >> j) & 1) cm |= 1u << p.pCm[j];
+    TCm[r] = (uint16_t)stg_swz(cm);
+  }
+  for (int r = tid; r < BN; r += NT) {
+    uint32_t cn = 0;
+    for (int j = 0; j < 8; ++j)
+      if ((r >> j) & 1) cn |= 1u << p.pCn[j];
+    TCn[r] = (uint16_t)stg_swz(cn);
+  }
+  for (int h = tid; h < nhC; h += NT) {
+    uint32_t m = p.maskC;
+    for (int i = 0; i < p.runC; ++i) m &= m - 1;
+    uint32_t r = 0, x = (uint32_t)h;
+    while (m) {
+      const uint32_t low = m & (~m + 1u);
+      if (x & 1u) r |= low;
+      x >>= 1;
+      m &= m - 1;
+    }
+    hiC[h] = r;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(tfull), 1);
+    mbar_init(smem_u32(tempty), 1);
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int tile_bits = p.n_om + p.n_on;
+  const int64_t n_tiles = (int64_t(p.n_inst)) << tile_bits;
+  const uint32_t tile_mask = (1u << tile_bits) - 1u;
+  const int k_iters = 1 << p.n_ok;
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
+
+  if (warp == prod_warp) {
+    if (lane == 0) {
+      // TMA producer (as in k_tc_tma_persist)
+      int64_t g = 0, issued = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const Inst3 It = map_inst(t >> tile_bits, p.im);
+        const uint32_t r = (uint32_t)t & tile_mask;
+        const uint32_t on = r & ((1u << p.n_on) - 1u);
+        const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
+        int64_t oA = 0, oB = 0;
+        for (int j = 0; j < p.n_om; ++j)
+          if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j];
+        for (int j = 0; j < p.n_on; ++j)
+          if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j];
+        for (int it = 0; it < k_iters; ++it, ++g) {
+          const int buf = (int)(g % NST);
+          if (g >= NST && !mbar_wait_bounded(smem_u32(&empty[buf]), (uint32_t)(((g / NST) - 1) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          int64_t okA = 0, okB = 0;
+          for (int j = 0; j < p.n_ok; ++j)
+            if ((it >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+          const int rowA = (int)((oA + okA) >> KT), rowB = (int)((oB + okB) >> KT);
+          const uint32_t st = sbase + buf * S::STAGE;
+          const uint32_t fb = smem_u32(&full[buf]);
+          mbar_arrive_expect_tx(fb, S::STAGE);
+          tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)It.a, fb);
+          tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)It.a, fb);
+          tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)It.b, fb);
+          tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)It.b, fb);
+          issued = g + 1;
+        }
+      }
+      for (int64_t x = issued - NST > 0 ? issued - NST : 0; x < issued; ++x)
+        if (!mbar_wait_bounded(smem_u32(&full[x % NST]), (uint32_t)((x / NST) & 1), p.status)) ok = false;
+    }
+  } else if (warp == mma_warp) {
+    if (lane == 0) {
+      // MMA issuer: tile j waits until the epilogue has drained tile j - 1
+      const uint32_t id_pos = instr_desc(p.bf16, 0, BN), id_neg = instr_desc(p.bf16, 1, BN);
+      int64_t g = 0;
+      int64_t j = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++j) {
+        if (j >= 1 && !mbar_wait_bounded(smem_u32(tempty), (uint32_t)((j - 1) & 1), p.status)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        for (int it = 0; it < k_iters; ++it, ++g) {
+          const int buf = (int)(g % NST);
+          if (!mbar_wait_bounded(smem_u32(&full[buf]), (uint32_t)((g / NST) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t st = sbase + buf * S::STAGE;
+#pragma unroll
+          for (int jj = 0; jj < BK / 16; ++jj) {
+            const uint64_t ar = kmajor_desc(st + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t ai = kmajor_desc(st + S::A_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t br = kmajor_desc(st + 2 * S::A_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint64_t bi = kmajor_desc(st + 2 * S::A_BYTES + S::B_BYTES + jj * 32, S::SBO, S::LAYOUT);
+            const uint32_t first = (it == 0 && jj == 0) ? 0u : 1u;
+            mma_f16(tmem, ar, br, id_pos, first);
+            mma_f16(tmem, ai, bi, id_neg, 1u);
+            mma_f16(tmem + BN, ar, bi, id_pos, first);
+            mma_f16(tmem + BN, ai, br, id_pos, 1u);
+          }
+          mma_commit(smem_u32(&empty[buf]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(tfull));
+      }
+      mma_commit(smem_u32(done));
+      if (!mbar_wait_bounded(smem_u32(done), 0u, p.status)) ok = false;
+    }
+  } else {
+    // epilogue: thread = one TMEM lane (row), 128 columns of Dr and of Di
+    const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+    const int row = (warp & 3) * 32 + lane;
+    const int col0 = (warp >> 2) * 128;
+    const uint32_t lowmask = (1u << p.runC) - 1u;
+    int64_t j = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++j) {
+      if (tid == 0) flag[0] = mbar_wait_bounded(smem_u32(tfull), (uint32_t)(j & 1), p.status) ? 1 : 0;
+      group_bar<ET>(1);
+      if (flag[0] == 0) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const Inst3 It = map_inst(t >> tile_bits, p.im);
+      const uint32_t r = (uint32_t)t & tile_mask;
+      const uint32_t on = r & ((1u << p.n_on) - 1u);
+      const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
+      int64_t oC = 0;
+      for (int q = 0; q < p.n_om; ++q)
+        if ((om >> q) & 1u) oC += int64_t(1) << p.om_C[q];
+      for (int q = 0; q < p.n_on; ++q)
+        if ((on >> q) & 1u) oC += int64_t(1) << p.on_C[q];
+      const int64_t sa = It.a * p.n_slots, sbb = It.b * p.n_slots, sc = It.c * p.n_slots;
+      int sh = 0;
+      {
+        const float a = p.maxabs[sa + p.slotA], bb = p.maxabs[sbb + p.slotB];
+        if (a > 0.f && bb > 0.f) {
+          int ea, eb;
+          frexpf(a, &ea);
+          frexpf(bb, &eb);
+          sh = ea + eb + p.nK + 1 - 15;
+        }
+      }
+      const float scale = ldexpf(1.f, -sh);
+      float mx = 0.f;
+      const uint32_t rm = TCm[row];
+      T* Cre = reinterpret_cast<T*>(p.C) + It.c * p.strideC + oC;
+      // columns 8g..8g+7 of the row are 8 consecutive entries of C: one 16-byte store each
+      auto store8 = [&](int col, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t i0, uint32_t i1,
+                        uint32_t i2, uint32_t i3) {
+        const uint32_t x = stg_swz(rm ^ TCn[col]);  // C-tile index, low 3 bits 0
+        const uint32_t off = hiC[x >> p.runC] + (x & lowmask);
+        *reinterpret_cast<uint4*>(Cre + off) = make_uint4(r0, r1, r2, r3);
+        *reinterpret_cast<uint4*>(Cre + p.planeC + off) = make_uint4(i0, i1, i2, i3);
+      };
+      // drain the first 128 - HOLD columns storing as it goes, then the last HOLD columns
+      // into registers; TMEM is handed back before those are stored
+      constexpr int HOLD = TcwShape<BK>::HOLD;
+#pragma unroll 1
+      for (int c = 0; c < 128 - HOLD; c += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(tmem + lane_addr + col0 + c, vr);
+        tmem_ld16(tmem + lane_addr + BN + col0 + c, vi);
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          uint32_t a[4], b[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int v = 8 * g + 2 * q;
+            a[q] = pack2<T>(vr[v] * scale, vr[v + 1] * scale);
+            b[q] = pack2<T>(vi[v] * scale, vi[v + 1] * scale);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(vr[v]), fabsf(vr[v + 1])), fmaxf(fabsf(vi[v]), fabsf(vi[v + 1]))));
+          }
+          store8(col0 + c + 8 * g, a[0], a[1], a[2], a[3], b[0], b[1], b[2], b[3]);
+        }
+      }
+      uint32_t pr[HOLD / 2 + 1], pi[HOLD / 2 + 1];
+#pragma unroll
+      for (int c = 0; c < HOLD; c += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(tmem + lane_addr + col0 + 128 - HOLD + c, vr);
+        tmem_ld16(tmem + lane_addr + BN + col0 + 128 - HOLD + c, vi);
+#pragma unroll
+        for (int q = 0; q < 16; q += 2) {
+          pr[(c + q) >> 1] = pack2<T>(vr[q] * scale, vr[q + 1] * scale);
+          pi[(c + q) >> 1] = pack2<T>(vi[q] * scale, vi[q + 1] * scale);
+          mx = fmaxf(mx, fmaxf(fmaxf(fabsf(vr[q]), fabsf(vr[q + 1])), fmaxf(fabsf(vi[q]), fabsf(vi[q + 1]))));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      group_bar<ET>(1);
+      if (tid == 0) mbar_arrive(smem_u32(tempty));
+#pragma unroll
+      for (int g = 0; g < HOLD / 8; ++g)
+        store8(col0 + 128 - HOLD + 8 * g, pr[4 * g], pr[4 * g + 1], pr[4 * g + 2], pr[4 * g + 3], pi[4 * g],
+               pi[4 * g + 1], pi[4 * g + 2], pi[4 * g + 3]);
+      mx *= scale * (1.f + 0x1p-8f);  // bound on the stored maximum (see tc_epilogue)
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) red[warp] = mx;
+      group_bar<ET>(1);
+      if (tid == 0) {
+        float m = 0.f;
+        for (int w = 0; w < S::EW; ++w) m = fmaxf(m, red[w]);
+        atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+        if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
+}
+
+template <int BK>
+size_t tma_wide_smem_bytes_t(int runC) {
+  using S = TcwShape<BK>;
+  return 1024 + S::PIPE + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + 256) * 2 + 16 + (2 * S::NST + 3) * 8 + 16 +
+         S::EW * 4 + 16 + 64;
+}
+
 template <int BN, int BK, int NG>
 size_t tma_persist_smem_bytes_t(int runC) {
   using S = TcpShape<BN, BK, NG>;
@@ -1032,6 +1347,17 @@ cudaError_t launch_tma_persist_ng(const TcParams& p, cudaStream_t s) {
   const int64_t tiles = int64_t(p.n_inst) << (p.n_om + p.n_on);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count_cached());
   k_tc_tma_persist<T, BN, BK, NG><<<grid, TcpShape<BN, BK, NG>::THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, int BK>
+cudaError_t launch_tma_wide(const TcParams& p, cudaStream_t s) {
+  const size_t smem = tma_wide_smem_bytes_t<BK>(p.runC);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_wide<T, BK>), smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = int64_t(p.n_inst) << (p.n_om + p.n_on);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count_cached());
+  k_tc_tma_wide<T, BK><<<grid, TcwShape<BK>::THREADS, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -1068,6 +1394,9 @@ cudaError_t launch_tma_st(const TcParams& p, dim3 grid, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_tma_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
   if (p.persistent && p.splitk == 1 && p.n_inst >= 1) {
+    // 256-wide tiles: only with the direct epilogue (no room for a staging buffer)
+    if (p.bn == 256 && p.direct && p.runC >= 3 && p.bk == 32) return launch_tma_wide<T, 32>(p, s);
+    if (p.bn == 256 && p.direct && p.runC >= 3 && p.bk == 16) return launch_tma_wide<T, 16>(p, s);
     if (p.bn == 128 && p.bk == 32) return launch_tma_persist_t<T, 128, 32>(p, s);
     if (p.bn == 128 && p.bk == 16) return launch_tma_persist_t<T, 128, 16>(p, s);
     if (p.bn == 64 && p.bk == 32) return launch_tma_persist_t<T, 64, 32>(p, s);

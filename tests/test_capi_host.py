@@ -186,3 +186,31 @@ def test_tuning_cache_file_roundtrip_and_rejection(tmp_path):
         T.tune_load(str(tmp_path / "missing.txt"))
     T.tune_clear()
     assert T.tune_size() == 0
+
+
+def test_tensor_core_layouts_allow_direct_epilogues():
+    """The compiler orders a tensor-core step's K tile so that its operands' producers store
+    their results straight from registers: positions 0..2 of such a result are the producer's
+    first three tile columns and position 3 its first tile row.  On the 30-qubit plan the two
+    largest steps and most of the others qualify."""
+    c = grid_circuit(5, 6, 14, seed=1)
+    fixed, open_q = subcube_spec(30, 10, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=64, log2_cap=26, slices_min=6, slices_max=6)
+    d = p.describe()
+    ten = d["tensors"]
+    tc = [s for s in d["steps"] if s["tc"]]
+    assert tc
+    direct = []
+    for s in tc:
+        t = s["tc_tile"]
+        la, lb, lc = ten[s["a"]]["labels"], ten[s["b"]]["labels"], ten[s["c"]]["labels"]
+        rows, cols = (lb, la) if t["swap"] else (la, lb)
+        kt, nt = len(t["Kt"]), {64: 6, 128: 7, 256: 8}[t["bn"]]
+        # operands lead with Kt then Mt / Nt (the TMA boxes)
+        assert rows[:kt] == t["Kt"] and cols[:kt] == t["Kt"]
+        assert rows[kt:kt + 7] == t["Mt"] and cols[kt:kt + nt] == t["Nt"]
+        log2_flops = len(set(la) | set(lb))
+        direct.append((log2_flops, lc[:3] == t["Nt"][:3] and lc[3] == t["Mt"][0]))
+    direct.sort()
+    assert direct[-1][1] and direct[-2][1]
+    assert sum(dr for _, dr in direct) >= 0.75 * len(direct)

@@ -164,6 +164,29 @@ def test_tma_persistent_kernel(ctx, precision, shape, direct, monkeypatch):
     assert np.array_equal(got, ref)
 
 
+# 256-wide tiles with the direct epilogue over >= 2 x 152 output tiles take the persistent
+# kernel with one TMEM buffer: it drains the accumulators (half stored at once, half held in
+# registers), hands TMEM back and stores while the next tile's MMAs run.  2^4 .. 2^7 K tiles
+# of 32 per output tile; one to sixteen tiles across N.
+WIDE_SHAPES = [(14, 12, 10), (13, 9, 11), (15, 9, 9), (12, 10, 12), (16, 9, 8)]
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape", WIDE_SHAPES)
+def test_tma_persistent_wide_kernel(ctx, precision, shape, monkeypatch):
+    a, la, b, lb, lc = tma_case(*shape, seed=5 * sum(shape) + shape[1], direct=True)
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 5  # the persistent kernel ran
+    idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(8).integers(0, len(got), 510)]))
+    assert metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx)) <= TOL[precision]
+    # every tile bit for bit against the one-CTA-per-tile kernel
+    monkeypatch.setenv("TNC_NO_PERSIST", "1")
+    ctx1 = T.Context(0)
+    ref, _, _ = run(ctx1, precision, a, la, b, lb, lc)
+    assert int(ctx1.profile_read(cap=1)["kind"][0]) == 4
+    assert np.array_equal(got, ref)
+
+
 # Layouts the tensor-core kernels cannot load in place (a free label at the lowest position
 # of each operand): TTGT -- permute into the tensor-core layouts, contract, permute back.
 TTGT_SHAPES = [(8, 6, 7), (9, 8, 8), (10, 5, 6), (7, 10, 9), (12, 4, 12)]
