@@ -449,10 +449,14 @@ def sweep_labels(m, k, n, layout, seed):
     """Index labels of one sweep point.  'random': seeded random axis orders of A, B and C.
     'arranged': the order the step compiler gives tensor-core steps (K tile labels, then
     the M / N tile labels, lowest; C led by three tile columns, then the tile rows, then the
-    other tile columns), the rest random."""
+    other tile columns), the rest random; for GEPDOT shapes (M N <= 2^10, K >= 2^12) both
+    operands lead with all common labels in one order."""
     rng = np.random.default_rng(seed)
     ms, ks, ns = list(range(m)), list(range(100, 100 + k)), list(range(200, 200 + n))
     perm = lambda v: [int(x) for x in rng.permutation(v)] if v else []
+    if layout == "arranged" and m + n <= 10 and k >= 12:
+        # GEPDOT: both operands lead with the common labels in one order (contiguous K runs)
+        return ks + perm(ms), ks + perm(ns), perm(ms + ns)
     if layout == "arranged":
         kt = 5 if k >= 5 else 4
         nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
@@ -474,7 +478,8 @@ def run_sweep(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     out = []
     for (m, k, n) in pts:
-        layouts = ["arranged", "random"] if (m >= 7 and n >= 6 and k >= 4) else ["random"]
+        gepdot = m + n <= 10 and k >= 12
+        layouts = ["arranged", "random"] if ((m >= 7 and n >= 6 and k >= 4) or gepdot) else ["random"]
         for layout in layouts:
             seed = 1000003 * m + 1009 * k + n + (7 if layout == "random" else 0)
             la, lb, lc = sweep_labels(m, k, n, layout, seed)

@@ -255,7 +255,9 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
  *  bytes[s]   algorithmic bytes: (|A| + |B| + |C|) * element size per instance
  *  kind[s]    kernel class (0 generic, 1 split-K GEPDOT, 2 fused chain, 3 tensor-core with
  *             cp.async gathers, 4 tensor-core with TMA loads, 5 persistent tensor-core
- *             with TMA loads: short K loops, epilogue overlapped with the next tile)
+ *             with TMA loads: epilogue overlapped with the next tile's loads and MMAs,
+ *             6 permute + tensor-core + permute (tnc_contract only), 7 GEPDOT streamed
+ *             through a cp.async ring (split over K or not))
  *  ms[n]      (one extra entry) the whole call's device time
  * *n receives the number of steps. */
 tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,

@@ -178,7 +178,9 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   int kg = 256 / threads_out;
   kg = std::min(kg, 1 << kt);
   t.kgroups = std::max(1, kg);
-  // split over the outer common labels for GEPDOT-shaped steps, enough CTAs to fill the GPU
+  // split over the outer common labels for GEPDOT-shaped steps: four CTAs per SM, each with
+  // at least four K steps for the streaming kernel's cp.async ring while one CTA per SM
+  // remains
   t.splitk = 1;
   const int ko = (int)t.Ko.size();
   if (gepdot && ko > 0) {
@@ -186,8 +188,10 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     const int64_t want = (4 * 152 + tiles - 1) / tiles;
     int s = 0;
     while (s < ko && s < 10 && (int64_t(1) << s) < want) ++s;
+    while (s > 0 && ko - s < 2 && (tiles << (s - 1)) >= 152) --s;
     t.splitk = 1 << s;
   }
+  t.gepdot = gepdot;
   kind_out = t.splitk > 1 ? K_SPLITK : K_GENERIC;
   return t;
 }

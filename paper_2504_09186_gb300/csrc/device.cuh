@@ -12,6 +12,10 @@ namespace tnc {
 constexpr int kMaxTileBits = 16;  // per canonical tile set (M, N or K)
 constexpr int kMaxOuter = 40;     // outer labels per set
 constexpr int kThreads = 256;
+constexpr int kStreamStages = 3;  // shared-memory ring depth of k_stream
+// splits over K from which the partial sums are reduced by one warp per output
+// (k_splitk_reduce_wide) instead of one thread per output
+constexpr int kWideReduceSplit = 64;
 
 // Storage conversion: FP32 arithmetic, fp32 / fp16 / bf16 storage (round to nearest even).
 template <typename T>
@@ -84,6 +88,7 @@ struct GenParams {
   int32_t n_slots, slotA, slotB, slotC;
   float2* partials;                    // split-K partial sums [inst][split][planeC]
   int32_t smem_tables;                 // byte offset of the index tables in shared memory
+  int32_t stream;                      // 1: k_stream (raw tiles through a cp.async ring)
   InstMap im;                          // launch index -> instances (tree-like reuse)
 };
 

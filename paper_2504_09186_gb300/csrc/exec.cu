@@ -108,6 +108,7 @@ struct StepLaunch {
   int rm, rn;
   double flops = 0, bytes = 0;  // algorithmic, per instance (real flops 8MNK; bytes read + written)
   int plan_step = -1;           // the plan step a tensor-core launch runs
+  bool gepdot = false;          // a GEPDOT-shaped SIMT step (see make_stream)
 };
 
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
@@ -440,7 +441,27 @@ static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int
   L.kind = kind;
   L.rm = t.rm;
   L.rn = t.rn;
+  L.gepdot = t.gepdot;
   return L;
+}
+
+// GEPDOT-shaped steps with runs of at least 16 bytes in both operands and two or more K
+// steps per CTA stream their raw tiles through the k_stream ring (elements of eb bytes).
+static void make_stream(StepLaunch& L, size_t eb, bool disabled) {
+  GenParams& p = L.p;
+  if (disabled || !L.gepdot) return;
+  const int need = eb == 2 ? 3 : 2;  // log2 entries per 16 bytes
+  if (p.runA < need || p.runB < need) return;
+  if (((int64_t(1) << p.n_ok) / p.splitk) < 2) return;
+  const size_t stage = 2 * ((size_t(1) << (p.mt + p.kt)) + (size_t(1) << (p.kt + p.nt))) * eb;
+  const size_t rb = size_t(p.kgroups) * (size_t(1) << (p.mt + p.nt)) * 8;
+  size_t region = std::max(size_t(kStreamStages) * stage, rb);
+  region = (region + 15) & ~size_t(15);
+  const size_t tables = L.smem - size_t(p.smem_tables);
+  if (region + tables > 220 * 1024) return;  // within the 227 KB a CTA may take
+  p.stream = 1;
+  p.smem_tables = (int32_t)region;
+  L.smem = region + tables;
 }
 
 // ------------------------------------------------------------------ per-plan device program
@@ -518,6 +539,7 @@ struct tnc_context_s {
   bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
   bool no_persist = false;  // TNC_NO_PERSIST=1: short-K TMA steps use one CTA per tile
   bool no_reuse = false;    // TNC_NO_REUSE=1: every step runs for every (row, slice)
+  bool no_stream = false;   // TNC_NO_STREAM=1: GEPDOT steps load tiles synchronously (k_generic)
   ProfState prof;
   ~tnc_context_s() {
     bits.release();
@@ -872,6 +894,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     L.p.slotA = st.a;
     L.p.slotB = st.b;
     L.p.slotC = st.c;
+    make_stream(L, eb, ctx->no_stream);
     if (L.kind == K_SPLITK) partial_elems = std::max(partial_elems, size_t(W) * L.p.splitk * L.p.planeC);
     prog->steps.push_back(L);
   }
@@ -1021,6 +1044,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->no_persist = env3 && env3[0] == '1';
     const char* env4 = std::getenv("TNC_NO_REUSE");
     c->no_reuse = env4 && env4[0] == '1';
+    const char* env5 = std::getenv("TNC_NO_STREAM");
+    c->no_stream = env5 && env5[0] == '1';
     *out = c;
   });
 }
@@ -1160,7 +1185,9 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
         const double nz = reuse ? double(launch_count(tcs ? SL.tp.im : SL.p.im, n_inst)) : double(n_inst);
         ps.flops[k] = SL.flops * nz;  // what runs: reused results are computed once
         ps.bytes[k] = SL.bytes * nz;
-        ps.kind[k] = (SL.kind == K_TMA && SL.tp.persistent) ? 5 : SL.kind;
+        ps.kind[k] = (SL.kind == K_TMA && SL.tp.persistent) ? 5
+                     : ((SL.kind == K_GENERIC || SL.kind == K_SPLITK) && SL.p.stream) ? 7
+                                                                                      : SL.kind;
         ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
       }
       CUDA_OK(cudaEventRecord(ps.call_start(), s));
@@ -1471,6 +1498,7 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
     int kind = K_GENERIC;
     TileSpec t = tile_for(la, lb, lc, 1, kind);
     StepLaunch L = make_launch(t, kind, la, lb, lc);
+    make_stream(L, elem_bytes(precision), ctx->no_stream);
     // per-launch events (read with tnc_profile_read): the contraction and the whole call
     ProfState& ps = ctx->prof;
     ps.valid = false;
@@ -1577,7 +1605,10 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
       ps.flops.assign(1, 8.0 * std::ldexp(1.0, rank_a + rank_b - common));
       ps.bytes.assign(1, (std::ldexp(1.0, rank_a) + std::ldexp(1.0, rank_b) + std::ldexp(1.0, rank_c)) * 2.0 * double(eb));
-      ps.kind.assign(1, ttgt ? 6 : (L.kind == K_TMA && L.tp.persistent) ? 5 : L.kind);
+      ps.kind.assign(1, ttgt ? 6
+                           : (L.kind == K_TMA && L.tp.persistent) ? 5
+                           : ((L.kind == K_GENERIC || L.kind == K_SPLITK) && L.p.stream) ? 7
+                                                                                          : L.kind);
       ps.kernels.assign(1, (L.kind == K_SPLITK || ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1)) ? 2 : 1);
       if (ttgt) ps.kernels[0] += 3;
     }
@@ -1691,6 +1722,7 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
     int kind = K_GENERIC;
     TileSpec t = tile_for(la, lb, lc, 1, kind);
     StepLaunch L = make_launch(t, kind, la, lb, lc);
+    make_stream(L, elem_bytes(precision), false);
     if (L.kind == K_SPLITK) {
       const size_t need = size_t(L.p.splitk) * size_t(L.p.planeC) * sizeof(float2);
       if (need > kNoAllocScratchBytes - kNoAllocSlotBytes)

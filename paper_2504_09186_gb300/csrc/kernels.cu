@@ -154,6 +154,66 @@ __device__ __forceinline__ float block_max(float v, float* red) {
   return v;  // valid in thread 0
 }
 
+// After the K loop of k_generic / k_stream: the K groups' sums in a fixed order into the
+// C-native staging tile R, then either FP32 split-K partials or the scaled, converted tile.
+template <typename T, int RM, int RN>
+__device__ __forceinline__ void generic_finish(const GenParams& p, const Inst3 I, const float2 (&acc)[RM][RN],
+                                               bool active, int grp, int mi, int ni, int TM, int TN,
+                                               const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC,
+                                               float2* R, float* red, int64_t oC) {
+  const int tid = threadIdx.x;
+  // K groups in a fixed order
+  const int O = 1 << (p.mt + p.nt);
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) R[grp * O + TCm[mi + i * TM] + TCn[ni + j * TN]] = acc[i][j];
+  }
+  __syncthreads();
+  if (p.kgroups >= 8) {
+    // pairwise tree over the groups (group g adds group g + h, h = G/2, G/4, ..., 1): the
+    // same order on every run, log2(G) barriers instead of G dependent adds per output
+    for (int h = p.kgroups >> 1; h > 0; h >>= 1) {
+      for (int x = tid; x < h * O; x += kThreads) {
+        const float2 v = R[h * O + x];
+        R[x].x += v.x;
+        R[x].y += v.y;
+      }
+      __syncthreads();
+    }
+  } else if (p.kgroups > 1) {
+    for (int o = tid; o < O; o += kThreads) {
+      float2 s = R[o];
+      for (int g = 1; g < p.kgroups; ++g) {
+        const float2 v = R[g * O + o];
+        s.x += v.x;
+        s.y += v.y;
+      }
+      R[o] = s;
+    }
+    __syncthreads();
+  }
+  if (p.splitk > 1) {
+    // FP32 partial sums, indexed by C's flat index
+    float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
+    const uint32_t lowmask = (1u << p.runC) - 1u;
+    for (int t = tid; t < O; t += kThreads) part[hiC[t >> p.runC] + (uint32_t(t) & lowmask)] = R[t];
+    return;
+  }
+  // scale, convert, store
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
+  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
+  const float scale = ldexpf(1.f, -sh);
+  T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
+  const float mx = store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
+  const float bm = block_max(mx, red);
+  if (tid == 0) {
+    atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
+    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+  }
+}
+
 template <typename T, int RM, int RN>
 __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -263,45 +323,179 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
     }
     __syncthreads();
   }
-  // reduce the K groups in a fixed order into the C-native staging tile
-  const int O = 1 << (p.mt + p.nt);
-  if (active) {
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < RN; ++j) R[grp * O + TCm[mi + i * TM] + TCn[ni + j * TN]] = acc[i][j];
+  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC);
+}
+
+// Streaming variant of k_generic for GEPDOT-shaped steps (few outputs, a long K loop;
+// Sec. V-B).  Each K step's operand tiles are copied raw (16-bit or FP32 planes, in 16-byte
+// cp.async chunks) into a kStreamStages-deep shared-memory ring, so the next steps' loads are
+// in flight while one is multiplied; entries are converted to FP32 as they are read.  Every
+// thread visits the same k values in the same order as in k_generic, so the two kernels give
+// identical results.  Needs runs of at least 16 bytes at the low positions of A and B (every
+// chunk is contiguous in memory).  Tiles are swizzled by sw_chunk, which moves whole chunks.
+__device__ __forceinline__ void cpa16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Entry-index swizzle of a raw tile: the chunk-within-128-byte-line bits are XORed with the
+// two groups of line-index bits above them, so the rows a warp reads at once (a power of
+// two apart) fall on different banks.  Linear over GF(2) and leaves the low (within-chunk)
+// bits alone: offset tables are stored swizzled and combined with XOR, and a 16-byte chunk
+// stays one contiguous chunk.
+template <typename T>
+__device__ __forceinline__ uint32_t sw_chunk(uint32_t i) {
+  constexpr int C = sizeof(T) == 2 ? 3 : 2;  // log2 entries per 16-byte chunk
+  constexpr int L = C + 3;                   // log2 entries per 128-byte line
+  return i ^ ((((i >> L) ^ (i >> (L + 3))) & 7u) << C);
+}
+
+// Issue the cp.async copies of one raw planar tile (2^bits entries, runs of 2^run).
+template <typename T>
+__device__ __forceinline__ void stream_copy(const T* re, const T* im, int bits, int run, const uint32_t* hi,
+                                            uint32_t dst_re, uint32_t dst_im) {
+  constexpr int VE = 16 / sizeof(T);
+  const int n = 1 << bits;
+  const uint32_t lowmask = (1u << run) - 1u;
+  for (int t = threadIdx.x * VE; t < n; t += kThreads * VE) {
+    const uint32_t off = hi[t >> run] + (uint32_t(t) & lowmask);
+    const uint32_t d = sw_chunk<T>(uint32_t(t)) * uint32_t(sizeof(T));
+    cpa16(dst_re + d, re + off);
+    cpa16(dst_im + d, im + off);
+  }
+}
+
+template <typename T, int RM, int RN>
+__global__ void __launch_bounds__(kThreads) k_stream(const GenParams p) {
+  constexpr int NS = kStreamStages;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nA = 1 << (p.mt + p.kt), nB = 1 << (p.kt + p.nt);
+  const uint32_t stage_bytes = uint32_t(2 * (nA + nB)) * uint32_t(sizeof(T));
+  float2* R = reinterpret_cast<float2*>(smem);  // reduction / staging after the K loop
+  uint32_t* hiA = reinterpret_cast<uint32_t*>(smem + p.smem_tables);
+  uint32_t* hiB = hiA + (1 << (p.mt + p.kt - p.runA));
+  uint32_t* hiC = hiB + (1 << (p.kt + p.nt - p.runB));
+  uint16_t* TAm = reinterpret_cast<uint16_t*>(hiC + (1 << (p.mt + p.nt - p.runC)));
+  uint16_t* TAk = TAm + (1 << p.mt);
+  uint16_t* TBk = TAk + (1 << p.kt);
+  uint16_t* TBn = TBk + (1 << p.kt);
+  uint16_t* TCm = TBn + (1 << p.nt);
+  uint16_t* TCn = TCm + (1 << p.mt);
+  float* red = reinterpret_cast<float*>(TCn + (1 << p.nt) + 2);
+
+  const int tid = threadIdx.x;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
+  const uint32_t om = blockIdx.x & ((1u << p.n_om) - 1u);
+  const uint32_t on = p.n_om >= 32 ? 0u : (blockIdx.x >> p.n_om);
+  int64_t oA = 0, oB = 0, oC = 0;
+  for (int j = 0; j < p.n_om; ++j)
+    if ((om >> j) & 1u) {
+      oA += int64_t(1) << p.om_A[j];
+      oC += int64_t(1) << p.om_C[j];
+    }
+  for (int j = 0; j < p.n_on; ++j)
+    if ((on >> j) & 1u) {
+      oB += int64_t(1) << p.on_B[j];
+      oC += int64_t(1) << p.on_C[j];
+    }
+  {
+    const int nhA = 1 << (p.mt + p.kt - p.runA), nhB = 1 << (p.kt + p.nt - p.runB), nhC = 1 << (p.mt + p.nt - p.runC);
+    for (int h = tid; h < nhA; h += kThreads) hiA[h] = deposit_hi(h, p.maskA, p.runA);
+    for (int h = tid; h < nhB; h += kThreads) hiB[h] = deposit_hi(h, p.maskB, p.runB);
+    for (int h = tid; h < nhC; h += kThreads) hiC[h] = deposit_hi(h, p.maskC, p.runC);
+    // operand tables are stored swizzled (sw_chunk), the C staging tables plain
+    for (int x = tid; x < (1 << p.mt); x += kThreads) {
+      TAm[x] = (uint16_t)sw_chunk<T>(scatter_bits(x, p.pAm, p.mt));
+      TCm[x] = (uint16_t)scatter_bits(x, p.pCm, p.mt);
+    }
+    for (int x = tid; x < (1 << p.kt); x += kThreads) {
+      TAk[x] = (uint16_t)sw_chunk<T>(scatter_bits(x, p.pAk, p.kt));
+      TBk[x] = (uint16_t)sw_chunk<T>(scatter_bits(x, p.pBk, p.kt));
+    }
+    for (int x = tid; x < (1 << p.nt); x += kThreads) {
+      TBn[x] = (uint16_t)sw_chunk<T>(scatter_bits(x, p.pBn, p.nt));
+      TCn[x] = (uint16_t)scatter_bits(x, p.pCn, p.nt);
+    }
   }
   __syncthreads();
-  if (p.kgroups > 1) {
-    for (int o = tid; o < O; o += kThreads) {
-      float2 s = R[o];
-      for (int g = 1; g < p.kgroups; ++g) {
-        const float2 v = R[g * O + o];
-        s.x += v.x;
-        s.y += v.y;
-      }
-      R[o] = s;
+
+  const int TM = (1 << p.mt) / RM, TN = (1 << p.nt) / RN;
+  const int TPO = TM * TN;
+  const int grp = tid / TPO, r = tid % TPO;
+  const bool active = grp < p.kgroups;
+  const int mi = r % TM, ni = r / TM;
+  int am[RM], bn[RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) am[i] = active ? TAm[mi + i * TM] : 0;
+#pragma unroll
+  for (int j = 0; j < RN; ++j) bn[j] = active ? TBn[ni + j * TN] : 0;
+  float2 acc[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  const T* Abase = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
+  const T* Bbase = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
+  const int64_t KO = int64_t(1) << p.n_ok;
+  const int64_t per = KO / p.splitk;
+  const int64_t k0 = int64_t(blockIdx.y) * per;
+  const int nk = 1 << p.kt;
+  const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  // copies of K step `it` into stage it % NS; one commit group per call (empty past the end)
+  auto issue = [&](int64_t it) {
+    if (it < per) {
+      const int64_t ok = k0 + it;
+      int64_t okA = 0, okB = 0;
+      for (int j = 0; j < p.n_ok; ++j)
+        if ((ok >> j) & 1) {
+          okA += int64_t(1) << p.ok_A[j];
+          okB += int64_t(1) << p.ok_B[j];
+        }
+      const uint32_t st = sbase + uint32_t(it % NS) * stage_bytes;
+      const uint32_t esz = uint32_t(sizeof(T));
+      stream_copy<T>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, st, st + uint32_t(nA) * esz);
+      stream_copy<T>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, st + uint32_t(2 * nA) * esz,
+                     st + uint32_t(2 * nA + nB) * esz);
     }
-    __syncthreads();
+    cpa_commit();
+  };
+  for (int s0 = 0; s0 < NS - 1; ++s0) issue(s0);
+  for (int64_t it = 0; it < per; ++it) {
+    cpa_wait<NS - 2>();  // this thread's copies of step `it` have landed
+    __syncthreads();     // everyone's have, and everyone is done with step it - 1
+    issue(it + NS - 1);  // refills the stage of step it - 1
+    if (active) {
+      const T* Ar = reinterpret_cast<const T*>(smem + uint32_t(it % NS) * stage_bytes);
+      const T* Ai = Ar + nA;
+      const T* Br = Ai + nA;
+      const T* Bi = Br + nB;
+      for (int k = grp; k < nk; k += p.kgroups) {
+        const int ka = TAk[k], kb = TBk[k];
+        float2 a[RM], b[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = make_float2(Conv<T>::to_f(Ar[am[i] ^ ka]), Conv<T>::to_f(Ai[am[i] ^ ka]));
+#pragma unroll
+        for (int j = 0; j < RN; ++j) b[j] = make_float2(Conv<T>::to_f(Br[kb ^ bn[j]]), Conv<T>::to_f(Bi[kb ^ bn[j]]));
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+          }
+      }
+    }
   }
-  if (p.splitk > 1) {
-    // FP32 partial sums, indexed by C's flat index
-    float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
-    const uint32_t lowmask = (1u << p.runC) - 1u;
-    for (int t = tid; t < O; t += kThreads) part[hiC[t >> p.runC] + (uint32_t(t) & lowmask)] = R[t];
-    return;
-  }
-  // scale, convert, store
-  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
-  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
-  const float scale = ldexpf(1.f, -sh);
-  T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
-  const float mx = store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
-  const float bm = block_max(mx, red);
-  if (tid == 0) {
-    atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
-    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
-  }
+  cpa_wait<0>();
+  __syncthreads();  // the ring becomes the reduction buffer
+  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC);
 }
 
 // Fixed-order sum of split-K partials (blocked summation, Eq. 3), then scale and store.
@@ -322,6 +516,47 @@ __global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
       s.x += v.x;
       s.y += v.y;
     }
+    T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC;
+    const T re = Conv<T>::from_f(s.x * scale), im = Conv<T>::from_f(s.y * scale);
+    Cre[idx] = re;
+    Cre[p.planeC + idx] = im;
+    mx = fmaxf(fabsf(Conv<T>::to_f(re)), fabsf(Conv<T>::to_f(im)));
+  }
+  const float bm = block_max(mx, red);
+  if (threadIdx.x == 0) {
+    atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
+    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+  }
+}
+
+// The same sum for long splits over few outputs: one warp per output, lane l adds the
+// partials l, l + 32, l + 64, ... in order, then the lanes combine in a fixed butterfly
+// (xor 16, 8, 4, 2, 1), so the result is deterministic; 8 outputs per block.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_splitk_reduce_wide(const GenParams p) {
+  __shared__ float red[32];
+  const Inst3 I = map_inst(blockIdx.z, p.im);
+  const int lane = threadIdx.x & 31;
+  const int64_t idx = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
+  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
+  const float scale = ldexpf(1.f, -sh);
+  float mx = 0.f;
+  float2 s = make_float2(0.f, 0.f);
+  if (idx < p.planeC) {
+    const float2* part = p.partials + int64_t(blockIdx.z) * p.splitk * p.planeC + idx;
+#pragma unroll 8
+    for (int k = lane; k < p.splitk; k += 32) {
+      const float2 v = part[int64_t(k) * p.planeC];
+      s.x += v.x;
+      s.y += v.y;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (idx < p.planeC && lane == 0) {
     T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC;
     const T re = Conv<T>::from_f(s.x * scale), im = Conv<T>::from_f(s.y * scale);
     Cre[idx] = re;
@@ -716,6 +951,16 @@ template <typename T>
 using GenKernel = void (*)(const GenParams);
 
 template <typename T>
+GenKernel<T> pick_stream(int rm, int rn) {
+#define TNC_CASE(a, b) \
+  if (rm == a && rn == b) return k_stream<T, a, b>;
+  TNC_CASE(1, 1) TNC_CASE(1, 2) TNC_CASE(1, 4) TNC_CASE(2, 1) TNC_CASE(2, 2) TNC_CASE(2, 4)
+  TNC_CASE(4, 1) TNC_CASE(4, 2) TNC_CASE(4, 4)
+#undef TNC_CASE
+  return nullptr;
+}
+
+template <typename T>
 GenKernel<T> pick_generic(int rm, int rn) {
 #define TNC_CASE(a, b) \
   if (rm == a && rn == b) return k_generic<T, a, b>;
@@ -727,7 +972,11 @@ GenKernel<T> pick_generic(int rm, int rn) {
 
 cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, dim3 grid, size_t smem, cudaStream_t s) {
   void (*k)(const GenParams) = nullptr;
-  if (precision == 0) k = pick_generic<float>(rm, rn);
+  if (p.stream) {
+    if (precision == 0) k = pick_stream<float>(rm, rn);
+    else if (precision == 1) k = pick_stream<__half>(rm, rn);
+    else k = pick_stream<__nv_bfloat16>(rm, rn);
+  } else if (precision == 0) k = pick_generic<float>(rm, rn);
   else if (precision == 1) k = pick_generic<__half>(rm, rn);
   else k = pick_generic<__nv_bfloat16>(rm, rn);
   if (!k) return cudaErrorInvalidValue;
@@ -740,6 +989,14 @@ cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, di
 }
 
 cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_inst, cudaStream_t s) {
+  if (p.splitk >= kWideReduceSplit) {
+    constexpr int OPB = kThreads / 32;  // outputs per block
+    dim3 grid((unsigned)((p.planeC + OPB - 1) / OPB), 1, (unsigned)n_inst);
+    if (precision == 0) k_splitk_reduce_wide<float><<<grid, kThreads, 0, s>>>(p);
+    else if (precision == 1) k_splitk_reduce_wide<__half><<<grid, kThreads, 0, s>>>(p);
+    else k_splitk_reduce_wide<__nv_bfloat16><<<grid, kThreads, 0, s>>>(p);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((p.planeC + kThreads - 1) / kThreads), 1, (unsigned)n_inst);
   if (precision == 0) k_splitk_reduce<float><<<grid, kThreads, 0, s>>>(p);
   else if (precision == 1) k_splitk_reduce<__half><<<grid, kThreads, 0, s>>>(p);

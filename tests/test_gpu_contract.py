@@ -77,3 +77,25 @@ def test_large_shapes_sampled(ctx, precision, shape):
     idx = np.unique(np.concatenate([[0, len(got) - 1], rng.integers(0, len(got), 62)]))
     ref = pairwise.contract_at(aq, la, bq, lb, lc, idx)
     assert metrics.rel_err_norm(got[idx], ref) <= TOL[precision]
+
+
+# GEPDOT shapes (few outputs, long K; Sec. V-B) whose CTAs walk two or more K steps after
+# the split over K: raw tiles streamed through the cp.async ring (profile kind 7);
+# elementwise against the oracle and bit for bit against the kernel that loads each K step
+# synchronously (same k order per thread).
+GEPDOT = [(2, 22, 2), (1, 23, 3), (3, 21, 4), (0, 22, 2), (4, 20, 1)]
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf", "cbf16"])
+@pytest.mark.parametrize("shape", GEPDOT)
+def test_gepdot_streamed(ctx, precision, shape, monkeypatch):
+    a, la, b, lb, lc = make_case(*shape, seed=17 * sum(shape) + shape[2])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 7
+    ref = pairwise.contract(aq, la, bq, lb, lc)
+    assert metrics.rel_err_norm(got, ref) <= TOL[precision]
+    monkeypatch.setenv("TNC_NO_STREAM", "1")
+    ctx1 = T.Context(0)
+    sync, _, _ = run(ctx1, precision, a, la, b, lb, lc)
+    assert int(ctx1.profile_read(cap=1)["kind"][0]) in (0, 1)
+    assert np.array_equal(got, sync)
