@@ -42,29 +42,33 @@ N_SM = 152
 
 
 def measured_traffic(kind, flops_launch):
-    """DRAM bytes (read + write) of one launch of the dominant kernel, from the committed ncu
-    summary: per-instance bytes of a one-instance capture times the launch's instances.  None
-    when the kernel source changed since the capture or the launch is not that contraction."""
+    """DRAM bytes (read + write) of one launch of the dominant kernel, from a committed ncu
+    summary of a kernel of the same kind: per-instance bytes of a one-instance capture times the
+    launch's instances.  None when no summary matches the kind and the launch's flops, or when
+    the kernel's source changed since the capture (its SHA-1 is recorded beside the figures)."""
+    import glob
     import hashlib
     import re
 
-    path = os.path.join(ROOT, "profiles", "k_tc_tma_bn256_14x12x10_chalf.md")
-    if kind != 4 or not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    get = lambda key: re.search(rf"^{key}: (\S+)$", txt, re.M)
-    vals = {k: get(k) for k in ("traffic_flops_per_instance", "traffic_dram_bytes_per_instance",
-                                 "traffic_kernel_source_sha1")}
-    if not all(vals.values()):
-        return None
-    src = os.path.join(ROOT, "paper_2504_09186_gb300", "csrc", "tc_gemm.cu")
-    if hashlib.sha1(open(src, "rb").read()).hexdigest() != vals["traffic_kernel_source_sha1"].group(1):
-        return None
-    fpi = float(vals["traffic_flops_per_instance"].group(1))
-    inst = flops_launch / fpi
-    if abs(inst - round(inst)) > 1e-9 or round(inst) < 1:
-        return None
-    return float(vals["traffic_dram_bytes_per_instance"].group(1)) * round(inst)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        txt = open(path).read()
+
+        def get(key):
+            m = re.search(rf"^{key}: (\S+)$", txt, re.M)
+            return m.group(1) if m else None
+
+        vals = [get(k) for k in ("traffic_kind", "traffic_flops_per_instance", "traffic_dram_bytes_per_instance",
+                                 "traffic_kernel_source", "traffic_kernel_source_sha1")]
+        if None in vals or int(vals[0]) != kind:
+            continue
+        src = os.path.join(ROOT, vals[3])
+        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != vals[4]:
+            continue
+        inst = flops_launch / float(vals[1])
+        if abs(inst - round(inst)) > 1e-9 or round(inst) < 1:
+            continue
+        return float(vals[2]) * round(inst)
+    return None
 
 
 def load_peaks():
