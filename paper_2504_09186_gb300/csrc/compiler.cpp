@@ -73,10 +73,13 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     if (!contains(la, x)) N.push_back(x);
   const int m = (int)M.size(), k = (int)K.size(), n = (int)N.size();
   TileSpec t;
-  // GEPDOT steps (few outputs, long K) are bound by memory latency: operand tiles of 2^12
-  // entries double the bytes each CTA has in flight per K step
+  // GEPDOT steps (few outputs, long K) and the other streamed steps below are bound by memory:
+  // operand tiles of 2^12 entries double the bytes each CTA has in flight per K step
   const bool gepdot = (m + n <= 10) && (k >= 12);
-  const int tile_ab = gepdot ? TILE_AB + 1 : TILE_AB;
+  // memory-bound long K loops (GEPDOTs, and at most 4 rows or columns): each loaded entry
+  // feeds at most 4 multiply-adds, so they stream their tiles (k_stream)
+  const bool stream = gepdot || (k >= 12 && std::min(m, n) <= 2);
+  const int tile_ab = stream ? TILE_AB + 1 : TILE_AB;
   auto fits = [tile_ab](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
     const int mt = (int)Mt.size(), kt = (int)Kt.size(), nt = (int)Nt.size();
     return mt + kt <= tile_ab && kt + nt <= tile_ab && mt + nt <= TILE_C && mt + nt <= max_out_bits(mt, nt);
@@ -158,9 +161,9 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   const int mt = (int)t.Mt.size(), nt = (int)t.Nt.size(), kt = (int)t.Kt.size();
   const int out_bits = mt + nt;
   int lrm = 0, lrn = 0;
-  if (gepdot) {
-    // few outputs, long K: every thread takes the largest micro-tile (up to 4 x 4) over its
-    // own k values (8 shared-memory loads per 16 complex multiply-adds), the K groups are
+  if (stream) {
+    // few outputs per K step: every thread takes the largest micro-tile (up to 4 x 4) over
+    // its own k values (8 shared-memory loads per 16 complex multiply-adds), the K groups are
     // summed once at the end
     lrm = std::min(2, mt);
     lrn = std::min(2, nt);
@@ -192,6 +195,7 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     t.splitk = 1 << s;
   }
   t.gepdot = gepdot;
+  t.stream = stream;
   kind_out = t.splitk > 1 ? K_SPLITK : K_GENERIC;
   return t;
 }
@@ -288,9 +292,9 @@ void compile_plan(Plan& plan, bool fuse) {
     plan.tensors.push_back(ti);
   }
   // Tensor-core steps, decided on label sets from the root down: a step qualifies when both
-  // operands are intermediates, M >= 2^7 rows (the larger operand A), N >= 2^6 columns and
-  // K >= 2^4.  Its tile is Kt (4 or 5 common labels), Mt (7 of A's free labels) and Nt (6, 7
-  // or 8 of B's), and it requires its operands' layouts to start with Kt then Mt (A) / Nt (B):
+  // operands are intermediates, M >= 2^7 rows (the larger operand A), N >= 2^5 columns and
+  // K >= 2^4.  Its tile is Kt (4 or 5 common labels), Mt (7 of A's free labels) and Nt (5, 6,
+  // 7 or 8 of B's), and it requires its operands' layouts to start with Kt then Mt (A) / Nt (B):
   // every operand tile is then one contiguous block, a plain box for the tensor memory
   // accelerator.  Mt / Nt include the first three labels its own consumer requires of its
   // output, so the output tile covers the output's lowest positions (contiguous stores).
@@ -354,7 +358,7 @@ void compile_plan(Plan& plan, bool fuse) {
         std::swap(M, N);
       }
     }
-    if (a < n_leaves || b < n_leaves || M.size() < 7 || N.size() < 6 || K.size() < 4) continue;
+    if (a < n_leaves || b < n_leaves || M.size() < 7 || N.size() < 5 || K.size() < 4) continue;
     TcDec d;
     d.ok = true;
     d.rows = a;
@@ -363,8 +367,8 @@ void compile_plan(Plan& plan, bool fuse) {
     // most 8 K tiles the epilogue weighs, and 128-wide tiles run on the persistent kernel,
     // which overlaps it with the next tile
     const size_t kt0 = d.bk == 32 ? 5 : 4;
-    d.bn = (N.size() >= 8 && K.size() > kt0 + 3) ? 256 : (N.size() >= 7 ? 128 : 64);
-    const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : 6);
+    d.bn = (N.size() >= 8 && K.size() > kt0 + 3) ? 256 : (N.size() >= 7 ? 128 : (N.size() >= 6 ? 64 : 32));
+    const size_t kt = d.bk == 32 ? 5 : 4, nt = d.bn == 256 ? 8 : (d.bn == 128 ? 7 : (d.bn == 64 ? 6 : 5));
     // K-tile order: Kt[0..3] become the lowest positions of both operands, i.e. of both
     // producers' results.  A producer stores its tiles straight from registers (direct
     // epilogue) when its result's positions 0..2 are tile columns and position 3 a tile row:
@@ -461,7 +465,7 @@ void compile_plan(Plan& plan, bool fuse) {
     const auto& lb = plan.tensors[st.b].labels;
     const auto& lc = plan.tensors[st.c].labels;
     int kind = K_GENERIC;
-    // split sizing assumes every slice of the plan in flight (see split_instances in exec.cu)
+    // split sizing of the SIMT steps assumes every slice of the plan in flight, at most 2^12
     st.tile = choose_tile(la, lb, lc, 1 << std::min<int>((int)plan.sliced.size(), 12), kind);
     st.kind = kind;
     st.tc_ok = dec[s].ok;

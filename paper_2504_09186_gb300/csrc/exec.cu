@@ -108,22 +108,31 @@ struct StepLaunch {
   int rm, rn;
   double flops = 0, bytes = 0;  // algorithmic, per instance (real flops 8MNK; bytes read + written)
   int plan_step = -1;           // the plan step a tensor-core launch runs
-  bool gepdot = false;          // a GEPDOT-shaped SIMT step (see make_stream)
+  bool stream = false;          // a SIMT step that may stream its tiles (see make_stream)
 };
 
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
 // kernel's A (row side) and B operands (already swapped when the tile asked for it).
 // n_inst sizes the split over the outer common labels: enough CTAs for two waves.
 // Instances assumed when a step's split over K is sized: every slice of the plan for one
-// bitstring row (the unit of work of a full-plan call), at most 2^12.
-static int64_t split_instances(const Plan& P) { return int64_t(1) << std::min<size_t>(P.sliced.size(), 12); }
+// bitstring row (the unit of work of a full-plan call), at most 2^12, and at most the largest
+// power of two of instances whose arenas fit in 60% of the device's total memory (bytes_per_inst
+// each).  Neither the wave size a call picks nor the free memory enters, so a plan's results do
+// not depend on how many instances share a launch.
+static int64_t split_instances(const Plan& P, double bytes_per_inst, double total_mem) {
+  const int64_t all = int64_t(1) << std::min<size_t>(P.sliced.size(), 12);
+  const double fit = std::max(1.0, 0.6 * total_mem / std::max(1.0, bytes_per_inst));
+  int64_t cap = 1;
+  while (cap * 2 <= all && double(cap * 2) <= fit) cap *= 2;
+  return std::min(all, cap);
+}
 
 static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<int>& la, const std::vector<int>& lb,
                            const std::vector<int>& lc, int precision, int bn, int bk, int64_t n_inst,
                            int force_split = 0) {
   TcParams& q = L.tp;
   std::memset(&q, 0, sizeof(q));
-  const size_t nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6), kt = bk == 32 ? 5 : 4;
+  const size_t nt = bn == 256 ? 8 : (bn == 128 ? 7 : (bn == 64 ? 6 : 5)), kt = bk == 32 ? 5 : 4;
   if (t.Mt.size() != 7 || t.Nt.size() != nt || t.Kt.size() != kt) fail(TNC_E_PLAN, "bad tensor-core tile");
   for (int j = 0; j < 3; ++j)
     if (pos_of(la, t.Kt[j]) != j || pos_of(lb, t.Kt[j]) != j) fail(TNC_E_PLAN, "tensor-core operands not K-major");
@@ -169,7 +178,7 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   // persistent TMA kernels overlap each tile's epilogue with the next tile's loads and MMAs:
   // short K loops over many tiles (two TMEM accumulators: BN <= 128), and 256-wide tiles
   // with the direct epilogue whenever every SM gets two tiles or more
-  q.persistent = ((bn <= 128 && q.n_ok <= 3 && tiles >= 4 * 152) || (bn == 256 && q.direct && tiles >= 2 * 152)) ? 1 : 0;
+  q.persistent = ((bn >= 64 && bn <= 128 && q.n_ok <= 3 && tiles >= 4 * 152) || (bn == 256 && q.direct && tiles >= 2 * 152)) ? 1 : 0;
   // otherwise split over the outer common labels: at least two CTAs per SM (every split
   // keeping at least 4 K tiles), and whole waves (the last one at least 90% busy) when each
   // split keeps at least 256 K tiles, so the FP32 partial sums cost little
@@ -243,12 +252,13 @@ static bool tma_tile_from_layout(const std::vector<int>& la, const std::vector<i
   for (int x : la) (std::find(lb.begin(), lb.end(), x) != lb.end() ? K : M).push_back(x);
   for (int x : lb)
     if (std::find(la.begin(), la.end(), x) == la.end()) N.push_back(x);
-  if (M.size() < 7 || N.size() < 6 || K.size() < 4) return false;
+  if (M.size() < 7 || N.size() < 5 || K.size() < 4) return false;
   bk = K.size() >= 5 ? 32 : 16;
   // 256-wide tiles (all of TMEM, one CTA per SM) only for K loops of more than 8 K tiles;
-  // shorter loops take 128-wide tiles and the persistent kernel
-  bn = (N.size() >= 8 && K.size() > size_t(bk == 32 ? 8 : 7)) ? 256 : (N.size() >= 7 ? 128 : 64);
-  const size_t kt = bk == 32 ? 5 : 4, nt = bn == 256 ? 8 : (bn == 128 ? 7 : 6);
+  // shorter loops take 128-wide tiles and the persistent kernel; 32 columns when N = 2^5
+  bn = (N.size() >= 8 && K.size() > size_t(bk == 32 ? 8 : 7)) ? 256
+       : (N.size() >= 7 ? 128 : (N.size() >= 6 ? 64 : 32));
+  const size_t kt = bk == 32 ? 5 : 4, nt = bn == 256 ? 8 : (bn == 128 ? 7 : (bn == 64 ? 6 : 5));
   if (la.size() < kt + 7 || lb.size() < kt + nt || lc.size() < 3) return false;
   auto in = [](const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
   t = TileSpec();
@@ -441,15 +451,16 @@ static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int
   L.kind = kind;
   L.rm = t.rm;
   L.rn = t.rn;
-  L.gepdot = t.gepdot;
+  L.stream = t.stream;
   return L;
 }
 
-// GEPDOT-shaped steps with runs of at least 16 bytes in both operands and two or more K
-// steps per CTA stream their raw tiles through the k_stream ring (elements of eb bytes).
+// Memory-bound long-K steps (GEPDOTs, thin operands) with runs of at least 16 bytes in both
+// operands and two or more K steps per CTA stream their raw tiles through the k_stream ring
+// (elements of eb bytes).
 static void make_stream(StepLaunch& L, size_t eb, bool disabled) {
   GenParams& p = L.p;
-  if (disabled || !L.gepdot) return;
+  if (disabled || !L.stream) return;
   const int need = eb == 2 ? 3 : 2;  // log2 entries per 16 bytes
   if (p.runA < need || p.runB < need) return;
   if (((int64_t(1) << p.n_ok) / p.splitk) < 2) return;
@@ -468,6 +479,7 @@ static void make_stream(StepLaunch& L, size_t eb, bool disabled) {
 struct DeviceProgram {
   int device = 0, precision = 0, W = 0;
   bool fused = false;       // chains fused: tensors at their fused-arena offsets
+  int64_t split_inst = 1;   // instances the tensor-core splits over K are sized for
   int64_t inst_stride = 0;  // scalars
   int n_slots = 0, n_leaves = 0;
   DevBuf arena, maxabs, exps, leaf_src, leaf_desc, partials, open_pos, chain_links;
@@ -534,6 +546,7 @@ struct tnc_context_s {
   int id = 0;
   cudaStream_t stream = nullptr;
   int sm_count = 0;
+  size_t total_mem = 0;
   DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status, ttgt;
   bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
   bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
@@ -772,10 +785,10 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   std::memset(&L.cp, 0, sizeof(L.cp));
   L.rm = L.rn = 0;
   L.plan_step = si;
-  make_tc_launch(L, t, la, lb, lc, prog->precision, bn, st.tc_bk, split_instances(P), ch ? ch->split : 0);
+  make_tc_launch(L, t, la, lb, lc, prog->precision, bn, st.tc_bk, prog->split_inst, ch ? ch->split : 0);
   // persistent kernels: two TMEM buffers up to 128 columns; 256-wide tiles hand their one
   // buffer back after draining it into registers, which needs the direct epilogue
-  const bool can_persist = L.tp.splitk == 1 && (bn <= 128 || L.tp.direct);
+  const bool can_persist = L.tp.splitk == 1 && bn >= 64 && (bn <= 128 || L.tp.direct);
   const int64_t tiles_w = (int64_t(1) << (L.tp.n_om + L.tp.n_on)) * prog->W;
   const bool heuristic = (bn <= 128 && L.tp.n_ok <= 3 && tiles_w >= 4 * 152) || (bn == 256 && tiles_w >= 2 * 152);
   L.tp.persistent = (ch ? ch->persistent != 0 : heuristic) && can_persist ? 1 : 0;
@@ -820,6 +833,7 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   prog->n_slots = (int)P.tensors.size();
   prog->n_leaves = (int)P.net.leaves.size();
   const size_t eb = elem_bytes(precision);
+  prog->split_inst = split_instances(P, double(prog->inst_stride) * double(eb) * 1.25 + 4096.0, double(ctx->total_mem));
   prog->arena.reserve(size_t(prog->inst_stride) * eb * W + 256);
   prog->maxabs.reserve(size_t(prog->n_slots) * W * sizeof(float));
   prog->exps.reserve(size_t(prog->n_slots) * W * sizeof(int32_t));
@@ -865,7 +879,8 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
       L.bytes = (std::ldexp(1.0, (int)la.size()) + std::ldexp(1.0, (int)lb.size()) + std::ldexp(1.0, (int)lc.size())) *
                 2.0 * double(eb);
     }
-    if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc) {
+    // 32-wide tiles exist only in the TMA kernel
+    if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc && !(ctx->no_tma && st.tc_bn == 32)) {
       StepLaunch T = tc_launch(ctx, P, prog.get(), (int)s, nullptr);
       if (T.kind == K_TMA) {
         // a configuration tuned for this shape (tnc_autotune) replaces the heuristics
@@ -1023,6 +1038,7 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->device = device;
     c->id = g_ctx_ids++;
     c->sm_count = prop.multiProcessorCount;
+    c->total_mem = prop.totalGlobalMem;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

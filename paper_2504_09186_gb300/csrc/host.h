@@ -124,7 +124,8 @@ struct TileSpec {
   int rm = 1, rn = 1;            // register micro-tile
   int kgroups = 1;               // intra-CTA split of the K tile
   int splitk = 1;                // CTAs along the outer K labels
-  bool gepdot = false;           // few outputs, long K (streamed through a cp.async ring)
+  bool gepdot = false;           // few outputs, long K
+  bool stream = false;           // long K loop over a thin operand: streamed through a cp.async ring
 };
 
 struct Step {

@@ -47,7 +47,7 @@ struct TcShape {
   static constexpr int LAYOUT = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // SW128 / SW64 / SW32
   static constexpr int CHUNKS = BK / 8;                        // 16-byte chunks per row
   static constexpr int TMEM_COLS = 2 * BN;                     // Dr, Di
-  static constexpr int N_BITS = BN == 256 ? 8 : (BN == 128 ? 7 : 6);
+  static constexpr int N_BITS = BN == 256 ? 8 : (BN == 128 ? 7 : (BN == 64 ? 6 : 5));
   static constexpr int C_BITS = 7 + N_BITS;                    // log2 entries of the C tile
   static_assert(STAGES >= 3 && PIPE <= TC_PIPE_BUDGET, "bad pipeline");
 };
@@ -220,6 +220,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// CH (32 or 16) consecutive TMEM columns of this warp's lanes.
+template <int CH>
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float* v) {
+  if constexpr (CH == 32) tmem_ld32(taddr, v);
+  else tmem_ld16(taddr, v);
+}
+
 // Two values converted as Conv<T>::from_f does, packed low-first (the byte order of two
 // consecutive entries in memory).
 template <typename T>
@@ -255,19 +262,20 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
   const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
   const int row = (warp & 3) * 32 + lane;
   const int col0 = (warp >> 2) * (BN / 2);
+  constexpr int CH = BN / 2 >= 32 ? 32 : 16;  // TMEM columns per load (16 for 32-wide tiles)
   if (p.splitk > 1) {
     // FP32 partial sums by C's flat index; k_splitk_reduce sums them in a fixed order
     if (ok) {
       float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
       const uint32_t lowmask = (1u << p.runC) - 1u;
 #pragma unroll 1
-      for (int cc = 0; cc < BN / 2; cc += 32) {
-        float vr[32], vi[32];
-        tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-        tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+      for (int cc = 0; cc < BN / 2; cc += CH) {
+        float vr[CH], vi[CH];
+        tmem_ldn<CH>(tmem + lane_addr + col0 + cc, vr);
+        tmem_ldn<CH>(tmem + lane_addr + BN + col0 + cc, vi);
         const uint32_t rm = TCm[row];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < CH; ++j) {
           const uint32_t t = stg_swz(rm ^ TCn[col0 + cc + j]);  // the tables hold swizzled offsets
           part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(vr[j], vi[j]);
         }
@@ -300,12 +308,12 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
     const uint32_t lowmask = (1u << p.runC) - 1u;
     const uint32_t rm = TCm[row];
 #pragma unroll 1
-    for (int cc = 0; cc < BN / 2; cc += 32) {
-      float vr[32], vi[32];
-      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+    for (int cc = 0; cc < BN / 2; cc += CH) {
+      float vr[CH], vi[CH];
+      tmem_ldn<CH>(tmem + lane_addr + col0 + cc, vr);
+      tmem_ldn<CH>(tmem + lane_addr + BN + col0 + cc, vi);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < CH / 8; ++g) {
         const uint32_t t = stg_swz(rm ^ TCn[col0 + cc + 8 * g]);  // C-tile index, low 3 bits 0
         const uint32_t off = hiC[t >> p.runC] + (t & lowmask);
         Vec8<T> r8, i8;
@@ -322,13 +330,13 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
     mx *= scale * (1.f + 0x1p-8f);
   } else if (ok) {
 #pragma unroll 1
-    for (int cc = 0; cc < BN / 2; cc += 32) {
-      float vr[32], vi[32];
-      tmem_ld32(tmem + lane_addr + col0 + cc, vr);
-      tmem_ld32(tmem + lane_addr + BN + col0 + cc, vi);
+    for (int cc = 0; cc < BN / 2; cc += CH) {
+      float vr[CH], vi[CH];
+      tmem_ldn<CH>(tmem + lane_addr + col0 + cc, vr);
+      tmem_ldn<CH>(tmem + lane_addr + BN + col0 + cc, vi);
       const uint32_t rm = TCm[row];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < CH; ++j) {
         const uint32_t idx = rm ^ TCn[col0 + cc + j];  // swizzled staging index
 #if TNC_TC_SELFCHECK
         if (!tc_check(idx < uint32_t(CT), p.status, 16, idx, row)) continue;
@@ -1402,7 +1410,10 @@ cudaError_t launch_tma_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
     if (p.bn == 64 && p.bk == 32) return launch_tma_persist_t<T, 64, 32>(p, s);
     if (p.bn == 64 && p.bk == 16) return launch_tma_persist_t<T, 64, 16>(p, s);
   }
-  if (p.bn == 256) {
+  if (p.bn == 32) {
+    if (p.bk == 32) return launch_tma_st<T, 32, 32>(p, grid, s);
+    if (p.bk == 16) return launch_tma_st<T, 32, 16>(p, grid, s);
+  } else if (p.bn == 256) {
     if (p.bk == 32) return launch_tma_st<T, 256, 32>(p, grid, s);
     if (p.bk == 16) return launch_tma_st<T, 256, 16>(p, grid, s);
   } else if (p.bn == 128) {

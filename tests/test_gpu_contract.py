@@ -99,3 +99,21 @@ def test_gepdot_streamed(ctx, precision, shape, monkeypatch):
     sync, _, _ = run(ctx1, precision, a, la, b, lb, lc)
     assert int(ctx1.profile_read(cap=1)["kind"][0]) in (0, 1)
     assert np.array_equal(got, sync)
+
+
+# Long K loops over a thin operand (at most 4 rows or columns; not GEPDOT-sized outputs): the
+# same ring, the same checks.
+THIN = [(12, 14, 2), (14, 12, 1), (2, 13, 10)]
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf"])
+@pytest.mark.parametrize("shape", THIN)
+def test_thin_long_k_streamed(ctx, precision, shape, monkeypatch):
+    a, la, b, lb, lc = make_case(*shape, seed=19 * sum(shape) + shape[0])
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 7
+    assert metrics.rel_err_norm(got, pairwise.contract(aq, la, bq, lb, lc)) <= TOL[precision]
+    monkeypatch.setenv("TNC_NO_STREAM", "1")
+    ctx1 = T.Context(0)
+    sync, _, _ = run(ctx1, precision, a, la, b, lb, lc)
+    assert np.array_equal(got, sync)

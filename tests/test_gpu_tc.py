@@ -37,11 +37,11 @@ def kmajor_case(m, k, n, seed):
 
 
 def tma_case(m, k, n, seed, direct=False):
-    """Layouts the TMA kernel loads directly: A = [Kt | 7 row labels | rest], B = [Kt | 6-7
+    """Layouts the TMA kernel loads directly: A = [Kt | 7 row labels | rest], B = [Kt | 5-8
     column labels | rest], C's three lowest labels among the tile labels (direct: the first
     three tile columns in order, so the epilogue stores from registers without staging)."""
     kt = 5 if k >= 5 else 4
-    nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else 6)
+    nt = 8 if (n >= 8 and k > kt + 3) else (7 if n >= 7 else (6 if n >= 6 else 5))
     ks = list(range(100, 100 + k))
     ms = list(range(m))
     ns = list(range(200, 200 + n))
@@ -92,7 +92,9 @@ def test_tc_contract_elementwise(ctx, precision, shape):
     assert err <= TOL[precision], err
 
 
-TMA_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (8, 15, 6), (7, 14, 7), (7, 6, 8), (9, 8, 10)]
+# the last four: N = 2^5, 32-wide tiles (16-column TMEM loads in the epilogue), split and not
+TMA_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (8, 15, 6), (7, 14, 7), (7, 6, 8), (9, 8, 10),
+              (9, 8, 5), (8, 13, 5), (7, 4, 5), (12, 10, 5)]
 
 
 @pytest.mark.parametrize("precision", ["chalf", "cbf16"])
@@ -100,6 +102,7 @@ TMA_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (8, 15, 6
 def test_tma_contract(ctx, precision, shape):
     a, la, b, lb, lc = tma_case(*shape, seed=13 * sum(shape) + shape[2], direct=shape[0] % 2 == 1)
     got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) in (4, 5)  # a TMA tensor-core kernel ran
     if len(got) <= 1 << 16:
         err = metrics.rel_err_norm(got, pairwise.contract(aq, la, bq, lb, lc))
     else:
