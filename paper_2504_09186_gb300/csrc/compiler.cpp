@@ -134,6 +134,19 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     grow(t.Mt, M, m);
     grow(t.Nt, N, n);
     grow(t.Kt, Kab, k);
+  } else if (stream) {
+    // a long K loop over a thin operand: all of the thin side, then A's labels in A's order
+    // from its lowest position while they fit, so each tile row of A is one long run
+    grow(t.Nt, N, n);
+    for (int x : la) {
+      if (contains(t.Mt, x) || contains(t.Kt, x)) continue;
+      std::vector<int>& v = contains(K, x) ? t.Kt : t.Mt;
+      v.push_back(x);
+      if (!fits(t.Mt, t.Kt, t.Nt)) {
+        v.pop_back();
+        break;
+      }
+    }
   } else if (k + n <= 6) {
     // absorption of a small tensor: all of B on chip, a wide slice of A
     grow(t.Kt, Kab, k);
@@ -438,12 +451,23 @@ void compile_plan(Plan& plan, bool fuse) {
     TensorInfo ci;
     ci.labels = output_layout(plan.tensors[a].labels, plan.tensors[b].labels);
     const int cid = (int)plan.tensors.size();
-    if (!req[cid].empty()) {
-      // the consumer's tensor-core tile labels lead, in order; the rest keep their order
+    std::vector<int> lead = req[cid];
+    if (lead.empty() && dec[s].ok) {
+      // a tensor-core step whose consumer is not one: its own tile labels lead -- three tile
+      // columns, a tile row, then the rest of the tile -- so its epilogue stores straight from
+      // registers in runs as long as the tile
+      const TileSpec& t = dec[s].t;
+      lead = {t.Nt[0], t.Nt[1], t.Nt[2], t.Mt[0]};
+      lead.insert(lead.end(), t.Nt.begin() + 3, t.Nt.end());
+      lead.insert(lead.end(), t.Mt.begin() + 1, t.Mt.end());
+    }
+    if (!lead.empty()) {
+      // the leading labels in order (the consumer's tensor-core tile labels, or the step's
+      // own); the rest keep their order
       std::vector<int> rest;
       for (int x : ci.labels)
-        if (!contains(req[cid], x)) rest.push_back(x);
-      ci.labels = req[cid];
+        if (!contains(lead, x)) rest.push_back(x);
+      ci.labels = lead;
       ci.labels.insert(ci.labels.end(), rest.begin(), rest.end());
     }
     ci.producer = (int)s;

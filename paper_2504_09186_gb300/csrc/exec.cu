@@ -177,8 +177,11 @@ static void make_tc_launch(StepLaunch& L, const TileSpec& t, const std::vector<i
   const int64_t kit = int64_t(1) << q.n_ok;  // K tiles per output tile
   // persistent TMA kernels overlap each tile's epilogue with the next tile's loads and MMAs:
   // short K loops over many tiles (two TMEM accumulators: BN <= 128), and 256-wide tiles
-  // with the direct epilogue whenever every SM gets two tiles or more
-  q.persistent = ((bn >= 64 && bn <= 128 && q.n_ok <= 3 && tiles >= 4 * 152) || (bn == 256 && q.direct && tiles >= 2 * 152)) ? 1 : 0;
+  // with the direct epilogue whenever every SM gets two tiles or more and a tile's K loop is
+  // at most 256 K tiles (longer loops hide their epilogue, and the hardware's dynamic CTA
+  // scheduling balances long tiles better than a fixed tile order)
+  q.persistent = ((bn >= 64 && bn <= 128 && q.n_ok <= 3 && tiles >= 4 * 152) ||
+                  (bn == 256 && q.direct && tiles >= 2 * 152 && q.n_ok <= 8)) ? 1 : 0;
   // otherwise split over the outer common labels: at least two CTAs per SM (every split
   // keeping at least 4 K tiles), and whole waves (the last one at least 90% busy) when each
   // split keeps at least 256 K tiles, so the FP32 partial sums cost little
@@ -790,7 +793,8 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   // buffer back after draining it into registers, which needs the direct epilogue
   const bool can_persist = L.tp.splitk == 1 && bn >= 64 && (bn <= 128 || L.tp.direct);
   const int64_t tiles_w = (int64_t(1) << (L.tp.n_om + L.tp.n_on)) * prog->W;
-  const bool heuristic = (bn <= 128 && L.tp.n_ok <= 3 && tiles_w >= 4 * 152) || (bn == 256 && tiles_w >= 2 * 152);
+  const bool heuristic =
+      (bn <= 128 && L.tp.n_ok <= 3 && tiles_w >= 4 * 152) || (bn == 256 && L.tp.n_ok <= 8 && tiles_w >= 2 * 152);
   L.tp.persistent = (ch ? ch->persistent != 0 : heuristic) && can_persist ? 1 : 0;
   if (ch && ch->stages) L.tp.stages = ch->stages == 3 ? 3 : 0;
   const size_t eb = elem_bytes(prog->precision);
@@ -871,7 +875,14 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
       prog->steps.push_back(L);
       continue;
     }
-    StepLaunch L = make_launch(st.tile, st.kind, la, lb, lc);
+    // the plan's SIMT tiles size their splits over K for every slice in flight (at most
+    // 2^12); a program whose device holds fewer instances re-sizes them (only the split and
+    // the kind that follows from it change)
+    TileSpec tile = st.tile;
+    int kind = st.kind;
+    if (prog->split_inst < (int64_t(1) << std::min<size_t>(P.sliced.size(), 12)))
+      tile = tile_for(la, lb, lc, (int)prog->split_inst, kind);
+    StepLaunch L = make_launch(tile, kind, la, lb, lc);
     {
       int common = 0;
       for (int x : la) common += std::find(lb.begin(), lb.end(), x) != lb.end();
