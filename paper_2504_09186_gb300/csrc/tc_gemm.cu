@@ -725,13 +725,14 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
 // so the epilogue of one tile also overlaps the loads and MMAs of the next.  Each group
 // synchronises on its own named barrier; one thread per group waits on each mbarrier and
 // shares the outcome, so a timeout ends the group's loop for all of its threads together.
-template <int BN, int BK, int NG>
+template <int BN, int BK, int NG, bool DIRECT = false>
 struct TcpShape {
   static constexpr int ROWB = BK * 2;
   static constexpr int A_BYTES = TC_BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
   static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int STG = TC_BM * BN * 2 * 2;              // one staged C tile (2 planes, 16-bit)
+  // one staged C tile (2 planes, 16-bit); none when every tile stores straight from registers
+  static constexpr int STG = DIRECT ? 0 : TC_BM * BN * 2 * 2;
   static constexpr int NST_FIT = (204 * 1024 - NG * STG) / STAGE;
   static constexpr int NST = NST_FIT > 6 ? 6 : NST_FIT;
   static constexpr int PIPE = NST * STAGE;
@@ -755,9 +756,10 @@ __device__ __forceinline__ void group_bar(int id) {
   asm volatile("barrier.sync %0, %1;\n" ::"r"(id), "n"(N) : "memory");
 }
 
-template <typename T, int BN, int BK, int NG>
-__global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_persist(const __grid_constant__ TcParams p) {
-  using S = TcpShape<BN, BK, NG>;
+template <typename T, int BN, int BK, int NG, bool DIRECT>
+__global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
+    k_tc_tma_persist(const __grid_constant__ TcParams p) {
+  using S = TcpShape<BN, BK, NG, DIRECT>;
   constexpr int KT = BK == 32 ? 5 : 4;
   constexpr int NST = S::NST;
   constexpr int CT = TC_BM * BN;  // entries of the C tile
@@ -960,7 +962,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
       float mx = 0.f;
       const uint32_t rm = TCm[row];
       T* Cre = reinterpret_cast<T*>(p.C) + It.c * p.strideC + oC;
-      if (p.direct) {
+      if (DIRECT || p.direct) {
         // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores straight
         // from registers, no staging; one barrier per tile (TMEM release and block max)
 #pragma unroll 1
@@ -997,6 +999,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
         }
         continue;
       }
+      if constexpr (!DIRECT) {
 #pragma unroll 1
       for (int cc = 0; cc < CPW; cc += 32) {
         float vr[32], vi[32];
@@ -1029,6 +1032,7 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG>::THREADS, 1) k_tc_tma_per
         atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
         if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
       }
+      }  // !DIRECT
     }
   }
   __syncwarp();
@@ -1330,9 +1334,9 @@ size_t tma_wide_smem_bytes_t(int runC) {
          S::EW * 4 + 16 + 64;
 }
 
-template <int BN, int BK, int NG>
+template <int BN, int BK, int NG, bool DIRECT>
 size_t tma_persist_smem_bytes_t(int runC) {
-  using S = TcpShape<BN, BK, NG>;
+  using S = TcpShape<BN, BK, NG, DIRECT>;
   return 1024 + S::PIPE + NG * S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
          (2 * S::NST + 5) * 8 + 16 + NG * S::GW * 4 + 16 + 64;
 }
@@ -1347,14 +1351,14 @@ static int sm_count_cached() {
   return n;
 }
 
-template <typename T, int BN, int BK, int NG>
+template <typename T, int BN, int BK, int NG, bool DIRECT>
 cudaError_t launch_tma_persist_ng(const TcParams& p, cudaStream_t s) {
-  const size_t smem = tma_persist_smem_bytes_t<BN, BK, NG>(p.runC);
-  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_persist<T, BN, BK, NG>), smem);
+  const size_t smem = tma_persist_smem_bytes_t<BN, BK, NG, DIRECT>(p.runC);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_persist<T, BN, BK, NG, DIRECT>), smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = int64_t(p.n_inst) << (p.n_om + p.n_on);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, sm_count_cached());
-  k_tc_tma_persist<T, BN, BK, NG><<<grid, TcpShape<BN, BK, NG>::THREADS, smem, s>>>(p);
+  k_tc_tma_persist<T, BN, BK, NG, DIRECT><<<grid, TcpShape<BN, BK, NG, DIRECT>::THREADS, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -1369,11 +1373,17 @@ cudaError_t launch_tma_wide(const TcParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// two epilogue groups (and a shallower pipeline) for K loops of at most two K tiles
+// Two epilogue groups for short K loops (output-bound tiles): up to four K tiles with the
+// direct epilogue, up to two when staged (the staging buffers shorten the ring); one group
+// otherwise.  Direct variants reserve no staging buffer.
 template <typename T, int BN, int BK>
 cudaError_t launch_tma_persist_t(const TcParams& p, cudaStream_t s) {
-  if (p.n_ok <= 1) return launch_tma_persist_ng<T, BN, BK, 2>(p, s);
-  return launch_tma_persist_ng<T, BN, BK, 1>(p, s);
+  if (p.direct) {
+    if (p.n_ok <= 2) return launch_tma_persist_ng<T, BN, BK, 2, true>(p, s);
+    return launch_tma_persist_ng<T, BN, BK, 1, true>(p, s);
+  }
+  if (p.n_ok <= 1) return launch_tma_persist_ng<T, BN, BK, 2, false>(p, s);
+  return launch_tma_persist_ng<T, BN, BK, 1, false>(p, s);
 }
 
 template <int BN, int BK, int NST>
