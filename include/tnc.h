@@ -100,6 +100,16 @@ typedef struct {
                        /* every slice: per step max(flops / rate, bytes / HBM bandwidth)*/
                        /* (tensor-core rate for steps large enough for its tiles) times */
                        /* the times it runs under tree-like reuse (Sec. III-B)          */
+  int32_t slicing;     /* how the next sliced index is picked: 0 = smallest index     */
+                       /* overhead O(a) of Eq. 1; 1 = lifetime-aware: smallest growth */
+                       /* of the executed cost of all slices under tree-like reuse    */
+                       /* (Sec. III-B), where an index costs only over the steps whose */
+                       /* subtree fixes it.  With 1, objective 0 compares that cost.  */
+  int32_t branch_exchange; /* 1: on the kept trial, exchange the order of two          */
+                       /* consecutive contractions ((x g1) g2 -> (x g2) g1) while that */
+                       /* lowers the cost the slicing uses and every intermediate     */
+                       /* stays within the cap (Sec. III-C: nest sliced indices'      */
+                       /* lifetimes); at most 8 passes                                */
 } tnc_plan_opts;
 
 /* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:
@@ -128,8 +138,24 @@ typedef struct {
                                /* (Sec. VII-B) over the steps                          */
   double model_seconds_per_slice; /* modeled GB300 time of a call over every slice,    */
                                /* divided by 2^s (the objective = 1 cost; complex-half) */
+  double log2_executed_flops;  /* log2 complex multiply-adds of all 2^s slices of one   */
+                               /* bitstring under tree-like reuse (Sec. III-B)          */
 } tnc_plan_info;
 tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
+
+/* Statistics of each sliced index t (slice bit t; Sec. III-B lifetimes, Eq. 1 overheads),
+ * at the plan's final slice set.  Any output pointer may be NULL; cap >= n_sliced.
+ *  first_step, last_step  first / last step (in contraction order) whose operands hold
+ *                         the index: its lifetime
+ *  dep_steps              steps whose subtree fixes the index: they run once per value
+ *                         of it under tree-like reuse
+ *  overhead               2 C / C' with C the per-slice cost and C' that cost with t
+ *                         unsliced (Eq. 1's index overhead, taken last)
+ *  reuse_overhead         the same ratio of the executed cost of all slices under
+ *                         tree-like reuse
+ * Errors: TNC_E_INVALID_ARG (NULL plan, cap too small). */
+tnc_status tnc_plan_slice_stats(tnc_plan p, int32_t* first_step, int32_t* last_step, int32_t* dep_steps,
+                                double* overhead, double* reuse_overhead, int32_t cap);
 
 /* Sliced indices as wire segments: slice bit t (bit t of a slice id) fixes the wire of
  * qubit qubit[t] after cut[t] gates on that qubit.  cap >= n_sliced entries. */

@@ -1,5 +1,6 @@
 // extern "C" entry points of the host-side calls (circuit, network, plan, errors).
 // Device-side calls (context, amplitudes, contract, adjoint) are in exec.cu.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -102,7 +103,12 @@ tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* o
     o.temperature = opts->temperature;
     o.mode = opts->mode;
     o.objective = opts->objective;
+    o.slicing = opts->slicing;
+    o.branch_exchange = opts->branch_exchange;
     if (o.mode != 0 && o.mode != 1) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy) or 1 (stem)");
+    if (o.objective != 0 && o.objective != 1) fail(TNC_E_INVALID_ARG, "plan objective must be 0 or 1");
+    if (o.slicing != 0 && o.slicing != 1) fail(TNC_E_INVALID_ARG, "plan slicing must be 0 (Eq. 1) or 1 (reuse)");
+    if (o.branch_exchange != 0 && o.branch_exchange != 1) fail(TNC_E_INVALID_ARG, "branch_exchange must be 0 or 1");
     auto* p = new tnc_plan_s();
     try {
       plan_greedy(n->n, o, p->p);
@@ -139,6 +145,7 @@ tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info) {
     info->n_fused = P.n_fused;
     info->narrow_max = P.narrow_max;
     info->model_seconds_per_slice = P.model_seconds;
+    info->log2_executed_flops = P.log2_flops_executed;
   });
 }
 
@@ -210,6 +217,22 @@ std::string jlist(const std::vector<int>& v) {
 }
 }  // namespace
 
+tnc_status tnc_plan_slice_stats(tnc_plan p, int32_t* first_step, int32_t* last_step, int32_t* dep_steps,
+                                double* overhead, double* reuse_overhead, int32_t cap) {
+  return guarded([&] {
+    if (!p) fail(TNC_E_INVALID_ARG, "NULL plan");
+    const auto st = slice_stats(p->p);
+    if (cap < (int32_t)st.size()) fail(TNC_E_INVALID_ARG, "cap below the number of sliced indices");
+    for (size_t j = 0; j < st.size(); ++j) {
+      if (first_step) first_step[j] = st[j].first_step;
+      if (last_step) last_step[j] = st[j].last_step;
+      if (dep_steps) dep_steps[j] = st[j].dep_steps;
+      if (overhead) overhead[j] = st[j].overhead;
+      if (reuse_overhead) reuse_overhead[j] = st[j].reuse_overhead;
+    }
+  });
+}
+
 tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
   return guarded([&] {
     if (!p || !len) fail(TNC_E_INVALID_ARG, "NULL argument");
@@ -243,6 +266,16 @@ tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
            ",\"rn\":" + std::to_string(t.rn) + ",\"kgroups\":" + std::to_string(t.kgroups) +
            ",\"tc\":" + std::to_string(S.tc_ok ? 1 : 0) + ",\"chain\":" +
            std::to_string(i < P.step_chain.size() ? P.step_chain[i] : -1);
+      {
+        // narrow rate 2 N_common / (N_A + N_B) of the step (per-slice labels)
+        const auto& la = P.tensors[S.a].labels;
+        const auto& lb = P.tensors[S.b].labels;
+        int nk = 0;
+        for (int x : la) nk += std::find(lb.begin(), lb.end(), x) != lb.end();
+        char nb[48];
+        std::snprintf(nb, sizeof nb, "%.17g", la.size() + lb.size() ? 2.0 * nk / double(la.size() + lb.size()) : 0.0);
+        s += ",\"narrow\":" + std::string(nb);
+      }
       if (S.tc_ok) {
         const TileSpec& u = S.tc_tile;
         s += ",\"tc_tile\":{\"swap\":" + std::to_string(S.tc_swap ? 1 : 0) + ",\"bn\":" + std::to_string(S.tc_bn) +

@@ -106,6 +106,17 @@ struct PlanOpts {
   double temperature = 0.5;
   int mode = 0;       // 0 greedy, 1 stem
   int objective = 0;  // 0 fewest multiply-adds, 1 least modeled GB300 time
+  int slicing = 0;    // 0 index overhead of Eq. 1; 1 executed cost under tree-like reuse
+  int branch_exchange = 0;  // 1: reorder consecutive contractions to shorten lifetimes
+};
+
+// One sliced index of a plan (slice bit t): its lifetime in the contraction order, the steps
+// whose results depend on it, and its overheads at the plan's final slice set.
+struct SliceStat {
+  int first_step = -1, last_step = -1;  // first / last step with the index in an operand
+  int dep_steps = 0;                    // steps whose subtree fixes the index
+  double overhead = 1;                  // 2 C / C(without it): Eq. 1
+  double reuse_overhead = 1;            // the same ratio of executed cost under tree-like reuse
 };
 
 // Kernel classes of a compiled step.
@@ -167,6 +178,7 @@ struct Plan {
   std::vector<Step> steps;                 // compiled program (may fuse tree steps)
   int root = -1;
   double log2_flops_slice = 0, log2_flops_total = 0, overhead = 1;
+  double log2_flops_executed = 0;  // all slices of one bitstring row under tree-like reuse
   double model_seconds = 0;  // modeled GB300 time of one slice (step_model_seconds summed)
   int max_log2 = 0;
   int64_t arena_elems = 0;                 // per instance, in scalars, unfused program
@@ -188,6 +200,7 @@ struct Plan {
 };
 
 void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan);
+std::vector<SliceStat> slice_stats(const Plan& plan);
 // (Re)compile the program of a plan whose tree and slices are set.
 void compile_plan(Plan& plan, bool fuse);
 

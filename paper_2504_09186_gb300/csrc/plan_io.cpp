@@ -1,5 +1,5 @@
 // Plan persistence.  Binary little-endian file:
-//   "TNCPLAN3", n_qubits, n_gates, gates (arity, q0, q1, 16 complex128), open mask,
+//   "TNCPLAN4", n_qubits, n_gates, gates (arity, q0, q1, 16 complex128), open mask,
 //   options, sliced edge ids, tree pairs, cost summary.
 // Loading rebuilds the network from the stored circuit (the build is deterministic, so
 // edge ids match) and recompiles the step program.
@@ -12,7 +12,7 @@
 namespace tnc {
 
 namespace {
-const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '3'};
+const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '4'};
 
 template <class T>
 void put(std::ofstream& f, const T& v) {
@@ -54,6 +54,8 @@ void save_plan(const Plan& p, const std::string& path) {
   put<double>(f, p.opts.temperature);
   put<int32_t>(f, p.opts.mode);
   put<int32_t>(f, p.opts.objective);
+  put<int32_t>(f, p.opts.slicing);
+  put<int32_t>(f, p.opts.branch_exchange);
   put<int32_t>(f, (int32_t)p.sliced.size());
   for (int e : p.sliced) put<int32_t>(f, e);
   put<int32_t>(f, (int32_t)p.tree.size());
@@ -64,6 +66,7 @@ void save_plan(const Plan& p, const std::string& path) {
   put<double>(f, p.log2_flops_slice);
   put<double>(f, p.log2_flops_total);
   put<double>(f, p.overhead);
+  put<double>(f, p.log2_flops_executed);
   if (!f) fail(7, "write failed: " + path);
 }
 
@@ -104,6 +107,8 @@ void load_plan(const std::string& path, Plan& p) {
   p.opts.temperature = get<double>(f);
   p.opts.mode = get<int32_t>(f);
   p.opts.objective = get<int32_t>(f);
+  p.opts.slicing = get<int32_t>(f);
+  p.opts.branch_exchange = get<int32_t>(f);
   const int32_t ns = get<int32_t>(f);
   if (ns < 0 || ns > (int32_t)net.edges.size()) fail(7, "corrupt slice count");
   for (int i = 0; i < ns; ++i) {
@@ -124,6 +129,9 @@ void load_plan(const std::string& path, Plan& p) {
   p.log2_flops_slice = get<double>(f);
   p.log2_flops_total = get<double>(f);
   p.overhead = get<double>(f);
+  p.log2_flops_executed = get<double>(f);
+  if (p.opts.slicing < 0 || p.opts.slicing > 1 || p.opts.branch_exchange < 0 || p.opts.branch_exchange > 1)
+    fail(7, "corrupt plan options");
   compile_plan(p, true);
 }
 

@@ -204,13 +204,75 @@ double model_time(const Tree& t, const std::vector<char>& sliced, const std::vec
   return tot;
 }
 
-}  // namespace
+// Executed complex multiply-adds of all 2^s slices of one bitstring row under tree-like
+// reuse (Sec. III-B): each step's per-slice cost times the assignments of the sliced indices
+// its subtree fixes.  Lifetime-aware: an index costs only over the steps that depend on it.
+double reuse_cost(const Tree& t, const std::vector<char>& sliced, const std::vector<int>& sliced_list) {
+  std::vector<uint64_t> dep(t.sets.size(), 0);
+  const size_t n_leaves = t.sets.size() - t.pairs.size();
+  for (size_t i = 0; i < n_leaves; ++i)
+    for (size_t j = 0; j < sliced_list.size() && j < 64; ++j)
+      if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), sliced_list[j])) dep[i] |= uint64_t(1) << j;
+  double tot = 0;
+  for (size_t k = 0; k < t.pairs.size(); ++k) {
+    const auto& p = t.pairs[k];
+    dep[n_leaves + k] = dep[p.first] | dep[p.second];
+    const int u = (int)count_not_in(set_union(t.sets[p.first], t.sets[p.second]), sliced);
+    tot += std::ldexp(1.0, u + __builtin_popcountll(dep[n_leaves + k]));
+  }
+  return tot;
+}
 
-void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
-  if (o.trials < 1 || o.log2_cap < 1 || o.log2_cap > 34 || o.slices_min < 0 || o.slices_max < 0)
-    fail(1, "plan_greedy: bad options");
-  const int n_edges = (int)net.edges.size();
-  // contraction-level labels of each leaf: closed outputs are fixed per bitstring
+// Branch exchange (Sec. III-C): when step k2 contracts the result of step k1 = (x, g1) with
+// g2, the order of g1 and g2 may be exchanged -- k1 = (x, g2), k2 = (k1, g1) -- which leaves
+// k2's result unchanged and moves g1's indices' lifetimes later.  Swaps that lower the cost
+// (executed cost under reuse, or Eq. 1's when `reuse` is false) and keep every intermediate
+// within the cap are kept, pass after pass until none helps (at most `passes`).
+void branch_exchange(Tree& t, const std::vector<char>& sliced, const std::vector<int>& sliced_list, int log2_cap,
+                     bool reuse, int passes) {
+  const int L = (int)(t.sets.size() - t.pairs.size());
+  auto cost = [&]() { return reuse ? reuse_cost(t, sliced, sliced_list) : tree_cost(t, sliced); };
+  double cur = cost();
+  for (int pass = 0; pass < passes; ++pass) {
+    bool improved = false;
+    for (int k2 = 0; k2 < (int)t.pairs.size(); ++k2) {
+      for (int side = 0; side < 2; ++side) {
+        auto& p2 = t.pairs[k2];
+        const int n1 = side == 0 ? p2.first : p2.second;
+        const int g2 = side == 0 ? p2.second : p2.first;
+        if (n1 < L) continue;
+        const int k1 = n1 - L;
+        if (g2 >= L + k1) continue;  // g2 must exist before step k1
+        auto& p1 = t.pairs[k1];
+        for (int which = 0; which < 2; ++which) {
+          const int g1 = which == 0 ? p1.second : p1.first;
+          const int x = which == 0 ? p1.first : p1.second;
+          const LabelSet new_n1 = sym_diff(t.sets[x], t.sets[g2]);
+          if ((int)count_not_in(new_n1, sliced) > log2_cap) continue;
+          const auto save1 = p1, save2 = p2;
+          const LabelSet save_set = t.sets[n1];
+          p1 = {x, g2};
+          if (side == 0) p2 = {n1, g1};
+          else p2 = {g1, n1};
+          t.sets[n1] = new_n1;
+          const double c = cost();
+          if (c < cur * (1 - 1e-9)) {
+            cur = c;
+            improved = true;
+            break;
+          }
+          p1 = save1;
+          p2 = save2;
+          t.sets[n1] = save_set;
+        }
+      }
+    }
+    if (!improved) break;
+  }
+}
+
+// Contraction-level labels of each leaf: closed outputs are fixed per bitstring.
+std::vector<LabelSet> contraction_leaves(const Network& net) {
   std::vector<LabelSet> leaves;
   for (const Leaf& l : net.leaves) {
     LabelSet s;
@@ -219,6 +281,57 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
     std::sort(s.begin(), s.end());
     leaves.push_back(s);
   }
+  return leaves;
+}
+
+}  // namespace
+
+std::vector<SliceStat> slice_stats(const Plan& plan) {
+  Tree t;
+  t.sets = contraction_leaves(plan.net);
+  const int L = (int)t.sets.size();
+  for (auto& p : plan.tree) {
+    t.pairs.push_back(p);
+    t.sets.push_back(sym_diff(t.sets[p.first], t.sets[p.second]));
+  }
+  std::vector<char> sl(plan.net.edges.size(), 0);
+  for (int e : plan.sliced) sl[e] = 1;
+  const double c_all = tree_cost(t, sl), r_all = reuse_cost(t, sl, plan.sliced);
+  std::vector<SliceStat> out(plan.sliced.size());
+  for (size_t j = 0; j < plan.sliced.size(); ++j) {
+    const int e = plan.sliced[j];
+    SliceStat& st = out[j];
+    std::vector<char> dep(t.sets.size(), 0);
+    for (int i = 0; i < L; ++i) dep[i] = std::binary_search(t.sets[i].begin(), t.sets[i].end(), e) ? 1 : 0;
+    for (size_t k = 0; k < t.pairs.size(); ++k) {
+      const auto& p = t.pairs[k];
+      const bool in_op = std::binary_search(t.sets[p.first].begin(), t.sets[p.first].end(), e) ||
+                         std::binary_search(t.sets[p.second].begin(), t.sets[p.second].end(), e);
+      if (in_op) {
+        if (st.first_step < 0) st.first_step = (int)k;
+        st.last_step = (int)k;
+      }
+      dep[L + k] = dep[p.first] | dep[p.second];
+      st.dep_steps += dep[L + k];
+    }
+    std::vector<int> rest;
+    for (int x : plan.sliced)
+      if (x != e) rest.push_back(x);
+    sl[e] = 0;
+    st.overhead = 2.0 * c_all / tree_cost(t, sl);
+    st.reuse_overhead = r_all / reuse_cost(t, sl, rest);
+    sl[e] = 1;
+  }
+  return out;
+}
+
+void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
+  if (o.trials < 1 || o.log2_cap < 1 || o.log2_cap > 34 || o.slices_min < 0 || o.slices_max < 0)
+    fail(1, "plan_greedy: bad options");
+  const int n_edges = (int)net.edges.size();
+  if (o.slicing < 0 || o.slicing > 1 || o.branch_exchange < 0 || o.branch_exchange > 1)
+    fail(1, "plan_greedy: bad options");
+  std::vector<LabelSet> leaves = contraction_leaves(net);
   if (leaves.empty()) fail(5, "plan_greedy: empty network");
   std::vector<char> is_open(n_edges, 0);
   for (int e : net.open_edge) is_open[e] = 1;
@@ -259,14 +372,23 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       int pick = -1;
       double pick_cost = 0;
       int pick_over = -1;
+      const double rcur = o.slicing == 1 ? reuse_cost(t, sl, sliced) : 0.0;
       for (int e : cand) {
         sl[e] = 1;
-        double ce = tree_cost(t, sl);
+        double ov;
+        if (o.slicing == 1) {
+          // lifetime-aware: the executed cost under tree-like reuse grows by this factor
+          std::vector<int> with = sliced;
+          with.push_back(e);
+          ov = reuse_cost(t, sl, with) / rcur;
+        } else {
+          // index overhead O(e) = 2 C_e / C (Eq. 1)
+          ov = 2.0 * tree_cost(t, sl) / cur;
+        }
         int over = 0;
         for (auto& s : t.sets) over += (int)count_not_in(s, sl) > o.log2_cap;
         sl[e] = 0;
-        // index overhead O(e) = 2 C_e / C (Eq. 1); ties: fewer oversized tensors left
-        double ov = 2.0 * ce / cur;
+        // ties: fewer oversized tensors left
         if (pick < 0 || ov < pick_cost * (1 - 1e-12) || (std::fabs(ov - pick_cost) <= 1e-12 * pick_cost && over < pick_over)) {
           pick = e;
           pick_cost = ov;
@@ -292,7 +414,9 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       cur = tree_cost(t, sl);
     }
     const double total = std::ldexp(cur, (int)sliced.size());
-    const double score = o.objective == 1 ? model_time(t, sl, sliced) : total;
+    // objective 0 with the lifetime-aware slicer: executed multiply-adds under reuse
+    const double score =
+        o.objective == 1 ? model_time(t, sl, sliced) : (o.slicing == 1 ? reuse_cost(t, sl, sliced) : total);
     const bool within = (int)sliced.size() <= o.slices_max;
     bool better;
     if (within != best.within_max) better = within;
@@ -308,6 +432,15 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
     }
   }
   if (!std::isfinite(best.total)) fail(5, "plan_greedy: no trial met the size cap");
+  if (o.branch_exchange) {
+    // on the kept trial, with its slice set
+    std::vector<char> sl(n_edges, 0);
+    for (int e : best.sliced) sl[e] = 1;
+    branch_exchange(best.tree, sl, best.sliced, o.log2_cap, o.slicing == 1, 8);
+    best.per_slice = tree_cost(best.tree, sl);
+    best.total = std::ldexp(best.per_slice, (int)best.sliced.size());
+    best.unsliced = tree_cost(best.tree, std::vector<char>(n_edges, 0));
+  }
 
   plan = Plan();
   plan.net = net;
@@ -317,6 +450,11 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
   plan.log2_flops_slice = std::log2(best.per_slice);
   plan.log2_flops_total = std::log2(best.total);
   plan.overhead = best.total / best.unsliced;
+  {
+    std::vector<char> sl(n_edges, 0);
+    for (int e : best.sliced) sl[e] = 1;
+    plan.log2_flops_executed = std::log2(reuse_cost(best.tree, sl, best.sliced));
+  }
   compile_plan(plan, true);
 }
 

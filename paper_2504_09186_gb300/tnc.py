@@ -48,6 +48,8 @@ class tnc_plan_opts(C.Structure):
         ("temperature", C.c_double),
         ("mode", C.c_int32),
         ("objective", C.c_int32),
+        ("slicing", C.c_int32),
+        ("branch_exchange", C.c_int32),
     ]
 
 
@@ -68,6 +70,7 @@ class tnc_plan_info(C.Structure):
         ("n_fused", C.c_int32),
         ("narrow_max", C.c_double),
         ("model_seconds_per_slice", C.c_double),
+        ("log2_executed_flops", C.c_double),
     ]
 
 
@@ -115,6 +118,8 @@ def load_library(path: str = LIB_PATH):
         "tnc_plan_greedy": [vp, C.POINTER(tnc_plan_opts), C.POINTER(vp)],
         "tnc_plan_get_info": [vp, C.POINTER(tnc_plan_info)],
         "tnc_plan_sliced_cuts": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32],
+        "tnc_plan_slice_stats": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), i32],
         "tnc_plan_open_qubits": [vp, C.POINTER(C.c_int32), i32],
         "tnc_plan_describe": [vp, C.c_char_p, i64, C.POINTER(C.c_int64)],
         "tnc_plan_save": [vp, C.c_char_p],
@@ -187,9 +192,10 @@ def tnc_network_build(circuit, open_mask: Optional[np.ndarray]):
 
 
 def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5, mode=0,
-                    objective=0):
+                    objective=0, slicing=0, branch_exchange=0):
     lib = load_library()
-    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode, objective)
+    o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode, objective, slicing,
+                      branch_exchange)
     h = C.c_void_p()
     _check(lib.tnc_plan_greedy(network, C.byref(o), C.byref(h)))
     return h
@@ -206,11 +212,14 @@ class Plan:
     @classmethod
     def greedy(cls, circuit, open_qubits: Sequence[int] = (), seed: int = 1, trials: int = 16, log2_cap: int = 26,
                slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy",
-               objective: str = "flops") -> "Plan":
+               objective: str = "flops", slicing: str = "eq1", branch_exchange: bool = False) -> "Plan":
         """Plan for an `inputs.Circuit` (gate list) with the given open output qubits.
         mode: "greedy" (balanced pairwise order) or "stem" (one tensor absorbs leaves).
         objective: which trial is kept -- "flops" (fewest multiply-adds) or "time" (least
-        modeled GB300 time)."""
+        modeled GB300 time).
+        slicing: "eq1" (index overhead of Eq. 1) or "reuse" (lifetime-aware: executed cost
+        under tree-like reuse).  branch_exchange: reorder consecutive contractions of the
+        kept trial while that lowers the slicing's cost."""
         lib = load_library()
         arity, qubits, mats = circuit.gate_array()
         ch = tnc_circuit_from_gates(circuit.n_qubits, arity, qubits, mats)
@@ -220,7 +229,8 @@ class Plan:
             nh = tnc_network_build(ch, mask)
             try:
                 ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature,
-                                     {"greedy": 0, "stem": 1}[mode], {"flops": 0, "time": 1}[objective])
+                                     {"greedy": 0, "stem": 1}[mode], {"flops": 0, "time": 1}[objective],
+                                     {"eq1": 0, "reuse": 1}[slicing], int(bool(branch_exchange)))
             finally:
                 lib.tnc_network_destroy(nh)
         finally:
@@ -256,6 +266,19 @@ class Plan:
         i = tnc_plan_info()
         _check(load_library().tnc_plan_get_info(self.h, C.byref(i)))
         return {name: getattr(i, name) for name, _ in tnc_plan_info._fields_}
+
+    def slice_stats(self) -> dict:
+        """Per sliced index (slice bit t): lifetime (first / last step holding it), steps that
+        depend on it, and its Eq. 1 and tree-reuse overheads (tnc_plan_slice_stats)."""
+        n = self.info()["n_sliced"]
+        m = max(n, 1)
+        first, last, dep = (np.zeros(m, dtype=np.int32) for _ in range(3))
+        ov, rov = np.zeros(m), np.zeros(m)
+        _check(load_library().tnc_plan_slice_stats(self.h, _i32p(first), _i32p(last), _i32p(dep),
+                                                   ov.ctypes.data_as(C.POINTER(C.c_double)),
+                                                   rov.ctypes.data_as(C.POINTER(C.c_double)), m))
+        return {"first_step": first[:n], "last_step": last[:n], "dep_steps": dep[:n], "overhead": ov[:n],
+                "reuse_overhead": rov[:n]}
 
     def sliced_cuts(self):
         n = self.info()["n_sliced"]

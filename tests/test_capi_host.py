@@ -214,3 +214,68 @@ def test_tensor_core_layouts_allow_direct_epilogues():
     direct.sort()
     assert direct[-1][1] and direct[-2][1]
     assert sum(dr for _, dr in direct) >= 0.75 * len(direct)
+
+
+def _contraction_sets(d):
+    """Label sets of every tree node with the sliced labels kept: leaves without their closed
+    output legs (fixed per bitstring), intermediates as symmetric differences."""
+    sets = []
+    for lf in d["leaves"]:
+        sets.append({e for e in lf["labels"] if not (d["edges"][e][2] == 2 and not d["edges"][e][3])})
+    for a, b in d["tree"]:
+        sets.append(sets[a] ^ sets[b])
+    return sets
+
+
+@pytest.mark.parametrize("slicing,exchange", [("eq1", False), ("eq1", True), ("reuse", False), ("reuse", True)])
+def test_slice_stats_and_executed_cost_recount(slicing, exchange):
+    """Lifetimes, dependent steps, Eq. 1 and tree-reuse overheads of every sliced index, and
+    the executed cost under tree-like reuse (Sec. III-B), recounted from the plan's tree."""
+    c = grid_circuit(4, 4, 10, seed=1)
+    _, open_q = subcube_spec(16, 3, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=5, trials=6, log2_cap=10, slices_min=4, slicing=slicing,
+                      branch_exchange=exchange)
+    d, info, st = p.describe(), p.info(), p.slice_stats()
+    sets = _contraction_sets(d)
+    L, S = len(d["leaves"]), d["sliced"]
+    assert info["max_log2_size"] <= 10 and len(S) >= 4
+
+    def deps(e):
+        dep = [e in sets[i] for i in range(L)]
+        for a, b in d["tree"]:
+            dep.append(dep[a] or dep[b])
+        return dep
+
+    def cost(sl):
+        return sum(2.0 ** len((sets[a] | sets[b]) - set(sl)) for a, b in d["tree"])
+
+    def reuse_cost(sl):
+        dmask = [sum(1 << j for j, e in enumerate(sl) if e in sets[i]) for i in range(L)]
+        tot = 0.0
+        for a, b in d["tree"]:
+            dmask.append(dmask[a] | dmask[b])
+            tot += 2.0 ** (len((sets[a] | sets[b]) - set(sl)) + bin(dmask[-1]).count("1"))
+        return tot
+
+    assert math.isclose(info["log2_executed_flops"], math.log2(reuse_cost(S)), rel_tol=1e-12)
+    for t, e in enumerate(S):
+        steps = [k for k, (a, b) in enumerate(d["tree"]) if e in sets[a] or e in sets[b]]
+        assert st["first_step"][t] == steps[0] and st["last_step"][t] == steps[-1]
+        assert st["dep_steps"][t] == sum(deps(e)[L:])
+        rest = [x for x in S if x != e]
+        assert math.isclose(st["overhead"][t], 2 * cost(S) / cost(rest), rel_tol=1e-12)
+        assert math.isclose(st["reuse_overhead"][t], reuse_cost(S) / reuse_cost(rest), rel_tol=1e-12)
+
+
+def test_branch_exchange_never_raises_the_slicing_cost():
+    """Branch exchange keeps the kept trial's slice set and only takes swaps that lower the
+    cost its slicing uses: Eq. 1's per-slice cost, or the executed cost under reuse."""
+    c = grid_circuit(5, 6, 14, seed=1)
+    fixed, open_q = subcube_spec(30, 10, seed=2)
+    kw = dict(open_qubits=open_q, seed=3, trials=16, log2_cap=26, slices_min=6, slices_max=6)
+    for slicing, key in (("eq1", "log2_flops_per_slice"), ("reuse", "log2_executed_flops")):
+        a = T.Plan.greedy(c, slicing=slicing, **kw)
+        b = T.Plan.greedy(c, slicing=slicing, branch_exchange=True, **kw)
+        assert a.describe()["sliced"] == b.describe()["sliced"]
+        assert b.info()[key] <= a.info()[key] + 1e-12
+        assert b.info()["max_log2_size"] <= 26

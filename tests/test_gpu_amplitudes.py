@@ -181,3 +181,20 @@ def test_sharded_slices_with_gpu_chunks(ctx, tmp_path):
     full = ctx.amplitudes(p, fixed[None, :], "c64")
     assert np.allclose(got, full, rtol=1e-12, atol=1e-15)
     assert metrics.rel_err_norm(got[0], sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))) <= 1e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("c64", 1e-5), ("chalf", 1e-2)])
+def test_lifetime_aware_slicing_and_branch_exchange_plan(ctx, precision, tol):
+    """A plan sliced by executed cost under tree-like reuse, with branch exchange, contracts
+    to the state-vector amplitudes, and its reuse run equals the run of every slice."""
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=14, slices_min=4, slicing="reuse",
+                      branch_exchange=True)
+    assert p.info()["n_sliced"] >= 4
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    got = ctx.amplitudes(p, fixed[None, :], precision)[0]
+    assert metrics.rel_err_norm(got, ref) <= tol
+    n = 1 << p.info()["n_sliced"]
+    parts = sum(ctx.amplitudes(p, fixed[None, :], precision, slice_begin=s, slice_count=1)[0] for s in range(n))
+    assert metrics.rel_err_norm(parts, got) <= 1e-12 if precision == "c64" else metrics.rel_err_norm(parts, got) <= tol
