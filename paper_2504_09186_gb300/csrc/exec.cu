@@ -499,8 +499,18 @@ struct DeviceProgram {
   // CUDA graphs of one wave, keyed by the wave's launch parameters (see tnc_amplitudes)
   std::map<std::string, cudaGraphExec_t> graphs;
   std::map<std::string, int> graph_seen;
+  // concurrent schedule of the launches (see make_schedule): the lane each runs on and, per
+  // launch, the latest launch it must follow on every other lane (-1: none); a launch records
+  // its event only when a launch on another lane waits for it
+  int n_lanes = 1;
+  std::vector<int> lane;
+  std::vector<std::vector<int>> wait_on;  // [launch][lane]
+  std::vector<char> signals;
+  std::vector<cudaEvent_t> done_ev;
   ~DeviceProgram() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto e : done_ev)
+      if (e) cudaEventDestroy(e);
     arena.release();
     maxabs.release();
     exps.release();
@@ -511,6 +521,7 @@ struct DeviceProgram {
     chain_links.release();
     leaf_r.release();
     inst_c.release();
+    cudaGetLastError();  // a failed release must not surface as the next launch's error
   }
 };
 
@@ -556,8 +567,16 @@ struct tnc_context_s {
   bool no_persist = false;  // TNC_NO_PERSIST=1: short-K TMA steps use one CTA per tile
   bool no_reuse = false;    // TNC_NO_REUSE=1: every step runs for every (row, slice)
   bool no_stream = false;   // TNC_NO_STREAM=1: GEPDOT steps load tiles synchronously (k_generic)
+  bool serial = false;      // TNC_SERIAL=1: every launch of a wave on one stream
+  cudaStream_t lanes[4] = {nullptr, nullptr, nullptr, nullptr};  // streams of concurrent branches
+  cudaEvent_t fork_ev = nullptr, join_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   ProfState prof;
   ~tnc_context_s() {
+    for (auto l : lanes)
+      if (l) cudaStreamDestroy(l);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    for (auto e : join_ev)
+      if (e) cudaEventDestroy(e);
     bits.release();
     inst_slice.release();
     inst_row.release();
@@ -818,6 +837,83 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   return L;
 }
 
+// Concurrent schedule of an unfused program's launches (launch k = plan step k).  Launch k
+// must follow: the producers of its operands; every earlier launch that read or wrote arena
+// memory overlapping its result (the arena reuses the memory of dead tensors, assuming the
+// plan's order); and, when it splits over K, the previous launch that used the shared
+// partial-sum buffer.  Launches are dealt greedily to kLanes lanes: onto the lane of the
+// latest launch they follow when that launch is the lane's last, else onto the lane idle
+// longest.  Results do not change: every launch computes the same values in any order that
+// respects these dependencies.
+constexpr int kLanes = 4;
+
+static void make_schedule(const Plan& P, DeviceProgram* prog) {
+  const int n = (int)prog->steps.size();
+  for (auto e : prog->done_ev)
+    if (e) cudaEventDestroy(e);
+  prog->done_ev.clear();
+  prog->n_lanes = 1;
+  prog->lane.assign(n, 0);
+  prog->wait_on.assign(n, std::vector<int>(kLanes, -1));
+  prog->signals.assign(n, 0);
+  if (n != (int)P.steps.size() || n < 2) return;
+  for (const auto& L : prog->steps)
+    if (L.kind == K_CHAIN) return;
+  auto region = [&](int t) {
+    const int64_t off = prog_off(P, prog, t);
+    return std::make_pair(off, off + 2 * (int64_t(1) << P.tensors[t].labels.size()));
+  };
+  auto overlap = [](std::pair<int64_t, int64_t> x, std::pair<int64_t, int64_t> y) {
+    return x.first < y.second && y.first < x.second;
+  };
+  std::vector<int> producer(P.tensors.size(), -1);
+  std::vector<std::vector<int>> deps(n);
+  int last_split = -1;
+  for (int k = 0; k < n; ++k) {
+    const Step& st = P.steps[k];
+    const auto rc = region(st.c);
+    std::vector<int>& d = deps[k];
+    for (int t : {st.a, st.b})
+      if (producer[t] >= 0) d.push_back(producer[t]);
+    for (int j = 0; j < k; ++j) {
+      const Step& sj = P.steps[j];
+      if (overlap(rc, region(sj.c)) || overlap(rc, region(sj.a)) || overlap(rc, region(sj.b))) d.push_back(j);
+    }
+    const StepLaunch& L = prog->steps[k];
+    const bool split = L.kind == K_SPLITK || ((L.kind == K_TC || L.kind == K_TMA) && L.tp.splitk > 1);
+    if (split) {
+      if (last_split >= 0) d.push_back(last_split);
+      last_split = k;
+    }
+    producer[st.c] = k;
+  }
+  // lanes
+  std::vector<int> lane_last(kLanes, -1);
+  for (int k = 0; k < n; ++k) {
+    int pick = -1, best_dep = -1;
+    for (int j : deps[k])
+      for (int l = 0; l < kLanes; ++l)
+        if (lane_last[l] == j && j > best_dep) best_dep = j, pick = l;
+    if (pick < 0) {
+      pick = 0;
+      for (int l = 1; l < kLanes; ++l)
+        if (lane_last[l] < lane_last[pick]) pick = l;
+    }
+    prog->lane[k] = pick;
+    lane_last[pick] = k;
+    for (int j : deps[k]) {
+      const int l = prog->lane[j];
+      if (l != pick && j > prog->wait_on[k][l]) prog->wait_on[k][l] = j;
+    }
+    for (int l = 0; l < kLanes; ++l)
+      if (prog->wait_on[k][l] >= 0) prog->signals[prog->wait_on[k][l]] = 1;
+  }
+  prog->n_lanes = kLanes;
+  prog->done_ev.assign(n, nullptr);
+  for (int k = 0; k < n; ++k)
+    if (prog->signals[k]) CUDA_OK(cudaEventCreateWithFlags(&prog->done_ev[k], cudaEventDisableTiming));
+}
+
 static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W,
                                                     bool fuse) {
   const Plan& P = plan->p;
@@ -967,10 +1063,21 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   for (int j = 0; j < prog->n_open; ++j) opos[j] = (int8_t)pos_of(P.tensors[P.root].labels, P.net.open_edge[j]);
   prog->open_pos.reserve(opos.size());
   CUDA_OK(cudaMemcpy(prog->open_pos.p, opos.data(), opos.size(), cudaMemcpyHostToDevice));
+  if (!ctx->serial) make_schedule(P, prog.get());
   return prog;
 }
 
 static void set_device(tnc_context_s* ctx) { CUDA_OK(cudaSetDevice(ctx->device)); }
+
+// The context's lane streams and fork / join events, created on first use.
+static void ensure_lanes(tnc_context_s* ctx) {
+  if (ctx->fork_ev) return;
+  for (int l = 0; l < kLanes; ++l) {
+    CUDA_OK(cudaStreamCreateWithFlags(&ctx->lanes[l], cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&ctx->join_ev[l], cudaEventDisableTiming));
+  }
+  CUDA_OK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+}
 
 // Reads and clears the device status word (after the stream has drained).
 static void check_status(tnc_context_s* ctx) {
@@ -1073,6 +1180,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->no_reuse = env4 && env4[0] == '1';
     const char* env5 = std::getenv("TNC_NO_STREAM");
     c->no_stream = env5 && env5[0] == '1';
+    const char* env6 = std::getenv("TNC_SERIAL");
+    c->serial = env6 && env6[0] == '1';
     *out = c;
   });
 }
@@ -1246,10 +1355,30 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
                                  ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(),
                                  n, prog->maxabs.as<float>(), prog->exps.as<int32_t>(), prog->n_slots, base, cnt,
                                  prog->leaf_r.as<double2>(), s));
-      for (size_t k = 0; k < prog->steps.size(); ++k) {
-        if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
-        run_step(precision, prog->steps[k], cnt, s, reuse);
-        if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
+      if (prog->n_lanes > 1) {
+        // concurrent branches: fork the lanes from s, follow the schedule, join back into s
+        ensure_lanes(ctx);
+        CUDA_OK(cudaEventRecord(ctx->fork_ev, s));
+        for (int l = 0; l < prog->n_lanes; ++l) CUDA_OK(cudaStreamWaitEvent(ctx->lanes[l], ctx->fork_ev, 0));
+        for (size_t k = 0; k < prog->steps.size(); ++k) {
+          cudaStream_t ls = ctx->lanes[prog->lane[k]];
+          for (int l = 0; l < prog->n_lanes; ++l)
+            if (prog->wait_on[k][l] >= 0) CUDA_OK(cudaStreamWaitEvent(ls, prog->done_ev[prog->wait_on[k][l]], 0));
+          if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), ls));
+          run_step(precision, prog->steps[k], cnt, ls, reuse);
+          if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), ls));
+          if (prog->signals[k]) CUDA_OK(cudaEventRecord(prog->done_ev[k], ls));
+        }
+        for (int l = 0; l < prog->n_lanes; ++l) {
+          CUDA_OK(cudaEventRecord(ctx->join_ev[l], ctx->lanes[l]));
+          CUDA_OK(cudaStreamWaitEvent(s, ctx->join_ev[l], 0));
+        }
+      } else {
+        for (size_t k = 0; k < prog->steps.size(); ++k) {
+          if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
+          run_step(precision, prog->steps[k], cnt, s, reuse);
+          if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
+        }
       }
       CUDA_OK(launch_inst_scale(prog->leaf_r.as<double2>(), prog->n_leaves, cnt, prog->inst_c.as<double2>(), s));
       CUDA_OK(launch_root_accum(precision, prog->arena.p, prog->inst_stride, prog->root_off, prog->root_plane,
@@ -1407,10 +1536,12 @@ static void tune_program(tnc_context_s* ctx, const Plan& P, DeviceProgram* prog,
       g_tune.erase(key);
     }
   }
-  // captured waves hold the old launch parameters
+  // captured waves hold the old launch parameters, and a changed split changes the schedule
   for (auto& kv : prog->graphs) cudaGraphExecDestroy(kv.second);
   prog->graphs.clear();
   prog->graph_seen.clear();
+  CUDA_OK(cudaStreamSynchronize(s));
+  if (!ctx->serial) make_schedule(P, prog);
   CUDA_OK(cudaStreamSynchronize(s));
   check_status(ctx);
   if (info) {

@@ -198,3 +198,19 @@ def test_lifetime_aware_slicing_and_branch_exchange_plan(ctx, precision, tol):
     n = 1 << p.info()["n_sliced"]
     parts = sum(ctx.amplitudes(p, fixed[None, :], precision, slice_begin=s, slice_count=1)[0] for s in range(n))
     assert metrics.rel_err_norm(parts, got) <= 1e-12 if precision == "c64" else metrics.rel_err_norm(parts, got) <= tol
+
+
+def test_concurrent_branches_with_splits_match_serial(monkeypatch):
+    """A plan with split-K steps (GEPDOT-shaped) and many small branches: the concurrent
+    schedule equals the serial one bit for bit, per slice and over all slices."""
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 2, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=12, slices_min=3)
+    ctx = T.Context(0)
+    got = {prec: ctx.amplitudes(p, fixed[None, :], prec) for prec in ("c64", "chalf")}
+    one = ctx.amplitudes(p, fixed[None, :], "chalf", slice_begin=1, slice_count=1)
+    monkeypatch.setenv("TNC_SERIAL", "1")
+    ctx1 = T.Context(0)
+    for prec in ("c64", "chalf"):
+        assert np.array_equal(got[prec], ctx1.amplitudes(p, fixed[None, :], prec))
+    assert np.array_equal(one, ctx1.amplitudes(p, fixed[None, :], "chalf", slice_begin=1, slice_count=1))

@@ -88,3 +88,19 @@ def test_s30_autotuned_against_statevector(s30, tmp_path, clean_tuning_cache):
     assert T.tune_size() == n
     ctx2 = T.Context(0)  # a new context builds its own program from the cache
     assert np.array_equal(ctx2.amplitudes(p, fixed[None, :], "chalf")[0], tuned)
+
+
+@pytest.mark.parametrize("precision", ["chalf", "c64"])
+def test_s30_concurrent_branches_match_serial(s30, precision, monkeypatch):
+    """Independent subtrees run on concurrent streams (with the arena's memory hazards and the
+    shared split-K buffer as dependencies); eager, graph-captured and graph-replayed calls are
+    bit-identical to running every launch on one stream."""
+    _, fixed, p = s30
+    ctx = T.Context(0)
+    conc = ctx.amplitudes(p, fixed[None, :], precision)[0]
+    graph = [ctx.amplitudes(p, fixed[None, :], precision, use_graph=True)[0] for _ in range(3)]
+    monkeypatch.setenv("TNC_SERIAL", "1")
+    ser = T.Context(0).amplitudes(p, fixed[None, :], precision)[0]
+    assert np.array_equal(conc, ser)
+    for g in graph:
+        assert np.array_equal(g, ser)
