@@ -61,8 +61,8 @@ void add_unique(std::vector<int>& dst, int x) {
 constexpr int TILE_AB = 11;
 constexpr int TILE_C = 12;
 
-// Largest output tile (log2) that 256 threads cover with micro-tiles of up to 4 x 4.
-int max_out_bits(int mt, int nt) { return 8 + std::min(2, mt) + std::min(2, nt); }
+// Largest output tile (log2) that 256 threads cover with micro-tiles of up to 8 x 4.
+int max_out_bits(int mt, int nt) { return 8 + std::min(3, mt) + std::min(2, nt); }
 
 // Choose a tile for the generic / split-K kernels.
 TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, const std::vector<int>& lc,
@@ -80,9 +80,13 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   // feeds at most 4 multiply-adds, so they stream their tiles (k_stream)
   const bool stream = gepdot || (k >= 12 && std::min(m, n) <= 2);
   const int tile_ab = stream ? TILE_AB + 1 : TILE_AB;
-  auto fits = [tile_ab](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
+  // GEMM-shaped steps on the SIMT kernel (the complex64 path): 128 x 64 output tiles with
+  // 8 x 4 micro-tiles, 32 complex multiply-adds per 12 shared-memory loads
+  const bool wide_out = !stream && k + n > 6 && m >= 7 && n >= 6 && k >= 5;
+  const int tile_c = wide_out ? TILE_C + 1 : TILE_C;
+  auto fits = [tile_ab, tile_c](const std::vector<int>& Mt, const std::vector<int>& Kt, const std::vector<int>& Nt) {
     const int mt = (int)Mt.size(), kt = (int)Kt.size(), nt = (int)Nt.size();
-    return mt + kt <= tile_ab && kt + nt <= tile_ab && mt + nt <= TILE_C && mt + nt <= max_out_bits(mt, nt);
+    return mt + kt <= tile_ab && kt + nt <= tile_ab && mt + nt <= tile_c && mt + nt <= max_out_bits(mt, nt);
   };
   // labels each tile must hold so that loads and stores run over contiguous memory
   for (int need = 4; need >= 0; --need) {
@@ -153,7 +157,7 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
     grow(t.Nt, N, n);
     grow(t.Mt, M, std::min(m, 9));
   } else {
-    grow(t.Mt, M, std::min(m, 6));
+    grow(t.Mt, M, std::min(m, wide_out ? 7 : 6));
     grow(t.Nt, N, std::min(n, 6));
     grow(t.Kt, Kab, std::min(k, 5));
   }
@@ -184,7 +188,7 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   while (out_bits - lrm - lrn > 8) {
     if (lrm <= lrn && lrm < 2 && lrm < mt) ++lrm;
     else if (lrn < 2 && lrn < nt) ++lrn;
-    else if (lrm < 2 && lrm < mt) ++lrm;
+    else if (lrm < 3 && lrm < mt) ++lrm;
     else break;
   }
   if (out_bits - lrm - lrn > 8) fail(5, "compile: output tile too large");

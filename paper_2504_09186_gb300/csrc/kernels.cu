@@ -965,7 +965,7 @@ GenKernel<T> pick_generic(int rm, int rn) {
 #define TNC_CASE(a, b) \
   if (rm == a && rn == b) return k_generic<T, a, b>;
   TNC_CASE(1, 1) TNC_CASE(1, 2) TNC_CASE(1, 4) TNC_CASE(2, 1) TNC_CASE(2, 2) TNC_CASE(2, 4)
-  TNC_CASE(4, 1) TNC_CASE(4, 2) TNC_CASE(4, 4)
+  TNC_CASE(4, 1) TNC_CASE(4, 2) TNC_CASE(4, 4) TNC_CASE(8, 4)
 #undef TNC_CASE
   return nullptr;
 }
