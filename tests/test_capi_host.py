@@ -279,3 +279,31 @@ def test_branch_exchange_never_raises_the_slicing_cost():
         assert a.describe()["sliced"] == b.describe()["sliced"]
         assert b.info()[key] <= a.info()[key] + 1e-12
         assert b.info()["max_log2_size"] <= 26
+
+
+def test_plan_options_roundtrip_and_bad_values(tmp_path):
+    """The slicing and branch-exchange options survive a plan file round trip with the same
+    tree, slices, executed cost and statistics; out-of-range values are rejected."""
+    c = grid_circuit(4, 4, 10, seed=1)
+    _, open_q = subcube_spec(16, 3, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=5, trials=4, log2_cap=10, slices_min=3, slicing="reuse",
+                      branch_exchange=True)
+    path = str(tmp_path / "plan_v4.bin")
+    p.save(path)
+    q = T.Plan.load(path)
+    dp, dq = p.describe(), q.describe()
+    assert dp["tree"] == dq["tree"] and dp["sliced"] == dq["sliced"] and dp["steps"] == dq["steps"]
+    assert p.info()["log2_executed_flops"] == q.info()["log2_executed_flops"]
+    sp, sq = p.slice_stats(), q.slice_stats()
+    assert all(np.array_equal(sp[k], sq[k]) for k in sp)
+    for bad in (dict(objective=2), dict(slicing=2), dict(branch_exchange=-1)):
+        arity, qubits, mats = c.gate_array()
+        ch = T.tnc_circuit_from_gates(c.n_qubits, arity, qubits, mats)
+        nh = T.tnc_network_build(ch, np.zeros(c.n_qubits, dtype=np.uint8))
+        try:
+            with pytest.raises(T.TncError) as e:
+                T.tnc_plan_greedy(nh, 1, 2, 12, 0, 64, 0.5, 0, **bad)
+            assert e.value.status == T.TNC_E_INVALID_ARG
+        finally:
+            T.load_library().tnc_network_destroy(nh)
+            T.load_library().tnc_circuit_destroy(ch)
