@@ -72,6 +72,28 @@ tnc_status tnc_circuit_from_gates(int32_t n_qubits, int64_t n_gates, const int32
                                   tnc_circuit* out);
 void tnc_circuit_destroy(tnc_circuit c);
 
+/* A seeded random grid circuit of the family the paper simulates (Sec. I, Sec. VII): a
+ * rows x cols grid, qubit q = r * cols + c; each of `cycles` cycles applies one single-qubit
+ * gate per qubit, drawn from {sqrt(X), sqrt(Y), sqrt(W)} (each (I - i P)/sqrt 2, P = X, Y,
+ * (X + Y)/sqrt 2) -- uniformly in the first cycle, then uniformly from the two that differ
+ * from the qubit's previous gate -- then fSim(theta, phi) on the couplers of class A, B, C, D
+ * in turn (A / B: horizontal pairs starting at even / odd columns; C / D: vertical pairs
+ * starting at even / odd rows).  fsim_mode 0: theta = pi/2, phi = pi/6 everywhere; 1: both
+ * uniform in [0, pi) per gate.  Gate order: a cycle's single-qubit gates by qubit, then its
+ * fSim gates by coupler.  Draws come from splitmix64 streams seeded by `seed` (the gate
+ * choices) and by seed ^ 0xD1B54A32D192ED03 (the angles).  Matrices as in
+ * tnc_circuit_from_gates.  Errors: TNC_E_INVALID_ARG (grid outside 1..64 qubits, cycles < 0,
+ * bad fsim_mode). */
+tnc_status tnc_circuit_random_grid(int32_t rows, int32_t cols, int32_t cycles, uint64_t seed,
+                                   int32_t fsim_mode, tnc_circuit* out);
+
+/* The gates of a circuit in the layout tnc_circuit_from_gates reads (arity; qubits, -1 for
+ * the unused second qubit; matrices as 32 doubles per gate, zero-padded), for an oracle or a
+ * file.  n_qubits, n_gates: out (may be NULL).  With arity, qubits and matrices all NULL it
+ * only reports the sizes; otherwise cap >= n_gates and any of the three may be NULL. */
+tnc_status tnc_circuit_export(tnc_circuit c, int32_t* n_qubits, int64_t* n_gates, int32_t* arity,
+                              int32_t* qubits, double* matrices, int64_t cap);
+
 /* Build the tensor network of a circuit (Sec. II-A).  One tensor per 2-qubit gate with
  * its neighbouring 1-qubit gates multiplied in (a qubit without 2-qubit gates becomes
  * one rank-2 tensor); |0> inputs are fixed; output legs of qubits with
@@ -218,6 +240,14 @@ typedef struct {
 tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
                           const uint8_t* bitstrings, int64_t batch, int64_t slice_begin,
                           int64_t slice_count, double* out, void* stream);
+
+/* The same sum over an explicit list of slice ids (a seeded subset of the slices, say): the
+ * n_ids slices slice_ids[0..n_ids) (host array; each in [0, 2^s); a repeated id is counted
+ * each time), added in list order.  Tree-like reuse does not apply.  Otherwise as
+ * tnc_amplitudes.  Errors: TNC_E_INVALID_ARG (NULL or empty list, id out of range). */
+tnc_status tnc_amplitudes_ids(tnc_context ctx, tnc_plan p, const tnc_exec_opts* opts,
+                              const uint8_t* bitstrings, int64_t batch, const int64_t* slice_ids,
+                              int64_t n_ids, double* out, void* stream);
 
 /* Gradient environments (the derivative of L = sum_{b,i} w[b,i] * amp[b,i] with respect
  * to every gate matrix, holomorphic: dL/dU_g[o, i]).  Walks the contraction tree in

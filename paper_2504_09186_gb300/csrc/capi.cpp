@@ -1,6 +1,9 @@
 // extern "C" entry points of the host-side calls (circuit, network, plan, errors).
 // Device-side calls (context, amplitudes, contract, adjoint) are in exec.cu.
 #include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -70,6 +73,125 @@ tnc_status tnc_circuit_from_gates(int32_t n_qubits, int64_t n_gates, const int32
 }
 
 void tnc_circuit_destroy(tnc_circuit c) { delete c; }
+
+namespace {
+// splitmix64: the generator's one random stream (seed -> 64-bit draws)
+struct Split64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return double(next() >> 11) * (1.0 / 9007199254740992.0); }  // [0, 1)
+};
+}  // namespace
+
+tnc_status tnc_circuit_random_grid(int32_t rows, int32_t cols, int32_t cycles, uint64_t seed, int32_t fsim_mode,
+                                   tnc_circuit* out) {
+  return guarded([&] {
+    if (!out) fail(TNC_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (rows < 1 || cols < 1 || int64_t(rows) * cols > 64) fail(TNC_E_INVALID_ARG, "grid must hold 1..64 qubits");
+    if (cycles < 0) fail(TNC_E_INVALID_ARG, "cycles < 0");
+    if (fsim_mode != 0 && fsim_mode != 1) fail(TNC_E_INVALID_ARG, "fsim_mode must be 0 (fixed) or 1 (uniform)");
+    const int n = rows * cols;
+    const double pi = 3.14159265358979323846, r2 = 0.70710678118654752440;
+    // sqrt(X), sqrt(Y), sqrt(W) = (I - i P) / sqrt 2 with P = X, Y, (X + Y) / sqrt 2; U[out, in]
+    const cd w = std::polar(1.0, 0.25 * pi);
+    const cd one_q[3][4] = {{r2, cd(0, -r2), cd(0, -r2), r2},
+                            {r2, -r2, r2, r2},
+                            {r2, -r2 * w, r2 * std::conj(w), r2}};
+    Split64 g1{seed}, g2{seed ^ 0xD1B54A32D192ED03ull};
+    auto* c = new tnc_circuit_s();
+    c->c.n = n;
+    std::vector<int> prev(n, -1);
+    for (int k = 0; k < cycles; ++k) {
+      for (int q = 0; q < n; ++q) {
+        // the first cycle draws from all three gates, later ones from the two that differ
+        // from the qubit's previous gate (in index order)
+        int pick;
+        if (prev[q] < 0) {
+          pick = (int)(g1.next() % 3);
+        } else {
+          const int j = (int)(g1.next() % 2);
+          int others[2], m = 0;
+          for (int t = 0; t < 3; ++t)
+            if (t != prev[q]) others[m++] = t;
+          pick = others[j];
+        }
+        prev[q] = pick;
+        Gate G;
+        G.arity = 1;
+        G.q[0] = q;
+        G.q[1] = -1;
+        for (int i = 0; i < 16; ++i) G.m[i] = 0;
+        for (int i = 0; i < 4; ++i) G.m[i] = one_q[pick][i];
+        c->c.gates.push_back(G);
+      }
+      // fSim on coupler class A, B, C, D (cycle k mod 4) of the grid, lower qubit first
+      const char cls = "ABCD"[k % 4];
+      std::vector<std::pair<int, int>> pairs;
+      if (cls == 'A' || cls == 'B') {
+        for (int r = 0; r < rows; ++r)
+          for (int col = cls == 'A' ? 0 : 1; col + 1 < cols; col += 2) pairs.emplace_back(r * cols + col, r * cols + col + 1);
+      } else {
+        for (int r = cls == 'C' ? 0 : 1; r + 1 < rows; r += 2)
+          for (int col = 0; col < cols; ++col) pairs.emplace_back(r * cols + col, (r + 1) * cols + col);
+      }
+      for (auto& pq : pairs) {
+        double theta = pi / 2, phi = pi / 6;
+        if (fsim_mode == 1) {
+          theta = pi * g2.uniform();
+          phi = pi * g2.uniform();
+        }
+        // fSim(theta, phi) in the basis |q_a q_b>, q_a (the lower index) most significant
+        Gate G;
+        G.arity = 2;
+        G.q[0] = pq.first;
+        G.q[1] = pq.second;
+        for (int i = 0; i < 16; ++i) G.m[i] = 0;
+        G.m[0] = 1;
+        G.m[5] = std::cos(theta);
+        G.m[6] = cd(0, -std::sin(theta));
+        G.m[9] = cd(0, -std::sin(theta));
+        G.m[10] = std::cos(theta);
+        G.m[15] = std::polar(1.0, -phi);
+        c->c.gates.push_back(G);
+      }
+    }
+    *out = c;
+  });
+}
+
+tnc_status tnc_circuit_export(tnc_circuit c, int32_t* n_qubits, int64_t* n_gates, int32_t* arity, int32_t* qubits,
+                              double* matrices, int64_t cap) {
+  return guarded([&] {
+    if (!c) fail(TNC_E_INVALID_ARG, "NULL circuit");
+    const int64_t g = (int64_t)c->c.gates.size();
+    if (n_qubits) *n_qubits = c->c.n;
+    if (n_gates) *n_gates = g;
+    if (!arity && !qubits && !matrices) return;  // size query
+    if (cap < g) fail(TNC_E_INVALID_ARG, "cap below the number of gates");
+    for (int64_t i = 0; i < g; ++i) {
+      const Gate& G = c->c.gates[(size_t)i];
+      if (arity) arity[i] = G.arity;
+      if (qubits) {
+        qubits[2 * i] = G.q[0];
+        qubits[2 * i + 1] = G.arity == 2 ? G.q[1] : -1;
+      }
+      if (matrices) {
+        const int d = 1 << G.arity;
+        for (int j = 0; j < 32; ++j) matrices[32 * i + j] = 0;
+        for (int j = 0; j < d * d; ++j) {
+          matrices[32 * i + 2 * j] = G.m[j].real();
+          matrices[32 * i + 2 * j + 1] = G.m[j].imag();
+        }
+      }
+    }
+  });
+}
 
 tnc_status tnc_network_build(tnc_circuit c, const uint8_t* open_mask, tnc_network* out) {
   return guarded([&] {

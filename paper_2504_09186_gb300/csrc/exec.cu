@@ -1212,8 +1212,11 @@ struct AmpRun {
   cudaStream_t stream = nullptr;
 };
 
+// Slices [slice_begin, slice_begin + slice_count), or, when `ids` is given, the slice_count
+// slice ids listed there (slice_begin unused).
 static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
-                             int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
+                             int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream,
+                             const int64_t* ids = nullptr) {
   {
     if (!ctx || !plan || !opts || !out) fail(TNC_E_INVALID_ARG, "NULL argument");
     const Plan& P = plan->p;
@@ -1224,8 +1227,14 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
     // slice ids are int64: with s >= 63 sliced indices the ids [0, 2^63) address the slices
     // whose higher sliced indices are all 0
     const int64_t n_slices = P.sliced.size() >= 63 ? INT64_MAX : int64_t(1) << P.sliced.size();
-    if (slice_begin < 0 || slice_count < 1 || slice_count > n_slices - slice_begin)
+    if (ids) {
+      if (slice_count < 1) fail(TNC_E_INVALID_ARG, "no slice ids");
+      for (int64_t t = 0; t < slice_count; ++t)
+        if (ids[t] < 0 || ids[t] >= n_slices) fail(TNC_E_INVALID_ARG, "slice id outside [0, 2^s)");
+      slice_begin = 0;
+    } else if (slice_begin < 0 || slice_count < 1 || slice_count > n_slices - slice_begin) {
       fail(TNC_E_INVALID_ARG, "slice range outside [0, 2^s)");
+    }
     const bool all_open = (int)P.net.open_qubits.size() == n;
     if (!bitstrings && !(batch == 1 && all_open)) fail(TNC_E_INVALID_ARG, "bitstrings required");
     std::vector<uint8_t> bits(size_t(batch) * n, 0);
@@ -1276,7 +1285,7 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
     std::vector<int32_t> inst_row(n_inst);
     for (int64_t b = 0; b < batch; ++b)
       for (int64_t t = 0; t < slice_count; ++t) {
-        inst_slice[b * slice_count + t] = slice_begin + t;
+        inst_slice[b * slice_count + t] = ids ? ids[t] : slice_begin + t;
         inst_row[b * slice_count + t] = (int32_t)b;
       }
     std::vector<RootSeg> segs;
@@ -1305,7 +1314,8 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
     const bool prof = opts->profile != 0;
     const int n_waves = (int)((n_inst + W - 1) / W);
     // tree-like reuse needs instances laid out as whole rows of every slice
-    const bool reuse = prog->reuse_ok && slice_begin == 0 && slice_count == (int64_t(1) << P.sliced.size());
+    const bool reuse =
+        !ids && prog->reuse_ok && slice_begin == 0 && slice_count == (int64_t(1) << P.sliced.size());
     if (prof) {
       ProfState& ps = ctx->prof;
       ps.valid = false;
@@ -1416,6 +1426,14 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
 tnc_status tnc_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
                           int64_t batch, int64_t slice_begin, int64_t slice_count, double* out, void* stream) {
   return guarded([&] { run_amplitudes(ctx, plan, opts, bitstrings, batch, slice_begin, slice_count, out, stream); });
+}
+
+tnc_status tnc_amplitudes_ids(tnc_context ctx, tnc_plan plan, const tnc_exec_opts* opts, const uint8_t* bitstrings,
+                              int64_t batch, const int64_t* slice_ids, int64_t n_ids, double* out, void* stream) {
+  return guarded([&] {
+    if (!slice_ids) fail(TNC_E_INVALID_ARG, "NULL slice ids");
+    run_amplitudes(ctx, plan, opts, bitstrings, batch, 0, n_ids, out, stream, slice_ids);
+  });
 }
 
 // Times every admissible configuration of each TMA tensor-core step of `prog` at its wave

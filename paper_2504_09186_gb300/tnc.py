@@ -118,6 +118,9 @@ def load_library(path: str = LIB_PATH):
         "tnc_plan_greedy": [vp, C.POINTER(tnc_plan_opts), C.POINTER(vp)],
         "tnc_plan_get_info": [vp, C.POINTER(tnc_plan_info)],
         "tnc_plan_sliced_cuts": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i32],
+        "tnc_circuit_random_grid": [i32, i32, i32, C.c_uint64, i32, C.POINTER(vp)],
+        "tnc_circuit_export": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32), C.POINTER(C.c_double), i64],
         "tnc_plan_slice_stats": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), i32],
         "tnc_plan_open_qubits": [vp, C.POINTER(C.c_int32), i32],
@@ -127,6 +130,7 @@ def load_library(path: str = LIB_PATH):
         "tnc_plan_load": [C.c_char_p, C.POINTER(vp)],
         "tnc_context_create": [i32, C.POINTER(vp)],
         "tnc_amplitudes": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, i64, i64, vp, vp],
+        "tnc_amplitudes_ids": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, C.POINTER(C.c_int64), i64, vp, vp],
         "tnc_adjoint": [vp, vp, C.POINTER(tnc_exec_opts), u8p, i64, vp, vp, vp, vp],
         "tnc_contract": [vp, i32, vp, i32, C.POINTER(C.c_int32), vp, i32, C.POINTER(C.c_int32), vp, i32,
                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), vp],
@@ -202,6 +206,46 @@ def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slice
 
 
 # ------------------------------------------------------------------------- wrappers
+class GateList:
+    """A circuit as the packed arrays of the C boundary (the layout of
+    tnc_circuit_from_gates): arity (G,), qubits (G, 2), matrices (G, 32).  Plan.greedy
+    takes it like any object with `n_qubits` and `gate_array()`."""
+
+    def __init__(self, n_qubits: int, arity: np.ndarray, qubits: np.ndarray, matrices: np.ndarray):
+        self.n_qubits = int(n_qubits)
+        self.arity, self.qubits, self.matrices = arity, qubits, matrices
+
+    def __len__(self) -> int:
+        return len(self.arity)
+
+    def gate_array(self):
+        return self.arity, self.qubits, self.matrices
+
+
+def circuit_export(handle) -> GateList:
+    """The gates of a C circuit handle (tnc_circuit_export)."""
+    lib = load_library()
+    n, g = C.c_int32(), C.c_int64()
+    _check(lib.tnc_circuit_export(handle, C.byref(n), C.byref(g), None, None, None, 0))
+    arity = np.zeros(g.value, dtype=np.int32)
+    qubits = np.zeros((g.value, 2), dtype=np.int32)
+    mats = np.zeros((g.value, 32), dtype=np.float64)
+    _check(lib.tnc_circuit_export(handle, None, None, _i32p(arity), _i32p(qubits),
+                                  mats.ctypes.data_as(C.POINTER(C.c_double)), g.value))
+    return GateList(n.value, arity, qubits, mats)
+
+
+def random_grid(rows: int, cols: int, cycles: int, seed: int = 1, fsim_mode: str = "fixed") -> GateList:
+    """The library's seeded random grid circuit (tnc_circuit_random_grid)."""
+    lib = load_library()
+    h = C.c_void_p()
+    _check(lib.tnc_circuit_random_grid(rows, cols, cycles, seed, {"fixed": 0, "uniform": 1}[fsim_mode], C.byref(h)))
+    try:
+        return circuit_export(h)
+    finally:
+        lib.tnc_circuit_destroy(h)
+
+
 class Plan:
     """A contraction plan (tree + slices + compiled steps) of a circuit's network."""
 
@@ -347,6 +391,29 @@ class Context:
                              int(use_graph), int(fuse), int(profile))
         _check(lib.tnc_amplitudes(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count,
                                   C.c_void_p(ptr), C.c_void_p(stream)))
+        return out
+
+    def amplitudes_ids(self, plan: Plan, bitstrings: Optional[np.ndarray], slice_ids, precision: str = "c64",
+                       wave: int = 0, out=None, stream: int = 0, fuse: bool = True) -> np.ndarray:
+        """Amplitudes summed over the listed slice ids (tnc_amplitudes_ids)."""
+        lib = load_library()
+        info = plan.info()
+        ids = np.ascontiguousarray(slice_ids, dtype=np.int64)
+        if bitstrings is None:
+            batch, bp = 1, None
+        else:
+            bs = np.ascontiguousarray(bitstrings, dtype=np.uint8)
+            if bs.ndim == 1:
+                bs = bs[None, :]
+            batch, bp = bs.shape[0], bs.ctypes.data_as(C.POINTER(C.c_uint8))
+        if out is None:
+            out = np.zeros((batch, 1 << info["n_open"]), dtype=np.complex128)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave, 0,
+                             int(fuse), 0)
+        _check(lib.tnc_amplitudes_ids(self.h, plan.h, C.byref(opts), bp, batch,
+                                      ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids), C.c_void_p(ptr),
+                                      C.c_void_p(stream)))
         return out
 
     def autotune(self, plan: Plan, bitstrings: Optional[np.ndarray], precision: str = "chalf",

@@ -307,3 +307,72 @@ def test_plan_options_roundtrip_and_bad_values(tmp_path):
         finally:
             T.load_library().tnc_network_destroy(nh)
             T.load_library().tnc_circuit_destroy(ch)
+
+
+def _gates_of(gl):
+    """(qubits, matrix) pairs of a GateList (the boundary's packed layout)."""
+    out = []
+    for g in range(len(gl)):
+        a = int(gl.arity[g])
+        d = 1 << a
+        m = gl.matrices[g, 0:2 * d * d:2] + 1j * gl.matrices[g, 1:2 * d * d:2]
+        out.append((tuple(int(q) for q in gl.qubits[g, :a]), m.reshape(d, d)))
+    return out
+
+
+@pytest.mark.parametrize("rows,cols,cycles,mode", [(3, 4, 8, "fixed"), (2, 5, 6, "uniform"), (4, 4, 5, "fixed")])
+def test_random_grid_circuit_is_the_papers_family(rows, cols, cycles, mode):
+    """tnc_circuit_random_grid: per cycle one of {sqrt X, sqrt Y, sqrt W} on every qubit (never
+    the qubit's previous one), then fSim on the A, B, C, D coupler classes in turn -- the same
+    gates and couplers as the seeded Python generator's family; fixed fSim(pi/2, pi/6) or
+    angles in [0, pi); unitary; deterministic per seed."""
+    from inputs.circuits import SINGLE_QUBIT_SET, couplers, fsim
+
+    gl = T.random_grid(rows, cols, cycles, seed=11, fsim_mode=mode)
+    n = rows * cols
+    assert gl.n_qubits == n
+    gates = _gates_of(gl)
+    i, prev = 0, [-1] * n
+    for k in range(cycles):
+        for q in range(n):
+            qs, m = gates[i]
+            i += 1
+            assert qs == (q,)
+            idx = [t for t, u in enumerate(SINGLE_QUBIT_SET) if np.allclose(m, u, atol=1e-15)]
+            assert len(idx) == 1 and idx[0] != prev[q]
+            prev[q] = idx[0]
+        for pair in couplers(rows, cols, "ABCD"[k % 4]):
+            qs, m = gates[i]
+            i += 1
+            assert qs == pair
+            if mode == "fixed":
+                assert np.allclose(m, fsim(np.pi / 2, np.pi / 6), atol=1e-15)
+            else:
+                theta = np.arctan2(-m[1, 2].imag, m[1, 1].real)
+                phi = -np.angle(m[3, 3]) % (2 * np.pi)
+                assert 0 <= theta < np.pi and 0 <= phi < np.pi
+                assert np.allclose(m, fsim(theta, phi), atol=1e-12)
+    assert i == len(gates)
+    for _, m in gates:
+        assert np.allclose(m.conj().T @ m, np.eye(len(m)), atol=1e-14)
+    again = T.random_grid(rows, cols, cycles, seed=11, fsim_mode=mode)
+    assert np.array_equal(again.matrices, gl.matrices) and np.array_equal(again.qubits, gl.qubits)
+    other = T.random_grid(rows, cols, cycles, seed=12, fsim_mode=mode)
+    assert not np.array_equal(other.matrices, gl.matrices)
+    # the exported gates rebuild the same circuit through tnc_circuit_from_gates
+    arity, qubits, mats = gl.gate_array()
+    h = T.tnc_circuit_from_gates(n, arity, qubits, mats)
+    try:
+        back = T.circuit_export(h)
+    finally:
+        T.load_library().tnc_circuit_destroy(h)
+    assert np.array_equal(back.matrices, gl.matrices) and np.array_equal(back.arity, gl.arity)
+
+
+def test_random_grid_rejects_bad_arguments():
+    for args in ((0, 3, 2), (9, 8, 2), (2, 2, -1)):
+        with pytest.raises(T.TncError) as e:
+            T.random_grid(*args)
+        assert e.value.status == T.TNC_E_INVALID_ARG
+    with pytest.raises(KeyError):
+        T.random_grid(2, 2, 2, fsim_mode="other")

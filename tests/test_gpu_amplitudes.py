@@ -214,3 +214,42 @@ def test_concurrent_branches_with_splits_match_serial(monkeypatch):
     for prec in ("c64", "chalf"):
         assert np.array_equal(got[prec], ctx1.amplitudes(p, fixed[None, :], prec))
     assert np.array_equal(one, ctx1.amplitudes(p, fixed[None, :], "chalf", slice_begin=1, slice_count=1))
+
+
+def test_library_random_grid_circuit_against_statevector(ctx):
+    """A circuit made by tnc_circuit_random_grid (uniform fSim angles) contracts to the
+    state-vector amplitudes of its exported gates, in c64 and chalf."""
+    gl = T.random_grid(4, 4, 10, seed=7, fsim_mode="uniform")
+    gates = []
+    for g in range(len(gl)):
+        a = int(gl.arity[g])
+        d = 1 << a
+        m = gl.matrices[g, 0:2 * d * d:2] + 1j * gl.matrices[g, 1:2 * d * d:2]
+        gates.append((gl.qubits[g, :a], m.reshape(d, d)))
+    circ = custom_circuit(16, gates)
+    fixed, open_q = subcube_spec(16, 4, seed=2)
+    p = T.Plan.greedy(gl, open_qubits=open_q, seed=3, trials=8, log2_cap=12, slices_min=2)
+    ref = sv.circuit_amplitudes(circ, subcube_bitstrings(fixed, open_q))
+    for prec, tol in (("c64", 1e-5), ("chalf", 1e-2)):
+        assert metrics.rel_err_norm(ctx.amplitudes(p, fixed[None, :], prec)[0], ref) <= tol
+
+
+def test_amplitudes_over_listed_slice_ids(ctx):
+    """tnc_amplitudes_ids: the sum over a listed subset (out of order, one id repeated) equals
+    the sum of single-slice calls in list order, and a contiguous list equals the range call,
+    bit for bit."""
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 4, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=12, slices_min=4)
+    n = 1 << p.info()["n_sliced"]
+    ids = [5, 1, n - 1, 1, 7]
+    for prec in ("c64", "chalf"):
+        got = ctx.amplitudes_ids(p, fixed[None, :], ids, prec)
+        acc = np.zeros_like(got)
+        for sid in ids:
+            acc = acc + ctx.amplitudes(p, fixed[None, :], prec, slice_begin=sid, slice_count=1)
+        assert np.array_equal(got, acc)
+        rng = ctx.amplitudes(p, fixed[None, :], prec, slice_begin=2, slice_count=6)
+        assert np.array_equal(ctx.amplitudes_ids(p, fixed[None, :], list(range(2, 8)), prec), rng)
+    with pytest.raises(T.TncError):
+        ctx.amplitudes_ids(p, fixed[None, :], [n], "c64")
