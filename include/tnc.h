@@ -175,9 +175,15 @@ tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
  *                         unsliced (Eq. 1's index overhead, taken last)
  *  reuse_overhead         the same ratio of the executed cost of all slices under
  *                         tree-like reuse
+ *  post_steps             dependent steps after the lifetime (they depend on the index
+ *                         but no longer hold it)
+ *  merge_saving           the fraction of that executed cost which summing over the
+ *                         index right after its lifetime (post-lifetime merging,
+ *                         Sec. III-B) would save: half of every post-lifetime step
  * Errors: TNC_E_INVALID_ARG (NULL plan, cap too small). */
 tnc_status tnc_plan_slice_stats(tnc_plan p, int32_t* first_step, int32_t* last_step, int32_t* dep_steps,
-                                double* overhead, double* reuse_overhead, int32_t cap);
+                                double* overhead, double* reuse_overhead, int32_t* post_steps,
+                                double* merge_saving, int32_t cap);
 
 /* Sliced indices as wire segments: slice bit t (bit t of a slice id) fixes the wire of
  * qubit qubit[t] after cut[t] gates on that qubit.  cap >= n_sliced entries. */

@@ -340,7 +340,8 @@ std::string jlist(const std::vector<int>& v) {
 }  // namespace
 
 tnc_status tnc_plan_slice_stats(tnc_plan p, int32_t* first_step, int32_t* last_step, int32_t* dep_steps,
-                                double* overhead, double* reuse_overhead, int32_t cap) {
+                                double* overhead, double* reuse_overhead, int32_t* post_steps,
+                                double* merge_saving, int32_t cap) {
   return guarded([&] {
     if (!p) fail(TNC_E_INVALID_ARG, "NULL plan");
     const auto st = slice_stats(p->p);
@@ -351,6 +352,8 @@ tnc_status tnc_plan_slice_stats(tnc_plan p, int32_t* first_step, int32_t* last_s
       if (dep_steps) dep_steps[j] = st[j].dep_steps;
       if (overhead) overhead[j] = st[j].overhead;
       if (reuse_overhead) reuse_overhead[j] = st[j].reuse_overhead;
+      if (post_steps) post_steps[j] = st[j].post_steps;
+      if (merge_saving) merge_saving[j] = st[j].merge_saving;
     }
   });
 }

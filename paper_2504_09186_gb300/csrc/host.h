@@ -117,6 +117,10 @@ struct SliceStat {
   int dep_steps = 0;                    // steps whose subtree fixes the index
   double overhead = 1;                  // 2 C / C(without it): Eq. 1
   double reuse_overhead = 1;            // the same ratio of executed cost under tree-like reuse
+  int post_steps = 0;                   // dependent steps after the lifetime: they run once
+                                        // per value of the index, though it no longer appears
+  double merge_saving = 0;              // fraction of the executed cost (under reuse) that
+                                        // merging right after the lifetime would save
 };
 
 // Kernel classes of a compiled step.

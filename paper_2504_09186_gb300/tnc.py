@@ -122,7 +122,8 @@ def load_library(path: str = LIB_PATH):
         "tnc_circuit_export": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), C.POINTER(C.c_double), i64],
         "tnc_plan_slice_stats": [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                                 C.POINTER(C.c_double), C.POINTER(C.c_double), i32],
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double), i32],
         "tnc_plan_open_qubits": [vp, C.POINTER(C.c_int32), i32],
         "tnc_plan_describe": [vp, C.c_char_p, i64, C.POINTER(C.c_int64)],
         "tnc_plan_save": [vp, C.c_char_p],
@@ -316,13 +317,13 @@ class Plan:
         depend on it, and its Eq. 1 and tree-reuse overheads (tnc_plan_slice_stats)."""
         n = self.info()["n_sliced"]
         m = max(n, 1)
-        first, last, dep = (np.zeros(m, dtype=np.int32) for _ in range(3))
-        ov, rov = np.zeros(m), np.zeros(m)
-        _check(load_library().tnc_plan_slice_stats(self.h, _i32p(first), _i32p(last), _i32p(dep),
-                                                   ov.ctypes.data_as(C.POINTER(C.c_double)),
-                                                   rov.ctypes.data_as(C.POINTER(C.c_double)), m))
+        first, last, dep, post = (np.zeros(m, dtype=np.int32) for _ in range(4))
+        ov, rov, ms = np.zeros(m), np.zeros(m), np.zeros(m)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        _check(load_library().tnc_plan_slice_stats(self.h, _i32p(first), _i32p(last), _i32p(dep), dp(ov), dp(rov),
+                                                   _i32p(post), dp(ms), m))
         return {"first_step": first[:n], "last_step": last[:n], "dep_steps": dep[:n], "overhead": ov[:n],
-                "reuse_overhead": rov[:n]}
+                "reuse_overhead": rov[:n], "post_steps": post[:n], "merge_saving": ms[:n]}
 
     def sliced_cuts(self):
         n = self.info()["n_sliced"]

@@ -265,6 +265,16 @@ def test_slice_stats_and_executed_cost_recount(slicing, exchange):
         rest = [x for x in S if x != e]
         assert math.isclose(st["overhead"][t], 2 * cost(S) / cost(rest), rel_tol=1e-12)
         assert math.isclose(st["reuse_overhead"][t], reuse_cost(S) / reuse_cost(rest), rel_tol=1e-12)
+        # post-lifetime steps and the share of the executed cost merging would save
+        dep = deps(e)
+        post = [k for k in range(len(d["tree"])) if k > steps[-1] and dep[L + k]]
+        assert st["post_steps"][t] == len(post)
+        dmask = [sum(1 << j for j, x in enumerate(S) if x in sets[i]) for i in range(L)]
+        for a, b in d["tree"]:
+            dmask.append(dmask[a] | dmask[b])
+        saved = sum(0.5 * 2.0 ** (len((sets[a] | sets[b]) - set(S)) + bin(dmask[L + k]).count("1"))
+                    for k, (a, b) in enumerate(d["tree"]) if k in post)
+        assert math.isclose(st["merge_saving"][t], saved / reuse_cost(S), rel_tol=1e-12, abs_tol=1e-300)
 
 
 def test_branch_exchange_never_raises_the_slicing_cost():
