@@ -227,7 +227,7 @@ tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* o
     o.objective = opts->objective;
     o.slicing = opts->slicing;
     o.branch_exchange = opts->branch_exchange;
-    if (o.mode != 0 && o.mode != 1) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy) or 1 (stem)");
+    if (o.mode < 0 || o.mode > 2) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy), 1 (stem) or 2 (qubit split)");
     if (o.objective != 0 && o.objective != 1) fail(TNC_E_INVALID_ARG, "plan objective must be 0 or 1");
     if (o.slicing != 0 && o.slicing != 1) fail(TNC_E_INVALID_ARG, "plan slicing must be 0 (Eq. 1) or 1 (reuse)");
     if (o.branch_exchange != 0 && o.branch_exchange != 1) fail(TNC_E_INVALID_ARG, "branch_exchange must be 0 or 1");

@@ -104,7 +104,7 @@ struct PlanOpts {
   int slices_min = 0;
   int slices_max = 64;
   double temperature = 0.5;
-  int mode = 0;       // 0 greedy, 1 stem
+  int mode = 0;       // 0 greedy, 1 stem, 2 qubit split (sliced separator + fused stems)
   int objective = 0;  // 0 fewest multiply-adds, 1 least modeled GB300 time
   int slicing = 0;    // 0 index overhead of Eq. 1; 1 executed cost under tree-like reuse
   int branch_exchange = 0;  // 1: reorder consecutive contractions to shorten lifetimes

@@ -181,15 +181,34 @@ int tree_max(const Tree& t, const std::vector<char>& sliced) {
   return m;
 }
 
+// Number of sliced indices each tensor's subtree fixes (leaves: the sliced labels they
+// hold; intermediates: the union over their operands), for any number of sliced indices.
+std::vector<int> dep_counts(const Tree& t, const std::vector<int>& sliced_list) {
+  const size_t n_leaves = t.sets.size() - t.pairs.size();
+  const size_t words = (sliced_list.size() + 63) / 64;
+  std::vector<std::vector<uint64_t>> dep(t.sets.size(), std::vector<uint64_t>(words, 0));
+  for (size_t i = 0; i < n_leaves; ++i)
+    for (size_t j = 0; j < sliced_list.size(); ++j)
+      if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), sliced_list[j])) dep[i][j / 64] |= uint64_t(1) << (j % 64);
+  std::vector<int> cnt(t.sets.size(), 0);
+  for (size_t i = 0; i < n_leaves; ++i)
+    for (uint64_t w : dep[i]) cnt[i] += __builtin_popcountll(w);
+  for (size_t k = 0; k < t.pairs.size(); ++k) {
+    const auto& p = t.pairs[k];
+    for (size_t w = 0; w < words; ++w) {
+      dep[n_leaves + k][w] = dep[p.first][w] | dep[p.second][w];
+      cnt[n_leaves + k] += __builtin_popcountll(dep[n_leaves + k][w]);
+    }
+  }
+  return cnt;
+}
+
 // Modeled GB300 time of a call over all 2^s slices of one bitstring row: step_model_seconds
 // of every step times the number of times it runs under tree-like reuse (Sec. III-B), one
 // per assignment of the sliced indices its subtree fixes.
 double model_time(const Tree& t, const std::vector<char>& sliced, const std::vector<int>& sliced_list) {
-  std::vector<uint64_t> dep(t.sets.size(), 0);
+  const std::vector<int> dep = dep_counts(t, sliced_list);
   const size_t n_leaves = t.sets.size() - t.pairs.size();
-  for (size_t i = 0; i < n_leaves; ++i)
-    for (size_t j = 0; j < sliced_list.size() && j < 64; ++j)
-      if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), sliced_list[j])) dep[i] |= uint64_t(1) << j;
   double tot = 0;
   for (size_t k = 0; k < t.pairs.size(); ++k) {
     const auto& p = t.pairs[k];
@@ -198,8 +217,7 @@ double model_time(const Tree& t, const std::vector<char>& sliced, const std::vec
     const int a = (int)count_not_in(A, sliced), b = (int)count_not_in(B, sliced);
     const int u = (int)count_not_in(set_union(A, B), sliced);
     const int c = (int)count_not_in(sym_diff(A, B), sliced);
-    dep[n_leaves + k] = dep[p.first] | dep[p.second];
-    tot += step_model_seconds(a, b, c, a + b - u) * std::ldexp(1.0, __builtin_popcountll(dep[n_leaves + k]));
+    tot += step_model_seconds(a, b, c, a + b - u) * std::ldexp(1.0, dep[n_leaves + k]);
   }
   return tot;
 }
@@ -208,17 +226,13 @@ double model_time(const Tree& t, const std::vector<char>& sliced, const std::vec
 // reuse (Sec. III-B): each step's per-slice cost times the assignments of the sliced indices
 // its subtree fixes.  Lifetime-aware: an index costs only over the steps that depend on it.
 double reuse_cost(const Tree& t, const std::vector<char>& sliced, const std::vector<int>& sliced_list) {
-  std::vector<uint64_t> dep(t.sets.size(), 0);
+  const std::vector<int> dep = dep_counts(t, sliced_list);
   const size_t n_leaves = t.sets.size() - t.pairs.size();
-  for (size_t i = 0; i < n_leaves; ++i)
-    for (size_t j = 0; j < sliced_list.size() && j < 64; ++j)
-      if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), sliced_list[j])) dep[i] |= uint64_t(1) << j;
   double tot = 0;
   for (size_t k = 0; k < t.pairs.size(); ++k) {
     const auto& p = t.pairs[k];
-    dep[n_leaves + k] = dep[p.first] | dep[p.second];
     const int u = (int)count_not_in(set_union(t.sets[p.first], t.sets[p.second]), sliced);
-    tot += std::ldexp(1.0, u + __builtin_popcountll(dep[n_leaves + k]));
+    tot += std::ldexp(1.0, u + dep[n_leaves + k]);
   }
   return tot;
 }
@@ -284,6 +298,199 @@ std::vector<LabelSet> contraction_leaves(const Network& net) {
   return leaves;
 }
 
+// ------------------------------------------------------------------ qubit split (mode 2)
+//
+// Slicing a separator (Sec. II-A: a sliced index is fixed in every tensor holding it, so
+// slicing every index between two parts of the network makes them independent subtasks).
+// For a circuit network the cheapest balanced separator of the *qubits* is taken: the
+// qubits are bisected so that few 2-qubit gates straddle the two sides, every leaf goes to
+// one side, and the indices joining leaves on different sides are sliced.  Each side is
+// then contracted by one stem in circuit order (the stem picture of Sec. II-A / III-C),
+// which absorbs fused blocks of leaves: a block gathers consecutive leaves acting on at
+// most `fuse` qubits and is contracted first as a small branch, so that each absorption is
+// one large GEMM (K, N = 2^inputs, 2^outputs of the block) instead of a run of 2-qubit ones.
+
+// Balanced bisection of n qubits minimising the weight of the pairs split: Fiduccia-
+// Mattheyses passes (move the unlocked qubit of largest gain that keeps both sides within
+// [n - max_side, max_side], keep the best prefix of moves) from a seeded random start.
+std::vector<char> bisect_qubits(int n, const std::vector<std::vector<double>>& w, int max_side, Rng& rng,
+                                double* cut_out) {
+  std::vector<char> side(n, 0);
+  std::vector<int> perm(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int i = n - 1; i > 0; --i) std::swap(perm[i], perm[rng.next() % (uint64_t)(i + 1)]);
+  for (int i = 0; i < n / 2; ++i) side[perm[i]] = 1;
+  const int lo = n - max_side, hi = max_side;
+  for (int pass = 0; pass < 32; ++pass) {
+    std::vector<double> gain(n, 0.0);
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        if (w[q][r] != 0) gain[q] += side[r] != side[q] ? w[q][r] : -w[q][r];
+    std::vector<char> locked(n, 0);
+    int n1 = 0;
+    for (int q = 0; q < n; ++q) n1 += side[q];
+    std::vector<int> moves;
+    double cur = 0, best = 0;
+    size_t best_len = 0;
+    std::vector<double> tie(n);
+    for (int q = 0; q < n; ++q) tie[q] = rng.uniform();
+    for (int it = 0; it < n; ++it) {
+      int pick = -1;
+      for (int q = 0; q < n; ++q) {
+        if (locked[q]) continue;
+        const int m1 = n1 + (side[q] ? -1 : 1);
+        if (m1 < lo || m1 > hi) continue;
+        if (pick < 0 || gain[q] > gain[pick] + 1e-12 || (std::fabs(gain[q] - gain[pick]) <= 1e-12 && tie[q] < tie[pick]))
+          pick = q;
+      }
+      if (pick < 0) break;
+      locked[pick] = 1;
+      cur += gain[pick];
+      n1 += side[pick] ? -1 : 1;
+      side[pick] ^= 1;
+      moves.push_back(pick);
+      for (int r = 0; r < n; ++r)
+        if (w[pick][r] != 0 && !locked[r]) gain[r] += side[r] == side[pick] ? -2 * w[pick][r] : 2 * w[pick][r];
+      if (cur > best + 1e-9) best = cur, best_len = moves.size();
+    }
+    for (size_t i = best_len; i < moves.size(); ++i) side[moves[i]] ^= 1;
+    if (best <= 1e-9) break;
+  }
+  double cut = 0;
+  for (int q = 0; q < n; ++q)
+    for (int r = q + 1; r < n; ++r)
+      if (side[q] != side[r]) cut += w[q][r];
+  if (cut_out) *cut_out = cut;
+  return side;
+}
+
+// One side's stem: `ids` are its leaves in circuit order, `lq[i]` the qubits of leaf i's
+// unsliced labels.  Blocks are formed greedily: start at the earliest leaf not absorbed,
+// then add, among the leaves next in line on a qubit of the block (and next in line on all
+// of their own qubits), the one that adds the fewest new qubits while the block stays within
+// `fuse` qubits.  Appends the pairs to t and returns the stem's tensor id (-1 if no leaf).
+int fused_stem(const std::vector<int>& ids, const std::vector<std::vector<int>>& lq, int n_qubits, int fuse,
+               Tree& t) {
+  if (ids.empty()) return -1;
+  std::vector<std::vector<int>> queue(n_qubits);
+  for (int i : ids)
+    for (int q : lq[i]) queue[q].push_back(i);
+  std::vector<size_t> head(n_qubits, 0);
+  std::map<int, char> done;
+  auto at_head = [&](int l) {
+    for (int q : lq[l])
+      if (head[q] >= queue[q].size() || queue[q][head[q]] != l) return false;
+    return true;
+  };
+  auto pop = [&](int l) {
+    for (int q : lq[l]) ++head[q];
+    done[l] = 1;
+  };
+  auto join = [&](int x, int y) {
+    if (x < 0) return y;
+    t.pairs.emplace_back(x, y);
+    t.sets.push_back(sym_diff(t.sets[x], t.sets[y]));
+    return (int)t.sets.size() - 1;
+  };
+  int stem = -1;
+  size_t next = 0;
+  while (true) {
+    while (next < ids.size() && done.count(ids[next])) ++next;
+    if (next >= ids.size()) break;
+    const int first = ids[next];
+    std::vector<int> Q = lq[first];
+    pop(first);
+    int block = first;
+    while (true) {
+      int pick = -1;
+      size_t pick_new = 0;
+      for (int q : Q) {
+        if (head[q] >= queue[q].size()) continue;
+        const int l = queue[q][head[q]];
+        if (!at_head(l)) continue;
+        size_t add = 0;
+        for (int r : lq[l]) add += std::find(Q.begin(), Q.end(), r) == Q.end();
+        if (Q.size() + add > (size_t)fuse) continue;
+        if (pick < 0 || add < pick_new || (add == pick_new && l < pick)) pick = l, pick_new = add;
+      }
+      if (pick < 0) break;
+      for (int r : lq[pick])
+        if (std::find(Q.begin(), Q.end(), r) == Q.end()) Q.push_back(r);
+      pop(pick);
+      block = join(block, pick);
+    }
+    stem = join(stem, block);
+  }
+  return stem;
+}
+
+// The qubit-split tree of one bisection: returns false when a side is empty.
+bool split_tree(const Network& net, const std::vector<LabelSet>& leaves, const std::vector<char>& qside,
+                int fuse, Tree& t, std::vector<int>& sliced) {
+  const int L = (int)leaves.size();
+  const int n = net.circ.n;
+  std::vector<std::vector<int>> owners(net.edges.size());
+  for (int i = 0; i < L; ++i)
+    for (int e : leaves[i]) owners[e].push_back(i);
+  // leaves on one side follow their qubits; straddling leaves take the side that leaves
+  // fewer of their indices crossing (ties: the side of their first qubit)
+  std::vector<int> lside(L, -1);
+  std::vector<std::vector<int>> qs(L);
+  for (int i = 0; i < L; ++i) {
+    for (int e : leaves[i]) {
+      const int q = net.edges[e].qubit;
+      if (std::find(qs[i].begin(), qs[i].end(), q) == qs[i].end()) qs[i].push_back(q);
+    }
+    int c0 = 0, c1 = 0;
+    for (int q : qs[i]) (qside[q] ? c1 : c0)++;
+    if (c1 == 0) lside[i] = 0;
+    else if (c0 == 0) lside[i] = 1;
+  }
+  for (int i = 0; i < L; ++i) {
+    if (lside[i] >= 0) continue;
+    int cross[2] = {0, 0};
+    for (int s = 0; s < 2; ++s)
+      for (int e : leaves[i]) {
+        if (owners[e].size() != 2) continue;
+        const int o = owners[e][0] == i ? owners[e][1] : owners[e][0];
+        const int os = lside[o] >= 0 ? lside[o] : qside[net.edges[e].qubit];
+        cross[s] += os != s;
+      }
+    lside[i] = cross[0] < cross[1] ? 0 : cross[1] < cross[0] ? 1 : (qs[i].empty() ? 0 : qside[qs[i][0]]);
+  }
+  int count[2] = {0, 0};
+  for (int i = 0; i < L; ++i) count[lside[i]]++;
+  if (count[0] == 0 || count[1] == 0) return false;
+  std::vector<char> sl(net.edges.size(), 0);
+  sliced.clear();
+  for (size_t e = 0; e < owners.size(); ++e)
+    if (owners[e].size() == 2 && lside[owners[e][0]] != lside[owners[e][1]]) {
+      sl[e] = 1;
+      sliced.push_back((int)e);
+    }
+  // qubits of each leaf's unsliced labels drive the fusion
+  std::vector<std::vector<int>> lq(L);
+  for (int i = 0; i < L; ++i)
+    for (int e : leaves[i]) {
+      if (sl[e]) continue;
+      const int q = net.edges[e].qubit;
+      if (std::find(lq[i].begin(), lq[i].end(), q) == lq[i].end()) lq[i].push_back(q);
+    }
+  t = Tree();
+  t.sets = leaves;
+  // sliced labels stay in the sets (cost functions skip them); the order is per side
+  int root[2];
+  for (int s = 0; s < 2; ++s) {
+    std::vector<int> ids;
+    for (int i = 0; i < L; ++i)
+      if (lside[i] == s) ids.push_back(i);
+    root[s] = fused_stem(ids, lq, n, fuse, t);
+  }
+  t.pairs.emplace_back(root[0], root[1]);
+  t.sets.push_back(sym_diff(t.sets[root[0]], t.sets[root[1]]));
+  return true;
+}
+
 }  // namespace
 
 std::vector<SliceStat> slice_stats(const Plan& plan) {
@@ -318,18 +525,14 @@ std::vector<SliceStat> slice_stats(const Plan& plan) {
     // values right after its last step (Sec. III-B post-lifetime merging) would run each of
     // them once per assignment of the other sliced indices: half its executed cost saved.
     {
-      std::vector<uint64_t> dm(t.sets.size(), 0);
-      for (int i = 0; i < L; ++i)
-        for (size_t j = 0; j < plan.sliced.size() && j < 64; ++j)
-          if (std::binary_search(t.sets[i].begin(), t.sets[i].end(), plan.sliced[j])) dm[i] |= uint64_t(1) << j;
+      const std::vector<int> dm = dep_counts(t, plan.sliced);
       double saved = 0;
       for (size_t k = 0; k < t.pairs.size(); ++k) {
         const auto& p = t.pairs[k];
-        dm[L + k] = dm[p.first] | dm[p.second];
         if ((int)k > st.last_step && dep[L + k]) {
           ++st.post_steps;
           const int u = (int)count_not_in(set_union(t.sets[p.first], t.sets[p.second]), sl);
-          saved += 0.5 * std::ldexp(1.0, u + __builtin_popcountll(dm[L + k]));
+          saved += 0.5 * std::ldexp(1.0, u + dm[L + k]);
         }
       }
       st.merge_saving = saved / r_all;
@@ -365,17 +568,14 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
     bool within_max = false;
   } best;
 
-  for (int trial = 0; trial < o.trials; ++trial) {
-    Rng rng{o.seed * 0x100000001B3ull + 0x9E3779B97F4A7C15ull * (uint64_t)(trial + 1)};
-    Tree t;
-    if (leaves.size() == 1) t = Tree{{}, leaves};
-    else if (o.mode == 1) t = stem_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature,
-                                       (int)(rng.next() % leaves.size()));
-    else t = greedy_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature);
+  // One candidate tree, with the indices already sliced (a separator, mode 2): slice while
+  // an intermediate exceeds the cap, release separator indices the cap still admits, add
+  // indices up to slices_min, then compare it with the best so far.
+  auto consider = [&](Tree& t, std::vector<int> sliced) {
     std::vector<char> sl(n_edges, 0);
-    std::vector<int> sliced;
-    const double c0 = tree_cost(t, sl);
-    double cur = c0;
+    for (int e : sliced) sl[e] = 1;
+    const double c0 = tree_cost(t, std::vector<char>(n_edges, 0));
+    double cur = tree_cost(t, sl);
     auto try_slice = [&](bool only_oversized) -> int {
       // candidates: labels of oversized tensors (or every inner label)
       std::set<int> cand;
@@ -417,15 +617,32 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       }
       return pick;
     };
-    bool ok = true;
     while (tree_max(t, sl) > o.log2_cap) {
       int e = try_slice(true);
-      if (e < 0) { ok = false; break; }
+      if (e < 0) return;
       sl[e] = 1;
       sliced.push_back(e);
       cur = tree_cost(t, sl);
     }
-    if (!ok) continue;
+    // release sliced indices while every intermediate stays within the cap and the total
+    // cost 2^s * C does not grow (the separator of mode 2 may leave room under the cap)
+    while (!sliced.empty() && (int)sliced.size() > o.slices_min) {
+      int pick = -1;
+      double pick_cost = 0;
+      for (size_t j = 0; j < sliced.size(); ++j) {
+        const int e = sliced[j];
+        sl[e] = 0;
+        if (tree_max(t, sl) <= o.log2_cap) {
+          const double c = tree_cost(t, sl);
+          if (c <= 2.0 * cur * (1 + 1e-12) && (pick < 0 || c < pick_cost)) pick = (int)j, pick_cost = c;
+        }
+        sl[e] = 1;
+      }
+      if (pick < 0) break;
+      sl[sliced[pick]] = 0;
+      sliced.erase(sliced.begin() + pick);
+      cur = pick_cost;
+    }
     while ((int)sliced.size() < o.slices_min) {
       int e = try_slice(false);
       if (e < 0) break;
@@ -449,6 +666,42 @@ void plan_greedy(const Network& net, const PlanOpts& o, Plan& plan) {
       best.per_slice = cur;
       best.unsliced = c0;
       best.within_max = within;
+    }
+  };
+
+  // mode 2: qubit weights = 2-qubit leaves joining each pair of qubits
+  const int nq = net.circ.n;
+  std::vector<std::vector<double>> qw;
+  if (o.mode == 2) {
+    qw.assign(nq, std::vector<double>(nq, 0.0));
+    for (const LabelSet& l : leaves) {
+      std::vector<int> qs;
+      for (int e : l)
+        if (std::find(qs.begin(), qs.end(), net.edges[e].qubit) == qs.end()) qs.push_back(net.edges[e].qubit);
+      for (size_t i = 0; i < qs.size(); ++i)
+        for (size_t j = i + 1; j < qs.size(); ++j) qw[qs[i]][qs[j]] += 1, qw[qs[j]][qs[i]] += 1;
+    }
+  }
+  for (int trial = 0; trial < o.trials; ++trial) {
+    Rng rng{o.seed * 0x100000001B3ull + 0x9E3779B97F4A7C15ull * (uint64_t)(trial + 1)};
+    if (leaves.size() == 1) {
+      Tree t{{}, leaves};
+      consider(t, {});
+    } else if (o.mode == 2) {
+      if (nq < 2) fail(1, "plan_greedy: mode 2 needs at least two qubits");
+      // both sides within the cap when the circuit allows it
+      const int max_side = std::min(nq - 1, std::max((nq + 1) / 2, std::min(o.log2_cap, nq - 1)));
+      const std::vector<char> qside = bisect_qubits(nq, qw, max_side, rng, nullptr);
+      for (int fuse : {2, 4, 6, 8, 10}) {
+        Tree t;
+        std::vector<int> sep;
+        if (split_tree(net, leaves, qside, fuse, t, sep)) consider(t, sep);
+      }
+    } else {
+      Tree t = o.mode == 1 ? stem_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature,
+                                       (int)(rng.next() % leaves.size()))
+                           : greedy_tree(leaves, n_edges, rng, trial == 0 ? 0.0 : o.temperature);
+      consider(t, {});
     }
   }
   if (!std::isfinite(best.total)) fail(5, "plan_greedy: no trial met the size cap");

@@ -259,7 +259,9 @@ class Plan:
                slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy",
                objective: str = "flops", slicing: str = "eq1", branch_exchange: bool = False) -> "Plan":
         """Plan for an `inputs.Circuit` (gate list) with the given open output qubits.
-        mode: "greedy" (balanced pairwise order) or "stem" (one tensor absorbs leaves).
+        mode: "greedy" (balanced pairwise order), "stem" (one tensor absorbs leaves) or
+        "split" (a seeded balanced bisection of the qubits; the indices between the two
+        sides are sliced and each side is one stem absorbing fused blocks of gates).
         objective: which trial is kept -- "flops" (fewest multiply-adds) or "time" (least
         modeled GB300 time).
         slicing: "eq1" (index overhead of Eq. 1) or "reuse" (lifetime-aware: executed cost
@@ -274,7 +276,7 @@ class Plan:
             nh = tnc_network_build(ch, mask)
             try:
                 ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature,
-                                     {"greedy": 0, "stem": 1}[mode], {"flops": 0, "time": 1}[objective],
+                                     {"greedy": 0, "stem": 1, "split": 2}[mode], {"flops": 0, "time": 1}[objective],
                                      {"eq1": 0, "reuse": 1}[slicing], int(bool(branch_exchange)))
             finally:
                 lib.tnc_network_destroy(nh)

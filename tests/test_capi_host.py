@@ -63,7 +63,7 @@ def _recount(desc):
     return cost, biggest
 
 
-@pytest.mark.parametrize("mode", ["greedy", "stem"])
+@pytest.mark.parametrize("mode", ["greedy", "stem", "split"])
 @pytest.mark.parametrize("rows,cols,cycles,n_open,cap,smin", [(3, 4, 8, 0, 26, 0), (4, 4, 10, 4, 12, 3), (3, 3, 6, 2, 8, 0)])
 def test_plan_invariants(rows, cols, cycles, n_open, cap, smin, mode):
     c = grid_circuit(rows, cols, cycles, seed=1)
@@ -96,6 +96,74 @@ def test_plan_invariants(rows, cols, cycles, n_open, cap, smin, mode):
         q, cut, kind, is_open = d["edges"][e]
         assert kind == 0 and not is_open
     assert p.open_qubits() == list(open_q)
+
+
+def _subtree_leaves(d, node):
+    L = len(d["leaves"])
+    out, stack = set(), [node]
+    while stack:
+        x = stack.pop()
+        if x < L:
+            out.add(x)
+        else:
+            stack.extend(d["tree"][x - L])
+    return out
+
+
+@pytest.mark.parametrize("rows,cols,cycles,cap", [(4, 6, 12, 16), (4, 5, 10, 12), (3, 6, 8, 10)])
+def test_split_plan_slices_a_separator(rows, cols, cycles, cap):
+    """mode "split": the root joins two stems, one per side of a qubit bisection.  Every
+    sliced index joins leaves of different sides, and every index joining the sides is
+    sliced unless the cap left room for it (then the root contracts it).  Each side's leaves
+    act on its own qubits (the straddling 2-qubit leaves excepted), and both sides stay
+    within the cap."""
+    c = grid_circuit(rows, cols, cycles, seed=1)
+    p = T.Plan.greedy(c, seed=3, trials=4, log2_cap=cap, mode="split")
+    d, info = p.describe(), p.info()
+    L = len(d["leaves"])
+    sets = _contraction_sets(d)
+    root_a, root_b = d["tree"][-1]
+    side = {}
+    for s_, r in enumerate((root_a, root_b)):
+        for leaf in _subtree_leaves(d, r):
+            side[leaf] = s_
+    assert len(side) == L
+    owners = {}
+    for i in range(L):
+        for e in sets[i]:
+            owners.setdefault(e, []).append(i)
+    crossing = {e for e, ow in owners.items() if len(ow) == 2 and side[ow[0]] != side[ow[1]]}
+    sliced = set(d["sliced"])
+    assert sliced <= crossing
+    released = crossing - sliced
+    assert released == (sets[root_a] & sets[root_b]) - sliced
+    # the qubits each side acts on apart from straddling leaves are disjoint
+    qubits = [set(), set()]
+    for i in range(L):
+        qubits[side[i]] |= {d["edges"][e][0] for e in sets[i] if e not in crossing}
+    assert not (qubits[0] & qubits[1])
+    cost, biggest = _recount(d)
+    assert math.isclose(math.log2(cost), info["log2_flops_per_slice"], rel_tol=1e-12)
+    assert biggest == info["max_log2_size"] <= cap
+
+
+def test_s60_split_plan_total_is_bounded():
+    """The 60-qubit 6 x 10 grid, 24 cycles, one bitstring, cap 2^32: the qubit-split plan
+    slices the legs of the fSim gates across the middle column boundary.  Its total cost
+    2^s * C (complex multiply-adds of all slices) must stay below 2^105, against 2^136.6 for
+    the greedy tree this circuit got before (width 86 unsliced, 93 sliced indices).  Any
+    plan under this cap needs at least 28 sliced indices: every balanced separator of the
+    network is at least the 60 wires of a time cut."""
+    c = grid_circuit(6, 10, 24, seed=1)
+    p = T.Plan.greedy(c, open_qubits=[], seed=3, trials=4, log2_cap=32, mode="split", objective="time")
+    info = p.info()
+    d = p.describe()
+    cost, biggest = _recount(d)
+    total = math.log2(cost) + info["n_sliced"]
+    assert math.isclose(total, info["log2_total_flops"], rel_tol=1e-12)
+    assert biggest <= 32
+    assert 28 <= info["n_sliced"] <= 66
+    assert total <= 105.0
 
 
 def test_same_seed_same_plan_and_roundtrip(tmp_path):
