@@ -93,9 +93,11 @@ def parse():
                     help="s30 (default) / t12: sliced sub-cube amplitudes; s60: per-slice throughput of the "
                          "60-qubit circuit; d20: adjoint gradients; sw: single-step contraction sweep")
     ap.add_argument("--plan-trials", type=int, default=0, help="planner trials (0: the workload's own)")
-    ap.add_argument("--s60-slices", type=int, default=4, help="seeded slice sample of the s60 workload")
-    ap.add_argument("--s60-trials", type=int, default=16, help="planner trials of the s60 workload")
-    ap.add_argument("--s60-c64", type=int, default=2, help="slices of the sample also run in complex64")
+    ap.add_argument("--s60-slices", type=int, default=256, help="seeded slice sample of the s60 workload")
+    ap.add_argument("--s60-trials", type=int, default=4, help="planner trials (qubit bisections) of the s60 workload")
+    ap.add_argument("--s60-c64", type=int, default=2, help="slices of the sample also run alone in complex64")
+    ap.add_argument("--s60-sum-c64", type=int, default=8,
+                    help="the first slices of the sample summed in complex-half and complex64")
     ap.add_argument("--sw-shapes", default="", help="log2 M,K,N triples 'm,k,n;m,k,n' (default: a fixed set)")
     ap.add_argument("--precision", default="chalf", choices=["chalf", "cbf16", "c64"])
     ap.add_argument("--no-compare", action="store_true", help="skip the complex64 comparison run")
@@ -103,7 +105,7 @@ def parse():
                     help="run the heuristic tile configurations (no timing of the tensor-core steps first)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-cap", type=int, default=23, help="log2 size cap of the oracle sample")
-    ap.add_argument("--ref-subslices", type=int, default=24, help="oracle sub-slices per reference step")
+    ap.add_argument("--ref-subslices", type=int, default=4, help="oracle sub-slices per reference step")
     ap.add_argument("--plan", default="greedy", choices=["greedy", "stem"],
                     help="greedy: balanced pairwise order; stem: one tensor absorbs leaves (fused chains)")
     ap.add_argument("--no-fuse", action="store_true", help="run stem absorptions as separate kernels")
@@ -189,7 +191,7 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- oracle sample
 def oracle_sample(circ, fixed, open_q, cuts, cap_log2):
-    """Prepare a bounded oracle sample: slice 0 of the plan's slicing (cuts fixed to 0),
+    """Prepare a bounded oracle sample: slice 0 of the given slicing (cuts fixed to 0),
     split further by the oracle's own sub-slicing at 2^cap_log2; returns (run, n_sub):
     `run(i)` contracts sub-slice i, and a whole slice is the n_sub sub-slices."""
     from oracle import network as tn
@@ -203,6 +205,20 @@ def oracle_sample(circ, fixed, open_q, cuts, cap_log2):
         return tn.contract_network(sub, open_labels, order)
 
     return run, 2 ** len(extra)
+
+
+def oracle_slice_cuts(circ, fixed, open_q, n_sliced, cap_log2):
+    """The oracle's own slicing of the workload (no product code): the wire segments its
+    greedy order slices to keep every intermediate within 2^cap_log2 entries; the first
+    n_sliced of them define the slices, as (qubit, segment) cuts."""
+    from oracle import network as tn
+
+    tensors, open_labels = tn.circuit_tensors(circ, fixed, open_q)
+    _, extra = tn.search_order([t.labels for t in tensors], open_labels, cap_log2, trials=4)
+    cuts = [(lab[1], lab[2]) for lab in extra if lab[0] == "w"][:n_sliced]
+    if len(cuts) < n_sliced:
+        raise RuntimeError(f"the oracle's slicing gave {len(cuts)} cuts, fewer than {n_sliced}")
+    return cuts
 
 
 def timed_oracle(run, n_sub, min_seconds):
@@ -228,14 +244,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2504_09186_gb300 import tnc as T
-
     w, circ, fixed, open_q = workload(args.workload, 0)
-    if args.plan_trials > 0:
-        w = dict(w, trials=args.plan_trials)
-    plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
-                         slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
-    cuts = plan.sliced_cuts()
+    cuts = oracle_slice_cuts(circ, fixed, open_q, w["smin"], w["cap"])
     run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
     per_step = min(args.ref_subslices, n_sub)
     for _ in range(args.warmup):
@@ -386,7 +396,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cuts = plan.sliced_cuts()
+        cuts = oracle_slice_cuts(circ, fixed, open_q, w["smin"], w["cap"])
         run, n_sub = oracle_sample(circ, fixed, open_q, cuts, args.cpu_sample_cap)
         k, dt = timed_oracle(run, n_sub, 10.0)
         cpu = {"value": k / (dt * n_sub), "unit": "slices/s", "cores": cpu_cores(), "kind": "oracle",
@@ -526,6 +536,9 @@ def run_sweep(args):
 
 
 def run_s60(args):
+    """60-qubit workload: the qubit-split plan (cap 2^32), a seeded sample of distinct slice
+    ids contracted by one tnc_amplitudes_ids call; per-slice throughput, the total cost of
+    the plan, and complex-half against complex64 per slice and on a summed subset."""
     import torch
 
     from inputs import grid_circuit, random_bitstrings
@@ -535,16 +548,18 @@ def run_s60(args):
     circ = grid_circuit(6, 10, 24, seed=1)
     bits = random_bitstrings(60, 1, seed=4)
     t0 = time.perf_counter()
-    plan = T.Plan.greedy(circ, open_qubits=[], seed=3, trials=args.s60_trials, log2_cap=32)
+    plan = T.Plan.greedy(circ, open_qubits=[], seed=3, trials=args.s60_trials, log2_cap=32, mode="split",
+                         objective="time")
     plan_s = time.perf_counter() - t0
     info = plan.info()
     s = info["n_sliced"]
     rng = np.random.default_rng(4)
     space = 1 << min(s, 62)
-    ids = []
+    ids, seen = [], set()
     while len(ids) < args.s60_slices:
         x = int(rng.integers(0, space))
-        if x not in ids:
+        if x not in seen:
+            seen.add(x)
             ids.append(x)
     ctx = T.Context(0)
     stream = torch.cuda.Stream()
@@ -552,12 +567,11 @@ def run_s60(args):
     out = torch.zeros((1, 1), dtype=torch.complex128, device="cuda")
     peaks = load_peaks()
 
-    def one(prec, sid, profile):
+    def timed(prec, sids, profile=False):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.amplitudes(plan, bits, prec, slice_begin=sid, slice_count=1, out=out, stream=stream.cuda_stream,
-                       profile=profile)
+        ctx.amplitudes_ids(plan, bits, sids, prec, out=out, stream=stream.cuda_stream, profile=profile)
         e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1), complex(out.cpu().numpy()[0, 0])
@@ -568,36 +582,53 @@ def run_s60(args):
         tune = ctx.autotune(plan, bits, "chalf", slice_begin=ids[0], slice_count=1)
         tune["setup_s"] = time.perf_counter() - t0
     for _ in range(max(1, args.warmup)):
-        one("chalf", ids[0], False)
+        timed("chalf", ids[:1])
     with ClockSampler(0) as clk:
-        res = [one("chalf", sid, True) for sid in ids]
-        prof = ctx.profile_read()
+        ms_all, amp_sum = timed("chalf", ids)
     clocks = clk.summary()
-    ms = [r[0] for r in res]
-    per_slice_s = sum(ms) / len(ms) / 1e3
+    per_slice_s = ms_all / len(ids) / 1e3
     value = 1.0 / per_slice_s
+    # per-step device times on a few slices (a separate, profiled call)
+    n_prof = min(4, len(ids))
+    ms_prof, _ = timed("chalf", ids[:n_prof], profile=True)
+    prof = ctx.profile_read()
     k = int(np.argmax(prof["ms"]))
     roof = roofline_of(int(prof["kind"][k]), prof["flops"][k] / prof["launches"][k], prof["bytes"][k] / prof["launches"][k],
                        prof["ms"][k] / prof["launches"][k], peaks)
     roof["traffic"] = None
-    roof["kernel"] = {"step": k, "kind": int(prof["kind"][k]), "share_of_slice_time": float(prof["ms"][k] / prof["ms"].sum())}
+    roof["kernel"] = {"step": k, "kind": int(prof["kind"][k]), "share_of_slice_time": float(prof["ms"][k] / prof["ms"].sum()),
+                      "profiled_slices": n_prof}
+    # complex-half against complex64: single slices, and the sum over the first few
     cmp64 = []
-    for sid, (_, a16) in list(zip(ids, res))[: args.s60_c64]:
-        try:
-            ms64, a64 = one("c64", sid, False)
-            cmp64.append({"slice": sid, "ms": ms64, "rel_err_chalf_vs_c64": abs(a16 - a64) / max(abs(a64), 1e-300)})
-        except Exception as exc:  # a complex64 arena that does not fit is reported, not fatal
-            cmp64.append({"slice": sid, "error": str(exc).splitlines()[0]})
-    line = {"metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 1, "steps": len(ids),
-            "warmup": max(1, args.warmup), "ms_per_step": per_slice_s * 1e3, "higher_is_better": True,
+    per16 = []
+    for sid in ids[: args.s60_c64]:
+        _, a16 = timed("chalf", [sid])
+        ms64, a64 = timed("c64", [sid])
+        per16.append(a16)
+        cmp64.append({"slice": sid, "ms_c64": ms64, "rel_err_chalf_vs_c64": abs(a16 - a64) / max(abs(a64), 1e-300)})
+    summed = None
+    if args.s60_sum_c64 > 0:
+        sub = ids[: args.s60_sum_c64]
+        _, s16 = timed("chalf", sub)
+        ms64, s64 = timed("c64", sub)
+        summed = {"slices": len(sub), "ms_c64": ms64, "rel_err_chalf_vs_c64": abs(s16 - s64) / max(abs(s64), 1e-300)}
+    line = {"metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 1, "steps": 1,
+            "warmup": max(1, args.warmup), "ms_per_step": ms_all, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-            "config": {"workload": "s60: 6x10 grid RQC, 24 cycles, cap 2^32 chalf entries, one bitstring; "
-                                   "per-slice time over a seeded slice sample",
-                       "slice_ids": ids, "sliced_indices": s, "plan_trials": args.s60_trials, "plan_seconds": plan_s,
+            "config": {"workload": "s60: 6x10 grid RQC, 24 cycles, cap 2^32 chalf entries, one bitstring; qubit-split "
+                                   "plan; one tnc_amplitudes_ids call over a seeded sample of distinct slice ids",
+                       "slices_per_step": len(ids), "slice_id_seed": 4, "sliced_indices": s,
+                       "plan_mode": "split", "plan_trials": args.s60_trials, "plan_seconds": plan_s,
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"],
+                       "log2_total_cmacs": info["log2_total_flops"],
+                       "plan_max_log2_size": info["max_log2_size"],
+                       "plan_model_seconds_per_slice": info["model_seconds_per_slice"],
                        "complex_tflops": 8 * 2 ** info["log2_flops_per_slice"] * value / 1e12,
-                       "extrapolated_total_log2_seconds": s - float(np.log2(value)), "autotune": tune},
-            "per_slice_ms": ms, "complex64": cmp64, "roofline": roof, "clocks": clocks}
+                       "extrapolated_total_log2_seconds": s - float(np.log2(value)), "autotune": tune,
+                       "l2": "intermediates of 2^27..2^32 entries (0.5..16 GiB): L2-cold by size"},
+            "amplitude_sum_chalf": [amp_sum.real, amp_sum.imag],
+            "complex64": {"per_slice": cmp64, "summed": summed}, "roofline": roof, "clocks": clocks,
+            "profiled_ms": ms_prof}
     print(json.dumps(line))
 
 

@@ -285,23 +285,26 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
                         const int32_t* labels_c, int32_t* c_exp2, void* stream);
 
 /* The same single contraction as tnc_contract, for callers that cannot allocate device
- * memory: code running while a stream is being captured into a CUDA graph, real-time
- * threads that must not take the allocator's locks or implicit device syncs, and
- * applications whose own pool allocator has already reserved the device's memory.  It
- * takes no context and allocates nothing: the scratch it needs (a few max/exponent
- * slots and, for split-over-K shapes, the FP32 partial sums) is one file-scope device
- * array of 4 MiB that every GPU which loads this library holds until the process exits.
+ * memory: real-time threads that must not take the allocator's locks or wait on the
+ * device synchronisations an allocation may imply, and applications whose own pool
+ * allocator has already reserved the device's memory.  It takes no context and allocates
+ * nothing: the scratch it needs (a few max/exponent slots and, for split-over-K shapes,
+ * the FP32 partial sums) is one file-scope device array of 4 MiB that every GPU which
+ * loads this library holds until the process exits.
  * There is no counterpart in the paper; this is an interface choice of this library.
  *  - Device: the caller's current device; a, b, c must live there.  The first call on a
  *    device looks up the array's device address (cudaGetSymbolAddress); make that first
  *    call before any stream capture.
  *  - Arithmetic: always the FP32 SIMT kernels (never the tensor-core kernel).
- *  - Limit: the split-K partials must fit in 4 MiB - 256 B; the tile policy keeps them
- *    at most 1024 splits x 256 outputs x 8 B = 2 MiB, and a contraction needing more is
- *    rejected with TNC_E_INVALID_ARG and a message giving the size it needs.
+ *  - Limit: the split-K partials must fit in 4 MiB - 256 B.  A split step has at most
+ *    2^10 outputs, and its split count is halved (each CTA then sums a longer K range)
+ *    until splits x outputs x 8 B fits, so no contraction this library accepts needs
+ *    more; the check that would reject a larger need with TNC_E_INVALID_ARG (the message
+ *    gives the size) remains as a guard.
  *  - Sharing: every call uses the same array; the slots are cleared on each call, but
  *    calls that overlap on the GPU (several streams, or several host threads) race on it.
- *  - stream: cudaStream_t or NULL (the legacy default stream); returns after C is ready.
+ *  - stream: cudaStream_t or NULL (the legacy default stream); the call copies C's
+ *    exponent to the host and synchronises the stream, so it returns after C is ready.
  * Other arguments, layouts and errors are those of tnc_contract. */
 tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a, const int32_t* labels_a,
                                 const void* b, int32_t rank_b, const int32_t* labels_b, void* c,

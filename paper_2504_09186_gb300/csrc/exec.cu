@@ -1897,6 +1897,11 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int kind = K_GENERIC;
     TileSpec t = tile_for(la, lb, lc, 1, kind);
+    // fewer splits over K (same tiles, longer K range per CTA) until the FP32 partial sums
+    // fit the static array: at most 2^10 outputs per GEPDOT tile leaves room for 2^8 splits
+    const size_t room = kNoAllocScratchBytes - kNoAllocSlotBytes;
+    while (t.splitk > 1 && size_t(t.splitk) * (size_t(1) << lc.size()) * sizeof(float2) > room) t.splitk /= 2;
+    if (t.splitk == 1) kind = K_GENERIC;
     StepLaunch L = make_launch(t, kind, la, lb, lc);
     make_stream(L, elem_bytes(precision), false);
     if (L.kind == K_SPLITK) {

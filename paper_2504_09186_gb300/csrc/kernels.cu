@@ -28,14 +28,20 @@
 
 namespace tnc {
 
+// The attribute belongs to the kernel on one device, so the cache is keyed by both: a
+// call on another device sets it there too.
 cudaError_t set_smem_once(const void* kernel, size_t bytes) {
   static std::mutex mu;
-  static std::map<const void*, size_t> done;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
-  auto it = done.find(kernel);
+  const auto key = std::make_pair(dev, kernel);
+  auto it = done.find(key);
   if (it != done.end() && it->second >= bytes) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done[kernel] = bytes;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[key] = bytes;
   return e;
 }
 

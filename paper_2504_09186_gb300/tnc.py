@@ -397,7 +397,7 @@ class Context:
         return out
 
     def amplitudes_ids(self, plan: Plan, bitstrings: Optional[np.ndarray], slice_ids, precision: str = "c64",
-                       wave: int = 0, out=None, stream: int = 0, fuse: bool = True) -> np.ndarray:
+                       wave: int = 0, out=None, stream: int = 0, fuse: bool = True, profile: bool = False) -> np.ndarray:
         """Amplitudes summed over the listed slice ids (tnc_amplitudes_ids)."""
         lib = load_library()
         info = plan.info()
@@ -413,7 +413,7 @@ class Context:
             out = np.zeros((batch, 1 << info["n_open"]), dtype=np.complex128)
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
         opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave, 0,
-                             int(fuse), 0)
+                             int(fuse), int(profile))
         _check(lib.tnc_amplitudes_ids(self.h, plan.h, C.byref(opts), bp, batch,
                                       ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids), C.c_void_p(ptr),
                                       C.c_void_p(stream)))

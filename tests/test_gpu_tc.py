@@ -216,3 +216,28 @@ def test_ttgt_random_layouts(ctx, precision, shape):
         idx = np.unique(np.concatenate([[0, len(got) - 1], np.random.default_rng(9).integers(0, len(got), 510)]))
         err = metrics.rel_err_norm(got[idx], pairwise.contract_at(aq, la, bq, lb, lc, idx))
     assert err <= TOL[precision], err
+
+
+# Every output entry of the persistent kernels at the dominant step shape of the 30-qubit
+# plan (M = 2^14, K = 2^12, N = 2^10, one instance) against the FP64 oracle, element by
+# element.  Bound per entry: the output is rounded once to the storage type (unit roundoff
+# u = 2^-11 fp16, 2^-8 bf16 per real component, so at most 2u |c| for the complex entry),
+# plus the FP32 accumulation over K = 2^12 products, whose typical size is
+# 2^-24 sqrt(K) rms(C) = 2^-18 rms(C); 1e-4 rms(C) leaves a wide margin for it.
+FULL_CASES = [((14, 12, 10), True), ((14, 5, 10), True), ((14, 5, 10), False)]
+UNIT = {"chalf": 2.0 ** -11, "cbf16": 2.0 ** -8}
+
+
+@pytest.mark.parametrize("precision", ["chalf", "cbf16"])
+@pytest.mark.parametrize("shape,direct", FULL_CASES)
+def test_persistent_kernels_every_output_against_oracle(ctx, precision, shape, direct):
+    a, la, b, lb, lc = tma_case(*shape, seed=3 * sum(shape) + int(direct), direct=direct)
+    got, aq, bq = run(ctx, precision, a, la, b, lb, lc)
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 5  # a persistent kernel ran
+    ref = pairwise.contract(aq, la, bq, lb, lc)
+    assert len(ref) == 1 << (shape[0] + shape[2])
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    bound = 2 * UNIT[precision] * np.abs(ref) + 1e-4 * rms
+    bad = np.flatnonzero(np.abs(got - ref) > bound)
+    assert bad.size == 0, (bad[:8], got[bad[:8]], ref[bad[:8]])
+    assert metrics.rel_err_norm(got, ref) <= TOL[precision]
