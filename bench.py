@@ -347,18 +347,33 @@ def run_ours(args):
     clocks = clk.summary()
     value = n_slices * world / (ms / 1e3)
 
+    peaks = load_peaks()
     # complex64 beside it, and the error of both against each other / the oracle golden
     c64 = None
     if not args.no_compare and args.precision != "c64":
-        ms64, _, amp64 = timed("c64", max(1, min(args.steps, 3)), 1, False)
+        ms64, prof64, amp64 = timed("c64", max(1, min(args.steps, 3)), 1, True)
         c64 = {"slices_per_s": n_slices * world / (ms64 / 1e3), "ms_per_step": ms64,
                "rel_err_vs_c64": metrics.rel_err_norm(amp, amp64)}
+        if prof64 is not None and len(prof64["ms"]):
+            k64 = int(np.argmax(prof64["ms"]))
+            tf32 = measure_tf32_peak()
+            r64 = roofline_tf32(int(prof64["kind"][k64]), prof64["flops"][k64] / prof64["launches"][k64],
+                                prof64["bytes"][k64] / prof64["launches"][k64],
+                                prof64["ms"][k64] / prof64["launches"][k64], tf32, peaks)
+            r64["traffic"] = None
+            r64["kernel"] = {"step": k64, "kind": int(prof64["kind"][k64]),
+                             "share_of_step_time": float(prof64["ms"][k64] / prof64["ms"].sum())}
+            c64["roofline"] = r64
+            c64["tf32_peak_tflops_measured"] = tf32
+            c64["tensor_core_steps"] = int(sum(1 for x in prof64["kind"] if int(x) == 4))
     golden = os.path.join(ROOT, "tests", "golden", "s30_subcube_amplitudes.txt")
     err_golden = None
     if args.workload == "s30" and rank == 0 and os.path.exists(golden):
         ref = np.loadtxt(golden)
         ref = ref[:, 0] + 1j * ref[:, 1]
         err_golden = metrics.rel_err_norm(amp, ref)
+        if c64 is not None:
+            c64["rel_err_vs_oracle"] = metrics.rel_err_norm(amp64, ref)
 
     # end to end: host bitstrings in, host amplitudes out, through the public API
     host_out = np.zeros((1, n_out), dtype=np.complex128)
@@ -373,7 +388,6 @@ def run_ours(args):
     d2h = host_out.nbytes
 
     # roofline of the dominant kernel (largest device time), from the live events
-    peaks = load_peaks()
     k = int(np.argmax(prof["ms"]))
     per_launch_ms = prof["ms"][k] / prof["launches"][k]
     kind = int(prof["kind"][k])
@@ -435,6 +449,52 @@ def run_ours(args):
 
 
 # --------------------------------------------------------------------------- other workloads
+def measure_tf32_peak():
+    """Dense TF32 tensor throughput of this GPU, measured: cuBLAS FP32 GEMM with TF32 math,
+    8192^3 (2 N^3 flops), best of 10 launches timed with CUDA events."""
+    import torch
+
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32)
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = None
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def roofline_tf32(kind, flops, nbytes, ms, tf32_peak, peaks):
+    """Roofline of a complex64 launch.  On the 3xTF32 tensor-core kernel (kind 4) every real
+    product is three TF32 products, so the tensor pipe executes 3x the algorithmic flops:
+    achieved = 3 flops / time against the measured TF32 peak, tensor-bound above that
+    balance.  Complex64 SIMT kernels: roofline_of."""
+    if kind != 4:
+        return roofline_of(kind, flops, nbytes, ms, peaks)
+    if 3 * flops / max(nbytes, 1.0) >= tf32_peak * 1e3 / peaks["hbm_gbs"]:
+        r = {"bound": "tensor", "achieved": 3 * flops / (ms * 1e-3) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+             "peak_kind": "cuBLAS TF32 GEMM 8192^3, measured in this run",
+             "complex_tflops": flops / (ms * 1e-3) / 1e12}
+    else:
+        r = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "peak_kind": "STREAM-style copy, measured"}
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
+
+
 def roofline_of(kind, flops, nbytes, ms, peaks):
     """Roofline of one kernel launch from its algorithmic flops / bytes and device time.
     Tensor-core kernels (kinds 3-6) are tensor-bound above the machine balance

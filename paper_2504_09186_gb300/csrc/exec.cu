@@ -230,20 +230,43 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 4-D view of a planar 16-bit tensor laid out [Kt (2^kt entries) | rows ...]:
 // (k, row, plane, instance) with a box of 2^kt x box_rows x 1 x 1, swizzled to match the
 // K-major shared-memory layout of the MMA (32B swizzle for 32-byte rows, 64B for 64-byte).
+// FP32 entries (the complex64 3xTF32 kernel) take 16 entries (64 bytes) per box row: a
+// 16-entry K run is the 4-D view with a 64B swizzle; a 32-entry run is the 5-D view
+// (k low 16, k high bit, row, plane, instance) whose box takes one half.
 static void encode_tile_map(CUtensorMap* m, const void* base, int rank, int kt, int box_rows, int64_t inst_stride,
-                            int64_t n_inst) {
+                            int64_t n_inst, size_t eb = 2) {
   if ((int64_t(1) << (rank - kt)) < box_rows || rank > 32) fail(TNC_E_PLAN, "tensor map: operand rank out of range");
   if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) fail(TNC_E_PLAN, "tensor map: base not 16-byte aligned");
   const int64_t plane = int64_t(1) << rank;
   const int64_t istr = std::max<int64_t>(inst_stride, 2 * plane);
-  cuuint64_t dims[4] = {cuuint64_t(1) << kt, cuuint64_t(1) << (rank - kt), 2, (cuuint64_t)std::max<int64_t>(1, n_inst)};
-  cuuint64_t strides[3] = {(cuuint64_t(1) << kt) * 2, (cuuint64_t)plane * 2, (cuuint64_t)istr * 2};
-  cuuint32_t box[4] = {1u << kt, (cuuint32_t)box_rows, 1, 1};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUtensorMapSwizzle sw = kt == 5 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
-  const CUresult r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims, strides,
-                                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const cuuint64_t ni = (cuuint64_t)std::max<int64_t>(1, n_inst);
+  CUresult r;
+  if (eb == 2) {
+    cuuint64_t dims[4] = {cuuint64_t(1) << kt, cuuint64_t(1) << (rank - kt), 2, ni};
+    cuuint64_t strides[3] = {(cuuint64_t(1) << kt) * 2, (cuuint64_t)plane * 2, (cuuint64_t)istr * 2};
+    cuuint32_t box[4] = {1u << kt, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapSwizzle sw = kt == 5 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+    r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else if (kt == 4) {
+    cuuint64_t dims[4] = {16, cuuint64_t(1) << (rank - 4), 2, ni};
+    cuuint64_t strides[3] = {16 * 4, (cuuint64_t)plane * 4, (cuuint64_t)istr * 4};
+    cuuint32_t box[4] = {16, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[5] = {16, 2, cuuint64_t(1) << (rank - 5), 2, ni};
+    cuuint64_t strides[4] = {16 * 4, 32 * 4, (cuuint64_t)plane * 4, (cuuint64_t)istr * 4};
+    cuuint32_t box[5] = {16, 1, (cuuint32_t)box_rows, 1, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    r = tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   if (r != CUDA_SUCCESS) fail(TNC_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
 }
 
@@ -562,7 +585,8 @@ struct tnc_context_s {
   int sm_count = 0;
   size_t total_mem = 0;
   DevBuf bits, inst_slice, inst_row, segs, acc, scratch, partials, status, ttgt;
-  bool no_tc = false;  // TNC_NO_TC=1 in the environment: fp16/bf16 steps on the SIMT kernel
+  bool no_tc = false;  // TNC_NO_TC=1 in the environment: every step on the SIMT kernels
+  bool no_tc64 = false; // TNC_NO_TC64=1: complex64 steps on the SIMT kernels (3xTF32 off)
   bool no_tma = false; // TNC_NO_TMA=1: tensor-core steps gather their tiles with cp.async
   bool no_persist = false;  // TNC_NO_PERSIST=1: short-K TMA steps use one CTA per tile
   bool no_reuse = false;    // TNC_NO_REUSE=1: every step runs for every (row, slice)
@@ -794,6 +818,12 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   const auto& lc = P.tensors[st.c].labels;
   TileSpec t = st.tc_tile;
   int bn = st.tc_bn;
+  if (prog->precision == TNC_C64 && bn == 256) {
+    // the 3xTF32 kernel keeps hi and lo parts of every stage: 128-wide tiles at most
+    t.No.insert(t.No.begin(), t.Nt.begin() + 7, t.Nt.end());
+    t.Nt.resize(7);
+    bn = 128;
+  }
   if (ch && ch->bn && ch->bn < bn) {
     // a narrower tile loads a prefix of B's tile labels (B is laid out [Kt | Nt | ...]); the
     // rest become the lowest outer labels
@@ -815,6 +845,7 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   const bool heuristic =
       (bn <= 128 && L.tp.n_ok <= 3 && tiles_w >= 4 * 152) || (bn == 256 && L.tp.n_ok <= 8 && tiles_w >= 2 * 152);
   L.tp.persistent = (ch ? ch->persistent != 0 : heuristic) && can_persist ? 1 : 0;
+  if (prog->precision == TNC_C64) L.tp.persistent = 0;  // one CTA per tile (3xTF32 kernel)
   if (ch && ch->stages) L.tp.stages = ch->stages == 3 ? 3 : 0;
   const size_t eb = elem_bytes(prog->precision);
   char* arena = prog->arena.as<char>();
@@ -824,8 +855,8 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
   if (!ctx->no_tma) {
     // operands are laid out [Kt | Mt/Nt | ...] by the compiler: load tiles with TMA
     const int kt = st.tc_bk == 32 ? 5 : 4;
-    encode_tile_map(&L.tp.tmA, L.tp.A, (int)la.size(), kt, 128, prog->inst_stride, prog->W);
-    encode_tile_map(&L.tp.tmB, L.tp.B, (int)lb.size(), kt, bn, prog->inst_stride, prog->W);
+    encode_tile_map(&L.tp.tmA, L.tp.A, (int)la.size(), kt, 128, prog->inst_stride, prog->W, eb);
+    encode_tile_map(&L.tp.tmB, L.tp.B, (int)lb.size(), kt, bn, prog->inst_stride, prog->W, eb);
     L.kind = K_TMA;
     if (ctx->no_persist) L.tp.persistent = 0;
   }
@@ -987,7 +1018,8 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
                 2.0 * double(eb);
     }
     // 32-wide tiles exist only in the TMA kernel
-    if (precision != TNC_C64 && st.tc_ok && !ctx->no_tc && !(ctx->no_tma && st.tc_bn == 32)) {
+    const bool tc64 = precision == TNC_C64 && !ctx->no_tc64 && !ctx->no_tma;
+    if ((precision != TNC_C64 || tc64) && st.tc_ok && !ctx->no_tc && !(ctx->no_tma && st.tc_bn == 32)) {
       StepLaunch T = tc_launch(ctx, P, prog.get(), (int)s, nullptr);
       if (T.kind == K_TMA) {
         // a configuration tuned for this shape (tnc_autotune) replaces the heuristics
@@ -1182,6 +1214,8 @@ tnc_status tnc_context_create(int32_t device, tnc_context* out) {
     c->no_stream = env5 && env5[0] == '1';
     const char* env6 = std::getenv("TNC_SERIAL");
     c->serial = env6 && env6[0] == '1';
+    const char* env7 = std::getenv("TNC_NO_TC64");
+    c->no_tc64 = env7 && env7[0] == '1';
     *out = c;
   });
 }
@@ -1707,12 +1741,18 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
     bool ttgt = false;
     std::vector<int> la2, lb2, lc2;
     PermParams perm_a, perm_b, perm_c;
-    const bool tma_a = precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma && tma_tile_from_layout(la, lb, lc, tct, bn, bk);
-    const bool tma_b = !tma_a && precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma &&
-                       tma_tile_from_layout(lb, la, lc, tct, bn, bk);
+    // complex64 takes the 3xTF32 kernel on operands already in the TMA layouts
+    const bool tc_ok = !ctx->no_tc && !ctx->no_tma && (precision != TNC_C64 || !ctx->no_tc64);
+    const bool tma_a = tc_ok && tma_tile_from_layout(la, lb, lc, tct, bn, bk);
+    const bool tma_b = !tma_a && tc_ok && tma_tile_from_layout(lb, la, lc, tct, bn, bk);
     if (tma_a || tma_b) {
       const std::vector<int>& ra = tma_a ? la : lb;
       const std::vector<int>& rb = tma_a ? lb : la;
+      if (precision == TNC_C64 && bn == 256) {
+        tct.No.insert(tct.No.begin(), tct.Nt.begin() + 7, tct.Nt.end());
+        tct.Nt.resize(7);
+        bn = 128;
+      }
       make_tc_launch(L, tct, ra, rb, lc, precision, bn, bk, 1);
       float2* part = nullptr;
       if (L.tp.splitk > 1) {
@@ -1722,10 +1762,10 @@ tnc_status tnc_contract(tnc_context ctx, int32_t precision, const void* a, int32
       bind_tc(L, tma_a ? a : b, tma_a ? b : a, c, 0, mx, ex, 3, tma_a ? 0 : 1, tma_a ? 1 : 0, 2, ctx->status.as<int32_t>(),
               part);
       const int kt = bk == 32 ? 5 : 4;
-      encode_tile_map(&L.tp.tmA, L.tp.A, (int)ra.size(), kt, 128, 0, 1);
-      encode_tile_map(&L.tp.tmB, L.tp.B, (int)rb.size(), kt, bn, 0, 1);
+      encode_tile_map(&L.tp.tmA, L.tp.A, (int)ra.size(), kt, 128, 0, 1, eb);
+      encode_tile_map(&L.tp.tmB, L.tp.B, (int)rb.size(), kt, bn, 0, 1, eb);
       L.kind = K_TMA;
-      if (ctx->no_persist) L.tp.persistent = 0;
+      if (ctx->no_persist || precision == TNC_C64) L.tp.persistent = 0;
     } else if (precision != TNC_C64 && !ctx->no_tc && !ctx->no_tma &&
                ttgt_layouts(la.size() >= lb.size() ? la : lb, la.size() >= lb.size() ? lb : la, la2, lb2, lc2) &&
                ttgt_fits(la2.size(), lb2.size(), lc2.size(), eb)) {

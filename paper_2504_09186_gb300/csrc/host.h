@@ -88,13 +88,15 @@ void gate_envs_from_leaf_envs(const Network& net, const std::vector<SmallTensor>
 // time (complex-half storage, 4 bytes per entry), at the rates this library's kernels reach
 // on GB300.  Steps large enough for tensor-core tiles (M >= 2^7, N >= 2^6 or the reverse,
 // K >= 2^4): 1.8 PF/s and 4.5 TB/s (the tensor-core GEMM and its direct epilogue).  Others:
-// the FP32-lane rate of 40 TF/s and 1.5 TB/s (the SIMT tiled kernels).
+// the FP32-lane rate of 40 TF/s and 1.5 TB/s (the SIMT tiled kernels), except absorptions
+// into a large tensor (2^24 entries or more) through a thin operand, measured at 0.7 TB/s.
 inline double step_model_seconds(int a, int b, int c, int k) {
   const int m = a - k, n = b - k;
   const double flops = 8.0 * std::ldexp(1.0, a + b - k);
   const double bytes = 4.0 * (std::ldexp(1.0, a) + std::ldexp(1.0, b) + std::ldexp(1.0, c));
   const bool tc = std::max(m, n) >= 7 && std::min(m, n) >= 6 && k >= 4;
-  return tc ? std::max(flops / 1.8e15, bytes / 4.5e12) : std::max(flops / 4.0e13, bytes / 1.5e12);
+  const double bw = std::max(a, b) >= 24 ? 0.7e12 : 1.5e12;
+  return tc ? std::max(flops / 1.8e15, bytes / 4.5e12) : std::max(flops / 4.0e13, bytes / bw);
 }
 
 struct PlanOpts {

@@ -386,13 +386,13 @@ int fused_stem(const std::vector<int>& ids, const std::vector<std::vector<int>>&
     for (int q : lq[l]) ++head[q];
     done[l] = 1;
   };
-  auto join = [&](int x, int y) {
-    if (x < 0) return y;
-    t.pairs.emplace_back(x, y);
-    t.sets.push_back(sym_diff(t.sets[x], t.sets[y]));
-    return (int)t.sets.size() - 1;
+  auto add_qubits = [](std::vector<int>& Q, const std::vector<int>& more) {
+    for (int r : more)
+      if (std::find(Q.begin(), Q.end(), r) == Q.end()) Q.push_back(r);
   };
-  int stem = -1;
+  // blocks in the order the stem absorbs them: their leaves and qubits
+  std::vector<std::vector<int>> blocks;
+  std::vector<std::vector<int>> bq;
   size_t next = 0;
   while (true) {
     while (next < ids.size() && done.count(ids[next])) ++next;
@@ -400,7 +400,7 @@ int fused_stem(const std::vector<int>& ids, const std::vector<std::vector<int>>&
     const int first = ids[next];
     std::vector<int> Q = lq[first];
     pop(first);
-    int block = first;
+    std::vector<int> block{first};
     while (true) {
       int pick = -1;
       size_t pick_new = 0;
@@ -414,12 +414,40 @@ int fused_stem(const std::vector<int>& ids, const std::vector<std::vector<int>>&
         if (pick < 0 || add < pick_new || (add == pick_new && l < pick)) pick = l, pick_new = add;
       }
       if (pick < 0) break;
-      for (int r : lq[pick])
-        if (std::find(Q.begin(), Q.end(), r) == Q.end()) Q.push_back(r);
+      add_qubits(Q, lq[pick]);
       pop(pick);
-      block = join(block, pick);
+      block.push_back(pick);
     }
-    stem = join(stem, block);
+    blocks.push_back(block);
+    bq.push_back(Q);
+  }
+  // consecutive blocks whose qubits together stay within `fuse` become one branch: the stem
+  // absorbs them one after the other, so contracting them first changes nothing but the
+  // number (and the width) of the large absorptions
+  std::vector<std::vector<int>> merged{blocks[0]};
+  std::vector<std::vector<int>> mq{bq[0]};
+  for (size_t b = 1; b < blocks.size(); ++b) {
+    std::vector<int> u = mq.back();
+    add_qubits(u, bq[b]);
+    if (u.size() <= (size_t)fuse) {
+      merged.back().insert(merged.back().end(), blocks[b].begin(), blocks[b].end());
+      mq.back() = u;
+    } else {
+      merged.push_back(blocks[b]);
+      mq.push_back(bq[b]);
+    }
+  }
+  auto join = [&](int x, int y) {
+    if (x < 0) return y;
+    t.pairs.emplace_back(x, y);
+    t.sets.push_back(sym_diff(t.sets[x], t.sets[y]));
+    return (int)t.sets.size() - 1;
+  };
+  int stem = -1;
+  for (const auto& blk : merged) {
+    int branch = -1;
+    for (int l : blk) branch = join(branch, l);
+    stem = join(stem, branch);
   }
   return stem;
 }

@@ -368,8 +368,14 @@ __device__ __forceinline__ void tc_epilogue(const TcParams& p, uint32_t tmem, bo
         continue;
     }
 #endif
-    *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + stg_swz(t));
-    *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + stg_swz(t));
+    // 8 entries: one 16-byte vector of 16-bit values, two of FP32 values
+    constexpr int VE = 16 / int(sizeof(T));
+#pragma unroll
+    for (int v = 0; v < 8 / VE; ++v) {
+      *reinterpret_cast<uint4*>(Cre + off + v * VE) = *reinterpret_cast<const uint4*>(stg + stg_swz(t) + v * VE);
+      *reinterpret_cast<uint4*>(Cre + p.planeC + off + v * VE) =
+          *reinterpret_cast<const uint4*>(stg + CT + stg_swz(t) + v * VE);
+    }
   }
   // block max -> tensor max
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -706,6 +712,424 @@ __global__ void __launch_bounds__(TC_THREADS, (NST == 3 ? 2 : 1)) k_tc_tma(const
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   ok = __syncthreads_and(ok);
   tc_epilogue<T, BN, S::TMEM_COLS>(p, tmem, ok, smem, TCm, TCn, hiC, red, oC, I);
+}
+
+// Complex64 on the tensor cores (3xTF32).  kind::tf32 MMAs read 32-bit operands with a
+// 10-bit stored mantissa, so each FP32 operand entry x is split in shared memory into
+// hi = x rounded to TF32 and lo = (x - hi) rounded to TF32 (x - hi is exact in FP32), and
+// every real product is taken as hi_a hi_b + hi_a lo_b + lo_a hi_b: the dropped lo_a lo_b
+// and the rounding of lo are each about 2^-22 of |a b|.  Per 8-wide k step twelve MMAs
+// (six per accumulator) form
+//   Dr = Ar Br - Ai Bi,  Di = Ar Bi + Ai Br   (each product in three parts).
+// The tensor core adds into its FP32 accumulator without rounding to nearest (the sums are
+// cut toward zero), a bias that grows with the length of the accumulation: over a K loop
+// of 2^12 it shrank results by about 2e-4.  So each 8-wide k step accumulates from zero
+// into one of two TMEM buffers, and the drain warps add that chunk to FP32 sums held in
+// registers with ordinary round-to-nearest adds while the MMAs fill the other buffer; the
+// biased chain is six MMAs long.
+// The operand layouts are those of k_tc_tma ([Kt | Mt | ...], [Kt | Nt | ...]) with FP32
+// entries: a K tile of 16 entries is one 64-byte row (SW64); a compiled 32-wide K tile is
+// loaded as two halves through a 5-D tensor map (k low 16, k high bit, row, plane, instance).
+// Warp roles (12 warps):
+//   warp 0 lane 0   TMA loads of a stage's hi half, on "full";
+//   warp 1 lane 0   waits on "conv", issues the MMAs of each k step into TMEM buffer
+//                   (step & 1) after "acc empty", commits them to "acc full" and each stage
+//                   to "empty";
+//   warps 2..3      split the landed stage (hi in place, lo into the stage's second half),
+//                   fence their writes to the async proxy and arrive on "conv";
+//   warps 4..11     drain: lane quadrant (warp & 3), column half ((warp - 4) >> 2); add each
+//                   chunk to the register sums, release the buffer on "acc empty"; then
+//                   the epilogue (scale, FP32 stores, straight from registers or staged).
+// Every wait is bounded as in the other kernels.
+constexpr int TF32_THREADS = 384;
+template <int BN>
+struct Tf32Shape {
+  static constexpr int ROWB = 64;                             // 16 FP32 entries per tile row
+  static constexpr int A_BYTES = TC_BM * ROWB;                // one plane of the A tile
+  static constexpr int B_BYTES = BN * ROWB;
+  static constexpr int HALF = 2 * A_BYTES + 2 * B_BYTES;      // Ar, Ai, Br, Bi (hi parts)
+  static constexpr int STAGE = 2 * HALF;                      // + their lo parts
+  static constexpr int NST_FIT = TC_PIPE_BUDGET / STAGE;
+  static constexpr int NST = NST_FIT > 4 ? 4 : NST_FIT;
+  static constexpr int PIPE = NST * STAGE;
+  static constexpr int STG = TC_BM * BN * 2 * 4;              // staged C tile (2 planes, FP32)
+  static constexpr int REGION = PIPE > STG ? PIPE : STG;
+  static constexpr int SBO = 8 * ROWB;
+  static constexpr int LAYOUT = 4;                            // SW64
+  static constexpr int TMEM_COLS = 4 * BN;                    // two buffers of (Dr, Di)
+  static constexpr int N_BITS = BN == 128 ? 7 : (BN == 64 ? 6 : 5);
+  static constexpr int C_BITS = 7 + N_BITS;
+  static constexpr int CONV_THREADS = 64;                     // warps 2..3
+  static constexpr int DRAIN_WARPS = 8;                       // warps 4..11
+  static constexpr int HC = BN / 2;                           // columns per drain thread and plane
+  static_assert(NST >= 3, "pipeline");
+};
+
+// Instruction descriptor, kind::tf32: FP32 accumulate, TF32 A and B (format 2), K-major.
+__device__ __forceinline__ uint32_t instr_desc_tf32(int neg_a, int n) {
+  uint32_t d = 0;
+  d |= 1u << 4;                     // D format F32
+  d |= 2u << 7;                     // A format TF32
+  d |= 2u << 10;                    // B format TF32
+  d |= uint32_t(neg_a) << 13;       // negate A
+  d |= uint32_t(n >> 3) << 17;      // N
+  d |= uint32_t(TC_BM >> 4) << 24;  // M
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 5-D tiled TMA load (coordinates innermost first) completing on an mbarrier.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// Round an FP32 bit pattern to the nearest TF32 value (ties away from zero; finite inputs).
+__device__ __forceinline__ uint32_t tf32_round_bits(uint32_t x) { return (x + 0x1000u) & 0xFFFFE000u; }
+
+// Sixteen or thirty-two consecutive TMEM columns of this warp's lanes, added to acc.
+template <int CH>
+__device__ __forceinline__ void tmem_add(uint32_t taddr, float* acc) {
+  float v[CH];
+  tmem_ldn<CH>(taddr, v);
+#pragma unroll
+  for (int i = 0; i < CH; ++i) acc[i] += v[i];
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TF32_THREADS, 1) k_tc_tma_tf32(const __grid_constant__ TcParams p) {
+  using S = Tf32Shape<BN>;
+  constexpr int NST = S::NST;
+  constexpr int HC = S::HC;
+  constexpr int CH = HC >= 32 ? 32 : 16;
+  constexpr int CT = TC_BM * BN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::REGION);        // [2^(C_BITS - runC)]
+  const int nhC = 1 << (S::C_BITS - p.runC);
+  uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);               // [128]
+  uint16_t* TCn = TCm + TC_BM;                                           // [BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(TCn + BN) + 15) & ~uintptr_t(7));
+  uint64_t* full = bars;                 // [NST] TMA loads of a stage have landed
+  uint64_t* conv = bars + NST;           // [NST] the stage is split into hi and lo parts
+  uint64_t* empty = bars + 2 * NST;      // [NST] the MMAs reading the stage have completed
+  uint64_t* accf = bars + 3 * NST;       // [2] a k step's MMAs into TMEM buffer b completed
+  uint64_t* acce = accf + 2;             // [2] TMEM buffer b drained
+  uint64_t* done = acce + 2;             // all MMAs have completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);                  // [12]
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Inst3 I = map_inst(blockIdx.z, p.im);
+  const uint32_t on = blockIdx.x & ((1u << p.n_on) - 1u);
+  const uint32_t om = p.n_on >= 31 ? 0u : (blockIdx.x >> p.n_on);
+  int64_t oA = 0, oB = 0, oC = 0;
+  for (int j = 0; j < p.n_om; ++j)
+    if ((om >> j) & 1u) oA += int64_t(1) << p.om_A[j], oC += int64_t(1) << p.om_C[j];
+  for (int j = 0; j < p.n_on; ++j)
+    if ((on >> j) & 1u) oB += int64_t(1) << p.on_B[j], oC += int64_t(1) << p.on_C[j];
+  constexpr int nb = S::N_BITS;
+  for (int r = tid; r < TC_BM; r += TF32_THREADS) {
+    uint32_t cm = 0;
+    for (int j = 0; j < 7; ++j)
+      if ((r >> j) & 1) cm |= 1u << p.pCm[j];
+    TCm[r] = (uint16_t)stg_swz(cm);
+  }
+  for (int r = tid; r < BN; r += TF32_THREADS) {
+    uint32_t cn = 0;
+    for (int j = 0; j < nb; ++j)
+      if ((r >> j) & 1) cn |= 1u << p.pCn[j];
+    TCn[r] = (uint16_t)stg_swz(cn);
+  }
+  for (int h = tid; h < nhC; h += TF32_THREADS) {
+    uint32_t m = p.maskC;
+    for (int i = 0; i < p.runC; ++i) m &= m - 1;
+    uint32_t r = 0, x = (uint32_t)h;
+    while (m) {
+      const uint32_t low = m & (~m + 1u);
+      if (x & 1u) r |= low;
+      x >>= 1;
+      m &= m - 1;
+    }
+    hiC[h] = r;
+  }
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&conv[s]), S::CONV_THREADS);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), S::DRAIN_WARPS);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // a compiled 32-wide K tile (kt = 5) is loaded as two 16-wide halves
+  const int kt = p.bk == 32 ? 5 : 4;
+  const int halves = kt == 5 ? 2 : 1;
+  const int n_total = 1 << p.n_ok;
+  const int per = n_total / p.splitk;
+  const int it0 = blockIdx.y * per;
+  const int n_iter = per * halves;   // stages
+  const int n_steps = 2 * n_iter;    // 8-wide k steps (TMEM chunks)
+  const uint32_t sbase = smem_u32(smem);
+  bool ok = true;
+  float accR[HC], accI[HC];
+#pragma unroll
+  for (int i = 0; i < HC; ++i) accR[i] = accI[i] = 0.f;
+  const int q = warp & 3, hcol = ((warp - 4) >> 2) * HC;  // drain warps: lane quadrant, first column
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: the hi half of each stage (Ar, Ai, Br, Bi as FP32)
+      int issued = 0;
+      for (int it = 0; it < n_iter; ++it) {
+        const int buf = it % NST;
+        if (it >= NST && !mbar_wait_bounded(smem_u32(&empty[buf]), (uint32_t)((it / NST - 1) & 1), p.status)) {
+          ok = false;
+          break;
+        }
+        const int g = it0 + it / halves, kh = it % halves;
+        int64_t okA = 0, okB = 0;
+        for (int j = 0; j < p.n_ok; ++j)
+          if ((g >> j) & 1) okA += int64_t(1) << p.ok_A[j], okB += int64_t(1) << p.ok_B[j];
+        const int rowA = (int)((oA + okA) >> kt), rowB = (int)((oB + okB) >> kt);
+        const uint32_t st = sbase + buf * S::STAGE;
+        const uint32_t fb = smem_u32(&full[buf]);
+        mbar_arrive_expect_tx(fb, S::HALF);
+        if (kt == 4) {
+          tma_load_4d(st, &p.tmA, 0, rowA, 0, (int)I.a, fb);
+          tma_load_4d(st + S::A_BYTES, &p.tmA, 0, rowA, 1, (int)I.a, fb);
+          tma_load_4d(st + 2 * S::A_BYTES, &p.tmB, 0, rowB, 0, (int)I.b, fb);
+          tma_load_4d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, rowB, 1, (int)I.b, fb);
+        } else {
+          tma_load_5d(st, &p.tmA, 0, kh, rowA, 0, (int)I.a, fb);
+          tma_load_5d(st + S::A_BYTES, &p.tmA, 0, kh, rowA, 1, (int)I.a, fb);
+          tma_load_5d(st + 2 * S::A_BYTES, &p.tmB, 0, kh, rowB, 0, (int)I.b, fb);
+          tma_load_5d(st + 2 * S::A_BYTES + S::B_BYTES, &p.tmB, 0, kh, rowB, 1, (int)I.b, fb);
+        }
+        issued = it + 1;
+      }
+      for (int it = issued - NST > 0 ? issued - NST : 0; it < issued; ++it)
+        if (!mbar_wait_bounded(smem_u32(&full[it % NST]), (uint32_t)((it / NST) & 1), p.status)) ok = false;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: k step u accumulates from zero into TMEM buffer u & 1
+      const uint32_t id_pos = instr_desc_tf32(0, BN), id_neg = instr_desc_tf32(1, BN);
+      for (int it = 0; it < n_iter && ok; ++it) {
+        const int buf = it % NST;
+        if (!mbar_wait_bounded(smem_u32(&conv[buf]), (uint32_t)((it / NST) & 1), p.status)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t st = sbase + buf * S::STAGE;
+        for (int j = 0; j < 2; ++j) {
+          const int u = 2 * it + j, b = u & 1;
+          if (u >= 2 && !mbar_wait_bounded(smem_u32(&acce[b]), (uint32_t)((u / 2 - 1) & 1), p.status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t dr = tmem + b * 2 * BN, di = dr + BN;
+          // 8 TF32 entries = 32 bytes of each row per MMA
+          const uint32_t o = j * 32;
+          const uint64_t arh = kmajor_desc(st + o, S::SBO, S::LAYOUT);
+          const uint64_t aih = kmajor_desc(st + S::A_BYTES + o, S::SBO, S::LAYOUT);
+          const uint64_t brh = kmajor_desc(st + 2 * S::A_BYTES + o, S::SBO, S::LAYOUT);
+          const uint64_t bih = kmajor_desc(st + 2 * S::A_BYTES + S::B_BYTES + o, S::SBO, S::LAYOUT);
+          const uint64_t arl = kmajor_desc(st + S::HALF + o, S::SBO, S::LAYOUT);
+          const uint64_t ail = kmajor_desc(st + S::HALF + S::A_BYTES + o, S::SBO, S::LAYOUT);
+          const uint64_t brl = kmajor_desc(st + S::HALF + 2 * S::A_BYTES + o, S::SBO, S::LAYOUT);
+          const uint64_t bil = kmajor_desc(st + S::HALF + 2 * S::A_BYTES + S::B_BYTES + o, S::SBO, S::LAYOUT);
+          // Dr = Ar Br - Ai Bi; the small cross terms first
+          mma_tf32(dr, arh, brl, id_pos, 0u);
+          mma_tf32(dr, arl, brh, id_pos, 1u);
+          mma_tf32(dr, aih, bil, id_neg, 1u);
+          mma_tf32(dr, ail, bih, id_neg, 1u);
+          mma_tf32(dr, arh, brh, id_pos, 1u);
+          mma_tf32(dr, aih, bih, id_neg, 1u);
+          // Di = Ar Bi + Ai Br
+          mma_tf32(di, arh, bil, id_pos, 0u);
+          mma_tf32(di, arl, bih, id_pos, 1u);
+          mma_tf32(di, aih, brl, id_pos, 1u);
+          mma_tf32(di, ail, brh, id_pos, 1u);
+          mma_tf32(di, arh, bih, id_pos, 1u);
+          mma_tf32(di, aih, brh, id_pos, 1u);
+          mma_commit(smem_u32(&accf[b]));
+        }
+        mma_commit(smem_u32(&empty[buf]));
+      }
+      mma_commit(smem_u32(done));
+    }
+  } else if (warp < 4) {
+    // converters: hi = tf32(x) in place, lo = tf32(x - hi) in the stage's second half
+    const int ct = tid - 64;
+    for (int it = 0; it < n_iter; ++it) {
+      const int buf = it % NST;
+      if (!mbar_wait_bounded(smem_u32(&full[buf]), (uint32_t)((it / NST) & 1), p.status)) {
+        ok = false;
+        break;
+      }
+      uint4* hi = reinterpret_cast<uint4*>(smem + buf * S::STAGE);
+      uint4* lo = reinterpret_cast<uint4*>(smem + buf * S::STAGE + S::HALF);
+#pragma unroll 4
+      for (int v = ct; v < S::HALF / 16; v += S::CONV_THREADS) {
+        const uint4 x = hi[v];
+        uint4 h, l;
+        h.x = tf32_round_bits(x.x);
+        h.y = tf32_round_bits(x.y);
+        h.z = tf32_round_bits(x.z);
+        h.w = tf32_round_bits(x.w);
+        l.x = tf32_round_bits(__float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x)));
+        l.y = tf32_round_bits(__float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y)));
+        l.z = tf32_round_bits(__float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z)));
+        l.w = tf32_round_bits(__float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w)));
+        hi[v] = h;
+        lo[v] = l;
+      }
+      fence_async_shared();  // the tensor core reads these writes through the async proxy
+      mbar_arrive(smem_u32(&conv[buf]));
+    }
+  } else {
+    // drain: add every k step's chunk to the register sums (round to nearest)
+    const uint32_t lane_addr = uint32_t(q * 32) << 16;
+    for (int u = 0; u < n_steps; ++u) {
+      const int b = u & 1;
+      bool got = true;
+      if (lane == 0) got = mbar_wait_bounded(smem_u32(&accf[b]), (uint32_t)((u / 2) & 1), p.status);
+      got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+      if (!got) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t dr = tmem + lane_addr + b * 2 * BN + hcol;
+#pragma unroll
+      for (int c = 0; c < HC; c += CH) {
+        tmem_add<CH>(dr + c, accR + c);
+        tmem_add<CH>(dr + BN + c, accI + c);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
+    }
+  }
+  // all MMAs done (waited for even after a timeout, so TMEM is never freed under them)
+  const bool fin = mbar_wait_bounded(smem_u32(done), 0u, p.status);
+  ok = ok && fin;
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  ok = __syncthreads_and(ok);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
+  if (!ok) return;
+  // epilogue from the drain warps' registers (FP32 storage)
+  const bool drain = warp >= 4;
+  const int row = q * 32 + lane;
+  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
+  const uint32_t lowmask = (1u << p.runC) - 1u;
+  if (p.splitk > 1) {
+    if (drain) {
+      float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
+      const uint32_t rm = TCm[row];
+#pragma unroll
+      for (int j = 0; j < HC; ++j) {
+        const uint32_t t = stg_swz(rm ^ TCn[hcol + j]);
+        part[hiC[t >> p.runC] + (t & lowmask)] = make_float2(accR[j], accI[j]);
+      }
+    }
+    return;
+  }
+  int sh = 0;
+  {
+    const float a = p.maxabs[sa + p.slotA], b = p.maxabs[sbb + p.slotB];
+    if (a > 0.f && b > 0.f) {
+      int ea, eb;
+      frexpf(a, &ea);
+      frexpf(b, &eb);
+      sh = ea + eb + p.nK + 1 - 15;
+    }
+  }
+  const float scale = ldexpf(1.f, -sh);
+  float* stg = reinterpret_cast<float*>(smem);  // [2][CT]: the pipeline's buffers are free now
+  float* Cre = reinterpret_cast<float*>(p.C) + I.c * p.strideC + oC;
+  float mx = 0.f;
+  if (drain) {
+    const uint32_t rm = TCm[row];
+#pragma unroll
+    for (int j = 0; j < HC; ++j) mx = fmaxf(mx, fmaxf(fabsf(accR[j]), fabsf(accI[j])));
+    if (p.direct) {
+      // columns 8g..8g+7 of a row are 8 consecutive entries of C
+#pragma unroll
+      for (int g = 0; g < HC / 8; ++g) {
+        const uint32_t t = stg_swz(rm ^ TCn[hcol + 8 * g]);
+        const uint32_t off = hiC[t >> p.runC] + (t & lowmask);
+        float4 r0, r1, i0, i1;
+        r0 = make_float4(accR[8 * g] * scale, accR[8 * g + 1] * scale, accR[8 * g + 2] * scale, accR[8 * g + 3] * scale);
+        r1 = make_float4(accR[8 * g + 4] * scale, accR[8 * g + 5] * scale, accR[8 * g + 6] * scale, accR[8 * g + 7] * scale);
+        i0 = make_float4(accI[8 * g] * scale, accI[8 * g + 1] * scale, accI[8 * g + 2] * scale, accI[8 * g + 3] * scale);
+        i1 = make_float4(accI[8 * g + 4] * scale, accI[8 * g + 5] * scale, accI[8 * g + 6] * scale, accI[8 * g + 7] * scale);
+        *reinterpret_cast<float4*>(Cre + off) = r0;
+        *reinterpret_cast<float4*>(Cre + off + 4) = r1;
+        *reinterpret_cast<float4*>(Cre + p.planeC + off) = i0;
+        *reinterpret_cast<float4*>(Cre + p.planeC + off + 4) = i1;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < HC; ++j) {
+        const uint32_t idx = rm ^ TCn[hcol + j];  // swizzled staging index
+        stg[idx] = accR[j] * scale;
+        stg[CT + idx] = accI[j] * scale;
+      }
+    }
+  }
+  mx *= scale;
+  __syncthreads();
+  if (!p.direct) {
+    for (int t = tid * 8; t < CT; t += TF32_THREADS * 8) {
+      const uint32_t off = hiC[t >> p.runC] + (uint32_t(t) & lowmask);
+      const uint32_t so = stg_swz(t);
+      *reinterpret_cast<uint4*>(Cre + off) = *reinterpret_cast<const uint4*>(stg + so);
+      *reinterpret_cast<uint4*>(Cre + off + 4) = *reinterpret_cast<const uint4*>(stg + so + 4);
+      *reinterpret_cast<uint4*>(Cre + p.planeC + off) = *reinterpret_cast<const uint4*>(stg + CT + so);
+      *reinterpret_cast<uint4*>(Cre + p.planeC + off + 4) = *reinterpret_cast<const uint4*>(stg + CT + so + 4);
+    }
+  }
+  // block max -> tensor max
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int w = 0; w < TF32_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+    atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+  }
 }
 
 // Persistent variant of k_tc_tma for short K loops (at most eight K tiles per output tile)
@@ -1436,7 +1860,33 @@ cudaError_t launch_tma_bn_bk(const TcParams& p, dim3 grid, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+template <int BN>
+size_t tf32_smem_bytes(int runC) {
+  using S = Tf32Shape<BN>;
+  return 1024 + S::REGION + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 + (3 * S::NST + 5) * 8 + 16 +
+         16 * 4 + 64;
+}
+
+template <int BN>
+cudaError_t launch_tf32_bn(const TcParams& p, dim3 grid, cudaStream_t s) {
+  const size_t smem = tf32_smem_bytes<BN>(p.runC);
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_tc_tma_tf32<BN>), smem);
+  if (e != cudaSuccess) return e;
+  k_tc_tma_tf32<BN><<<grid, TF32_THREADS, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// complex64: the 3xTF32 kernel (one CTA per tile; widths 32, 64 and 128)
+cudaError_t launch_tc_tma_tf32(const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (p.persistent) return cudaErrorInvalidValue;
+  if (p.bn == 128) return launch_tf32_bn<128>(p, grid, s);
+  if (p.bn == 64) return launch_tf32_bn<64>(p, grid, s);
+  if (p.bn == 32) return launch_tf32_bn<32>(p, grid, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_tc_tma(int precision, const TcParams& p, dim3 grid, cudaStream_t s) {
+  if (precision == 0) return launch_tc_tma_tf32(p, grid, s);
   if (precision == 1) return launch_tma_bn_bk<__half>(p, grid, s);
   if (precision == 2) return launch_tma_bn_bk<__nv_bfloat16>(p, grid, s);
   return cudaErrorInvalidValue;

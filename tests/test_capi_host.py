@@ -113,10 +113,10 @@ def _subtree_leaves(d, node):
 @pytest.mark.parametrize("rows,cols,cycles,cap", [(4, 6, 12, 16), (4, 5, 10, 12), (3, 6, 8, 10)])
 def test_split_plan_slices_a_separator(rows, cols, cycles, cap):
     """mode "split": the root joins two stems, one per side of a qubit bisection.  Every
-    sliced index joins leaves of different sides, and every index joining the sides is
-    sliced unless the cap left room for it (then the root contracts it).  Each side's leaves
-    act on its own qubits (the straddling 2-qubit leaves excepted), and both sides stay
-    within the cap."""
+    index joining the sides is sliced unless the cap left room for it (then the root
+    contracts it); indices inside a side are sliced only when that side alone exceeds the
+    cap.  Each side's leaves act on its own qubits (the straddling 2-qubit leaves excepted),
+    and every intermediate stays within the cap."""
     c = grid_circuit(rows, cols, cycles, seed=1)
     p = T.Plan.greedy(c, seed=3, trials=4, log2_cap=cap, mode="split")
     d, info = p.describe(), p.info()
@@ -134,9 +134,11 @@ def test_split_plan_slices_a_separator(rows, cols, cycles, cap):
             owners.setdefault(e, []).append(i)
     crossing = {e for e, ow in owners.items() if len(ow) == 2 and side[ow[0]] != side[ow[1]]}
     sliced = set(d["sliced"])
-    assert sliced <= crossing
     released = crossing - sliced
     assert released == (sets[root_a] & sets[root_b]) - sliced
+    # an index inside a side is sliced only if some intermediate exceeds the cap without it
+    for e in sliced - crossing:
+        assert max(len(x - (sliced - {e})) for x in sets) > cap
     # the qubits each side acts on apart from straddling leaves are disjoint
     qubits = [set(), set()]
     for i in range(L):

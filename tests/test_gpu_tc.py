@@ -241,3 +241,59 @@ def test_persistent_kernels_every_output_against_oracle(ctx, precision, shape, d
     bad = np.flatnonzero(np.abs(got - ref) > bound)
     assert bad.size == 0, (bad[:8], got[bad[:8]], ref[bad[:8]])
     assert metrics.rel_err_norm(got, ref) <= TOL[precision]
+
+
+# complex64 on the tensor cores (3xTF32): every FP32 operand entry is split into a TF32 high
+# part and a TF32 low part, and each real product is summed from three TF32 products.  Per
+# product the dropped low x low term and the rounding of the low parts are each about
+# 2^-22 |a b|; with FP32 accumulation the output error stays near FP32's own.  Bars: the
+# complex64 norm-wise 1e-5, and per entry 2^-16 |c| + 2^-16 rms(C) (the largest of the
+# K = 2^4..2^15 coherent sums of 2^-21 |a||b| stays below 2^-21 sqrt(K) rms(C) <= 2^-13.5
+# rms(C) only in the worst case; random signs keep it near 2^-21 rms(C)).
+C64_SHAPES = [(7, 4, 6), (7, 5, 7), (8, 9, 8), (9, 12, 7), (10, 4, 9), (7, 14, 7), (9, 8, 5), (7, 4, 5),
+              (12, 10, 5), (9, 8, 10), (8, 15, 6)]
+
+
+@pytest.mark.parametrize("shape", C64_SHAPES)
+def test_tma_contract_complex64_tf32(ctx, shape):
+    a, la, b, lb, lc = tma_case(*shape, seed=17 * sum(shape) + shape[1], direct=shape[2] % 2 == 0)
+    ta = torch.from_numpy(np.concatenate([a.real, a.imag])).to(torch.float32).cuda()
+    tb = torch.from_numpy(np.concatenate([b.real, b.imag])).to(torch.float32).cuda()
+    aq = ta.cpu().double().numpy()
+    bq = tb.cpu().double().numpy()
+    aq = aq[: a.size] + 1j * aq[a.size:]
+    bq = bq[: b.size] + 1j * bq[b.size:]
+    tc = torch.empty(2 << len(lc), dtype=torch.float32, device="cuda")
+    e = ctx.contract("c64", ta, la, tb, lb, tc, lc)
+    torch.cuda.synchronize()
+    assert int(ctx.profile_read(cap=1)["kind"][0]) == 4  # the TMA tensor-core kernel ran
+    cc = tc.double().cpu().numpy()
+    n = 1 << len(lc)
+    got = (cc[:n] + 1j * cc[n:]) * 2.0 ** e
+    if n <= 1 << 18:
+        idx = np.arange(n)
+        ref = pairwise.contract(aq, la, bq, lb, lc)
+    else:
+        idx = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(3).integers(0, n, 2046)]))
+        ref = pairwise.contract_at(aq, la, bq, lb, lc, idx)
+    got = got[idx]
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert metrics.rel_err_norm(got, ref) <= 1e-5
+    assert np.all(np.abs(got - ref) <= 2.0 ** -16 * (np.abs(ref) + rms))
+
+
+@pytest.mark.parametrize("no_tc64", [False, True])
+def test_complex64_plan_on_tensor_cores(no_tc64, monkeypatch):
+    # 20-qubit 4x5 grid, 12 cycles, 6 open qubits: the plan's large steps run on the 3xTF32
+    # kernel (or, with TNC_NO_TC64=1, on the SIMT kernels); both meet the complex64 bar
+    if no_tc64:
+        monkeypatch.setenv("TNC_NO_TC64", "1")
+    ctx64 = T.Context(0)
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=16, log2_cap=20)
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    got = ctx64.amplitudes(p, fixed[None, :], "c64", profile=True)[0]
+    kinds = set(int(k) for k in ctx64.profile_read()["kind"])
+    assert (4 in kinds) != no_tc64
+    assert metrics.rel_err_norm(got, ref) <= 1e-5
