@@ -96,7 +96,7 @@ def parse():
     ap.add_argument("--s60-slices", type=int, default=256, help="seeded slice sample of the s60 workload")
     ap.add_argument("--s60-trials", type=int, default=4, help="planner trials (qubit bisections) of the s60 workload")
     ap.add_argument("--s60-c64", type=int, default=2, help="slices of the sample also run alone in complex64")
-    ap.add_argument("--s60-sum-c64", type=int, default=8,
+    ap.add_argument("--s60-sum-c64", type=int, default=256,
                     help="the first slices of the sample summed in complex-half and complex64")
     ap.add_argument("--sw-shapes", default="", help="log2 M,K,N triples 'm,k,n;m,k,n' (default: a fixed set)")
     ap.add_argument("--precision", default="chalf", choices=["chalf", "cbf16", "c64"])
@@ -550,6 +550,7 @@ def run_sweep(args):
     dt = {"chalf": torch.float16, "cbf16": torch.bfloat16, "c64": torch.float32}
     pts = [tuple(int(x) for x in s.split(",")) for s in args.sw_shapes.split(";")] if args.sw_shapes else SW_POINTS
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    tf32 = measure_tf32_peak()
     out = []
     for (m, k, n) in pts:
         gepdot = m + n <= 10 and k >= 12
@@ -559,7 +560,7 @@ def run_sweep(args):
             la, lb, lc = sweep_labels(m, k, n, layout, seed)
             for prec in ("chalf", "cbf16", "c64"):
                 if prec == "c64" and (m + k + n > 40 or max(m + k, k + n, m + n) > 28):
-                    continue  # FP32 SIMT path: keep each point under a few seconds
+                    continue  # keep each complex64 point (SIMT on random layouts) under a few seconds
                 if prec == "cbf16" and layout == "random":
                     continue  # same kernels and rates as chalf
                 g = torch.Generator(device="cuda")
@@ -578,7 +579,7 @@ def run_sweep(args):
                     times.append(float(pr["ms"][0]))
                 ms = statistics.median(times)
                 kind, fl, by = int(pr["kind"][0]), float(pr["flops"][0]), float(pr["bytes"][0])
-                r = roofline_of(kind, fl, by, ms, peaks)
+                r = roofline_tf32(kind, fl, by, ms, tf32, peaks) if prec == "c64" else roofline_of(kind, fl, by, ms, peaks)
                 out.append({"m": m, "k": k, "n": n, "layout": layout, "precision": prec, "kernel_kind": kind,
                             "launches": int(pr["launches"][0]), "ms": ms, "tflops": fl / ms / 1e9,
                             "gbs": by / ms / 1e6, "bound": r["bound"], "frac": r["frac"]})
@@ -590,7 +591,9 @@ def run_sweep(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": "sw: single pairwise contractions, log2 (M,K,N) points, complex normal(0, 1/sqrt(K))",
                        "value_point": [head["m"], head["k"], head["n"], head["layout"], head["precision"]],
-                       "l2": "256 MiB flush before every timed call", "timing": "contraction kernels only (CUDA events)"},
+                       "l2": "256 MiB flush before every timed call", "timing": "contraction kernels only (CUDA events)",
+                       "tf32_peak_tflops_measured": tf32,
+                       "c64_frac": "3xTF32 tensor-core points: 3 x 8MNK / time over the measured TF32 peak"},
             "points": out}
     print(json.dumps(line))
 
