@@ -684,6 +684,8 @@ def run_s60(args):
                        "plan_mode": "split", "plan_trials": args.s60_trials, "plan_seconds": plan_s,
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"],
                        "log2_total_cmacs": info["log2_total_flops"],
+                       "log2_executed_cmacs_all_slices_with_reuse": info["log2_executed_flops"],
+                       "log2_executed_cmacs_all_slices_with_reuse_and_merging": info["log2_executed_flops_merged"],
                        "plan_max_log2_size": info["max_log2_size"],
                        "plan_model_seconds_per_slice": info["model_seconds_per_slice"],
                        "complex_tflops": 8 * 2 ** info["log2_flops_per_slice"] * value / 1e12,

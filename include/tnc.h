@@ -162,6 +162,9 @@ typedef struct {
                                /* divided by 2^s (the objective = 1 cost; complex-half) */
   double log2_executed_flops;  /* log2 complex multiply-adds of all 2^s slices of one   */
                                /* bitstring under tree-like reuse (Sec. III-B)          */
+  double log2_executed_flops_merged; /* the same with post-lifetime merging (Sec. III-B; */
+                               /* tnc_exec_opts.reserved[1]): each sliced index summed    */
+                               /* right after the step that contracts it                  */
 } tnc_plan_info;
 tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info);
 
@@ -228,7 +231,15 @@ typedef struct {
   int32_t reserved[3];   /* reserved[0], tnc_adjoint only: device memory (MiB) per instance
                             for the forward intermediates kept for the backward pass; above
                             it the largest are recomputed from their children when the
-                            backward pass reaches them (0 = keep all).  Others: 0. */
+                            backward pass reaches them (0 = keep all).
+                            reserved[1], tnc_amplitudes only: 1 = post-lifetime merging
+                            (Sec. III-B, (sum_i A_i) B for sum_i A_i B): on a call over every
+                            slice with tree-like reuse, the result of the step that contracts a
+                            sliced index is summed over that index's two values right away,
+                            so every later step runs half as often for it.  The sums
+                            associate differently from the unmerged call (not bit-identical;
+                            the same amplitudes within rounding).  Other calls ignore it.
+                            Others: 0. */
 } tnc_exec_opts;
 
 /* Amplitudes of a batch (Sec. I; the multi-amplitude batch of Sec. II-C), summed over

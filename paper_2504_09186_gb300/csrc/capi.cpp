@@ -268,6 +268,7 @@ tnc_status tnc_plan_get_info(tnc_plan p, tnc_plan_info* info) {
     info->narrow_max = P.narrow_max;
     info->model_seconds_per_slice = P.model_seconds;
     info->log2_executed_flops = P.log2_flops_executed;
+    info->log2_executed_flops_merged = P.log2_flops_executed_merged;
   });
 }
 

@@ -486,6 +486,26 @@ void compile_plan(Plan& plan, bool fuse) {
     plan.steps.push_back(st);
   }
   plan.root = plan.tree.empty() ? 0 : (int)plan.tensors.size() - 1;
+  // executed complex multiply-adds of all slices of one row under tree-like reuse with
+  // post-lifetime merging (Sec. III-B), the executor's rule: the step whose two operands both
+  // depend on a sliced index sums its result over that index (except the root step), and
+  // later steps no longer depend on it
+  {
+    std::vector<uint64_t> md(plan.tensors.size(), 0);
+    for (size_t i = 0; i < plan.tensors.size(); ++i) md[i] = plan.tensors[i].dep;
+    double ex = 0;
+    for (size_t s = 0; s < plan.steps.size(); ++s) {
+      const Step& st = plan.steps[s];
+      const uint64_t full = md[st.a] | md[st.b];
+      std::vector<int> u = plan.tensors[st.a].labels;
+      for (int x : plan.tensors[st.b].labels)
+        if (!contains(u, x)) u.push_back(x);
+      ex += std::ldexp(1.0, (int)u.size() + __builtin_popcountll(full));
+      const uint64_t m = s + 1 < plan.steps.size() ? (md[st.a] & md[st.b]) : 0;
+      md[st.c] = full & ~m;
+    }
+    plan.log2_flops_executed_merged = plan.steps.empty() ? 0.0 : std::log2(ex);
+  }
   // classify + tiles
   for (size_t s = 0; s < plan.steps.size(); ++s) {
     Step& st = plan.steps[s];

@@ -31,7 +31,10 @@ cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leav
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
-                              InstMap rm, cudaStream_t s);
+                              InstMap rm, cudaStream_t s, uint32_t merged = 0);
+cudaError_t launch_merge(int precision, void* arena, int64_t inst_stride, int64_t off, int64_t plane, int32_t* exps,
+                         float* maxabs, int n_slots, int slot, const double2* leaf_r, int n_leaves, int lu, int lv,
+                         int bit, InstMap im, int64_t nz, cudaStream_t s);
 cudaError_t launch_inst_scale(const double2* leaf_r, int n_leaves, int64_t n_inst, double2* c, cudaStream_t s);
 cudaError_t launch_maxabs(int precision, const void* x, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adj_root_init(float* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
@@ -109,6 +112,20 @@ struct StepLaunch {
   double flops = 0, bytes = 0;  // algorithmic, per instance (real flops 8MNK; bytes read + written)
   int plan_step = -1;           // the plan step a tensor-core launch runs
   bool stream = false;          // a SIMT step that may stream its tiles (see make_stream)
+  // post-lifetime merges run after the step (tree-like reuse only): sum the result over the
+  // two values of each sliced index whose edge this step contracts (see k_merge)
+  struct MergeOp {
+    int bit, lu, lv, slot;
+    int64_t off, plane;
+    InstMap im;  // launch index -> the t = 0 instance (the result's dependence without t)
+    void* arena;
+    int64_t inst_stride;
+    int32_t* exps;
+    float* maxabs;
+    int n_slots, n_leaves;
+    const double2* leaf_r;
+  };
+  std::vector<MergeOp> merges;
 };
 
 // Tensor-core launch of a step whose tile satisfies choose_tc_tile's rules.  la / lb are the
@@ -512,6 +529,8 @@ struct DeviceProgram {
   DevBuf leaf_r, inst_c;  // per (instance, leaf) rounding scale and per-instance product
   InstMap root_map{-1, 0, 0, 0};  // instance holding each slice's root (tree-like reuse)
   bool reuse_ok = false;          // the step maps above are set (waves of whole rows)
+  bool merge = false;             // post-lifetime merging requested for this program
+  uint32_t merged_mask = 0;       // slice bits summed by merges (the root sum skips them)
   std::vector<StepLaunch> steps;
   int root = 0;
   int64_t root_off = 0, root_plane = 1;
@@ -946,9 +965,10 @@ static void make_schedule(const Plan& P, DeviceProgram* prog) {
 }
 
 static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan_s* plan, int precision, int W,
-                                                    bool fuse) {
+                                                    bool fuse, bool merge = false) {
   const Plan& P = plan->p;
   auto prog = std::make_shared<DeviceProgram>();
+  prog->merge = merge;
   prog->device = ctx->device;
   prog->precision = precision;
   prog->W = W;
@@ -1071,20 +1091,63 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
   // maps only when it covers every slice (see tnc_amplitudes).
   {
     const bool reuse = reuse_shape && chain_links.empty() && prog->steps.size() == P.steps.size();
+    // post-lifetime merging (Sec. III-B): the step whose two operands both depend on sliced
+    // index t contracts t's edge; its result is summed over t right after it (not at the
+    // root step, where the root sum does the same), and every later tensor depends on t no
+    // longer.  mdep = the dependence masks with merged indices removed.
+    std::vector<uint32_t> mdep(P.tensors.size(), 0);
+    for (size_t i = 0; i < P.tensors.size(); ++i) mdep[i] = (uint32_t)P.tensors[i].dep;
+    std::vector<uint32_t> full(P.steps.size(), 0), mbits(P.steps.size(), 0);
+    for (size_t si = 0; si < P.steps.size(); ++si) {
+      const Step& st = P.steps[si];
+      full[si] = mdep[st.a] | mdep[st.b];
+      if (merge && reuse && si + 1 < P.steps.size()) mbits[si] = mdep[st.a] & mdep[st.b];
+      mdep[st.c] = full[si] & ~mbits[si];
+    }
+    // the two leaves holding each sliced index (its leaf-rounding scales enter the merge)
+    std::vector<std::vector<int>> holders(P.sliced.size());
+    for (size_t i = 0; i < P.leaf_fix.size(); ++i)
+      for (const auto& lf : P.leaf_fix[i])
+        if (lf.kind == 0 && lf.index < (int)holders.size()) holders[lf.index].push_back((int)i);
+    prog->merged_mask = 0;
     for (size_t si = 0; si < prog->steps.size(); ++si) {
       StepLaunch& L = prog->steps[si];
+      L.merges.clear();
       InstMap m{-1, 0, 0, 0};
       if (reuse) {
         const Step& st = P.steps[si];
         const bool tcs = (L.kind == K_TC || L.kind == K_TMA) && st.tc_swap;
         const int ta = tcs ? st.b : st.a, tb = tcs ? st.a : st.b;
-        m = InstMap{sbits, (uint32_t)P.tensors[st.c].dep, (uint32_t)P.tensors[ta].dep, (uint32_t)P.tensors[tb].dep};
+        m = InstMap{sbits, full[si], mdep[ta], mdep[tb]};
+        uint32_t left = full[si];
+        for (int t = 0; t < sbits; ++t) {
+          if (!((mbits[si] >> t) & 1u)) continue;
+          if (holders[t].size() != 2) fail(TNC_E_PLAN, "merge: a sliced index must sit in two leaves");
+          left &= ~(1u << t);
+          StepLaunch::MergeOp op;
+          op.bit = t;
+          op.lu = holders[t][0];
+          op.lv = holders[t][1];
+          op.slot = st.c;
+          op.off = OFF(st.c);
+          op.plane = int64_t(1) << P.tensors[st.c].labels.size();
+          op.im = InstMap{sbits, left, 0, 0};
+          op.arena = prog->arena.p;
+          op.inst_stride = prog->inst_stride;
+          op.exps = prog->exps.as<int32_t>();
+          op.maxabs = prog->maxabs.as<float>();
+          op.n_slots = prog->n_slots;
+          op.n_leaves = prog->n_leaves;
+          op.leaf_r = prog->leaf_r.as<double2>();
+          L.merges.push_back(op);
+          prog->merged_mask |= 1u << t;
+        }
       }
       L.p.im = m;
       L.tp.im = m;
     }
     prog->reuse_ok = reuse;
-    prog->root_map = reuse ? InstMap{sbits, (uint32_t)P.tensors[P.root].dep, 0, 0} : InstMap{-1, 0, 0, 0};
+    prog->root_map = reuse ? InstMap{sbits, mdep[P.root], 0, 0} : InstMap{-1, 0, 0, 0};
   }
   // root
   prog->root = P.root;
@@ -1164,10 +1227,14 @@ static void run_step(int precision, const StepLaunch& L0, int64_t n_inst, cudaSt
     }
     else CUDA_OK(launch_tc_gemm(precision, L.tp, L.grid, s));
     if (L.tp.splitk > 1) CUDA_OK(launch_splitk_reduce(precision, L.p, nz, s));
-    return;
+  } else {
+    CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
+    if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, nz, s));
   }
-  CUDA_OK(launch_generic(precision, L.rm, L.rn, L.p, L.grid, L.smem, s));
-  if (L.kind == K_SPLITK) CUDA_OK(launch_splitk_reduce(precision, L.p, nz, s));
+  if (reuse)
+    for (const auto& m : L.merges)
+      CUDA_OK(launch_merge(precision, m.arena, m.inst_stride, m.off, m.plane, m.exps, m.maxabs, m.n_slots, m.slot,
+                           m.leaf_r, m.n_leaves, m.lu, m.lv, m.bit, m.im, launch_count(m.im, n_inst), s));
 }
 
 }  // namespace tnc
@@ -1294,8 +1361,9 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
     }
     W = std::min<int64_t>({W, n_inst, 65535});
     const bool fuse = opts->fuse != 0;
+    const bool merge = opts->reserved[1] != 0;
     const std::string key = std::to_string(ctx->id) + "/" + std::to_string(precision) + "/" + std::to_string(W) + "/" +
-                            std::to_string(fuse ? 1 : 0);
+                            std::to_string(fuse ? 1 : 0) + "/" + std::to_string(merge ? 1 : 0);
     auto it = plan->programs.find(key);
     std::shared_ptr<DeviceProgram> prog;
     if (it == plan->programs.end()) {
@@ -1304,7 +1372,7 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
         if (jt->first.rfind(std::to_string(ctx->id) + "/", 0) == 0) jt = plan->programs.erase(jt);
         else ++jt;
       }
-      prog = build_program(ctx, plan, precision, (int)W, fuse);
+      prog = build_program(ctx, plan, precision, (int)W, fuse, merge);
       plan->programs[key] = prog;
     } else {
       prog = it->second;
@@ -1429,7 +1497,7 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
                                 prog->open_pos.as<int8_t>(), prog->n_open, ctx->segs.as<RootSeg>() + wave_segs[w].first,
                                 wave_segs[w].second, prog->exps.as<int32_t>(), prog->n_slots, prog->root,
                                 ctx->acc.as<double2>(), prog->inst_c.as<double2>(),
-                                reuse ? prog->root_map : InstMap{-1, 0, 0, 0}, s));
+                                reuse ? prog->root_map : InstMap{-1, 0, 0, 0}, s, reuse ? prog->merged_mask : 0u));
       if (capture) {
         cudaGraph_t g = nullptr;
         CUDA_OK(cudaStreamEndCapture(s, &g));

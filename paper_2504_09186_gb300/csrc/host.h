@@ -185,6 +185,7 @@ struct Plan {
   int root = -1;
   double log2_flops_slice = 0, log2_flops_total = 0, overhead = 1;
   double log2_flops_executed = 0;  // all slices of one bitstring row under tree-like reuse
+  double log2_flops_executed_merged = 0;  // ... with post-lifetime merging (computed by compile_plan)
   double model_seconds = 0;  // modeled GB300 time of one slice (step_model_seconds summed)
   int max_log2 = 0;
   int64_t arena_elems = 0;                 // per instance, in scalars, unfused program

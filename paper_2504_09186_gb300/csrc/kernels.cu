@@ -671,7 +671,7 @@ template <typename T>
 __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                              const int8_t* __restrict__ open_pos, int n_open, const RootSeg* __restrict__ segs,
                              const int32_t* __restrict__ exps, int n_slots, int root_slot, double2* acc,
-                             const double2* __restrict__ cfac, InstMap rm) {
+                             const double2* __restrict__ cfac, InstMap rm, uint32_t merged) {
   const int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n_out = int64_t(1) << n_open;
   if (o >= n_out) return;
@@ -683,6 +683,9 @@ __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, i
   double2* a = acc + int64_t(s.row) * n_out + o;
   double re = a->x, im = a->y;
   for (int i = s.begin; i < s.end; ++i) {
+    // slices whose merged indices (post-lifetime merging) are not all 0 are already summed
+    // into the slice with those indices 0
+    if (rm.s >= 0 && (uint32_t(i) & merged)) continue;
     // the root of a slice is stored at the instance that keeps only the slice bits it
     // depends on (tree-like reuse); the leaf-rounding scale is per instance
     const int64_t ir = rm.s < 0 ? int64_t(i) : ((int64_t(i) >> rm.s << rm.s) | (int64_t(i) & int64_t(rm.dep_c)));
@@ -700,6 +703,89 @@ __global__ void k_root_accum(const T* __restrict__ arena, int64_t inst_stride, i
   }
   a->x = re;
   a->y = im;
+}
+
+// Post-lifetime merging (Sec. III-B: (sum_i A_i) B in place of sum_i A_i B).  Once the
+// step that contracts sliced index t has run, its result X depends on t only through its
+// values and everything downstream is linear in X, so the two values of t are summed at once
+// and the rest of the tree runs once for both:
+//   X'(t=0) = X(t=0) 2^(E0-E) + f X(t=1) 2^(E1-E),   E = max(E0, E1) + 2,
+// stored in place at the t = 0 instance, exponent E.  f = r_u r_v (t=1) / r_u r_v (t=0) is the
+// ratio of the leaf-rounding scales of the two leaves holding t (the only leaves whose
+// values differ between the two instances), so that the root's per-slice scale of the t = 0
+// slice stays exact for the merged sum.  Launch index y enumerates (row, assignment of the
+// result's other sliced indices) through `im` (dep_c without t).
+__device__ __forceinline__ double2 merge_factor(const double2* leaf_r, int n_leaves, int lu, int lv, int64_t i0,
+                                                int64_t i1) {
+  if (!leaf_r) return make_double2(1.0, 0.0);
+  auto mul = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+  const double2 n = mul(leaf_r[i1 * n_leaves + lu], leaf_r[i1 * n_leaves + lv]);
+  const double2 d = mul(leaf_r[i0 * n_leaves + lu], leaf_r[i0 * n_leaves + lv]);
+  const double dd = d.x * d.x + d.y * d.y;
+  return make_double2((n.x * d.x + n.y * d.y) / dd, (n.y * d.x - n.x * d.y) / dd);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_merge(T* arena, int64_t inst_stride, int64_t off, int64_t plane,
+                                               const int32_t* __restrict__ exps, int n_slots, int slot,
+                                               const double2* __restrict__ leaf_r, int n_leaves, int lu, int lv,
+                                               int bit, InstMap im) {
+  const Inst3 I = map_inst(blockIdx.y, im);
+  const int64_t i0 = I.c, i1 = I.c | (int64_t(1) << bit);
+  const int E0 = exps[i0 * n_slots + slot], E1 = exps[i1 * n_slots + slot];
+  const int E = max(E0, E1) + 2;
+  const float s0 = ldexpf(1.f, E0 - E), s1 = ldexpf(1.f, E1 - E);
+  const double2 f = merge_factor(leaf_r, n_leaves, lu, lv, i0, i1);
+  const float fr = (float)f.x * s1, fi = (float)f.y * s1;
+  T* x0 = arena + i0 * inst_stride + off;
+  const T* x1 = arena + i1 * inst_stride + off;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < plane; j += int64_t(gridDim.x) * blockDim.x) {
+    const float ar = Conv<T>::to_f(x0[j]) * s0, ai = Conv<T>::to_f(x0[plane + j]) * s0;
+    const float br = Conv<T>::to_f(x1[j]), bi = Conv<T>::to_f(x1[plane + j]);
+    x0[j] = Conv<T>::from_f(ar + fr * br - fi * bi);
+    x0[plane + j] = Conv<T>::from_f(ai + fr * bi + fi * br);
+  }
+}
+
+// The merged tensor's exponent and a bound on its stored |re|, |im| (for the next producer's
+// scaling): |x0| s0 + |f| (|re x1| + |im x1|) s1 <= m0 s0 + 2 |f| m1 s1.  Runs after k_merge,
+// which reads the old exponents.
+__global__ void k_merge_meta(int32_t* exps, float* maxabs, int n_slots, int slot, const double2* __restrict__ leaf_r,
+                             int n_leaves, int lu, int lv, int bit, InstMap im, int64_t nz) {
+  const int64_t z = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  const Inst3 I = map_inst(z, im);
+  const int64_t i0 = I.c, i1 = I.c | (int64_t(1) << bit);
+  const int E0 = exps[i0 * n_slots + slot], E1 = exps[i1 * n_slots + slot];
+  const int E = max(E0, E1) + 2;
+  const double2 f = merge_factor(leaf_r, n_leaves, lu, lv, i0, i1);
+  const double af = sqrt(f.x * f.x + f.y * f.y);
+  const double m = maxabs[i0 * n_slots + slot] * ldexp(1.0, E0 - E) + 2.0 * af * maxabs[i1 * n_slots + slot] * ldexp(1.0, E1 - E);
+  maxabs[i0 * n_slots + slot] = (float)(m * (1.0 + 0x1p-8));
+  exps[i0 * n_slots + slot] = E;
+}
+
+cudaError_t launch_merge(int precision, void* arena, int64_t inst_stride, int64_t off, int64_t plane, int32_t* exps,
+                         float* maxabs, int n_slots, int slot, const double2* leaf_r, int n_leaves, int lu, int lv,
+                         int bit, InstMap im, int64_t nz, cudaStream_t s) {
+  if (nz <= 0) return cudaSuccess;
+  const int64_t per = (plane + 255) / 256;
+  const unsigned bx = (unsigned)std::min<int64_t>(per, std::max<int64_t>(1, (4 * 152 + nz - 1) / nz));
+  const dim3 grid(bx, (unsigned)nz, 1);
+  if (precision == 0)
+    k_merge<float><<<grid, 256, 0, s>>>((float*)arena, inst_stride, off, plane, exps, n_slots, slot, leaf_r, n_leaves, lu,
+                                        lv, bit, im);
+  else if (precision == 1)
+    k_merge<__half><<<grid, 256, 0, s>>>((__half*)arena, inst_stride, off, plane, exps, n_slots, slot, leaf_r, n_leaves,
+                                         lu, lv, bit, im);
+  else
+    k_merge<__nv_bfloat16><<<grid, 256, 0, s>>>((__nv_bfloat16*)arena, inst_stride, off, plane, exps, n_slots, slot,
+                                                leaf_r, n_leaves, lu, lv, bit, im);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_merge_meta<<<(unsigned)((nz + 127) / 128), 128, 0, s>>>(exps, maxabs, n_slots, slot, leaf_r, n_leaves, lu, lv, bit,
+                                                             im, nz);
+  return cudaGetLastError();
 }
 
 // Root cotangent of every instance: dL/droot[o] = w[row, o] (holomorphic derivative of
@@ -1031,18 +1117,18 @@ cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leav
 cudaError_t launch_root_accum(int precision, const void* arena, int64_t inst_stride, int64_t root_off, int64_t plane,
                               const int8_t* open_pos, int n_open, const RootSeg* segs, int n_segs,
                               const int32_t* exps, int n_slots, int root_slot, double2* acc, const double2* cfac,
-                              InstMap rm, cudaStream_t s) {
+                              InstMap rm, cudaStream_t s, uint32_t merged) {
   const int64_t n_out = int64_t(1) << n_open;
   dim3 grid((unsigned)((n_out + 255) / 256), (unsigned)n_segs);
   if (precision == 0)
     k_root_accum<float><<<grid, 256, 0, s>>>((const float*)arena, inst_stride, root_off, plane, open_pos, n_open, segs,
-                                             exps, n_slots, root_slot, acc, cfac, rm);
+                                             exps, n_slots, root_slot, acc, cfac, rm, merged);
   else if (precision == 1)
     k_root_accum<__half><<<grid, 256, 0, s>>>((const __half*)arena, inst_stride, root_off, plane, open_pos, n_open,
-                                              segs, exps, n_slots, root_slot, acc, cfac, rm);
+                                              segs, exps, n_slots, root_slot, acc, cfac, rm, merged);
   else
     k_root_accum<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)arena, inst_stride, root_off, plane,
-                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc, cfac, rm);
+                                                     open_pos, n_open, segs, exps, n_slots, root_slot, acc, cfac, rm, merged);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ class tnc_plan_info(C.Structure):
         ("narrow_max", C.c_double),
         ("model_seconds_per_slice", C.c_double),
         ("log2_executed_flops", C.c_double),
+        ("log2_executed_flops_merged", C.c_double),
     ]
 
 
@@ -368,11 +369,15 @@ class Context:
 
     def amplitudes(self, plan: Plan, bitstrings: Optional[np.ndarray], precision: str = "c64",
                    slice_begin: int = 0, slice_count: Optional[int] = None, wave: int = 0, out=None,
-                   stream: int = 0, profile: bool = False, fuse: bool = True, use_graph: bool = False) -> np.ndarray:
+                   stream: int = 0, profile: bool = False, fuse: bool = True, use_graph: bool = False,
+                   merge: bool = False) -> np.ndarray:
         """Amplitudes of every row x every open-qubit assignment, summed over the slices.
 
         `out` may be a host numpy complex128 array or a torch complex128 CUDA tensor of
-        shape (batch, 2^n_open); a new host array is returned when it is None."""
+        shape (batch, 2^n_open); a new host array is returned when it is None.
+        merge: post-lifetime merging (Sec. III-B) on calls that cover every slice with
+        tree-like reuse: each sliced index is summed right after the step that contracts it
+        (tnc_exec_opts.reserved[1] = 1)."""
         lib = load_library()
         info = plan.info()
         if slice_count is None:
@@ -392,6 +397,7 @@ class Context:
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
         opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave,
                              int(use_graph), int(fuse), int(profile))
+        opts.reserved[1] = int(merge)
         _check(lib.tnc_amplitudes(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count,
                                   C.c_void_p(ptr), C.c_void_p(stream)))
         return out

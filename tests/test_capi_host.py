@@ -456,3 +456,44 @@ def test_random_grid_rejects_bad_arguments():
         assert e.value.status == T.TNC_E_INVALID_ARG
     with pytest.raises(KeyError):
         T.random_grid(2, 2, 2, fsim_mode="other")
+
+
+def _merged_executed_recount(d):
+    """Executed complex multiply-adds of all slices of one row under tree-like reuse, with
+    and without post-lifetime merging, recounted from the plan description: a tensor depends
+    on the sliced indices its leaves hold; with merging, the step whose two operands both
+    depend on an index sums its result over it (not at the root step), so later tensors no
+    longer depend on it."""
+    L = len(d["leaves"])
+    sliced = list(d["sliced"])
+    bit = {e: t for t, e in enumerate(sliced)}
+    dep = [frozenset(bit[e] for e in lf["labels"] if e in bit) for lf in d["leaves"]]
+    mdep = list(dep)
+    plain = merged = 0.0
+    n = len(d["tree"])
+    for s_, (a, b) in enumerate(d["tree"]):
+        u = len(set(d["tensors"][a]["labels"]) | set(d["tensors"][b]["labels"]))
+        full_plain = dep[a] | dep[b]
+        plain += 2.0 ** (u + len(full_plain))
+        dep.append(full_plain)
+        full = mdep[a] | mdep[b]
+        merged += 2.0 ** (u + len(full))
+        both = (mdep[a] & mdep[b]) if s_ + 1 < n else frozenset()
+        mdep.append(full - both)
+    return plain, merged
+
+
+def test_post_lifetime_merging_cost_recount():
+    # a 20-qubit plan whose sliced indices die early: merging halves the later steps' runs
+    c = grid_circuit(4, 5, 12, seed=1)
+    _, open_q = subcube_spec(20, 4, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=12, slices_min=8, slices_max=64)
+    info, d = p.info(), p.describe()
+    plain, merged = _merged_executed_recount(d)
+    assert math.isclose(math.log2(plain), info["log2_executed_flops"], rel_tol=1e-12)
+    assert math.isclose(math.log2(merged), info["log2_executed_flops_merged"], rel_tol=1e-12)
+    assert merged <= 0.75 * plain
+    # the 60-qubit split plan: every separator index lives until the root, nothing to merge
+    s60 = T.Plan.greedy(grid_circuit(6, 10, 24, seed=1), open_qubits=[], seed=3, trials=2, log2_cap=32, mode="split")
+    i60 = s60.info()
+    assert math.isclose(i60["log2_executed_flops_merged"], i60["log2_executed_flops"], rel_tol=1e-12)
