@@ -109,6 +109,8 @@ def parse():
     ap.add_argument("--plan", default="greedy", choices=["greedy", "stem"],
                     help="greedy: balanced pairwise order; stem: one tensor absorbs leaves (fused chains)")
     ap.add_argument("--no-fuse", action="store_true", help="run stem absorptions as separate kernels")
+    ap.add_argument("--cluster-chains", action="store_true",
+                    help="stem plan: fused chains of up to 2^15 entries on thread-block clusters")
     return ap.parse_args()
 
 
@@ -291,7 +293,8 @@ def run_ours(args):
     if args.plan_trials > 0:
         w = dict(w, trials=args.plan_trials)
     plan = T.Plan.greedy(circ, open_qubits=open_q, seed=w["plan_seed"], trials=w["trials"], log2_cap=w["cap"],
-                         slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan)
+                         slices_min=w["smin"], slices_max=w["smax"] if args.plan == "greedy" else 64, mode=args.plan,
+                         cluster_chains=args.cluster_chains)
     info = plan.info()
     fuse = not args.no_fuse
     n_slices = 1 << info["n_sliced"]
@@ -426,7 +429,7 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {w['rows']}x{w['cols']} grid RQC, {w['cycles']} cycles, "
                                    f"{n_slices} slices (cap 2^{w['cap']}), {n_out}-amplitude sub-cube per GPU",
                        "precision": args.precision, "slices_per_step": n_slices * world,
-                       "plan": args.plan, "plan_trials": w["trials"], "fused_chains": bool(fuse and info["n_fused"] > 0),
+                       "plan": args.plan, "plan_trials": w["trials"], "fused_chains": bool(fuse and info["n_fused"] > 0), "cluster_chains": bool(args.cluster_chains),
                        "plan_log2_cmacs_per_slice": info["log2_flops_per_slice"], "sliced_indices": info["n_sliced"],
                        "complex_tflops": total_flops / (ms / 1e3) / 1e12,
                        "l2": "256 MiB flush before every timed step; intermediates up to 2^26 entries > L2",

@@ -132,6 +132,10 @@ typedef struct {
                        /* lowers the cost the slicing uses and every intermediate     */
                        /* stays within the cap (Sec. III-C: nest sliced indices'      */
                        /* lifetimes); at most 8 passes                                */
+  int32_t cluster_chains; /* 1: fused chains (Sec. IV) may hold tiles of up to 2^15     */
+                       /* entries, spread over a thread-block cluster of up to 8 CTAs */
+                       /* whose links read peers' shared memory (DSMEM); 0: one CTA, */
+                       /* 2^12 entries                                                */
 } tnc_plan_opts;
 
 /* Greedy contraction order and slicing (Sec. II-A slicing; Sec. III-A, Eq. 1:

@@ -227,10 +227,12 @@ tnc_status tnc_plan_greedy(tnc_network n, const tnc_plan_opts* opts, tnc_plan* o
     o.objective = opts->objective;
     o.slicing = opts->slicing;
     o.branch_exchange = opts->branch_exchange;
+    o.cluster_chains = opts->cluster_chains;
     if (o.mode < 0 || o.mode > 2) fail(TNC_E_INVALID_ARG, "plan mode must be 0 (greedy), 1 (stem) or 2 (qubit split)");
     if (o.objective != 0 && o.objective != 1) fail(TNC_E_INVALID_ARG, "plan objective must be 0 or 1");
     if (o.slicing != 0 && o.slicing != 1) fail(TNC_E_INVALID_ARG, "plan slicing must be 0 (Eq. 1) or 1 (reuse)");
     if (o.branch_exchange != 0 && o.branch_exchange != 1) fail(TNC_E_INVALID_ARG, "branch_exchange must be 0 or 1");
+    if (o.cluster_chains != 0 && o.cluster_chains != 1) fail(TNC_E_INVALID_ARG, "cluster_chains must be 0 or 1");
     auto* p = new tnc_plan_s();
     try {
       plan_greedy(n->n, o, p->p);
@@ -381,6 +383,27 @@ tnc_status tnc_plan_describe(tnc_plan p, char* buf, int64_t cap, int64_t* len) {
     for (size_t i = 0; i < P.tensors.size(); ++i)
       s += (i ? "," : "") + std::string("{\"labels\":") + jlist(P.tensors[i].labels) +
            ",\"offset\":" + std::to_string(P.tensors[i].offset) + "}";
+    // fused chains: their steps, the first operand's on-chip labels and the largest on-chip
+    // tile (log2 entries; above 12 the chain runs on a cluster of 2^(bits - 12) CTAs)
+    s += "],\"chains\":[";
+    for (size_t ci = 0; ci < P.chains.size(); ++ci) {
+      const Chain& ch = P.chains[ci];
+      std::vector<int> I = ch.inner0;
+      size_t mx = I.size();
+      for (int sidx : ch.steps) {
+        const auto& a = P.tensors[P.steps[sidx].a].labels;
+        const auto& b = P.tensors[P.steps[sidx].b].labels;
+        std::vector<int> nI;
+        for (int x : I)
+          if (std::find(b.begin(), b.end(), x) == b.end()) nI.push_back(x);
+        for (int x : b)
+          if (std::find(a.begin(), a.end(), x) == a.end()) nI.push_back(x);
+        I = nI;
+        mx = std::max(mx, I.size());
+      }
+      s += (ci ? "," : "") + std::string("{\"steps\":") + jlist(ch.steps) + ",\"inner0\":" + jlist(ch.inner0) +
+           ",\"tile_bits\":" + std::to_string(mx) + "}";
+    }
     s += "],\"steps\":[";
     for (size_t i = 0; i < P.steps.size(); ++i) {
       const Step& S = P.steps[i];

@@ -549,7 +549,8 @@ void compile_plan(Plan& plan, bool fuse) {
                           std::ldexp(1.0, __builtin_popcountll(plan.tensors[st.c].dep) - (int)plan.sliced.size());
   }
   // fused chains (Sec. IV): follow the big operand through consecutive absorptions of
-  // small tensors (rank <= 6) while the on-chip label set stays within 2^12 entries.  The
+  // small tensors (rank <= 6) while the on-chip label set stays within 2^15 entries (a
+  // tile above 2^12 is spread over a thread-block cluster of up to 8 CTAs).  The
   // first big operand keeps on chip its four lowest positions (contiguous loads) and every
   // label the chain contracts; labels brought in by the small tensors join it; the chain's
   // result must have its three lowest positions on chip (contiguous stores).  A fused
@@ -562,7 +563,10 @@ void compile_plan(Plan& plan, bool fuse) {
       return st.kind == K_GENERIC && !st.tc_ok && plan.tensors[st.b].labels.size() <= 6 &&
              plan.tensors[st.a].labels.size() >= 10;
     };
-    constexpr size_t kInnerMax = 12;
+    // 2^12 entries per CTA (the chain kernel's buffers), times up to 2^3 CTAs per cluster
+    // when the plan allows cluster-cooperative chains
+    constexpr size_t kTileBitsCta = 12;
+    const size_t kInnerMax = kTileBitsCta + (plan.opts.cluster_chains ? 3 : 0);
     for (size_t i = 0; i < plan.steps.size(); ++i) {
       if (plan.step_chain[i] >= 0 || !is_link(i)) continue;
       const std::vector<int>& A0 = plan.tensors[plan.steps[i].a].labels;
@@ -610,7 +614,9 @@ void compile_plan(Plan& plan, bool fuse) {
       }
       if (best_len >= 2) {
         // widen the on-chip set with A0's untouched low-position labels while every tile of
-        // the chain stays within 2^12 entries (larger tiles amortize each CTA's setup)
+        // the chain stays within 2^12 entries, or within the chain's own largest tile when
+        // that is larger (larger tiles amortize each CTA's setup; a wider tile would only
+        // spread the chain over more CTAs)
         auto max_tile = [&](const std::vector<int>& in0) {
           std::vector<int> I = in0;
           size_t mx = I.size();
@@ -627,10 +633,11 @@ void compile_plan(Plan& plan, bool fuse) {
           }
           return mx;
         };
+        const size_t widen_to = std::max<size_t>(kTileBitsCta, max_tile(best_inner));
         for (int x : A0) {
           if (contains(best_inner, x)) continue;
           best_inner.push_back(x);
-          if (max_tile(best_inner) > kInnerMax) {
+          if (max_tile(best_inner) > widen_to) {
             best_inner.pop_back();
             break;
           }

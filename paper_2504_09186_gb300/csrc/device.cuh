@@ -136,7 +136,11 @@ struct TcParams {
 
 // Fused chain of absorptions (Sec. IV): one tile of the big tensor stays on chip while
 // every link contracts it with a small tensor.
-constexpr int kChainMaxBits = 12;  // on-chip tile <= 2^12 complex entries
+constexpr int kChainMaxBits = 12;  // on-chip tile <= 2^12 complex entries per CTA
+// Cluster-cooperative chains (Sec. IV: the core array's fused sections): a thread-block
+// cluster of up to 2^3 CTAs holds a tile of up to 2^(12 + 3) entries in distributed shared
+// memory, each CTA the 2^12 entries whose top tile bits equal its rank in the cluster.
+constexpr int kChainClusterBits = 3;
 struct ChainLink {
   int64_t g_off;     // arena offset (scalars, instance 0) of the small operand
   int64_t g_plane;   // 2^rank(small operand)
@@ -148,6 +152,12 @@ struct ChainLink {
   // bit scatters of x, so they split over x's low and high six bits
   uint16_t ib_lo[64], ib_hi[64];
   uint8_t gb_lo[64], gb_hi[64];
+  // ... and over the cluster rank (cluster-cooperative chain: x is the entry within the CTA,
+  // the rank holds the tile's top cl_bits bits)
+  uint16_t ib_top[8];
+  uint8_t gb_top[8];
+  int32_t in_ibits, out_ibits;  // per-CTA index bits of the link's input and output tiles
+  int32_t remote;               // 1: some input entries sit in other CTAs of the cluster
 };
 struct ChainParams {
   const void* arena;
@@ -162,6 +172,7 @@ struct ChainParams {
   float* maxabs;
   int32_t* exps;
   int32_t n_slots, slotA0, slotC;
+  int32_t cl_bits;                    // log2 CTAs per cluster (0: one CTA holds the tile)
 };
 
 // Index permutation of a planar binary-index tensor (the transposes of TTGT, Sec. V-A,

@@ -694,7 +694,7 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
   const std::vector<int>& la0 = P.tensors[first.a].labels;
   const std::vector<int>& lcn = P.tensors[last.c].labels;
   std::vector<int> prev = order_by(ch.inner0, la0);
-  if (prev.size() > (size_t)kChainMaxBits) fail(TNC_E_PLAN, "chain tile too large");
+  if (prev.size() > size_t(kChainMaxBits + kChainClusterBits)) fail(TNC_E_PLAN, "chain tile too large");
   for (int x : prev) c.maskA0 |= 1u << pos(la0, x);
   c.runA0 = low_run(c.maskA0);
   c.bits0 = (int)prev.size();
@@ -702,8 +702,36 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
   c.planeA0 = int64_t(1) << la0.size();
   c.slotA0 = first.a;
   c.n_links = (int)ch.steps.size();
+  // the labels each link contracts, and the largest on-chip tile of the chain: above 2^12
+  // entries the tile is spread over a cluster of 2^cb CTAs by its top cb bits
+  const size_t nl = ch.steps.size();
+  std::vector<std::vector<int>> Ks(nl);
+  size_t max_bits = prev.size();
+  {
+    std::vector<int> I = prev;
+    for (size_t l = 0; l < nl; ++l) {
+      const Step& st = P.steps[ch.steps[l]];
+      const std::vector<int>& la = P.tensors[st.a].labels;
+      const std::vector<int>& lg = P.tensors[st.b].labels;
+      std::vector<int> nI;
+      for (int x : lg)
+        if (pos(la, x) >= 0) Ks[l].push_back(x);
+      for (int x : I)
+        if (pos(Ks[l], x) < 0) nI.push_back(x);
+      for (int x : lg)
+        if (pos(la, x) < 0) nI.push_back(x);
+      I = nI;
+      max_bits = std::max(max_bits, I.size());
+    }
+  }
+  const int cb = max_bits > size_t(kChainMaxBits) ? int(max_bits) - kChainMaxBits : 0;
+  // inter-CTA labels (the top cb bits of a tile) of the intermediate tiles: those contracted
+  // latest, keeping the previous tile's where they tie (Sec. IV, Eq. 2: indices chosen by
+  // their remaining lifetime, so that most links read only their own CTA's entries)
+  std::vector<int> J(prev.end() - cb, prev.end());
   double bytes = double(int64_t(1) << la0.size());
-  for (int sidx : ch.steps) {
+  for (size_t l = 0; l < nl; ++l) {
+    const int sidx = ch.steps[l];
     const Step& st = P.steps[sidx];
     const std::vector<int>& la = P.tensors[st.a].labels;
     const std::vector<int>& lg = P.tensors[st.b].labels;
@@ -715,8 +743,43 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
     for (int x : K)
       if (pos(prev, x) < 0) fail(TNC_E_PLAN, "chain: contracted label not on chip");
     cur.insert(cur.end(), N.begin(), N.end());
-    cur = order_by(cur, lc);
-    if (cur.size() > (size_t)kChainMaxBits || K.size() > 6 || N.size() > 6) fail(TNC_E_PLAN, "chain link too large");
+    if (l + 1 == nl || cb == 0) {
+      cur = order_by(cur, lc);  // the result's own order (the last tile is stored in it)
+    } else {
+      auto next_use = [&](int x) {
+        for (size_t m = l + 1; m < nl; ++m)
+          if (pos(Ks[m], x) >= 0) return int(m);
+        return int(nl);
+      };
+      // the labels contracted latest (never, for most); among equals, those that are
+      // inter-CTA already (no swap now), then the result's top labels (no swap at the end)
+      const std::vector<int>& lcl = P.tensors[last.c].labels;
+      std::vector<int> final_top = order_by(std::vector<int>(lcl.begin(), lcl.end()), lcl);
+      final_top.erase(final_top.begin(), final_top.end() - std::min<size_t>(final_top.size(), size_t(cb)));
+      std::vector<int> cand = cur;
+      std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) {
+        const int ux = next_use(x), uy = next_use(y);
+        if (ux != uy) return ux > uy;
+        const bool jx = pos(J, x) >= 0, jy = pos(J, y) >= 0;
+        if (jx != jy) return jx;
+        return (pos(final_top, x) >= 0) > (pos(final_top, y) >= 0);
+      });
+      std::vector<int> nJ(cand.begin(), cand.begin() + cb);
+      // kept labels stay in their previous top positions
+      std::vector<int> top;
+      for (int x : J)
+        if (pos(nJ, x) >= 0) top.push_back(x);
+      for (int x : nJ)
+        if (pos(top, x) < 0) top.push_back(x);
+      std::vector<int> intra;
+      for (int x : cur)
+        if (pos(top, x) < 0) intra.push_back(x);
+      cur = order_by(intra, lc);
+      cur.insert(cur.end(), top.begin(), top.end());
+      J = top;
+    }
+    if (cur.size() > size_t(kChainMaxBits + kChainClusterBits) || K.size() > 6 || N.size() > 6)
+      fail(TNC_E_PLAN, "chain link too large");
     ChainLink lk;
     std::memset(&lk, 0, sizeof(lk));
     lk.g_off = OFF(st.b);
@@ -726,6 +789,10 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
     lk.out_bits = (int)cur.size();
     lk.k_bits = (int)K.size();
     lk.n_bits = (int)N.size();
+    lk.in_ibits = (int)prev.size() - cb;
+    lk.out_ibits = (int)cur.size() - cb;
+    if (lk.in_ibits < 0 || lk.out_ibits < 0 || lk.in_ibits > kChainMaxBits || lk.out_ibits > kChainMaxBits)
+      fail(TNC_E_PLAN, "chain: tile not divisible over the cluster");
     for (int k = 0; k < (1 << K.size()); ++k) {
       uint32_t ai = 0, gi = 0;
       for (size_t j = 0; j < K.size(); ++j)
@@ -739,10 +806,10 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
         if ((n >> j) & 1) gi |= 1u << pos(lg, N[j]);
       lk.gn[n] = (uint8_t)gi;
     }
-    // bit scatters of x, split over its low and high six bits
-    auto scatter = [&](uint32_t v, int shift, bool want_in) {
+    // bit scatters of the output index: `count` bits of v placed at output bits shift..
+    auto scatter = [&](uint32_t v, int shift, int count, bool want_in) {
       uint32_t r = 0;
-      for (size_t j = 0; j + shift < cur.size() && j < 6; ++j) {
+      for (int j = 0; j < count && size_t(j + shift) < cur.size(); ++j) {
         if (!((v >> j) & 1)) continue;
         const int lab = cur[j + shift];
         const int pi = pos(prev, lab);
@@ -751,11 +818,31 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
       }
       return r;
     };
+    // single CTA: x = the whole output index; cluster: x = its low out_ibits bits, the rank
+    // = its top cb bits
+    const int xb = cb ? lk.out_ibits : (int)cur.size();
     for (uint32_t v = 0; v < 64; ++v) {
-      lk.ib_lo[v] = (uint16_t)scatter(v, 0, true);
-      lk.ib_hi[v] = (uint16_t)scatter(v, 6, true);
-      lk.gb_lo[v] = (uint8_t)scatter(v, 0, false);
-      lk.gb_hi[v] = (uint8_t)scatter(v, 6, false);
+      lk.ib_lo[v] = (uint16_t)scatter(v, 0, std::min(6, xb), true);
+      lk.ib_hi[v] = (uint16_t)scatter(v, 6, std::max(0, std::min(6, xb - 6)), true);
+      lk.gb_lo[v] = (uint8_t)scatter(v, 0, std::min(6, xb), false);
+      lk.gb_hi[v] = (uint8_t)scatter(v, 6, std::max(0, std::min(6, xb - 6)), false);
+    }
+    for (uint32_t v = 0; v < 8; ++v) {
+      lk.ib_top[v] = (uint16_t)scatter(v, xb, cb, true);
+      lk.gb_top[v] = (uint8_t)scatter(v, xb, cb, false);
+    }
+    // local link: the output's inter-CTA labels are the input's, in the same order, and
+    // neither the other output labels nor the contracted ones are inter-CTA in the input
+    lk.remote = 0;
+    if (cb) {
+      for (int j = 0; j < cb; ++j)
+        if (pos(prev, cur[xb + j]) != lk.in_ibits + j) lk.remote = 1;
+      for (int j = 0; j < xb; ++j) {
+        const int pi = pos(prev, cur[j]);
+        if (pi >= lk.in_ibits) lk.remote = 1;
+      }
+      for (int x : K)
+        if (pos(prev, x) >= lk.in_ibits) lk.remote = 1;
     }
     links.push_back(lk);
     L.flops += 8.0 * std::ldexp(1.0, (int)(la.size() + N.size()));
@@ -765,6 +852,7 @@ static StepLaunch make_chain_launch(const Plan& P, const Chain& ch, std::vector<
   for (int x : prev) c.maskC |= 1u << pos(lcn, x);
   c.runC = low_run(c.maskC);
   c.bitsC = (int)prev.size();
+  c.cl_bits = cb;
   c.offC = OFF(last.c);
   c.planeC = int64_t(1) << lcn.size();
   c.slotC = last.c;

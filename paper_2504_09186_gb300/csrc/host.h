@@ -110,6 +110,7 @@ struct PlanOpts {
   int objective = 0;  // 0 fewest multiply-adds, 1 least modeled GB300 time
   int slicing = 0;    // 0 index overhead of Eq. 1; 1 executed cost under tree-like reuse
   int branch_exchange = 0;  // 1: reorder consecutive contractions to shorten lifetimes
+  int cluster_chains = 0;   // 1: fused chains may hold up to 2^15 entries on a CTA cluster
 };
 
 // One sliced index of a plan (slice bit t): its lifetime in the contraction order, the steps

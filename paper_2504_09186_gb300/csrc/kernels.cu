@@ -24,6 +24,8 @@
 #include <map>
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "device.cuh"
 
 namespace tnc {
@@ -1015,13 +1017,229 @@ __global__ void __launch_bounds__(kThreads) k_chain(const ChainParams p) {
   }
 }
 
+// Cluster-cooperative chain (Sec. IV: the core array's fused sections, with the cluster's
+// distributed shared memory in the role of the CPEs' RMA).  A cluster of 2^cl_bits CTAs holds
+// one tile of up to 2^(12 + cl_bits) entries: every tile of the chain (the first operand's,
+// each link's result) is spread by its top cl_bits labels (the inter-CTA indices), CTA r
+// holding the entries whose inter-CTA indices spell r.  The compiler keeps as inter-CTA
+// indices the labels contracted latest (Eq. 2: chosen by remaining lifetime), so most links
+// read only their own CTA's entries; where a link contracts one of them, or the last tile
+// takes the result's order, its inputs come from the other CTAs' shared memory (DSMEM)
+// -- the batched index swap of Eq. 2, done while the link computes.  Such a link is
+// bracketed by cluster barriers (every input written before anyone reads it; every read of a
+// buffer done before its owner overwrites it); a link that reads only its own CTA's entries
+// needs a CTA barrier only.
+template <typename T, int V>
+__device__ __forceinline__ void load_range_v(const T* __restrict__ re, const T* __restrict__ im, int n, uint32_t base,
+                                             int run, const uint32_t* __restrict__ hi, float2* __restrict__ dst) {
+  const uint32_t lowmask = (1u << run) - 1u;
+  for (int t = threadIdx.x * V; t < n; t += kThreads * V) {
+    const uint32_t g = base + uint32_t(t);
+    const uint32_t off = hi[g >> run] + (g & lowmask);
+    const Vec<T, V> r = *reinterpret_cast<const Vec<T, V>*>(re + off);
+    const Vec<T, V> i = *reinterpret_cast<const Vec<T, V>*>(im + off);
+#pragma unroll
+    for (int v = 0; v < V; ++v) dst[t + v] = make_float2(Conv<T>::to_f(r.v[v]), Conv<T>::to_f(i.v[v]));
+  }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ float store_range_v(T* __restrict__ re, T* __restrict__ im, int n, uint32_t base, int run,
+                                               const uint32_t* __restrict__ hi, const float2* __restrict__ src,
+                                               float scale) {
+  const uint32_t lowmask = (1u << run) - 1u;
+  float mx = 0.f;
+  for (int t = threadIdx.x * V; t < n; t += kThreads * V) {
+    const uint32_t g = base + uint32_t(t);
+    const uint32_t off = hi[g >> run] + (g & lowmask);
+    Vec<T, V> r, i;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float2 x = src[t + v];
+      r.v[v] = Conv<T>::from_f(x.x * scale);
+      i.v[v] = Conv<T>::from_f(x.y * scale);
+      mx = fmaxf(mx, fmaxf(fabsf(Conv<T>::to_f(r.v[v])), fabsf(Conv<T>::to_f(i.v[v]))));
+    }
+    *reinterpret_cast<Vec<T, V>*>(re + off) = r;
+    *reinterpret_cast<Vec<T, V>*>(im + off) = i;
+  }
+  return mx;
+}
+
+// the vector width of a run of 2^run entries, at most 16 bytes
+template <typename T>
+__device__ __forceinline__ int range_vec(int run) {
+  constexpr int VMAX = 16 / sizeof(T);
+  return min(1 << run, VMAX);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chain_cluster(const ChainParams p) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float2* peer[2][1 << kChainClusterBits];
+  float2* buf[2];
+  buf[0] = reinterpret_cast<float2*>(smem);
+  buf[1] = buf[0] + (1 << kChainMaxBits);
+  float2* gs = buf[1] + (1 << kChainMaxBits);                       // [64]
+  uint16_t* kin = reinterpret_cast<uint16_t*>(gs + 64);              // [64]
+  uint16_t* ibl = kin + 64;                                          // [64]
+  uint16_t* ibh = ibl + 64;                                          // [64]
+  uint16_t* ibt = ibh + 64;                                          // [8]
+  uint8_t* kg = reinterpret_cast<uint8_t*>(ibt + 8);                 // [64]
+  uint8_t* gbl = kg + 64;                                            // [64]
+  uint8_t* gbh = gbl + 64;                                           // [64]
+  uint8_t* gbt = gbh + 64;                                           // [8]
+  float* red = reinterpret_cast<float*>(gbt + 8);                    // [36]
+  uint32_t* hiA = reinterpret_cast<uint32_t*>(red + 36);             // [2^(bits0 - runA0)]
+  uint32_t* hiC = hiA + (1 << (p.bits0 - p.runA0));                  // [2^(bitsC - runC)]
+  const int tid = threadIdx.x;
+  const uint32_t r = cluster.block_rank();
+  const int cl = 1 << p.cl_bits;
+  const int64_t inst = blockIdx.z;
+  const uint32_t o = blockIdx.x >> p.cl_bits;  // a cluster = consecutive CTAs along x
+  int64_t oA = 0, oC = 0;
+  for (int j = 0; j < p.n_o; ++j)
+    if ((o >> j) & 1u) oA += int64_t(1) << p.o_A[j], oC += int64_t(1) << p.o_C[j];
+  for (int h = tid; h < (1 << (p.bits0 - p.runA0)); h += kThreads) hiA[h] = deposit_hi(h, p.maskA0, p.runA0);
+  for (int h = tid; h < (1 << (p.bitsC - p.runC)); h += kThreads) hiC[h] = deposit_hi(h, p.maskC, p.runC);
+  if (tid < cl) {
+    peer[0][tid] = cluster.map_shared_rank(buf[0], tid);
+    peer[1][tid] = cluster.map_shared_rank(buf[1], tid);
+  }
+  __syncthreads();
+  const T* tbase = reinterpret_cast<const T*>(p.arena) + inst * p.stride;
+  const T* A0 = tbase + p.offA0 + oA;
+  {
+    // the first tile in A0's position order: this CTA's entries share its top cl_bits bits
+    const int ib0 = p.bits0 - p.cl_bits, v = range_vec<T>(min(p.runA0, ib0));
+    const int n0 = 1 << ib0;
+    const uint32_t base = r << ib0;
+    if (v >= 8) load_range_v<T, (16 / sizeof(T) >= 8 ? 8 : 1)>(A0, A0 + p.planeA0, n0, base, p.runA0, hiA, buf[0]);
+    else if (v == 4) load_range_v<T, 4>(A0, A0 + p.planeA0, n0, base, p.runA0, hiA, buf[0]);
+    else if (v == 2) load_range_v<T, 2>(A0, A0 + p.planeA0, n0, base, p.runA0, hiA, buf[0]);
+    else load_range_v<T, 1>(A0, A0 + p.planeA0, n0, base, p.runA0, hiA, buf[0]);
+  }
+  const int64_t sb = inst * p.n_slots;
+  float bound = 1.41421356f * p.maxabs[sb + p.slotA0];
+  int esum = p.exps[sb + p.slotA0];
+  cluster.sync();  // every CTA's part of the first tile is on chip
+  int cur = 0;
+  for (int l = 0; l < p.n_links; ++l) {
+    const ChainLink* L = p.links + l;
+    const bool remote = L->remote != 0;
+    if (remote && l > 0) cluster.sync();  // the other CTAs' inputs of this link are written
+    const T* g = tbase + L->g_off;
+    for (int t = tid; t < L->g_size; t += kThreads) gs[t] = make_float2(Conv<T>::to_f(g[t]), Conv<T>::to_f(g[L->g_plane + t]));
+    const int nk = 1 << L->k_bits;
+    if (tid < 64) {
+      kin[tid] = L->kin[tid];
+      kg[tid] = L->kg[tid];
+      ibl[tid] = L->ib_lo[tid];
+      ibh[tid] = L->ib_hi[tid];
+      gbl[tid] = L->gb_lo[tid];
+      gbh[tid] = L->gb_hi[tid];
+      if (tid < 8) {
+        ibt[tid] = L->ib_top[tid];
+        gbt[tid] = L->gb_top[tid];
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float cn = 0.f;
+      for (int n = 0; n < (1 << L->n_bits); ++n) {
+        float sum = 0.f;
+        for (int q = 0; q < nk; ++q) {
+          const float2 v = gs[L->gn[n] + kg[q]];
+          sum += sqrtf(v.x * v.x + v.y * v.y);
+        }
+        cn = fmaxf(cn, sum);
+      }
+      red[32] = cn;
+    }
+    const float2* in = buf[cur];
+    float2* out = buf[cur ^ 1];
+    const int nout = 1 << L->out_ibits, in_ib = L->in_ibits;
+    const uint32_t ibr = ibt[r], gbr = gbt[r];
+    for (int x = tid; x < nout; x += kThreads) {
+      const uint32_t ib = ibl[x & 63] + ibh[(x >> 6) & 63] + ibr;
+      const int gb = gbl[x & 63] + gbh[(x >> 6) & 63] + gbr;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < nk; ++q) {
+        const uint32_t idx = ib + kin[q];
+        const uint32_t owner = idx >> in_ib, loc = idx & ((1u << in_ib) - 1u);
+        const float2 a = owner == r ? in[loc] : peer[cur][owner][loc];
+        const float2 b = gs[gb + kg[q]];
+        acc.x = fmaf(a.x, b.x, acc.x);
+        acc.x = fmaf(-a.y, b.y, acc.x);
+        acc.y = fmaf(a.x, b.y, acc.y);
+        acc.y = fmaf(a.y, b.x, acc.y);
+      }
+      out[x] = acc;
+    }
+    if (remote) cluster.sync();  // every read of this CTA's inputs is done before reuse
+    else __syncthreads();
+    bound *= red[32];
+    esum += p.exps[sb + L->slot_g];
+    cur ^= 1;
+  }
+  int sh = 0;
+  if (bound > 0.f) {
+    frexpf(bound, &sh);  // bound < 2^sh
+    sh -= 15;
+  }
+  const float scale = ldexpf(1.f, -sh);
+  T* C = reinterpret_cast<T*>(const_cast<void*>(p.arena)) + inst * p.stride + p.offC + oC;
+  float mx = 0.f;
+  {
+    const int ibC = p.bitsC - p.cl_bits, v = range_vec<T>(min(p.runC, ibC));
+    const int nC = 1 << ibC;
+    const uint32_t base = r << ibC;
+    if (v >= 8) mx = store_range_v<T, (16 / sizeof(T) >= 8 ? 8 : 1)>(C, C + p.planeC, nC, base, p.runC, hiC, buf[cur], scale);
+    else if (v == 4) mx = store_range_v<T, 4>(C, C + p.planeC, nC, base, p.runC, hiC, buf[cur], scale);
+    else if (v == 2) mx = store_range_v<T, 2>(C, C + p.planeC, nC, base, p.runC, hiC, buf[cur], scale);
+    else mx = store_range_v<T, 1>(C, C + p.planeC, nC, base, p.runC, hiC, buf[cur], scale);
+  }
+  const float bm = block_max(mx, red);
+  if (tid == 0) {
+    atomic_max_nonneg(&p.maxabs[sb + p.slotC], bm);
+    if (o == 0 && r == 0) p.exps[sb + p.slotC] = esum + sh;
+  }
+}
+
 size_t chain_smem_bytes(int bits0, int runA0, int bitsC, int runC) {
   return (size_t(2) << kChainMaxBits) * 8 + 64 * 8 + 3 * 64 * 2 + 3 * 64 + 36 * 4 + (size_t(1) << (bits0 - runA0)) * 4 +
-         (size_t(1) << (bitsC - runC)) * 4 + 16;
+         (size_t(1) << (bitsC - runC)) * 4 + 16 + 8 * 3;
+}
+
+template <typename T>
+cudaError_t launch_chain_cluster_t(const ChainParams& p, int64_t n_inst, size_t smem, cudaStream_t s) {
+  cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k_chain_cluster<T>), smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((1u << p.n_o) << p.cl_bits, 1, (unsigned)n_inst);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1u << p.cl_bits;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_chain_cluster<T>, p);
 }
 
 cudaError_t launch_chain(int precision, const ChainParams& p, int64_t n_inst, cudaStream_t s) {
   const size_t smem = chain_smem_bytes(p.bits0, p.runA0, p.bitsC, p.runC);
+  if (p.cl_bits > 0) {
+    if (p.cl_bits > kChainClusterBits) return cudaErrorInvalidValue;
+    if (precision == 0) return launch_chain_cluster_t<float>(p, n_inst, smem, s);
+    if (precision == 1) return launch_chain_cluster_t<__half>(p, n_inst, smem, s);
+    return launch_chain_cluster_t<__nv_bfloat16>(p, n_inst, smem, s);
+  }
   dim3 grid(1u << p.n_o, 1, (unsigned)n_inst);
   cudaError_t e;
   if (precision == 0) {

@@ -12,7 +12,7 @@
 namespace tnc {
 
 namespace {
-const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '4'};
+const char kMagic[8] = {'T', 'N', 'C', 'P', 'L', 'A', 'N', '5'};
 
 template <class T>
 void put(std::ofstream& f, const T& v) {
@@ -56,6 +56,7 @@ void save_plan(const Plan& p, const std::string& path) {
   put<int32_t>(f, p.opts.objective);
   put<int32_t>(f, p.opts.slicing);
   put<int32_t>(f, p.opts.branch_exchange);
+  put<int32_t>(f, p.opts.cluster_chains);
   put<int32_t>(f, (int32_t)p.sliced.size());
   for (int e : p.sliced) put<int32_t>(f, e);
   put<int32_t>(f, (int32_t)p.tree.size());
@@ -109,6 +110,8 @@ void load_plan(const std::string& path, Plan& p) {
   p.opts.objective = get<int32_t>(f);
   p.opts.slicing = get<int32_t>(f);
   p.opts.branch_exchange = get<int32_t>(f);
+  p.opts.cluster_chains = get<int32_t>(f);
+  if (p.opts.cluster_chains != 0 && p.opts.cluster_chains != 1) fail(7, "corrupt plan options");
   const int32_t ns = get<int32_t>(f);
   if (ns < 0 || ns > (int32_t)net.edges.size()) fail(7, "corrupt slice count");
   for (int i = 0; i < ns; ++i) {

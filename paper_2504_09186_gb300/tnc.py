@@ -50,6 +50,7 @@ class tnc_plan_opts(C.Structure):
         ("objective", C.c_int32),
         ("slicing", C.c_int32),
         ("branch_exchange", C.c_int32),
+        ("cluster_chains", C.c_int32),
     ]
 
 
@@ -198,10 +199,10 @@ def tnc_network_build(circuit, open_mask: Optional[np.ndarray]):
 
 
 def tnc_plan_greedy(network, seed=1, trials=16, log2_cap=26, slices_min=0, slices_max=64, temperature=0.5, mode=0,
-                    objective=0, slicing=0, branch_exchange=0):
+                    objective=0, slicing=0, branch_exchange=0, cluster_chains=0):
     lib = load_library()
     o = tnc_plan_opts(seed, trials, log2_cap, slices_min, slices_max, temperature, mode, objective, slicing,
-                      branch_exchange)
+                      branch_exchange, cluster_chains)
     h = C.c_void_p()
     _check(lib.tnc_plan_greedy(network, C.byref(o), C.byref(h)))
     return h
@@ -258,7 +259,8 @@ class Plan:
     @classmethod
     def greedy(cls, circuit, open_qubits: Sequence[int] = (), seed: int = 1, trials: int = 16, log2_cap: int = 26,
                slices_min: int = 0, slices_max: int = 64, temperature: float = 0.5, mode: str = "greedy",
-               objective: str = "flops", slicing: str = "eq1", branch_exchange: bool = False) -> "Plan":
+               objective: str = "flops", slicing: str = "eq1", branch_exchange: bool = False,
+               cluster_chains: bool = False) -> "Plan":
         """Plan for an `inputs.Circuit` (gate list) with the given open output qubits.
         mode: "greedy" (balanced pairwise order), "stem" (one tensor absorbs leaves) or
         "split" (a seeded balanced bisection of the qubits; the indices between the two
@@ -267,7 +269,8 @@ class Plan:
         modeled GB300 time).
         slicing: "eq1" (index overhead of Eq. 1) or "reuse" (lifetime-aware: executed cost
         under tree-like reuse).  branch_exchange: reorder consecutive contractions of the
-        kept trial while that lowers the slicing's cost."""
+        kept trial while that lowers the slicing's cost.  cluster_chains: fused chains may
+        hold tiles of up to 2^15 entries on a thread-block cluster (default 2^12, one CTA)."""
         lib = load_library()
         arity, qubits, mats = circuit.gate_array()
         ch = tnc_circuit_from_gates(circuit.n_qubits, arity, qubits, mats)
@@ -278,7 +281,8 @@ class Plan:
             try:
                 ph = tnc_plan_greedy(nh, seed, trials, log2_cap, slices_min, slices_max, temperature,
                                      {"greedy": 0, "stem": 1, "split": 2}[mode], {"flops": 0, "time": 1}[objective],
-                                     {"eq1": 0, "reuse": 1}[slicing], int(bool(branch_exchange)))
+                                     {"eq1": 0, "reuse": 1}[slicing], int(bool(branch_exchange)),
+                                     int(bool(cluster_chains)))
             finally:
                 lib.tnc_network_destroy(nh)
         finally:

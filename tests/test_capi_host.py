@@ -368,7 +368,7 @@ def test_plan_options_roundtrip_and_bad_values(tmp_path):
     _, open_q = subcube_spec(16, 3, seed=2)
     p = T.Plan.greedy(c, open_qubits=open_q, seed=5, trials=4, log2_cap=10, slices_min=3, slicing="reuse",
                       branch_exchange=True)
-    path = str(tmp_path / "plan_v4.bin")
+    path = str(tmp_path / "plan_v5.bin")
     p.save(path)
     q = T.Plan.load(path)
     dp, dq = p.describe(), q.describe()
@@ -376,7 +376,7 @@ def test_plan_options_roundtrip_and_bad_values(tmp_path):
     assert p.info()["log2_executed_flops"] == q.info()["log2_executed_flops"]
     sp, sq = p.slice_stats(), q.slice_stats()
     assert all(np.array_equal(sp[k], sq[k]) for k in sp)
-    for bad in (dict(objective=2), dict(slicing=2), dict(branch_exchange=-1)):
+    for bad in (dict(objective=2), dict(slicing=2), dict(branch_exchange=-1), dict(cluster_chains=2)):
         arity, qubits, mats = c.gate_array()
         ch = T.tnc_circuit_from_gates(c.n_qubits, arity, qubits, mats)
         nh = T.tnc_network_build(ch, np.zeros(c.n_qubits, dtype=np.uint8))

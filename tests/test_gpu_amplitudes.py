@@ -279,3 +279,26 @@ def test_post_lifetime_merging(ctx, precision):
     assert f_plain == pytest.approx(8 * 2.0 ** info["log2_executed_flops"], rel=1e-9)
     assert f_merged == pytest.approx(8 * 2.0 ** info["log2_executed_flops_merged"], rel=1e-9)
     assert np.array_equal(merged, ctx.amplitudes(p, fixed[None, :], precision, fuse=False, merge=True)[0])
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf"])
+def test_cluster_cooperative_chains(ctx, precision):
+    """Fused chains whose on-chip tile exceeds one CTA's 2^12 entries run on a thread-block
+    cluster (Sec. IV): 20-qubit stem plan whose chains hold tiles of 2^15 entries over eight
+    CTAs, links reading their inputs from peer CTAs' shared memory.  Against the state vector,
+    and against the same plan without fusion."""
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(20, 6, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=20, mode="stem", cluster_chains=True)
+    chains = p.describe()["chains"]
+    assert any(ch["tile_bits"] > 12 for ch in chains)
+    assert all(ch["tile_bits"] <= 12 for ch in T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=20,
+                                                               mode="stem").describe()["chains"])
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    fused = ctx.amplitudes(p, fixed[None, :], precision, fuse=True, profile=True)[0]
+    assert 2 in set(int(k) for k in ctx.profile_read()["kind"])  # the chain kernels ran
+    plain = ctx.amplitudes(p, fixed[None, :], precision, fuse=False)[0]
+    assert metrics.rel_err_norm(fused, ref) <= TOL[precision]
+    assert metrics.rel_err_norm(fused, plain) <= TOL[precision]
+    # deterministic
+    assert np.array_equal(fused, ctx.amplitudes(p, fixed[None, :], precision, fuse=True)[0])
