@@ -92,6 +92,44 @@ __device__ __forceinline__ int product_shift(float a, float b, int nK) {
 // stored swizzled and combined with XOR.
 __device__ __forceinline__ uint32_t sw16(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
 
+// Complex multiply-adds of a micro-tile with paired FP32 FMAs (fma.rn.f32x2: two IEEE
+// round-to-nearest FMAs in one instruction).  Per product, lane 0 does re += a.re b.re then
+// re += (-a.im) b.im, lane 1 does im += a.re b.im then im += a.im b.re: each component sees the
+// same FMAs in the same order as the scalar form, so the results are bit-identical to it.
+__device__ __forceinline__ uint64_t pack2f(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2f(uint64_t v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+template <int RM, int RN>
+__device__ __forceinline__ void cmac_tile(float2 (&acc)[RM][RN], const float2 (&a)[RM], const float2 (&b)[RN]) {
+  uint64_t a1[RM], a2[RM], b1[RN], b2[RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    a1[i] = pack2f(a[i].x, a[i].x);
+    a2[i] = pack2f(-a[i].y, a[i].y);
+  }
+#pragma unroll
+  for (int j = 0; j < RN; ++j) {
+    b1[j] = pack2f(b[j].x, b[j].y);
+    b2[j] = pack2f(b[j].y, b[j].x);
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      uint64_t c = pack2f(acc[i][j].x, acc[i][j].y);
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a1[i]), "l"(b1[j]));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a2[i]), "l"(b2[j]));
+      acc[i][j] = unpack2f(c);
+    }
+}
+
 template <typename T, int V, bool SW>
 __device__ __forceinline__ void load_tile_v(const T* __restrict__ re, const T* __restrict__ im, int bits, int run,
                                             const uint32_t* __restrict__ hi, float2* __restrict__ dst) {
@@ -168,7 +206,7 @@ template <typename T, int RM, int RN>
 __device__ __forceinline__ void generic_finish(const GenParams& p, const Inst3 I, const float2 (&acc)[RM][RN],
                                                bool active, int grp, int mi, int ni, int TM, int TN,
                                                const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC,
-                                               float2* R, float* red, int64_t oC) {
+                                               float2* R, float* red, int64_t oC, bool first_tile) {
   const int tid = threadIdx.x;
   // K groups in a fixed order
   const int O = 1 << (p.mt + p.nt);
@@ -218,7 +256,7 @@ __device__ __forceinline__ void generic_finish(const GenParams& p, const Inst3 I
   const float bm = block_max(mx, red);
   if (tid == 0) {
     atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
-    if (blockIdx.x == 0 && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+    if (first_tile && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
 }
 
@@ -241,21 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
 
   const int tid = threadIdx.x;
   const Inst3 I = map_inst(blockIdx.z, p.im);
-  // outer coordinates of this tile
-  const uint32_t om = blockIdx.x & ((1u << p.n_om) - 1u);
-  const uint32_t on = p.n_om >= 32 ? 0u : (blockIdx.x >> p.n_om);
-  int64_t oA = 0, oB = 0, oC = 0;
-  for (int j = 0; j < p.n_om; ++j)
-    if ((om >> j) & 1u) {
-      oA += int64_t(1) << p.om_A[j];
-      oC += int64_t(1) << p.om_C[j];
-    }
-  for (int j = 0; j < p.n_on; ++j)
-    if ((on >> j) & 1u) {
-      oB += int64_t(1) << p.on_B[j];
-      oC += int64_t(1) << p.on_C[j];
-    }
-  // index tables
+  // index tables (built once; the CTA then strides over the outer tiles)
   {
     const int nhA = 1 << (p.mt + p.kt - p.runA), nhB = 1 << (p.kt + p.nt - p.runB), nhC = 1 << (p.mt + p.nt - p.runC);
     for (int h = tid; h < nhA; h += kThreads) hiA[h] = deposit_hi(h, p.maskA, p.runA);
@@ -288,50 +312,60 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   for (int i = 0; i < RM; ++i) am[i] = active ? TAm[mi + i * TM] : 0;
 #pragma unroll
   for (int j = 0; j < RN; ++j) bn[j] = active ? TBn[ni + j * TN] : 0;
-  float2 acc[RM][RN];
-#pragma unroll
-  for (int i = 0; i < RM; ++i)
-#pragma unroll
-    for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-
-  const T* Abase = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
-  const T* Bbase = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
   const int64_t KO = int64_t(1) << p.n_ok;
   const int64_t per = KO / p.splitk;
   const int64_t k0 = int64_t(blockIdx.y) * per;
   const int nk = 1 << p.kt;
-  for (int64_t ok = k0; ok < k0 + per; ++ok) {
-    int64_t okA = 0, okB = 0;
-    for (int j = 0; j < p.n_ok; ++j)
-      if ((ok >> j) & 1) {
-        okA += int64_t(1) << p.ok_A[j];
-        okB += int64_t(1) << p.ok_B[j];
+  const uint32_t n_tiles = 1u << (p.n_om + p.n_on);
+  for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // outer coordinates of this tile
+    const uint32_t om = tile & ((1u << p.n_om) - 1u);
+    const uint32_t on = p.n_om >= 32 ? 0u : (tile >> p.n_om);
+    int64_t oA = 0, oB = 0, oC = 0;
+    for (int j = 0; j < p.n_om; ++j)
+      if ((om >> j) & 1u) {
+        oA += int64_t(1) << p.om_A[j];
+        oC += int64_t(1) << p.om_C[j];
       }
-    load_tile<T, true>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
-    load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
-    __syncthreads();
-    if (active) {
-      for (int k = grp; k < nk; k += p.kgroups) {
-        const int ka = TAk[k], kb = TBk[k];
-        float2 a[RM], b[RN];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
-#pragma unroll
-        for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < RN; ++j) {
-            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
-            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
-            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
-            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
-          }
+    for (int j = 0; j < p.n_on; ++j)
+      if ((on >> j) & 1u) {
+        oB += int64_t(1) << p.on_B[j];
+        oC += int64_t(1) << p.on_C[j];
       }
+    float2 acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    const T* Abase = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
+    const T* Bbase = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
+    for (int64_t ok = k0; ok < k0 + per; ++ok) {
+      int64_t okA = 0, okB = 0;
+      for (int j = 0; j < p.n_ok; ++j)
+        if ((ok >> j) & 1) {
+          okA += int64_t(1) << p.ok_A[j];
+          okB += int64_t(1) << p.ok_B[j];
+        }
+      load_tile<T, true>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
+      load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
+      __syncthreads();
+      if (active) {
+        for (int k = grp; k < nk; k += p.kgroups) {
+          const int ka = TAk[k], kb = TBk[k];
+          float2 a[RM], b[RN];
+#pragma unroll
+          for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
+#pragma unroll
+          for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
+          cmac_tile<RM, RN>(acc, a, b);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC, tile == 0);
+    __syncthreads();  // R (the staging tile) is the next tile's A tile
   }
-  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC);
 }
 
 // Streaming variant of k_generic for GEPDOT-shaped steps (few outputs, a long K loop;
@@ -489,21 +523,13 @@ __global__ void __launch_bounds__(kThreads) k_stream(const GenParams p) {
         for (int i = 0; i < RM; ++i) a[i] = make_float2(Conv<T>::to_f(Ar[am[i] ^ ka]), Conv<T>::to_f(Ai[am[i] ^ ka]));
 #pragma unroll
         for (int j = 0; j < RN; ++j) b[j] = make_float2(Conv<T>::to_f(Br[kb ^ bn[j]]), Conv<T>::to_f(Bi[kb ^ bn[j]]));
-#pragma unroll
-        for (int i = 0; i < RM; ++i)
-#pragma unroll
-          for (int j = 0; j < RN; ++j) {
-            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
-            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
-            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
-            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
-          }
+        cmac_tile<RM, RN>(acc, a, b);
       }
     }
   }
   cpa_wait<0>();
   __syncthreads();  // the ring becomes the reduction buffer
-  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC);
+  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC, blockIdx.x == 0);
 }
 
 // Fixed-order sum of split-K partials (blocked summation, Eq. 3), then scale and store.
@@ -1293,6 +1319,13 @@ cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, di
   if (smem > 48 * 1024) {
     cudaError_t e = set_smem_once(reinterpret_cast<const void*>(k), smem);
     if (e != cudaSuccess) return e;
+  }
+  if (!p.stream) {
+    // k_generic strides over its outer tiles: about 32 CTAs per SM over the grid's
+    // (split, instance) columns, so each CTA builds its index tables once for many tiles
+    const unsigned cols = grid.y * grid.z;
+    const unsigned cap = std::max(1u, (152u * 32u + cols - 1) / cols);
+    grid.x = std::min(grid.x, cap);
   }
   k<<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();

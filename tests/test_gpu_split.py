@@ -62,3 +62,35 @@ def test_split_plan_sampled_slices_with_tensor_core_blocks(ctx, precision):
             assert np.linalg.norm(got) < 1e-9
         else:
             assert metrics.rel_err_norm(got, ref) <= TOL[precision]
+
+
+def test_sixty_qubit_slice_against_the_oracle(ctx):
+    """The 60-qubit grid circuit itself (6 x 10, 24 cycles, one bitstring): a split plan at
+    cap 2^26 slices over a hundred indices, so one slice (about 2^36 multiply-adds) is within
+    the FP64 oracle's reach.  A seeded slice id (indices 63 and up at 0) on the GPU against the
+    oracle's network contraction with the same cuts fixed.  complex64 within 1e-5; complex-half
+    within the bound derived for one slice, 4 * 2^-11 * sqrt(stored tensors) (every stored
+    tensor rounded once to fp16, the roundings adding in quadrature)."""
+    from inputs import random_bitstrings
+    from oracle import network as tn
+
+    c = grid_circuit(6, 10, 24, seed=1)
+    bits = random_bitstrings(60, 1, seed=4)[0]
+    p = T.Plan.greedy(c, open_qubits=[], seed=3, trials=4, log2_cap=26, mode="split", objective="time")
+    info = p.info()
+    assert info["n_sliced"] > 100 and info["max_log2_size"] <= 26
+    cuts = p.sliced_cuts()
+    sid = int(np.random.default_rng(9).integers(0, 1 << 62))
+    tensors, open_labels = tn.circuit_tensors(c, bits, [])
+    tensors = tn.fix_labels(tensors, {("w", q, j): (sid >> t) & 1 for t, (q, j) in enumerate(cuts)})
+    order, extra = tn.search_order([t.labels for t in tensors], open_labels, 23, trials=2)
+    ref = 0.0
+    for k in range(1 << len(extra)):
+        sub = tn.fix_labels(tensors, {lab: (k >> t) & 1 for t, lab in enumerate(extra)})
+        ref = ref + complex(tn.contract_network(sub, open_labels, order))
+    assert abs(ref) > 0
+    got64 = complex(ctx.amplitudes_ids(p, bits[None, :], [sid], "c64")[0, 0])
+    got16 = complex(ctx.amplitudes_ids(p, bits[None, :], [sid], "chalf")[0, 0])
+    assert abs(got64 - ref) <= 1e-5 * abs(ref)
+    bound = 4 * 2.0 ** -11 * np.sqrt(info["n_leaves"] + info["n_steps"])
+    assert abs(got16 - ref) <= bound * abs(ref)
