@@ -198,18 +198,18 @@ TileSpec choose_tile(const std::vector<int>& la, const std::vector<int>& lb, con
   int kg = 256 / threads_out;
   kg = std::min(kg, 1 << kt);
   t.kgroups = std::max(1, kg);
-  // split over the outer common labels for GEPDOT-shaped steps: four CTAs per SM, each with
-  // at least four K steps for the streaming kernel's cp.async ring while one CTA per SM
-  // remains
+  // split over the outer common labels for GEPDOT-shaped steps whose tiles leave SMs idle:
+  // one wave of two CTAs per SM (the streaming kernel's occupancy), each with at least four
+  // K steps for its cp.async ring.  Any count: CTA y takes the outer K steps
+  // [y KO / splitk, (y + 1) KO / splitk)
   t.splitk = 1;
   const int ko = (int)t.Ko.size();
   if (gepdot && ko > 0) {
     const int64_t tiles = (int64_t(1) << (t.Mo.size() + t.No.size())) * std::max(1, n_inst_hint);
-    const int64_t want = (4 * 152 + tiles - 1) / tiles;
-    int s = 0;
-    while (s < ko && s < 10 && (int64_t(1) << s) < want) ++s;
-    while (s > 0 && ko - s < 2 && (tiles << (s - 1)) >= 152) --s;
-    t.splitk = 1 << s;
+    const int64_t slots = 2 * 152;
+    int64_t s = tiles >= slots ? 1 : (slots + tiles - 1) / tiles;
+    s = std::min<int64_t>(s, (int64_t(1) << ko) / 4);
+    t.splitk = (int)std::max<int64_t>(1, s);
   }
   t.gepdot = gepdot;
   t.stream = stream;

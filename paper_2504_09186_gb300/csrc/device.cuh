@@ -89,6 +89,7 @@ struct GenParams {
   float2* partials;                    // split-K partial sums [inst][split][planeC]
   int32_t smem_tables;                 // byte offset of the index tables in shared memory
   int32_t stream;                      // 1: k_stream (raw tiles through a cp.async ring)
+  int32_t kvb;                         // each K group takes chunks of 2^kvb consecutive k (0: one k)
   InstMap im;                          // launch index -> instances (tree-like reuse)
 };
 

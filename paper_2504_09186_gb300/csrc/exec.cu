@@ -501,8 +501,24 @@ static StepLaunch make_launch(const TileSpec& t, int kind, const std::vector<int
 // Memory-bound long-K steps (GEPDOTs, thin operands) with runs of at least 16 bytes in both
 // operands and two or more K steps per CTA stream their raw tiles through the k_stream ring
 // (elements of eb bytes).
+//
+// When both operands lead with the same K tile labels (K tile bits 0..c-1 at tile positions
+// 0..c-1 of A and of B, 2^c entries = 8 bytes), each K group takes k in chunks of 2^c: a
+// chunk of one tile row is one 8-byte shared-memory load in k_stream.  k_generic visits k
+// in the same order (the chunk order is set whether or not the step streams), so the two
+// kernels stay bit-identical.
 static void make_stream(StepLaunch& L, size_t eb, bool disabled) {
   GenParams& p = L.p;
+  p.kvb = 0;
+  if (L.stream) {
+    const int c = eb == 2 ? 2 : 1;
+    bool lead = p.kt >= c;
+    for (int v = 0; lead && v < c; ++v) lead = p.pAk[v] == v && p.pBk[v] == v;
+    if (lead) {
+      p.kvb = c;
+      p.kgroups = std::max(1, std::min(p.kgroups, (1 << p.kt) >> c));
+    }
+  }
   if (disabled || !L.stream) return;
   const int need = eb == 2 ? 3 : 2;  // log2 entries per 16 bytes
   if (p.runA < need || p.runB < need) return;

@@ -92,42 +92,56 @@ __device__ __forceinline__ int product_shift(float a, float b, int nK) {
 // stored swizzled and combined with XOR.
 __device__ __forceinline__ uint32_t sw16(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
 
-// Complex multiply-adds of a micro-tile with paired FP32 FMAs (fma.rn.f32x2: two IEEE
-// round-to-nearest FMAs in one instruction).  Per product, lane 0 does re += a.re b.re then
-// re += (-a.im) b.im, lane 1 does im += a.re b.im then im += a.im b.re: each component sees the
-// same FMAs in the same order as the scalar form, so the results are bit-identical to it.
-__device__ __forceinline__ uint64_t pack2f(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 unpack2f(uint64_t v) {
-  float lo, hi;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-  return make_float2(lo, hi);
-}
+// Complex multiply-adds of a micro-tile in FP32: re += a.re b.re then re += (-a.im) b.im,
+// im += a.re b.im then im += a.im b.re (the order every SIMT kernel here keeps).
 template <int RM, int RN>
 __device__ __forceinline__ void cmac_tile(float2 (&acc)[RM][RN], const float2 (&a)[RM], const float2 (&b)[RN]) {
-  uint64_t a1[RM], a2[RM], b1[RN], b2[RN];
-#pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    a1[i] = pack2f(a[i].x, a[i].x);
-    a2[i] = pack2f(-a[i].y, a[i].y);
-  }
-#pragma unroll
-  for (int j = 0; j < RN; ++j) {
-    b1[j] = pack2f(b[j].x, b[j].y);
-    b2[j] = pack2f(b[j].y, b[j].x);
-  }
 #pragma unroll
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < RN; ++j) {
-      uint64_t c = pack2f(acc[i][j].x, acc[i][j].y);
-      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a1[i]), "l"(b1[j]));
-      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(c) : "l"(a2[i]), "l"(b2[j]));
-      acc[i][j] = unpack2f(c);
+      acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+      acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+      acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+      acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
     }
+}
+
+template <typename T>
+struct MixFma;
+template <>
+struct MixFma<__half> {
+  static __device__ __forceinline__ float fma(uint16_t a, uint16_t b, float c) {
+    asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(c) : "h"(a), "h"(b));
+    return c;
+  }
+};
+template <>
+struct MixFma<__nv_bfloat16> {
+  static __device__ __forceinline__ float fma(uint16_t a, uint16_t b, float c) {
+    asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(c) : "h"(a), "h"(b));
+    return c;
+  }
+};
+__device__ __forceinline__ uint16_t word16(const uint2& w, int v) {
+  const uint32_t x = v < 2 ? w.x : w.y;
+  return (uint16_t)((v & 1) ? (x >> 16) : (x & 0xFFFFu));
+}
+template <typename T, int RM, int RN>
+__device__ __forceinline__ void cmac_tile16(float2 (&acc)[RM][RN], const uint2 (&ar)[RM], const uint2 (&ai)[RM],
+                                            const uint2 (&br)[RN], const uint2 (&bi)[RN], int v) {
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const uint16_t xr = word16(ar[i], v), xi = word16(ai[i], v), nxi = xi ^ 0x8000u;
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const uint16_t yr = word16(br[j], v), yi = word16(bi[j], v);
+      acc[i][j].x = MixFma<T>::fma(xr, yr, acc[i][j].x);
+      acc[i][j].x = MixFma<T>::fma(nxi, yi, acc[i][j].x);
+      acc[i][j].y = MixFma<T>::fma(xr, yi, acc[i][j].y);
+      acc[i][j].y = MixFma<T>::fma(xi, yr, acc[i][j].y);
+    }
+  }
 }
 
 template <typename T, int V, bool SW>
@@ -313,8 +327,9 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
 #pragma unroll
   for (int j = 0; j < RN; ++j) bn[j] = active ? TBn[ni + j * TN] : 0;
   const int64_t KO = int64_t(1) << p.n_ok;
-  const int64_t per = KO / p.splitk;
-  const int64_t k0 = int64_t(blockIdx.y) * per;
+  // CTA y of the split takes the outer K steps [y KO / splitk, (y + 1) KO / splitk)
+  const int64_t k0 = int64_t(blockIdx.y) * KO / p.splitk;
+  const int64_t per = (int64_t(blockIdx.y) + 1) * KO / p.splitk - k0;
   const int nk = 1 << p.kt;
   const uint32_t n_tiles = 1u << (p.n_om + p.n_on);
   for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -351,15 +366,19 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
       load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
       __syncthreads();
       if (active) {
-        for (int k = grp; k < nk; k += p.kgroups) {
-          const int ka = TAk[k], kb = TBk[k];
-          float2 a[RM], b[RN];
+        // K group grp takes chunks c = grp, grp + kgroups, ... of 2^kvb consecutive k
+        const int V = 1 << p.kvb;
+        for (int c = grp; c < (nk >> p.kvb); c += p.kgroups)
+          for (int v = 0; v < V; ++v) {
+            const int k = (c << p.kvb) | v;
+            const int ka = TAk[k], kb = TBk[k];
+            float2 a[RM], b[RN];
 #pragma unroll
-          for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
+            for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
 #pragma unroll
-          for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
-          cmac_tile<RM, RN>(acc, a, b);
-        }
+            for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
+            cmac_tile<RM, RN>(acc, a, b);
+          }
       }
       __syncthreads();
     }
@@ -412,7 +431,7 @@ __device__ __forceinline__ void stream_copy(const T* re, const T* im, int bits, 
 }
 
 template <typename T, int RM, int RN>
-__global__ void __launch_bounds__(kThreads) k_stream(const GenParams p) {
+__global__ void __launch_bounds__(kThreads, 2) k_stream(const GenParams p) {
   constexpr int NS = kStreamStages;
   extern __shared__ __align__(16) unsigned char smem[];
   const int nA = 1 << (p.mt + p.kt), nB = 1 << (p.kt + p.nt);
@@ -484,25 +503,38 @@ __global__ void __launch_bounds__(kThreads) k_stream(const GenParams p) {
   const T* Abase = reinterpret_cast<const T*>(p.A) + I.a * p.strideA + oA;
   const T* Bbase = reinterpret_cast<const T*>(p.B) + I.b * p.strideB + oB;
   const int64_t KO = int64_t(1) << p.n_ok;
-  const int64_t per = KO / p.splitk;
-  const int64_t k0 = int64_t(blockIdx.y) * per;
+  // CTA y of the split takes the outer K steps [y KO / splitk, (y + 1) KO / splitk)
+  const int64_t k0 = int64_t(blockIdx.y) * KO / p.splitk;
+  const int64_t per = (int64_t(blockIdx.y) + 1) * KO / p.splitk - k0;
   const int nk = 1 << p.kt;
   const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-  // copies of K step `it` into stage it % NS; one commit group per call (empty past the end)
+  // operand offsets of outer K step `nok` (the next one to copy), advanced one step at a time
+  // by the bits that flip: the trailing ones of nok clear, the next bit sets
+  int64_t nok = k0, okA = 0, okB = 0;
+  for (int j = 0; j < p.n_ok; ++j)
+    if ((nok >> j) & 1) {
+      okA += int64_t(1) << p.ok_A[j];
+      okB += int64_t(1) << p.ok_B[j];
+    }
+  // copies of K step `it` (= nok - k0) into stage it % NS; one commit group per call (empty
+  // past the end)
   auto issue = [&](int64_t it) {
     if (it < per) {
-      const int64_t ok = k0 + it;
-      int64_t okA = 0, okB = 0;
-      for (int j = 0; j < p.n_ok; ++j)
-        if ((ok >> j) & 1) {
-          okA += int64_t(1) << p.ok_A[j];
-          okB += int64_t(1) << p.ok_B[j];
-        }
       const uint32_t st = sbase + uint32_t(it % NS) * stage_bytes;
       const uint32_t esz = uint32_t(sizeof(T));
       stream_copy<T>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, st, st + uint32_t(nA) * esz);
       stream_copy<T>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, st + uint32_t(2 * nA) * esz,
                      st + uint32_t(2 * nA + nB) * esz);
+      int j = 0;
+      for (; j < p.n_ok && ((nok >> j) & 1); ++j) {
+        okA -= int64_t(1) << p.ok_A[j];
+        okB -= int64_t(1) << p.ok_B[j];
+      }
+      if (j < p.n_ok) {
+        okA += int64_t(1) << p.ok_A[j];
+        okB += int64_t(1) << p.ok_B[j];
+      }
+      ++nok;
     }
     cpa_commit();
   };
@@ -516,14 +548,54 @@ __global__ void __launch_bounds__(kThreads) k_stream(const GenParams p) {
       const T* Ai = Ar + nA;
       const T* Br = Ai + nA;
       const T* Bi = Br + nB;
-      for (int k = grp; k < nk; k += p.kgroups) {
-        const int ka = TAk[k], kb = TBk[k];
-        float2 a[RM], b[RN];
+      if (p.kvb == 0) {
+        for (int k = grp; k < nk; k += p.kgroups) {
+          const int ka = TAk[k], kb = TBk[k];
+          float2 a[RM], b[RN];
 #pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = make_float2(Conv<T>::to_f(Ar[am[i] ^ ka]), Conv<T>::to_f(Ai[am[i] ^ ka]));
+          for (int i = 0; i < RM; ++i) a[i] = make_float2(Conv<T>::to_f(Ar[am[i] ^ ka]), Conv<T>::to_f(Ai[am[i] ^ ka]));
 #pragma unroll
-        for (int j = 0; j < RN; ++j) b[j] = make_float2(Conv<T>::to_f(Br[kb ^ bn[j]]), Conv<T>::to_f(Bi[kb ^ bn[j]]));
-        cmac_tile<RM, RN>(acc, a, b);
+          for (int j = 0; j < RN; ++j) b[j] = make_float2(Conv<T>::to_f(Br[kb ^ bn[j]]), Conv<T>::to_f(Bi[kb ^ bn[j]]));
+          cmac_tile<RM, RN>(acc, a, b);
+        }
+      } else {
+        // chunks of VE consecutive k (kvb = log2 VE): the chunk of each tile row and column
+        // is one contiguous, 8-byte aligned run (the low tile bits of both operands are K
+        // bits 0..kvb-1, which the swizzle leaves alone); the lanes of a warp take adjacent
+        // chunks, so one load instruction reads 256 contiguous bytes
+        constexpr int VE = 8 / sizeof(T);
+        for (int c = grp; c < nk / VE; c += p.kgroups) {
+          const int ka = TAk[c * VE], kb = TBk[c * VE];
+          uint2 vr[RM], vi[RM], wr[RN], wi[RN];
+#pragma unroll
+          for (int i = 0; i < RM; ++i) {
+            vr[i] = *reinterpret_cast<const uint2*>(Ar + (am[i] ^ ka));
+            vi[i] = *reinterpret_cast<const uint2*>(Ai + (am[i] ^ ka));
+          }
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            wr[j] = *reinterpret_cast<const uint2*>(Br + (kb ^ bn[j]));
+            wi[j] = *reinterpret_cast<const uint2*>(Bi + (kb ^ bn[j]));
+          }
+          if constexpr (sizeof(T) == 2) {
+#pragma unroll
+            for (int v = 0; v < VE; ++v) cmac_tile16<T, RM, RN>(acc, vr, vi, wr, wi, v);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VE; ++v) {
+              float2 a[RM], b[RN];
+#pragma unroll
+              for (int i = 0; i < RM; ++i)
+                a[i] = make_float2(Conv<T>::to_f(reinterpret_cast<const T*>(&vr[i])[v]),
+                                   Conv<T>::to_f(reinterpret_cast<const T*>(&vi[i])[v]));
+#pragma unroll
+              for (int j = 0; j < RN; ++j)
+                b[j] = make_float2(Conv<T>::to_f(reinterpret_cast<const T*>(&wr[j])[v]),
+                                   Conv<T>::to_f(reinterpret_cast<const T*>(&wi[j])[v]));
+              cmac_tile<RM, RN>(acc, a, b);
+            }
+          }
+        }
       }
     }
   }
