@@ -366,19 +366,23 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
       load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
       __syncthreads();
       if (active) {
-        // K group grp takes chunks c = grp, grp + kgroups, ... of 2^kvb consecutive k
-        const int V = 1 << p.kvb;
-        for (int c = grp; c < (nk >> p.kvb); c += p.kgroups)
-          for (int v = 0; v < V; ++v) {
-            const int k = (c << p.kvb) | v;
-            const int ka = TAk[k], kb = TBk[k];
-            float2 a[RM], b[RN];
+        // K group grp takes k = grp, grp + kgroups, ..., or (kvb > 0) chunks c = grp,
+        // grp + kgroups, ... of 2^kvb consecutive k
+        auto mac = [&](int k) {
+          const int ka = TAk[k], kb = TBk[k];
+          float2 a[RM], b[RN];
 #pragma unroll
-            for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
+          for (int i = 0; i < RM; ++i) a[i] = As[am[i] ^ ka];
 #pragma unroll
-            for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
-            cmac_tile<RM, RN>(acc, a, b);
-          }
+          for (int j = 0; j < RN; ++j) b[j] = Bs[kb ^ bn[j]];
+          cmac_tile<RM, RN>(acc, a, b);
+        };
+        if (p.kvb == 0) {
+          for (int k = grp; k < nk; k += p.kgroups) mac(k);
+        } else {
+          for (int c = grp; c < (nk >> p.kvb); c += p.kgroups)
+            for (int v = 0; v < (1 << p.kvb); ++v) mac((c << p.kvb) | v);
+        }
       }
       __syncthreads();
     }

@@ -1201,8 +1201,9 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
   uint64_t* tempty = tfull + 2;
   uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);                       // [NG][GW]
-  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + NG * GW);  // [NG]
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);                       // [NG][2][GW]
+  volatile int32_t* flag = reinterpret_cast<volatile int32_t*>(red + NG * 2 * GW);  // [NG]
+  int32_t* cnt = const_cast<int32_t*>(flag) + NG;                               // [NG][2]
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int prod_warp = NG * GW, mma_warp = NG * GW + 1;
@@ -1238,9 +1239,11 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), 1);
+      // the direct epilogue's warps hand TMEM back one by one
+      mbar_init(smem_u32(&tempty[b]), (DIRECT || p.direct) ? GW : 1);
     }
     mbar_init(smem_u32(done), 1);
+    for (int q = 0; q < 2 * NG; ++q) cnt[q] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -1347,12 +1350,130 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
     constexpr int CPW = S::CPW;
     const int gq = warp / GW, lw = warp % GW, gtid = tid - gq * GT;
     T* stg = reinterpret_cast<T*>(smem + S::PIPE + gq * S::STG);  // [2][CT]
-    float* gred = red + gq * GW;
+    float* gred = red + gq * 2 * GW;
     const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
     const int row = (warp & 3) * 32 + lane;
     const int col0 = (lw >> 2) * CPW;
     const uint32_t lowmask = (1u << p.runC) - 1u;
-    for (int64_t t = blockIdx.x + int64_t(gq) * gridDim.x, j = gq; t < n_tiles; t += NG * int64_t(gridDim.x), j += NG) {
+    if (DIRECT || p.direct) {
+      // Direct epilogue, warps independent: each waits for its tile, drains its TMEM columns
+      // into 16-bit registers (scaled, converted), hands TMEM back (tempty counts the GW warps
+      // of the group), then stores runs of 8 columns as 16-byte vectors (C's lowest positions
+      // are tile columns 0..2, then row 0).  The group's maximum goes through a per-tile-parity
+      // slot of red; the last warp of the group to finish (cnt) publishes it.  A warp reaches
+      // tile j + 4 of its group only after every warp has handed back tile j + 2, i.e. has
+      // finished tile j, so two parity slots suffice.
+      const uint32_t rm = TCm[row];
+      int64_t inst_cached = -1;
+      int sh = 0;
+      float scale = 1.f;
+      int64_t sa = 0, sbb = 0, sc = 0;
+      T* Cbase = nullptr;
+      for (int64_t t = blockIdx.x + int64_t(gq) * gridDim.x, j = gq; t < n_tiles; t += NG * int64_t(gridDim.x), j += NG) {
+        const int b = (int)(j & 1);
+        const int par = (int)((j / NG) & 1);
+        const uint32_t acc = tmem + uint32_t(b * 2 * BN);
+        int wok = 1;
+        if (lane == 0) wok = mbar_wait_bounded(smem_u32(&tfull[b]), (uint32_t)((j >> 1) & 1), p.status) ? 1 : 0;
+        wok = __shfl_sync(0xffffffffu, wok, 0);
+        if (!wok) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int64_t inst = t >> tile_bits;
+        if (inst != inst_cached) {
+          inst_cached = inst;
+          const Inst3 It = map_inst(inst, p.im);
+          sa = It.a * p.n_slots;
+          sbb = It.b * p.n_slots;
+          sc = It.c * p.n_slots;
+          sh = 0;
+          const float a = p.maxabs[sa + p.slotA], bb = p.maxabs[sbb + p.slotB];
+          if (a > 0.f && bb > 0.f) {
+            int ea, eb;
+            frexpf(a, &ea);
+            frexpf(bb, &eb);
+            sh = ea + eb + p.nK + 1 - 15;
+          }
+          scale = ldexpf(1.f, -sh);
+          Cbase = reinterpret_cast<T*>(p.C) + It.c * p.strideC;
+        }
+        const uint32_t r = (uint32_t)t & tile_mask;
+        const uint32_t on = r & ((1u << p.n_on) - 1u);
+        const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
+        int64_t oC = 0;
+        for (int q = 0; q < p.n_om; ++q)
+          if ((om >> q) & 1u) oC += int64_t(1) << p.om_C[q];
+        for (int q = 0; q < p.n_on; ++q)
+          if ((on >> q) & 1u) oC += int64_t(1) << p.on_C[q];
+        T* Cre = Cbase + oC;
+        float mx = 0.f;
+        // columns 8g..8g+7 of the row are 8 consecutive entries of C: one 16-byte store per plane
+        auto store8 = [&](int col, const uint32_t* r4, const uint32_t* i4) {
+          const uint32_t x = stg_swz(rm ^ TCn[col]);  // C-tile index, low 3 bits 0
+          const uint32_t off = hiC[x >> p.runC] + (x & lowmask);
+          *reinterpret_cast<uint4*>(Cre + off) = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+          *reinterpret_cast<uint4*>(Cre + p.planeC + off) = make_uint4(i4[0], i4[1], i4[2], i4[3]);
+        };
+        // the first CPW - HOLD columns are stored as they are drained, the last HOLD are held
+        // in registers while TMEM goes back to the MMA warp
+        constexpr int HOLD = CPW / 2;
+#pragma unroll 1
+        for (int c = 0; c < CPW - HOLD; c += 16) {
+          float vr[16], vi[16];
+          tmem_ld16(acc + lane_addr + col0 + c, vr);
+          tmem_ld16(acc + lane_addr + BN + col0 + c, vi);
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            uint32_t r4[4], i4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int v = 8 * g + 2 * q;
+              r4[q] = pack2<T>(vr[v] * scale, vr[v + 1] * scale);
+              i4[q] = pack2<T>(vi[v] * scale, vi[v + 1] * scale);
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(vr[v]), fabsf(vr[v + 1])), fmaxf(fabsf(vi[v]), fabsf(vi[v + 1]))));
+            }
+            store8(col0 + c + 8 * g, r4, i4);
+          }
+        }
+        uint32_t pr[HOLD / 2], pi[HOLD / 2];
+#pragma unroll
+        for (int c = 0; c < HOLD; c += 16) {
+          float vr[16], vi[16];
+          tmem_ld16(acc + lane_addr + col0 + CPW - HOLD + c, vr);
+          tmem_ld16(acc + lane_addr + BN + col0 + CPW - HOLD + c, vi);
+#pragma unroll
+          for (int q = 0; q < 16; q += 2) {
+            pr[(c + q) >> 1] = pack2<T>(vr[q] * scale, vr[q + 1] * scale);
+            pi[(c + q) >> 1] = pack2<T>(vi[q] * scale, vi[q + 1] * scale);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(vr[q]), fabsf(vr[q + 1])), fmaxf(fabsf(vi[q]), fabsf(vi[q + 1]))));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+#pragma unroll
+        for (int g = 0; g < HOLD / 8; ++g) store8(col0 + CPW - HOLD + 8 * g, pr + 4 * g, pi + 4 * g);
+        mx *= scale * (1.f + 0x1p-8f);  // bound on the stored maximum (see tc_epilogue)
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+          float* slot = red + (gq * 2 + par) * GW;
+          slot[lw] = mx;
+          __threadfence_block();
+          if (atomicAdd(&cnt[gq * 2 + par], 1) == GW - 1) {
+            __threadfence_block();
+            float m = 0.f;
+            for (int w = 0; w < GW; ++w) m = fmaxf(m, *reinterpret_cast<volatile float*>(&slot[w]));
+            cnt[gq * 2 + par] = 0;
+            atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
+            if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+          }
+        }
+      }
+    }
+    for (int64_t t = blockIdx.x + int64_t(gq) * gridDim.x, j = gq; t < n_tiles && !(DIRECT || p.direct);
+         t += NG * int64_t(gridDim.x), j += NG) {
       const int b = (int)(j & 1);
       const uint32_t acc = tmem + uint32_t(b * 2 * BN);
       if (gtid == 0) flag[gq] = mbar_wait_bounded(smem_u32(&tfull[b]), (uint32_t)((j >> 1) & 1), p.status) ? 1 : 0;
@@ -1386,43 +1507,6 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
       float mx = 0.f;
       const uint32_t rm = TCm[row];
       T* Cre = reinterpret_cast<T*>(p.C) + It.c * p.strideC + oC;
-      if (DIRECT || p.direct) {
-        // columns 8g..8g+7 of a row are 8 consecutive entries of C: 16-byte stores straight
-        // from registers, no staging; one barrier per tile (TMEM release and block max)
-#pragma unroll 1
-        for (int cc = 0; cc < CPW; cc += 32) {
-          float vr[32], vi[32];
-          tmem_ld32(acc + lane_addr + col0 + cc, vr);
-          tmem_ld32(acc + lane_addr + BN + col0 + cc, vi);
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const uint32_t x = stg_swz(rm ^ TCn[col0 + cc + 8 * g]);  // C-tile index, low 3 bits 0
-            const uint32_t off = hiC[x >> p.runC] + (x & lowmask);
-            Vec8<T> r8, i8;
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              r8.v[v] = Conv<T>::from_f(vr[8 * g + v] * scale);
-              i8.v[v] = Conv<T>::from_f(vi[8 * g + v] * scale);
-              mx = fmaxf(mx, fmaxf(fabsf(vr[8 * g + v]), fabsf(vi[8 * g + v])));
-            }
-            *reinterpret_cast<Vec8<T>*>(Cre + off) = r8;
-            *reinterpret_cast<Vec8<T>*>(Cre + p.planeC + off) = i8;
-          }
-        }
-        mx *= scale * (1.f + 0x1p-8f);
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) gred[lw] = mx;
-        group_bar<GT>(1 + gq);
-        if (gtid == 0) {
-          mbar_arrive(smem_u32(&tempty[b]));
-          float m = 0.f;
-          for (int w = 0; w < GW; ++w) m = fmaxf(m, gred[w]);
-          atomicMax(reinterpret_cast<unsigned int*>(&p.maxabs[sc + p.slotC]), __float_as_uint(m));
-          if (r == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
-        }
-        continue;
-      }
       if constexpr (!DIRECT) {
 #pragma unroll 1
       for (int cc = 0; cc < CPW; cc += 32) {
@@ -1762,7 +1846,7 @@ template <int BN, int BK, int NG, bool DIRECT>
 size_t tma_persist_smem_bytes_t(int runC) {
   using S = TcpShape<BN, BK, NG, DIRECT>;
   return 1024 + S::PIPE + NG * S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
-         (2 * S::NST + 5) * 8 + 16 + NG * S::GW * 4 + 16 + 64;
+         (2 * S::NST + 5) * 8 + 16 + NG * 2 * S::GW * 4 + 16 + 16 + 64;
 }
 
 static int sm_count_cached() {
