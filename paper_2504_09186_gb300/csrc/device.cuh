@@ -93,6 +93,15 @@ struct GenParams {
   InstMap im;                          // launch index -> instances (tree-like reuse)
 };
 
+// One SIMT step of a wave inside the persistent steps kernel (k_steps): the contraction's
+// units, then (split over K) the reduce's blocks after a grid barrier.
+struct StepOp {
+  GenParams p;
+  int32_t rm, rn;   // register micro-tile
+  int32_t reduce;   // 0: no split, 1: a thread per output, 2: a warp per output
+  int32_t pad;
+};
+
 // Leaf gather: fix sliced legs and closed output legs, convert, scale.
 struct LeafDesc {
   int64_t src;      // offset (complex entries) of the full leaf in the FP64 source array

@@ -144,29 +144,58 @@ __device__ __forceinline__ void cmac_tile16(float2 (&acc)[RM][RN], const uint2 (
   }
 }
 
-template <typename T, int V, bool SW>
+// A vector of V entries read at L2 (ld.global.cg): data written by other CTAs earlier in the
+// same launch (the persistent steps kernel, after a grid barrier) is never served stale from
+// the non-coherent or L1 paths.
+template <typename T, int V>
+__device__ __forceinline__ Vec<T, V> ld_cg(const T* p) {
+  constexpr int B = int(sizeof(T)) * V;
+  Vec<T, V> r;
+  if constexpr (B == 16) {
+    const uint4 x = __ldcg(reinterpret_cast<const uint4*>(p));
+    memcpy(&r, &x, 16);
+  } else if constexpr (B == 8) {
+    const uint2 x = __ldcg(reinterpret_cast<const uint2*>(p));
+    memcpy(&r, &x, 8);
+  } else if constexpr (B == 4) {
+    const unsigned int x = __ldcg(reinterpret_cast<const unsigned int*>(p));
+    memcpy(&r, &x, 4);
+  } else {
+    const unsigned short x = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    memcpy(&r, &x, 2);
+  }
+  return r;
+}
+
+template <typename T, int V, bool SW, bool COH = false>
 __device__ __forceinline__ void load_tile_v(const T* __restrict__ re, const T* __restrict__ im, int bits, int run,
                                             const uint32_t* __restrict__ hi, float2* __restrict__ dst) {
   const int n = 1 << bits;
   const uint32_t lowmask = (1u << run) - 1u;
   for (int t = threadIdx.x * V; t < n; t += kThreads * V) {
     const uint32_t off = hi[t >> run] + (uint32_t(t) & lowmask);
-    const Vec<T, V> r = *reinterpret_cast<const Vec<T, V>*>(re + off);
-    const Vec<T, V> i = *reinterpret_cast<const Vec<T, V>*>(im + off);
+    Vec<T, V> r, i;
+    if constexpr (COH) {
+      r = ld_cg<T, V>(re + off);
+      i = ld_cg<T, V>(im + off);
+    } else {
+      r = *reinterpret_cast<const Vec<T, V>*>(re + off);
+      i = *reinterpret_cast<const Vec<T, V>*>(im + off);
+    }
 #pragma unroll
     for (int v = 0; v < V; ++v)
       dst[SW ? sw16(uint32_t(t + v)) : uint32_t(t + v)] = make_float2(Conv<T>::to_f(r.v[v]), Conv<T>::to_f(i.v[v]));
   }
 }
 
-template <typename T, bool SW = false>
+template <typename T, bool SW = false, bool COH = false>
 __device__ __forceinline__ void load_tile(const T* re, const T* im, int bits, int run, const uint32_t* hi, float2* dst) {
   constexpr int VMAX = 16 / sizeof(T);
   const int v = min(1 << run, VMAX);
-  if (v >= 8) load_tile_v<T, (VMAX >= 8 ? 8 : 1), SW>(re, im, bits, run, hi, dst);
-  else if (v == 4) load_tile_v<T, 4, SW>(re, im, bits, run, hi, dst);
-  else if (v == 2) load_tile_v<T, 2, SW>(re, im, bits, run, hi, dst);
-  else load_tile_v<T, 1, SW>(re, im, bits, run, hi, dst);
+  if (v >= 8) load_tile_v<T, (VMAX >= 8 ? 8 : 1), SW, COH>(re, im, bits, run, hi, dst);
+  else if (v == 4) load_tile_v<T, 4, SW, COH>(re, im, bits, run, hi, dst);
+  else if (v == 2) load_tile_v<T, 2, SW, COH>(re, im, bits, run, hi, dst);
+  else load_tile_v<T, 1, SW, COH>(re, im, bits, run, hi, dst);
 }
 
 template <typename T, int V>
@@ -216,11 +245,13 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 
 // After the K loop of k_generic / k_stream: the K groups' sums in a fixed order into the
 // C-native staging tile R, then either FP32 split-K partials or the scaled, converted tile.
+// Returns this thread's largest stored magnitude (0 for partials); generic_publish takes the
+// CTA's maximum once, after all of its tiles.
 template <typename T, int RM, int RN>
-__device__ __forceinline__ void generic_finish(const GenParams& p, const Inst3 I, const float2 (&acc)[RM][RN],
-                                               bool active, int grp, int mi, int ni, int TM, int TN,
-                                               const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC,
-                                               float2* R, float* red, int64_t oC, bool first_tile) {
+__device__ __forceinline__ float generic_finish(const GenParams& p, const Inst3 I, const float2 (&acc)[RM][RN],
+                                                bool active, int grp, int mi, int ni, int TM, int TN,
+                                                const uint16_t* TCm, const uint16_t* TCn, const uint32_t* hiC,
+                                                float2* R, int64_t oC, float scale, uint32_t by, uint32_t bz) {
   const int tid = threadIdx.x;
   // K groups in a fixed order
   const int O = 1 << (p.mt + p.nt);
@@ -256,27 +287,37 @@ __device__ __forceinline__ void generic_finish(const GenParams& p, const Inst3 I
   }
   if (p.splitk > 1) {
     // FP32 partial sums, indexed by C's flat index
-    float2* part = p.partials + (int64_t(blockIdx.z) * p.splitk + blockIdx.y) * p.planeC + oC;
+    float2* part = p.partials + (int64_t(bz) * p.splitk + by) * p.planeC + oC;
     const uint32_t lowmask = (1u << p.runC) - 1u;
     for (int t = tid; t < O; t += kThreads) part[hiC[t >> p.runC] + (uint32_t(t) & lowmask)] = R[t];
-    return;
+    return 0.f;
   }
   // scale, convert, store
-  const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
-  const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
-  const float scale = ldexpf(1.f, -sh);
   T* Cre = reinterpret_cast<T*>(p.C) + I.c * p.strideC + oC;
-  const float mx = store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
+  return store_tile<T>(Cre, Cre + p.planeC, p.mt + p.nt, p.runC, hiC, R, scale);
+}
+
+// The output scale of a launch's instance: 2^-sh with sh from the operands' stored maxima.
+__device__ __forceinline__ int generic_shift(const GenParams& p, const Inst3 I) {
+  return product_shift(p.maxabs[I.a * p.n_slots + p.slotA], p.maxabs[I.b * p.n_slots + p.slotB], p.nK);
+}
+
+// The CTA's largest stored magnitude into C's maximum, and (the CTA of tile 0) C's exponent.
+__device__ __forceinline__ void generic_publish(const GenParams& p, const Inst3 I, float mx, float* red, int sh,
+                                                bool first) {
   const float bm = block_max(mx, red);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
+    const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
     atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
-    if (first_tile && blockIdx.y == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+    if (first) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
 }
 
-template <typename T, int RM, int RN>
-__global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// One CTA of the tiled SIMT contraction: split column by, instance column bz, tiles bx,
+// bx + gx, ... of the outer tile grid (k_generic, and each unit of k_steps).
+template <typename T, int RM, int RN, bool COH = false>
+__device__ __forceinline__ void generic_cta(const GenParams& p, unsigned char* smem, uint32_t bx, uint32_t gx,
+                                            uint32_t by, uint32_t bz) {
   float2* As = reinterpret_cast<float2*>(smem);
   float2* Bs = As + (1 << (p.mt + p.kt));
   float2* R = As;  // reduction / staging after the K loop
@@ -292,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   float* red = reinterpret_cast<float*>(TCn + (1 << p.nt) + 2);  // 4-byte aligned (+2 pads)
 
   const int tid = threadIdx.x;
-  const Inst3 I = map_inst(blockIdx.z, p.im);
+  const Inst3 I = map_inst(bz, p.im);
   // index tables (built once; the CTA then strides over the outer tiles)
   {
     const int nhA = 1 << (p.mt + p.kt - p.runA), nhB = 1 << (p.kt + p.nt - p.runB), nhC = 1 << (p.mt + p.nt - p.runC);
@@ -328,11 +369,15 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
   for (int j = 0; j < RN; ++j) bn[j] = active ? TBn[ni + j * TN] : 0;
   const int64_t KO = int64_t(1) << p.n_ok;
   // CTA y of the split takes the outer K steps [y KO / splitk, (y + 1) KO / splitk)
-  const int64_t k0 = int64_t(blockIdx.y) * KO / p.splitk;
-  const int64_t per = (int64_t(blockIdx.y) + 1) * KO / p.splitk - k0;
+  const int64_t k0 = int64_t(by) * KO / p.splitk;
+  const int64_t per = (int64_t(by) + 1) * KO / p.splitk - k0;
   const int nk = 1 << p.kt;
   const uint32_t n_tiles = 1u << (p.n_om + p.n_on);
-  for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  // one output scale per instance; the maximum is published once per CTA
+  const int sh = p.splitk == 1 ? generic_shift(p, I) : 0;
+  const float scale = ldexpf(1.f, -sh);
+  float mx = 0.f;
+  for (uint32_t tile = bx; tile < n_tiles; tile += gx) {
     // outer coordinates of this tile
     const uint32_t om = tile & ((1u << p.n_om) - 1u);
     const uint32_t on = p.n_om >= 32 ? 0u : (tile >> p.n_om);
@@ -362,8 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
           okA += int64_t(1) << p.ok_A[j];
           okB += int64_t(1) << p.ok_B[j];
         }
-      load_tile<T, true>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
-      load_tile<T, true>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
+      load_tile<T, true, COH>(Abase + okA, Abase + okA + p.planeA, p.mt + p.kt, p.runA, hiA, As);
+      load_tile<T, true, COH>(Bbase + okB, Bbase + okB + p.planeB, p.kt + p.nt, p.runB, hiB, Bs);
       __syncthreads();
       if (active) {
         // K group grp takes k = grp, grp + kgroups, ..., or (kvb > 0) chunks c = grp,
@@ -386,9 +431,16 @@ __global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
       }
       __syncthreads();
     }
-    generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC, tile == 0);
+    mx = fmaxf(mx, generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, oC, scale, by, bz));
     __syncthreads();  // R (the staging tile) is the next tile's A tile
   }
+  if (p.splitk == 1) generic_publish(p, I, mx, red, sh, bx == 0);
+}
+
+template <typename T, int RM, int RN>
+__global__ void __launch_bounds__(kThreads) k_generic(const GenParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  generic_cta<T, RM, RN>(p, smem, blockIdx.x, gridDim.x, blockIdx.y, blockIdx.z);
 }
 
 // Streaming variant of k_generic for GEPDOT-shaped steps (few outputs, a long K loop;
@@ -605,21 +657,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const GenParams p) {
   }
   cpa_wait<0>();
   __syncthreads();  // the ring becomes the reduction buffer
-  generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, red, oC, blockIdx.x == 0);
+  const int sh = p.splitk == 1 ? generic_shift(p, I) : 0;
+  const float mx = generic_finish<T, RM, RN>(p, I, acc, active, grp, mi, ni, TM, TN, TCm, TCn, hiC, R, oC, ldexpf(1.f, -sh),
+                                             blockIdx.y, blockIdx.z);
+  if (p.splitk == 1) generic_publish(p, I, mx, red, sh, blockIdx.x == 0);
 }
 
-// Fixed-order sum of split-K partials (blocked summation, Eq. 3), then scale and store.
+// Fixed-order sum of split-K partials (blocked summation, Eq. 3), then scale and store: block
+// bx of launch index bz (k_splitk_reduce, and the reduce units of k_steps).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
-  __shared__ float red[32];
-  const Inst3 I = map_inst(blockIdx.z, p.im);
-  const int64_t idx = int64_t(blockIdx.x) * kThreads + threadIdx.x;
+__device__ __forceinline__ void splitk_reduce_cta(const GenParams& p, float* red, uint32_t bx, uint32_t bz) {
+  const Inst3 I = map_inst(bz, p.im);
+  const int64_t idx = int64_t(bx) * kThreads + threadIdx.x;
   const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
   const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
   const float scale = ldexpf(1.f, -sh);
   float mx = 0.f;
   if (idx < p.planeC) {
-    const float2* part = p.partials + int64_t(blockIdx.z) * p.splitk * p.planeC + idx;
+    const float2* part = p.partials + int64_t(bz) * p.splitk * p.planeC + idx;
     float2 s = part[0];
     for (int k = 1; k < p.splitk; ++k) {
       const float2 v = part[int64_t(k) * p.planeC];
@@ -635,26 +690,31 @@ __global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
   const float bm = block_max(mx, red);
   if (threadIdx.x == 0) {
     atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
-    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+    if (bx == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_splitk_reduce(const GenParams p) {
+  __shared__ float red[32];
+  splitk_reduce_cta<T>(p, red, blockIdx.x, blockIdx.z);
 }
 
 // The same sum for long splits over few outputs: one warp per output, lane l adds the
 // partials l, l + 32, l + 64, ... in order, then the lanes combine in a fixed butterfly
 // (xor 16, 8, 4, 2, 1), so the result is deterministic; 8 outputs per block.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_splitk_reduce_wide(const GenParams p) {
-  __shared__ float red[32];
-  const Inst3 I = map_inst(blockIdx.z, p.im);
+__device__ __forceinline__ void splitk_reduce_wide_cta(const GenParams& p, float* red, uint32_t bx, uint32_t bz) {
+  const Inst3 I = map_inst(bz, p.im);
   const int lane = threadIdx.x & 31;
-  const int64_t idx = int64_t(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5);
+  const int64_t idx = int64_t(bx) * (kThreads / 32) + (threadIdx.x >> 5);
   const int64_t sa = I.a * p.n_slots, sbb = I.b * p.n_slots, sc = I.c * p.n_slots;
   const int sh = product_shift(p.maxabs[sa + p.slotA], p.maxabs[sbb + p.slotB], p.nK);
   const float scale = ldexpf(1.f, -sh);
   float mx = 0.f;
   float2 s = make_float2(0.f, 0.f);
   if (idx < p.planeC) {
-    const float2* part = p.partials + int64_t(blockIdx.z) * p.splitk * p.planeC + idx;
+    const float2* part = p.partials + int64_t(bz) * p.splitk * p.planeC + idx;
 #pragma unroll 8
     for (int k = lane; k < p.splitk; k += 32) {
       const float2 v = part[int64_t(k) * p.planeC];
@@ -676,7 +736,105 @@ __global__ void __launch_bounds__(kThreads) k_splitk_reduce_wide(const GenParams
   const float bm = block_max(mx, red);
   if (threadIdx.x == 0) {
     atomic_max_nonneg(&p.maxabs[sc + p.slotC], bm);
-    if (blockIdx.x == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+    if (bx == 0) p.exps[sc + p.slotC] = p.exps[sa + p.slotA] + p.exps[sbb + p.slotB] + sh;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_splitk_reduce_wide(const GenParams p) {
+  __shared__ float red[32];
+  splitk_reduce_wide_cta<T>(p, red, blockIdx.x, blockIdx.z);
+}
+
+// Grid-wide barrier of the persistent steps kernel (all CTAs co-resident: cooperative launch).
+// bar[0] counts arrivals, bar[1] is the generation.  The last CTA to arrive resets the count,
+// then opens the next generation; the others wait for it, at most about two seconds, after
+// which the wait records TNC_E_TIMEOUT and the kernel returns.
+__device__ __forceinline__ bool grid_barrier(uint32_t* bar, int32_t* status) {
+  __shared__ int ok_flag;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = bar + 1;
+    const uint32_t g = *gen;
+    __threadfence();  // this CTA's writes before the arrival
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int it = 0;
+      while (*gen == g) {
+        if (++it > (1 << 24)) {
+          atomicExch(status, 4);  // TNC_E_TIMEOUT
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();  // the other CTAs' writes before this CTA's next reads
+    ok_flag = ok;
+  }
+  __syncthreads();
+  return ok_flag != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void generic_unit(int rm, int rn, const GenParams& p, unsigned char* smem, uint32_t bx,
+                                             uint32_t gx, uint32_t by, uint32_t bz) {
+#define TNC_UNIT(a, b) \
+  if (rm == a && rn == b) return generic_cta<T, a, b, true>(p, smem, bx, gx, by, bz);
+  TNC_UNIT(1, 1) TNC_UNIT(1, 2) TNC_UNIT(1, 4) TNC_UNIT(2, 1) TNC_UNIT(2, 2) TNC_UNIT(2, 4)
+  TNC_UNIT(4, 1) TNC_UNIT(4, 2) TNC_UNIT(4, 4) TNC_UNIT(8, 4)
+#undef TNC_UNIT
+}
+
+// One persistent launch for all SIMT steps of a wave (Sec. III-A: a wave's subtasks in one
+// launch).  Ops run in program order; each op's CTAs (tile strides x splits x launch indices)
+// are spread over the grid, then a grid barrier; a split op's reduce blocks follow after
+// another.  Results are bit-identical to the per-step launches: every tile, split and reduce
+// block computes the same sums in the same order wherever it runs.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_steps(const StepOp* __restrict__ ops, int n_ops, int64_t n_inst,
+                                                   int reuse, uint32_t* bar, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) GenParams P;
+  __shared__ float red[32];
+  for (int o = 0; o < n_ops; ++o) {
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&ops[o].p);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&P);
+      for (int i = threadIdx.x; i < int(sizeof(GenParams) / 4); i += kThreads) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !reuse) P.im = InstMap{-1, 0u, 0u, 0u};
+    __syncthreads();
+    const int rm = ops[o].rm, rn = ops[o].rn, reduce = ops[o].reduce;
+    const int64_t nz = P.im.s < 0 ? n_inst : ((n_inst >> P.im.s) << __popc(P.im.dep_c));
+    const uint32_t gy = (uint32_t)P.splitk;
+    const int64_t n_tiles = int64_t(1) << (P.n_om + P.n_on);
+    // tile strides per (split, launch index) column: about eight units per CTA
+    const int64_t cols = int64_t(gy) * nz;
+    const uint32_t gx = (uint32_t)max(int64_t(1), min(n_tiles, (int64_t(8) * gridDim.x + cols - 1) / cols));
+    const int64_t units = int64_t(gx) * cols;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const uint32_t bx = (uint32_t)(u % gx);
+      const int64_t r = u / gx;
+      generic_unit<T>(rm, rn, P, smem, bx, gx, (uint32_t)(r % gy), (uint32_t)(r / gy));
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, status)) return;
+    if (reduce) {
+      const int64_t per = reduce == 2 ? (P.planeC + kThreads / 32 - 1) / (kThreads / 32) : (P.planeC + kThreads - 1) / kThreads;
+      const int64_t runits = per * nz;
+      for (int64_t u = blockIdx.x; u < runits; u += gridDim.x) {
+        if (reduce == 2) splitk_reduce_wide_cta<T>(P, red, (uint32_t)(u % per), (uint32_t)(u / per));
+        else splitk_reduce_cta<T>(P, red, (uint32_t)(u % per), (uint32_t)(u / per));
+        __syncthreads();
+      }
+      if (!grid_barrier(bar, status)) return;
+    }
   }
 }
 
@@ -1405,6 +1563,27 @@ cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, di
   }
   k<<<grid, kThreads, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+// The persistent steps kernel: one cooperative launch (every CTA resident, as the grid
+// barrier needs) of as many CTAs as fit on the device at `smem` bytes each.
+cudaError_t launch_steps(int precision, const StepOp* ops, int n_ops, int64_t n_inst, int reuse, uint32_t* bar,
+                         int32_t* status, size_t smem, cudaStream_t s) {
+  const void* k = precision == 0 ? reinterpret_cast<const void*>(k_steps<float>)
+                  : precision == 1 ? reinterpret_cast<const void*>(k_steps<__half>)
+                                   : reinterpret_cast<const void*>(k_steps<__nv_bfloat16>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = set_smem_once(k, smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1 || n_sm < 1) return cudaErrorInvalidConfiguration;
+  void* args[] = {&ops, &n_ops, &n_inst, &reuse, &bar, &status};
+  return cudaLaunchCooperativeKernel(k, dim3((unsigned)(per_sm * n_sm)), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_inst, cudaStream_t s) {
