@@ -243,6 +243,13 @@ typedef struct {
                             so every later step runs half as often for it.  The sums
                             associate differently from the unmerged call (not bit-identical;
                             the same amplitudes within rounding).  Other calls ignore it.
+                            reserved[2], tnc_amplitudes / tnc_amplitudes_ids: 1 = run each
+                            wave's steps as one persistent launch (Sec. III-A: a wave's
+                            subtasks in one launch) when every step of the program is a SIMT
+                            contraction without merges: one cooperative kernel takes the steps
+                            in order, its CTAs sharing each step's tiles, with a grid barrier
+                            between steps.  Bit-identical to the per-step launches.  Other
+                            programs, and profiled calls, run per step.
                             Others: 0. */
 } tnc_exec_opts;
 
@@ -337,7 +344,9 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
  *             cp.async gathers, 4 tensor-core with TMA loads, 5 persistent tensor-core
  *             with TMA loads: epilogue overlapped with the next tile's loads and MMAs,
  *             6 permute + tensor-core + permute (tnc_contract only), 7 GEPDOT streamed
- *             through a cp.async ring (split over K or not))
+ *             through a cp.async ring (split over K or not), 8 every step in one persistent
+ *             launch (tnc_exec_opts.reserved[2]): entry 0 holds that launch's time and count,
+ *             the other entries none)
  *  ms[n]      (one extra entry) the whole call's device time
  * *n receives the number of steps. */
 tnc_status tnc_profile_read(tnc_context ctx, double* ms, int32_t* launches, double* flops, double* bytes,

@@ -24,6 +24,8 @@ namespace tnc {
 
 cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t launch_splitk_reduce(int precision, const GenParams& p, int64_t n_inst, cudaStream_t s);
+cudaError_t launch_steps(int precision, const StepOp* ops, const int32_t* phases, int n_phases, int64_t n_inst,
+                         int reuse, uint32_t* bar, int32_t* status, size_t smem, cudaStream_t s);
 cudaError_t launch_leaf_gather(int precision, const LeafDesc* leaves, int n_leaves, const double2* src, void* arena,
                                int64_t inst_stride, const int64_t* inst_slice, const int32_t* inst_row,
                                const uint8_t* bits, int n_qubits, float* maxabs, int32_t* exps, int n_slots,
@@ -565,6 +567,11 @@ struct DeviceProgram {
   std::vector<std::vector<int>> wait_on;  // [launch][lane]
   std::vector<char> signals;
   std::vector<cudaEvent_t> done_ev;
+  // one persistent launch for the steps (programs of SIMT steps only; tnc_exec_opts.reserved[2])
+  bool persist_ok = false;
+  int n_phases = 0;
+  size_t steps_smem = 0;
+  DevBuf step_ops, step_phases, steps_bar;
   ~DeviceProgram() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : done_ev)
@@ -579,6 +586,9 @@ struct DeviceProgram {
     chain_links.release();
     leaf_r.release();
     inst_c.release();
+    step_ops.release();
+    step_phases.release();
+    steps_bar.release();
     cudaGetLastError();  // a failed release must not surface as the next launch's error
   }
 };
@@ -1001,18 +1011,11 @@ static StepLaunch tc_launch(const tnc_context_s* ctx, const Plan& P, const Devic
 // respects these dependencies.
 constexpr int kLanes = 4;
 
-static void make_schedule(const Plan& P, DeviceProgram* prog) {
+// The launches each launch k must follow: its operands' producers, every earlier launch whose
+// tensors share arena memory with its result (the arena reuses regions), and the previous
+// split launch (split launches share one partial-sum buffer).  Programs of plan steps only.
+static std::vector<std::vector<int>> step_deps(const Plan& P, const DeviceProgram* prog) {
   const int n = (int)prog->steps.size();
-  for (auto e : prog->done_ev)
-    if (e) cudaEventDestroy(e);
-  prog->done_ev.clear();
-  prog->n_lanes = 1;
-  prog->lane.assign(n, 0);
-  prog->wait_on.assign(n, std::vector<int>(kLanes, -1));
-  prog->signals.assign(n, 0);
-  if (n != (int)P.steps.size() || n < 2) return;
-  for (const auto& L : prog->steps)
-    if (L.kind == K_CHAIN) return;
   auto region = [&](int t) {
     const int64_t off = prog_off(P, prog, t);
     return std::make_pair(off, off + 2 * (int64_t(1) << P.tensors[t].labels.size()));
@@ -1041,6 +1044,22 @@ static void make_schedule(const Plan& P, DeviceProgram* prog) {
     }
     producer[st.c] = k;
   }
+  return deps;
+}
+
+static void make_schedule(const Plan& P, DeviceProgram* prog) {
+  const int n = (int)prog->steps.size();
+  for (auto e : prog->done_ev)
+    if (e) cudaEventDestroy(e);
+  prog->done_ev.clear();
+  prog->n_lanes = 1;
+  prog->lane.assign(n, 0);
+  prog->wait_on.assign(n, std::vector<int>(kLanes, -1));
+  prog->signals.assign(n, 0);
+  if (n != (int)P.steps.size() || n < 2) return;
+  for (const auto& L : prog->steps)
+    if (L.kind == K_CHAIN) return;
+  const std::vector<std::vector<int>> deps = step_deps(P, prog);
   // lanes
   std::vector<int> lane_last(kLanes, -1);
   for (int k = 0; k < n; ++k) {
@@ -1252,6 +1271,52 @@ static std::shared_ptr<DeviceProgram> build_program(tnc_context_s* ctx, tnc_plan
     }
     prog->reuse_ok = reuse;
     prog->root_map = reuse ? InstMap{sbits, mdep[P.root], 0, 0} : InstMap{-1, 0, 0, 0};
+  }
+  // the steps as one persistent launch (k_steps), for programs whose steps are all SIMT
+  // contractions without merges.  Streamed steps run their tiled form (bit-identical; their
+  // shared-memory region also fits the tiled layout).  Phases: a step's phase is one past the
+  // latest phase of the launches it must follow (step_deps), and the steps go in phase order.
+  {
+    std::vector<StepOp> ops;
+    bool ok = !prog->steps.empty() && prog->steps.size() == P.steps.size();
+    for (const auto& L : prog->steps)
+      if ((L.kind != K_GENERIC && L.kind != K_SPLITK) || !L.merges.empty()) ok = false;
+    std::vector<int> order, phases;
+    if (ok) {
+      const auto deps = step_deps(P, prog.get());
+      std::vector<int> level(prog->steps.size(), 0);
+      for (size_t k = 0; k < level.size(); ++k)
+        for (int j : deps[k]) level[k] = std::max(level[k], level[j] + 1);
+      for (size_t k = 0; k < level.size(); ++k) order.push_back((int)k);
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return level[x] < level[y]; });
+      for (size_t i = 0; i < order.size(); ++i)
+        if (i == 0 || level[order[i]] != level[order[i - 1]]) phases.push_back((int)i);
+      phases.push_back((int)order.size());
+    }
+    size_t smem = 0;
+    for (int k : order) {
+      const StepLaunch& L = prog->steps[k];
+      StepOp op;
+      std::memset(&op, 0, sizeof(op));
+      op.p = L.p;
+      op.p.stream = 0;
+      op.rm = L.rm;
+      op.rn = L.rn;
+      op.reduce = L.kind == K_SPLITK ? (L.p.splitk >= kWideReduceSplit ? 2 : 1) : 0;
+      ops.push_back(op);
+      smem = std::max(smem, L.smem);
+    }
+    if (ok) {
+      prog->step_ops.reserve(ops.size() * sizeof(StepOp));
+      CUDA_OK(cudaMemcpy(prog->step_ops.p, ops.data(), ops.size() * sizeof(StepOp), cudaMemcpyHostToDevice));
+      prog->step_phases.reserve(phases.size() * sizeof(int32_t));
+      CUDA_OK(cudaMemcpy(prog->step_phases.p, phases.data(), phases.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+      prog->steps_bar.reserve(16);
+      CUDA_OK(cudaMemset(prog->steps_bar.p, 0, 16));
+      prog->n_phases = (int)phases.size() - 1;
+      prog->steps_smem = smem;
+      prog->persist_ok = true;
+    }
   }
   // root
   prog->root = P.root;
@@ -1518,6 +1583,9 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
     CUDA_OK(cudaMemcpyAsync(ctx->segs.p, segs.data(), segs.size() * sizeof(RootSeg), cudaMemcpyHostToDevice, s));
     CUDA_OK(cudaMemsetAsync(ctx->acc.p, 0, size_t(batch) * n_out * sizeof(double2), s));
     const bool prof = opts->profile != 0;
+    // one persistent launch for the steps of each wave (requested and the program eligible);
+    // profiled, it reports the launch as its first step, kind 8
+    const bool persist = opts->reserved[2] != 0 && prog->persist_ok;
     const int n_waves = (int)((n_inst + W - 1) / W);
     // tree-like reuse needs instances laid out as whole rows of every slice
     const bool reuse =
@@ -1541,6 +1609,10 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
                      : ((SL.kind == K_GENERIC || SL.kind == K_SPLITK) && SL.p.stream) ? 7
                                                                                       : SL.kind;
         ps.kernels[k] = (SL.kind == K_SPLITK || ((SL.kind == K_TC || SL.kind == K_TMA) && SL.tp.splitk > 1)) ? 2 : 1;
+        if (persist) {
+          ps.kind[k] = 8;
+          ps.kernels[k] = k == 0 ? 1 : 0;
+        }
       }
       CUDA_OK(cudaEventRecord(ps.call_start(), s));
     }
@@ -1556,7 +1628,7 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
                std::to_string(wave_segs[w].second) + "/" + std::to_string((uintptr_t)ctx->inst_slice.p) + "/" +
                std::to_string((uintptr_t)ctx->inst_row.p) + "/" + std::to_string((uintptr_t)ctx->bits.p) + "/" +
                std::to_string((uintptr_t)ctx->segs.p) + "/" + std::to_string((uintptr_t)ctx->acc.p) + "/" +
-               std::to_string((uintptr_t)s) + "/" + std::to_string(reuse ? 1 : 0);
+               std::to_string((uintptr_t)s) + "/" + std::to_string(reuse ? 1 : 0) + "/" + std::to_string(persist ? 1 : 0);
         auto git = prog->graphs.find(gkey);
         if (git != prog->graphs.end()) {
           CUDA_OK(cudaGraphLaunch(git->second, s));
@@ -1571,7 +1643,20 @@ static AmpRun run_amplitudes(tnc_context ctx, tnc_plan plan, const tnc_exec_opts
                                  ctx->inst_slice.as<int64_t>(), ctx->inst_row.as<int32_t>(), ctx->bits.as<uint8_t>(),
                                  n, prog->maxabs.as<float>(), prog->exps.as<int32_t>(), prog->n_slots, base, cnt,
                                  prog->leaf_r.as<double2>(), s));
-      if (prog->n_lanes > 1) {
+      if (persist) {
+        CUDA_OK(cudaMemsetAsync(prog->steps_bar.p, 0, 16, s));
+        if (prof) CUDA_OK(cudaEventRecord(ctx->prof.at(w, 0, 0), s));
+        CUDA_OK(launch_steps(precision, prog->step_ops.as<StepOp>(), prog->step_phases.as<int32_t>(), prog->n_phases,
+                             cnt, reuse ? 1 : 0, prog->steps_bar.as<uint32_t>(), ctx->status.as<int32_t>(),
+                             prog->steps_smem, s));
+        if (prof) {
+          CUDA_OK(cudaEventRecord(ctx->prof.at(w, 0, 1), s));
+          for (size_t k = 1; k < prog->steps.size(); ++k) {
+            CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 0), s));
+            CUDA_OK(cudaEventRecord(ctx->prof.at(w, (int)k, 1), s));
+          }
+        }
+      } else if (prog->n_lanes > 1) {
         // concurrent branches: fork the lanes from s, follow the schedule, join back into s
         ensure_lanes(ctx);
         CUDA_OK(cudaEventRecord(ctx->fork_ev, s));

@@ -791,46 +791,95 @@ __device__ __forceinline__ void generic_unit(int rm, int rn, const GenParams& p,
 }
 
 // One persistent launch for all SIMT steps of a wave (Sec. III-A: a wave's subtasks in one
-// launch).  Ops run in program order; each op's CTAs (tile strides x splits x launch indices)
-// are spread over the grid, then a grid barrier; a split op's reduce blocks follow after
-// another.  Results are bit-identical to the per-step launches: every tile, split and reduce
-// block computes the same sums in the same order wherever it runs.
+// launch).  The steps come grouped in phases: a phase holds steps that depend on no step of
+// the same phase (operands, arena memory, the shared partial-sum buffer), so their units run
+// together, spread over the grid; a grid barrier closes each phase, and the reduces of its
+// split steps run after it, before another barrier.  Results are bit-identical to per-step
+// launches: every tile, split and reduce block computes the same sums in the same order
+// wherever it runs.
+struct StepUnits {
+  uint32_t gx, gy;
+  int64_t units;
+};
+__device__ __forceinline__ StepUnits step_units(const StepOp& op, int64_t n_inst, int reuse, int64_t target) {
+  const InstMap im = reuse ? op.p.im : InstMap{-1, 0u, 0u, 0u};
+  const int64_t nz = im.s < 0 ? n_inst : ((n_inst >> im.s) << __popc(im.dep_c));
+  const uint32_t gy = (uint32_t)op.p.splitk;
+  const int64_t n_tiles = int64_t(1) << (op.p.n_om + op.p.n_on);
+  const int64_t cols = int64_t(gy) * nz;
+  // tile strides per (split, launch index) column: about `target` units per step
+  const uint32_t gx = (uint32_t)max(int64_t(1), min(n_tiles, (target + cols - 1) / cols));
+  return StepUnits{gx, gy, int64_t(gx) * cols};
+}
+__device__ __forceinline__ int64_t reduce_units(const StepOp& op, int64_t n_inst, int reuse) {
+  if (!op.reduce) return 0;
+  const InstMap im = reuse ? op.p.im : InstMap{-1, 0u, 0u, 0u};
+  const int64_t nz = im.s < 0 ? n_inst : ((n_inst >> im.s) << __popc(im.dep_c));
+  const int64_t per =
+      op.reduce == 2 ? (op.p.planeC + kThreads / 32 - 1) / (kThreads / 32) : (op.p.planeC + kThreads - 1) / kThreads;
+  return per * nz;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_steps(const StepOp* __restrict__ ops, int n_ops, int64_t n_inst,
-                                                   int reuse, uint32_t* bar, int32_t* status) {
+__global__ void __launch_bounds__(kThreads) k_steps(const StepOp* __restrict__ ops, const int32_t* __restrict__ phases,
+                                                   int n_phases, int64_t n_inst, int reuse, uint32_t* bar,
+                                                   int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) GenParams P;
   __shared__ float red[32];
-  for (int o = 0; o < n_ops; ++o) {
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(&ops[o].p);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&P);
-      for (int i = threadIdx.x; i < int(sizeof(GenParams) / 4); i += kThreads) dst[i] = src[i];
-    }
+  int loaded = -1;
+  // the op's parameters into shared memory (uniform per CTA: every thread takes part)
+  auto load_op = [&](int o) {
+    if (o == loaded) return;
+    __syncthreads();
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&ops[o].p);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&P);
+    for (int i = threadIdx.x; i < int(sizeof(GenParams) / 4); i += kThreads) dst[i] = src[i];
     __syncthreads();
     if (threadIdx.x == 0 && !reuse) P.im = InstMap{-1, 0u, 0u, 0u};
     __syncthreads();
-    const int rm = ops[o].rm, rn = ops[o].rn, reduce = ops[o].reduce;
-    const int64_t nz = P.im.s < 0 ? n_inst : ((n_inst >> P.im.s) << __popc(P.im.dep_c));
-    const uint32_t gy = (uint32_t)P.splitk;
-    const int64_t n_tiles = int64_t(1) << (P.n_om + P.n_on);
-    // tile strides per (split, launch index) column: about eight units per CTA
-    const int64_t cols = int64_t(gy) * nz;
-    const uint32_t gx = (uint32_t)max(int64_t(1), min(n_tiles, (int64_t(8) * gridDim.x + cols - 1) / cols));
-    const int64_t units = int64_t(gx) * cols;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const uint32_t bx = (uint32_t)(u % gx);
-      const int64_t r = u / gx;
-      generic_unit<T>(rm, rn, P, smem, bx, gx, (uint32_t)(r % gy), (uint32_t)(r / gy));
+    loaded = o;
+  };
+  const int64_t target = int64_t(8) * gridDim.x;
+  for (int ph = 0; ph < n_phases; ++ph) {
+    const int o0 = phases[ph], o1 = phases[ph + 1];
+    int64_t total = 0;
+    bool any_reduce = false;
+    for (int o = o0; o < o1; ++o) {
+      total += step_units(ops[o], n_inst, reuse, target).units;
+      any_reduce |= ops[o].reduce != 0;
+    }
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+      int o = o0;
+      int64_t v = u;
+      StepUnits su = step_units(ops[o], n_inst, reuse, target);
+      while (v >= su.units) {
+        v -= su.units;
+        su = step_units(ops[++o], n_inst, reuse, target);
+      }
+      load_op(o);
+      const uint32_t bx = (uint32_t)(v % su.gx);
+      const int64_t r = v / su.gx;
+      generic_unit<T>(ops[o].rm, ops[o].rn, P, smem, bx, su.gx, (uint32_t)(r % su.gy), (uint32_t)(r / su.gy));
       __syncthreads();
     }
     if (!grid_barrier(bar, status)) return;
-    if (reduce) {
-      const int64_t per = reduce == 2 ? (P.planeC + kThreads / 32 - 1) / (kThreads / 32) : (P.planeC + kThreads - 1) / kThreads;
-      const int64_t runits = per * nz;
-      for (int64_t u = blockIdx.x; u < runits; u += gridDim.x) {
-        if (reduce == 2) splitk_reduce_wide_cta<T>(P, red, (uint32_t)(u % per), (uint32_t)(u / per));
-        else splitk_reduce_cta<T>(P, red, (uint32_t)(u % per), (uint32_t)(u / per));
+    if (any_reduce) {
+      int64_t rtotal = 0;
+      for (int o = o0; o < o1; ++o) rtotal += reduce_units(ops[o], n_inst, reuse);
+      for (int64_t u = blockIdx.x; u < rtotal; u += gridDim.x) {
+        int o = o0;
+        int64_t v = u;
+        int64_t ru = reduce_units(ops[o], n_inst, reuse);
+        while (v >= ru) {
+          v -= ru;
+          ru = reduce_units(ops[++o], n_inst, reuse);
+        }
+        load_op(o);
+        const int64_t per = ops[o].reduce == 2 ? (P.planeC + kThreads / 32 - 1) / (kThreads / 32)
+                                               : (P.planeC + kThreads - 1) / kThreads;
+        if (ops[o].reduce == 2) splitk_reduce_wide_cta<T>(P, red, (uint32_t)(v % per), (uint32_t)(v / per));
+        else splitk_reduce_cta<T>(P, red, (uint32_t)(v % per), (uint32_t)(v / per));
         __syncthreads();
       }
       if (!grid_barrier(bar, status)) return;
@@ -1567,8 +1616,8 @@ cudaError_t launch_generic(int precision, int rm, int rn, const GenParams& p, di
 
 // The persistent steps kernel: one cooperative launch (every CTA resident, as the grid
 // barrier needs) of as many CTAs as fit on the device at `smem` bytes each.
-cudaError_t launch_steps(int precision, const StepOp* ops, int n_ops, int64_t n_inst, int reuse, uint32_t* bar,
-                         int32_t* status, size_t smem, cudaStream_t s) {
+cudaError_t launch_steps(int precision, const StepOp* ops, const int32_t* phases, int n_phases, int64_t n_inst,
+                         int reuse, uint32_t* bar, int32_t* status, size_t smem, cudaStream_t s) {
   const void* k = precision == 0 ? reinterpret_cast<const void*>(k_steps<float>)
                   : precision == 1 ? reinterpret_cast<const void*>(k_steps<__half>)
                                    : reinterpret_cast<const void*>(k_steps<__nv_bfloat16>);
@@ -1582,7 +1631,7 @@ cudaError_t launch_steps(int precision, const StepOp* ops, int n_ops, int64_t n_
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1 || n_sm < 1) return cudaErrorInvalidConfiguration;
-  void* args[] = {&ops, &n_ops, &n_inst, &reuse, &bar, &status};
+  void* args[] = {&ops, &phases, &n_phases, &n_inst, &reuse, &bar, &status};
   return cudaLaunchCooperativeKernel(k, dim3((unsigned)(per_sm * n_sm)), dim3(kThreads), args, smem, s);
 }
 

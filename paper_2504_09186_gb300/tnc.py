@@ -374,14 +374,16 @@ class Context:
     def amplitudes(self, plan: Plan, bitstrings: Optional[np.ndarray], precision: str = "c64",
                    slice_begin: int = 0, slice_count: Optional[int] = None, wave: int = 0, out=None,
                    stream: int = 0, profile: bool = False, fuse: bool = True, use_graph: bool = False,
-                   merge: bool = False) -> np.ndarray:
+                   merge: bool = False, persistent: bool = False) -> np.ndarray:
         """Amplitudes of every row x every open-qubit assignment, summed over the slices.
 
         `out` may be a host numpy complex128 array or a torch complex128 CUDA tensor of
         shape (batch, 2^n_open); a new host array is returned when it is None.
         merge: post-lifetime merging (Sec. III-B) on calls that cover every slice with
         tree-like reuse: each sliced index is summed right after the step that contracts it
-        (tnc_exec_opts.reserved[1] = 1)."""
+        (tnc_exec_opts.reserved[1] = 1).
+        persistent: each wave's steps as one persistent launch when every step is a SIMT
+        contraction (tnc_exec_opts.reserved[2] = 1); bit-identical to per-step launches."""
         lib = load_library()
         info = plan.info()
         if slice_count is None:
@@ -402,13 +404,16 @@ class Context:
         opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave,
                              int(use_graph), int(fuse), int(profile))
         opts.reserved[1] = int(merge)
+        opts.reserved[2] = int(persistent)
         _check(lib.tnc_amplitudes(self.h, plan.h, C.byref(opts), bp, batch, slice_begin, slice_count,
                                   C.c_void_p(ptr), C.c_void_p(stream)))
         return out
 
     def amplitudes_ids(self, plan: Plan, bitstrings: Optional[np.ndarray], slice_ids, precision: str = "c64",
-                       wave: int = 0, out=None, stream: int = 0, fuse: bool = True, profile: bool = False) -> np.ndarray:
-        """Amplitudes summed over the listed slice ids (tnc_amplitudes_ids)."""
+                       wave: int = 0, out=None, stream: int = 0, fuse: bool = True, profile: bool = False,
+                       persistent: bool = False) -> np.ndarray:
+        """Amplitudes summed over the listed slice ids (tnc_amplitudes_ids); `persistent` as in
+        amplitudes()."""
         lib = load_library()
         info = plan.info()
         ids = np.ascontiguousarray(slice_ids, dtype=np.int64)
@@ -424,6 +429,7 @@ class Context:
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
         opts = tnc_exec_opts(PRECISIONS[precision] if isinstance(precision, str) else int(precision), wave, 0,
                              int(fuse), int(profile))
+        opts.reserved[2] = int(persistent)
         _check(lib.tnc_amplitudes_ids(self.h, plan.h, C.byref(opts), bp, batch,
                                       ids.ctypes.data_as(C.POINTER(C.c_int64)), len(ids), C.c_void_p(ptr),
                                       C.c_void_p(stream)))

@@ -302,3 +302,37 @@ def test_cluster_cooperative_chains(ctx, precision):
     assert metrics.rel_err_norm(fused, plain) <= TOL[precision]
     # deterministic
     assert np.array_equal(fused, ctx.amplitudes(p, fixed[None, :], precision, fuse=True)[0])
+
+
+@pytest.mark.parametrize("precision", ["c64", "chalf"])
+def test_persistent_steps_launch(precision, monkeypatch):
+    """Every step of a SIMT program in one persistent launch per wave (TNC_NO_TC=1 puts all
+    steps of this 20-qubit plan on the SIMT kernels): bit-identical to the per-step launches,
+    eagerly and graph-replayed, with tree-like reuse over all slices, over listed slice ids,
+    and with one-instance waves whose final GEPDOT splits over K (the reduce runs inside the
+    launch after a grid barrier); against the state vector at the path's tolerance."""
+    monkeypatch.setenv("TNC_NO_TC", "1")
+    ctx = T.Context(0)
+    c = grid_circuit(4, 5, 12, seed=1)
+    fixed, open_q = subcube_spec(c.n_qubits, 2, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=18)
+    assert p.info()["n_sliced"] >= 1
+    ref = sv.circuit_amplitudes(c, subcube_bitstrings(fixed, open_q))
+    row = fixed[None, :]
+    for wave in (0, 1):
+        base = ctx.amplitudes(p, row, precision, wave=wave, profile=True)[0]
+        kinds = set(int(k) for k in ctx.profile_read()["kind"])
+        assert kinds <= {0, 1, 7}
+        if wave == 1:
+            assert kinds & {1, 7}  # the final GEPDOT (split over K in one-instance waves)
+        per = ctx.amplitudes(p, row, precision, wave=wave, persistent=True, profile=True)[0]
+        prof = ctx.profile_read()
+        assert set(int(k) for k in prof["kind"]) == {8} and int(prof["launches"][0]) >= 1
+        assert np.array_equal(per, base)
+        for _ in range(3):
+            assert np.array_equal(ctx.amplitudes(p, row, precision, wave=wave, persistent=True, use_graph=True)[0], base)
+        assert metrics.rel_err_norm(per, ref) <= TOL[precision]
+    ids = np.array([0, 3, 1], dtype=np.int64) % (1 << p.info()["n_sliced"])
+    a = ctx.amplitudes_ids(p, row, ids, precision)
+    b = ctx.amplitudes_ids(p, row, ids, precision, persistent=True)
+    assert np.array_equal(a, b)
