@@ -1190,7 +1190,8 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
   constexpr int NT = S::THREADS, GW = S::GW, GT = S::GT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint32_t* hiC = reinterpret_cast<uint32_t*>(smem + S::PIPE + NG * S::STG);  // [2^(C_BITS - runC)]
+  int64_t* oCt = reinterpret_cast<int64_t*>(smem + S::PIPE + NG * S::STG);   // [2][1024] C offsets of tile bits
+  uint32_t* hiC = reinterpret_cast<uint32_t*>(oCt + 2048);                     // [2^(C_BITS - runC)]
   const int nhC = 1 << (S::C_BITS - p.runC);
   uint16_t* TCm = reinterpret_cast<uint16_t*>(hiC + nhC);                     // [128]
   uint16_t* TCn = TCm + TC_BM;                                                 // [BN]
@@ -1231,6 +1232,18 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
       m &= m - 1;
     }
     hiC[h] = r;
+  }
+  // C offset of a tile index (within an instance) = oCt[0][bits 0..9] + oCt[1][bits 10..19]
+  // (+ the bits from 20 up, summed in the epilogue): the deposit is additive over disjoint bits
+  for (int x = tid; x < 2048; x += NT) {
+    int64_t o = 0;
+    for (int j = 0; j < 10; ++j) {
+      const int b = (x >> 10) * 10 + j;  // tile-index bit
+      if (!((x >> j) & 1)) continue;
+      if (b < p.n_on) o += int64_t(1) << p.on_C[b];
+      else if (b < p.n_on + p.n_om) o += int64_t(1) << p.om_C[b - p.n_on];
+    }
+    oCt[x] = o;
   }
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -1400,13 +1413,9 @@ __global__ void __launch_bounds__(TcpShape<BN, BK, NG, DIRECT>::THREADS, 1)
           Cbase = reinterpret_cast<T*>(p.C) + It.c * p.strideC;
         }
         const uint32_t r = (uint32_t)t & tile_mask;
-        const uint32_t on = r & ((1u << p.n_on) - 1u);
-        const uint32_t om = p.n_on >= 31 ? 0u : (r >> p.n_on);
-        int64_t oC = 0;
-        for (int q = 0; q < p.n_om; ++q)
-          if ((om >> q) & 1u) oC += int64_t(1) << p.om_C[q];
-        for (int q = 0; q < p.n_on; ++q)
-          if ((on >> q) & 1u) oC += int64_t(1) << p.on_C[q];
+        int64_t oC = oCt[r & 1023u] + oCt[1024 + ((r >> 10) & 1023u)];
+        for (int b = 20; b < tile_bits; ++b)
+          if ((r >> b) & 1u) oC += int64_t(1) << (b < p.n_on ? p.on_C[b] : p.om_C[b - p.n_on]);
         T* Cre = Cbase + oC;
         float mx = 0.f;
         // columns 8g..8g+7 of the row are 8 consecutive entries of C: one 16-byte store per plane
@@ -1845,7 +1854,7 @@ size_t tma_wide_smem_bytes_t(int runC) {
 template <int BN, int BK, int NG, bool DIRECT>
 size_t tma_persist_smem_bytes_t(int runC) {
   using S = TcpShape<BN, BK, NG, DIRECT>;
-  return 1024 + S::PIPE + NG * S::STG + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
+  return 1024 + S::PIPE + NG * S::STG + 2048 * 8 + (size_t(1) << (S::C_BITS - runC)) * 4 + (TC_BM + BN) * 2 + 16 +
          (2 * S::NST + 5) * 8 + 16 + NG * 2 * S::GW * 4 + 16 + 16 + 64;
 }
 
