@@ -2195,7 +2195,8 @@ tnc_status tnc_contract_noalloc(int32_t precision, const void* a, int32_t rank_a
     int kind = K_GENERIC;
     TileSpec t = tile_for(la, lb, lc, 1, kind);
     // fewer splits over K (same tiles, longer K range per CTA) until the FP32 partial sums
-    // fit the static array: at most 2^10 outputs per GEPDOT tile leaves room for 2^8 splits
+    // fit the static array (the split policy's one wave of 304 CTAs over at most 2^10
+    // outputs needs 2.4 MiB, so this only guards)
     const size_t room = kNoAllocScratchBytes - kNoAllocSlotBytes;
     while (t.splitk > 1 && size_t(t.splitk) * (size_t(1) << lc.size()) * sizeof(float2) > room) t.splitk /= 2;
     if (t.splitk == 1) kind = K_GENERIC;

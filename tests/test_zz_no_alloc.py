@@ -49,8 +49,8 @@ def _stored(x, dtype):
     return v[:n] + 1j * v[n:]
 
 
-# (5, 19, 5): 2^10 outputs and a 2^19-long K; the tile policy's split count would need 8 MiB
-# of partial sums, so this entry point halves the split until they fit the static array
+# (5, 19, 5): 2^10 outputs and a 2^19-long K, the largest split-over-K case: its partial sums
+# (one wave of split CTAs over 2^10 outputs) take the most of the static array
 @pytest.mark.parametrize("precision,shape", [("c64", (2, 14, 2)), ("chalf", (3, 12, 2)), ("c64", (6, 5, 6)),
                                              ("cbf16", (2, 13, 3)), ("chalf", (5, 19, 5))])
 @pytest.mark.parametrize("side_stream", [False, True])
