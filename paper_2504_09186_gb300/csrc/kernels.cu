@@ -382,16 +382,16 @@ __device__ __forceinline__ void generic_cta(const GenParams& p, unsigned char* s
     const uint32_t om = tile & ((1u << p.n_om) - 1u);
     const uint32_t on = p.n_om >= 32 ? 0u : (tile >> p.n_om);
     int64_t oA = 0, oB = 0, oC = 0;
-    for (int j = 0; j < p.n_om; ++j)
-      if ((om >> j) & 1u) {
-        oA += int64_t(1) << p.om_A[j];
-        oC += int64_t(1) << p.om_C[j];
-      }
-    for (int j = 0; j < p.n_on; ++j)
-      if ((on >> j) & 1u) {
-        oB += int64_t(1) << p.on_B[j];
-        oC += int64_t(1) << p.on_C[j];
-      }
+    for (uint32_t m = om; m; m &= m - 1u) {  // the set bits only
+      const int j = __ffs(m) - 1;
+      oA += int64_t(1) << p.om_A[j];
+      oC += int64_t(1) << p.om_C[j];
+    }
+    for (uint32_t m = on; m; m &= m - 1u) {
+      const int j = __ffs(m) - 1;
+      oB += int64_t(1) << p.on_B[j];
+      oC += int64_t(1) << p.on_C[j];
+    }
     float2 acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
