@@ -497,3 +497,30 @@ def test_post_lifetime_merging_cost_recount():
     s60 = T.Plan.greedy(grid_circuit(6, 10, 24, seed=1), open_qubits=[], seed=3, trials=2, log2_cap=32, mode="split")
     i60 = s60.info()
     assert math.isclose(i60["log2_executed_flops_merged"], i60["log2_executed_flops"], rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("rows,cols,cycles,n_open,cap", [(4, 5, 12, 2, 18), (4, 5, 10, 2, 16), (4, 5, 14, 0, 20)])
+def test_gepdot_split_counts(rows, cols, cycles, n_open, cap):
+    """Split-K GEPDOT steps (M N <= 2^10 outputs, K >= 2^12): the CTAs of a step fill at most one
+    wave of two per SM (152 SMs) over the tiles of all instances a plan's program holds
+    (2^min(s, 12)), each CTA keeps at least four outer K steps, and a step is split-K exactly
+    when its split count exceeds one."""
+    c = grid_circuit(rows, cols, cycles, seed=1)
+    _, open_q = subcube_spec(c.n_qubits, n_open, seed=2)
+    p = T.Plan.greedy(c, open_qubits=open_q, seed=3, trials=8, log2_cap=cap)
+    inst = 2 ** min(p.info()["n_sliced"], 12)
+    seen = 0
+    for st in p.describe()["steps"]:
+        m = len(st["Mt"]) + len(st["Mo"])
+        k = len(st["Kt"]) + len(st["Ko"])
+        n = len(st["Nt"]) + len(st["No"])
+        if st["tc"] or not (m + n <= 10 and k >= 12):
+            continue
+        seen += 1
+        tiles = 2 ** (len(st["Mo"]) + len(st["No"])) * inst
+        split = st["splitk"]
+        assert split >= 1
+        assert split <= max(1, -(-2 * 152 // tiles))
+        assert split == 1 or split * 4 <= 2 ** len(st["Ko"])
+        assert (st["kind"] == 1) == (split > 1)
+    assert seen >= 1
