@@ -1621,7 +1621,8 @@ cudaError_t launch_steps(int precision, const StepOp* ops, const int32_t* phases
   const void* k = precision == 0 ? reinterpret_cast<const void*>(k_steps<float>)
                   : precision == 1 ? reinterpret_cast<const void*>(k_steps<__half>)
                                    : reinterpret_cast<const void*>(k_steps<__nv_bfloat16>);
-  if (smem > 48 * 1024) {
+  // always opt in: the kernel's static shared memory (the op's parameters) comes on top
+  if (smem > 0) {
     cudaError_t e = set_smem_once(k, smem);
     if (e != cudaSuccess) return e;
   }
